@@ -1,0 +1,48 @@
+"""Seeded synthetic inputs shared by the oracle side and the GPU side.
+
+This module holds workload descriptions and seeded random blocks only; it
+contains none of the method's arithmetic, so that the oracle and the CUDA
+library stay independent of each other while seeing identical inputs.
+
+Blocks of k vectors of length n are returned as float64 arrays of shape
+(k, n), C-contiguous; read as an n x k matrix this is column-major with
+leading dimension n, the layout the C ABI takes.
+"""
+import numpy as np
+
+# The workloads of the benchmark suite (unit cube and quarter annular cylinder
+# with r_in = 1, r_out = 2, height 1). "methods" lists the discretisations run.
+WORKLOADS = {
+    "cube_p2_e4_gauss": dict(geometry="cube", p=2, elems=(4, 4, 4), kernel="gauss",
+                              sigma=1.0, L=0.5, M=10, k=8, methods=("galerkin",)),
+    "cube_p2_e16_expsep": dict(geometry="cube", p=2, elems=(16, 16, 16), kernel="exp_sep",
+                                sigma=1.0, L=1.0, M=20, k=8, methods=("galerkin", "collocation")),
+    "annulus_p3_e32x32x16_gauss": dict(geometry="annulus", p=3, elems=(32, 32, 16), kernel="gauss",
+                                        sigma=1.0, L=0.5, M=50, k=16,
+                                        methods=("galerkin", "collocation")),
+    "annulus_p2_e64x32x16_exp": dict(geometry="annulus", p=2, elems=(64, 32, 16), kernel="exp",
+                                      sigma=1.0, L=1.0, M=100, k=32,
+                                      methods=("galerkin", "collocation")),
+}
+
+# Small parity cases: several 128-point tiles with ragged tails, sizes the
+# dense oracle finishes in seconds.
+PARITY_CASES = {
+    "cube_p2_e3x4x5_gauss": dict(geometry="cube", p=2, elems=(3, 4, 5), kernel="gauss", sigma=1.3, L=0.6),
+    "cube_p2_e6x5x7_expsep": dict(geometry="cube", p=2, elems=(6, 5, 7), kernel="exp_sep", sigma=1.0, L=1.0),
+    "cube_p3_e4x3x3_matern": dict(geometry="cube", p=3, elems=(4, 3, 3), kernel="matern32", sigma=0.8, L=0.7),
+    "cube_p2_e5x4x4_exp": dict(geometry="cube", p=2, elems=(5, 4, 4), kernel="exp", sigma=1.0, L=0.9),
+    "annulus_p2_e4x4x2_gauss": dict(geometry="annulus", p=2, elems=(4, 4, 2), kernel="gauss", sigma=1.0, L=0.5),
+    "annulus_p3_e4x3x2_exp": dict(geometry="annulus", p=3, elems=(4, 3, 2), kernel="exp", sigma=1.0, L=1.0),
+}
+
+
+def random_block(n, k, seed):
+    """k standard-normal vectors of length n (PCG64 stream from ``seed``)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.ascontiguousarray(rng.standard_normal((k, n)))
+
+
+def problem_args(spec):
+    """The geometry/discretisation fields of a workload (no M, k, methods)."""
+    return {key: spec[key] for key in ("geometry", "p", "elems", "kernel", "sigma", "L")}

@@ -1,0 +1,121 @@
+"""Geometry maps F : D^ -> D and det DF for the oracle (test infrastructure).
+
+Sec. 3.1 uses the geometric mapping F from the reference domain to the
+physical domain, its Jacobian determinant det DF(x^) in the trial space
+(Eq. trialspace) and J = sqrt(det DF) at the Greville points; Sec. 3.2 uses
+det DF at the quadrature points (Algorithm 1, step 2).
+
+Two domains are provided:
+
+* ``Cube``: the unit cube (or unit interval/square for d < 3); F is the
+  identity and det DF = 1.
+* ``QuarterAnnulus``: the quarter annular cylinder with inner radius r_in,
+  outer radius r_out and height h, written as the coarsest exact NURBS volume:
+  quadratic in direction 1 (the angle) with control points (1,0), (1,1), (0,1)
+  scaled by the radius and weights 1, sqrt(2)/2, 1; linear in direction 2
+  (radius r_in -> r_out) and direction 3 (height 0 -> h). F and DF are
+  evaluated from that NURBS definition (rational basis and quotient rule),
+  point by point.
+"""
+import numpy as np
+
+from . import splines
+
+
+class Cube:
+    name = "cube"
+
+    def __init__(self, d=3):
+        self.d = d
+
+    def F(self, Xh):
+        return np.array(Xh, dtype=np.float64, copy=True)
+
+    def detDF(self, Xh):
+        return np.ones(np.atleast_2d(Xh).shape[0])
+
+    def volume(self):
+        return 1.0
+
+
+class QuarterAnnulus:
+    name = "annulus"
+    d = 3
+
+    def __init__(self, r_in=1.0, r_out=2.0, height=1.0):
+        self.r_in, self.r_out, self.h = float(r_in), float(r_out), float(height)
+        self.knots = [np.array([0, 0, 0, 1, 1, 1.0]),
+                      np.array([0, 0, 1, 1.0]),
+                      np.array([0, 0, 1, 1.0])]
+        self.degrees = [2, 1, 1]
+        arc = np.array([[1.0, 0.0], [1.0, 1.0], [0.0, 1.0]])
+        warc = np.array([1.0, np.sqrt(2.0) / 2.0, 1.0])
+        radii = [self.r_in, self.r_out]
+        zs = [0.0, self.h]
+        # control points P[i1, i2, i3] and weights w[i1, i2, i3]
+        self.P = np.zeros((3, 2, 2, 3))
+        self.w = np.zeros((3, 2, 2))
+        for i1 in range(3):
+            for i2 in range(2):
+                for i3 in range(2):
+                    self.P[i1, i2, i3, 0] = radii[i2] * arc[i1, 0]
+                    self.P[i1, i2, i3, 1] = radii[i2] * arc[i1, 1]
+                    self.P[i1, i2, i3, 2] = zs[i3]
+                    self.w[i1, i2, i3] = warc[i1]
+
+    def _basis(self, Xh):
+        Xh = np.atleast_2d(np.asarray(Xh, dtype=np.float64))
+        B = [splines.bspline_basis(self.knots[j], self.degrees[j], Xh[:, j]) for j in range(3)]
+        dB = [splines.bspline_basis_deriv(self.knots[j], self.degrees[j], Xh[:, j]) for j in range(3)]
+        return B, dB
+
+    def _num_den(self, B):
+        # N(x) = sum w P B1 B2 B3, W(x) = sum w B1 B2 B3
+        wB = np.einsum("ijk,ai,aj,ak->a", self.w, B[0], B[1], B[2])
+        num = np.einsum("ijk,ijkc,ai,aj,ak->ac", self.w, self.P, B[0], B[1], B[2])
+        return num, wB
+
+    def F(self, Xh):
+        B, _ = self._basis(Xh)
+        num, den = self._num_den(B)
+        return num / den[:, None]
+
+    def DF(self, Xh):
+        """Jacobian matrix dF_c/dxh_e by the quotient rule, shape (npts, 3, 3)."""
+        B, dB = self._basis(Xh)
+        num, den = self._num_den(B)
+        J = np.zeros((num.shape[0], 3, 3))
+        for e in range(3):
+            Bs = [dB[j] if j == e else B[j] for j in range(3)]
+            dnum, dden = self._num_den(Bs)
+            J[:, :, e] = (dnum * den[:, None] - num * dden[:, None]) / (den ** 2)[:, None]
+        return J
+
+    def detDF(self, Xh):
+        """|det DF|, the change-of-variables factor.
+
+        With direction 1 = angle (counter-clockwise), 2 = radius (outward) and
+        3 = height the parametrisation is left-handed, so det DF itself is
+        negative; integrals over D use its absolute value.
+        """
+        return np.abs(np.linalg.det(self.DF(Xh)))
+
+    def weight_function(self, t):
+        """The NURBS denominator W(xh_1), a quadratic polynomial in the angle
+        parameter (the radial and axial weights are all 1)."""
+        b = splines.bspline_basis(self.knots[0], 2, t)
+        return b @ np.array([1.0, np.sqrt(2.0) / 2.0, 1.0])
+
+    def volume(self):
+        return 0.25 * np.pi * (self.r_out ** 2 - self.r_in ** 2) * self.h
+
+
+def make_geometry(name, d=3, geo=None):
+    if name == "cube":
+        return Cube(d)
+    if name == "annulus":
+        if d != 3:
+            raise ValueError("the annulus is three-dimensional")
+        geo = geo or (1.0, 2.0, 1.0)
+        return QuarterAnnulus(*geo)
+    raise ValueError(f"unknown geometry {name!r}")
