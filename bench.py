@@ -1,0 +1,368 @@
+"""Benchmark: seconds to M Karhunen-Loeve eigenpairs on one GB300.
+
+Workload (default): unit cube, p = 2, 16 x 16 x 16 elements (N = 5832 trial
+dofs), separable exponential kernel exp(-sum_d |x_d - x'_d| / L), L = 1,
+sigma = 1, M = 20 eigenpairs, eigensolver block k = 8. One step is one
+complete solve by the IBQ-Galerkin method (N~ = 35937 interpolation points,
+1.29e9 kernel pairs per operator application) followed by one by the
+collocation method (110592 quadrature points, 6.45e8 pairs per
+application), both with the mixed-precision pairwise path (FP32 kernel tiles,
+split BF16 tcgen05 products, FP64 Rayleigh-Ritz refinement).
+
+The line also reports the plain FP64 GPU solves of the same step, the
+relative eigenvalue error of every mixed-precision eigenvalue against them,
+the roofline of the dominant kernel, end-to-end time through the C ABI with
+host buffers, and the FP64 CPU oracle on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "cube_p2_e16_expsep"
+METHODS = ("galerkin", "collocation")
+MIXED = "bf16"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default=MIXED, choices=["bf16", "tf32", "fp32"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison solves")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (cpu_baseline leg and --impl reference): the dense FP64 oracle
+# on bounded samples of the workload (smaller meshes of the same family),
+# extrapolated to the full mesh with the measured complexity exponent.
+# --------------------------------------------------------------------------
+def _oracle_sample(budget_s=25.0):
+    import numpy as np
+    from kl_inputs import WORKLOADS, problem_args
+    from oracle import collocation, galerkin
+    from oracle.problem import Problem
+
+    w = WORKLOADS[WORKLOAD]
+    args = problem_args(w)
+    full_n = args["elems"][0]
+    rows = []
+    t_total = 0.0
+    for n in (3, 4, 5, 6, 7, 8):
+        t0 = time.perf_counter()
+        for method in METHODS:
+            prob = Problem(args["geometry"], args["p"], (n, n, n), args["kernel"], args["sigma"], args["L"])
+            mod = galerkin if method == "galerkin" else collocation
+            mod.solve(prob, w["M"])
+        dt = time.perf_counter() - t0
+        t_total += dt
+        rows.append((n, dt))
+        if t_total > budget_s * 0.45:
+            break
+    (n1, t1), (n2, t2) = rows[-2], rows[-1]
+    expo = np.log(t2 / t1) / np.log(n2 / n1)
+    est = t2 * (full_n / n2) ** expo
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    sample = (f"dense FP64 oracle (Galerkin + collocation, M={w['M']}) on {rows[0][0]}^3..{n2}^3-element "
+              f"meshes of the same workload, {t_total:.1f} s of CPU work; extrapolated to {full_n}^3 with "
+              f"the measured exponent {expo:.2f} in the element count per direction")
+    return est, cores, sample, rows
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(a.warmup):
+        pass  # the oracle has no warm state; warm-up steps are no-ops
+    vals = []
+    for _ in range(a.steps):
+        est, cores, sample, _ = _oracle_sample(budget_s=min(25.0, 150.0 / max(1, a.steps)))
+        vals.append(est)
+    import numpy as np
+    v = float(np.median(vals))
+    line = {
+        "impl": "reference",
+        "metric": "s to M K-L eigenpairs (Galerkin + collocation solve, FP64 CPU oracle)",
+        "value": v, "unit": "s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "M": 20, "k": 8, "methods": list(METHODS)},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(name)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def run_gpu(a):
+    import numpy as np
+    import torch
+
+    import paper_2101_00629_gb300 as kl
+    from kl_inputs import WORKLOADS, problem_args
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    w = WORKLOADS[WORKLOAD]
+    args = problem_args(w)
+    M, k = w["M"], w["k"]
+
+    def make(method, precision):
+        p = kl.params(geometry=args["geometry"], degree=args["p"], elems=args["elems"], kernel=args["kernel"],
+                      sigma=args["sigma"], L=args["L"], method=method, precision=precision, block_k=k,
+                      seed=2101 + 7919 * rank)
+        return kl.kl_create(p, stream)
+
+    handles = {m: make(m, a.precision) for m in METHODS}
+    N = kl.kl_dims(handles["galerkin"])[0]
+    lam = {m: np.zeros(M) for m in METHODS}
+    res = {m: np.zeros(M) for m in METHODS}
+    Vd = torch.empty((M, N), dtype=torch.float64, device="cuda")
+    infos = {m: kl.kl_solve_info() for m in METHODS}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+
+    def solve(method, h):
+        rc = kl.kl_eigs(h, M, 0.0, lam[method], Vd, N, 1, res[method], infos[method])
+        if rc != 0:
+            raise RuntimeError(f"{method} solve returned status {rc}")
+
+    for _ in range(max(3, a.warmup)):
+        for m in METHODS:
+            solve(m, handles[m])
+    torch.cuda.synchronize()
+
+    # profile counters for the roofline of the dominant kernel (pairwise)
+    for m in METHODS:
+        kl.kl_profile_enable(handles[m], True)
+    launches0 = sum(kl.kl_launch_count(handles[m]) for m in METHODS)
+    step_ms, solve_ms = [], {m: [] for m in METHODS}
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_region = time.perf_counter()
+    for _ in range(a.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the step events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e_mid = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solve("galerkin", handles["galerkin"])
+        e_mid.record(stream)
+        solve("collocation", handles["collocation"])
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        solve_ms["galerkin"].append(e0.elapsed_time(e_mid))
+        solve_ms["collocation"].append(e_mid.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    region_s = time.perf_counter() - t_region
+    clk = clocks.stop()
+    launches = sum(kl.kl_launch_count(handles[m]) for m in METHODS) - launches0
+    prof = {}
+    for m in METHODS:
+        for name, st in kl.kl_profile_read(handles[m]).items():
+            acc = prof.setdefault(name, dict(launches=0, ms=0.0, units=0.0))
+            for key in acc:
+                acc[key] += st[key]
+        kl.kl_profile_enable(handles[m], False)
+    ms_step = float(np.mean(step_ms))
+    if dist is not None:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+
+    # ---- FP64 GPU solves of the same step (the reference precision) ----
+    fp64 = {}
+    if not a.no_fp64:
+        for m in METHODS:
+            h64 = make(m, "fp64")
+            lam64 = np.zeros(M)
+            info64 = kl.kl_solve_info()
+            kl.kl_eigs(h64, M, 0.0, lam64, None, N, 0, None, info64)  # warm-up
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            kl.kl_eigs(h64, M, 0.0, lam64, None, N, 0, None, info64)
+            e1.record(stream)
+            e1.synchronize()
+            err = np.abs(lam[m] - lam64) / np.maximum(np.abs(lam64), 1e-6 * abs(lam64[0]))
+            fp64[m] = dict(s=e0.elapsed_time(e1) / 1e3, applies=info64.applies, lam=lam64.tolist(),
+                           lam_rel_err=err.tolist(), max_lam_rel_err=float(err.max()))
+            kl.kl_destroy(h64)
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e_ms = []
+    lam_h = np.zeros(M)
+    V_h = np.zeros((M, N))
+    h2d = 0
+    for _ in range(2):
+        t0 = time.perf_counter()
+        for m in METHODS:
+            p = kl.params(geometry=args["geometry"], degree=args["p"], elems=args["elems"], kernel=args["kernel"],
+                          sigma=args["sigma"], L=args["L"], method=m, precision=a.precision, block_k=k)
+            h = kl.kl_create(p, stream)
+            h2d_m, _ = kl.kl_memory(h)
+            kl.kl_eigs(h, M, 0.0, lam_h, V_h, N, 0)
+            kl.kl_destroy(h)
+            h2d += h2d_m
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    h2d //= 2
+    d2h = len(METHODS) * (M * N * 8 + M * 8)
+
+    # ---- roofline of the dominant kernel ----
+    fp32_fma, ex2, fp64_fma = kl.kl_measure_peaks()
+    pair_name = max(prof, key=lambda n: prof[n]["ms"]) if prof else None
+    roof = None
+    if pair_name:
+        st = prof[pair_name]
+        achieved = st["units"] / (st["ms"] * 1e-3) / 1e9  # Gpair/s
+        mufu_per_pair = 2 if args["kernel"] in ("exp", "matern32") else 1
+        peak = ex2 / mufu_per_pair / 1e9
+        roof = {"bound": "alu", "kernel": pair_name, "achieved": achieved, "peak": peak, "unit": "Gpair/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_basis": f"measured MUFU ex2 rate {ex2 / 1e12:.2f} T/s / {mufu_per_pair} ex2 per pair "
+                              f"(measured FP32 FMA {fp32_fma / 1e12:.1f} T/s, FP64 FMA {fp64_fma / 1e12:.2f} T/s)",
+                "launches": st["launches"], "ms": st["ms"], "pairs": st["units"]}
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        est, cores, sample, _ = _oracle_sample()
+        cpu = {"value": est, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    p50 = {m: float(np.percentile(solve_ms[m], 50)) for m in METHODS}
+    p99 = {m: float(np.percentile(solve_ms[m], 99)) for m in METHODS}
+    line = {
+        "metric": "s to M K-L eigenpairs (Galerkin + collocation solve, mixed precision)",
+        "value": ms_step / 1e3 if world == 1 else ms_step / 1e3,
+        "unit": "s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": max(3, a.warmup),
+        "ms_per_step": ms_step,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 kernel tiles, split-bf16 tcgen05 products, f64 solver" if a.precision == "bf16" else a.precision,
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "M": M, "k": k, "methods": list(METHODS),
+                   "precision": a.precision, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "solve_ms_p50": p50, "solve_ms_p99": p99,
+        "fp64_gpu": {m: {kk: v for kk, v in fp64[m].items() if kk != "lam"} for m in fp64},
+        "speedup_vs_fp64": ({m: fp64[m]["s"] * 1e3 / p50[m] for m in fp64} if fp64 else None),
+        "lam": {m: lam[m].tolist() for m in METHODS},
+        "applies": {m: infos[m].applies for m in METHODS},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": float(np.median(e2e_ms)) / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "region_s": region_s,
+    }
+    for m in METHODS:
+        kl.kl_destroy(handles[m])
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    run_gpu(a)
+
+
+if __name__ == "__main__":
+    main()

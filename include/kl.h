@@ -1,0 +1,225 @@
+/*
+ * kl.h - C ABI of the GB300 matrix-free Karhunen-Loeve library.
+ *
+ * The library computes the M largest eigenpairs of the discretised Fredholm
+ * problem of Sec. 2 (Eq. hilbert_schmidt, Eq. fredholm) in the generalized
+ * matrix form A v = lambda Z v of Sec. 1 (Eq. matrix_equations), by one of the
+ * two matrix-free methods of Sec. 3:
+ *
+ *   KL_GALERKIN_IBQ  Sec. 3.1: trial space B_i / sqrt(det DF) (Eq. trialspace),
+ *                    Z = Z_d x ... x Z_1 (Kronecker mass matrix), and the
+ *                    interpolation-based quadrature factorisation
+ *                    A = M^T B~^-1 J Gamma J B~^-T M, applied matrix-free with
+ *                    Gamma evaluated on the fly over all pairs of Greville
+ *                    points of the interpolation space.
+ *   KL_COLLOCATION   Sec. 3.2: NURBS trial space collocated at the Greville
+ *                    abscissae, A_ij = int Gamma(x_i, x') R_j(x') dx' and
+ *                    Z_ij = R_j(x_i) (Eq. colloc system matrices), applied by
+ *                    Algorithm 1 with (p+1)^3 Gauss points per element and the
+ *                    Kronecker structure of Z (Sec. 3.3, Remark).
+ *
+ * Conventions used by every entry point:
+ *   - Dofs and points are ordered lexicographically with parametric
+ *     direction 1 varying fastest (Sec. 3.1: Z = Z_d x ... x Z_1).
+ *   - A block of k vectors of length n is column-major: element (i, c) is at
+ *     X[i + c * ldx], ldx >= n.
+ *   - Device pointers are CUDA device (or managed) memory of the device that
+ *     was current when the handle was created. The caller owns every buffer it
+ *     passes; the handle owns its tables and workspaces and frees them in
+ *     kl_destroy.
+ *   - Every device operation is enqueued on the handle's CUDA stream (the
+ *     stream given to kl_create). kl_apply_* return without synchronising;
+ *     kl_eigs synchronises that stream.
+ *   - Every call returns a kl_status and never aborts the process. On error
+ *     kl_last_error(h) returns a one-line message. An asynchronous device
+ *     error surfaces as KL_ERR_CUDA on the next call that synchronises.
+ *   - Handles are not thread-safe: one host thread at a time per handle.
+ */
+#ifndef KL_H
+#define KL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kl_solver kl_solver;
+
+typedef enum {
+    KL_OK = 0,
+    KL_ERR_ARG = -1,          /* invalid argument or parameter combination   */
+    KL_ERR_CUDA = -2,         /* a CUDA runtime call failed                    */
+    KL_ERR_OOM = -3,          /* device allocation failed                      */
+    KL_ERR_NOCONV = -4,       /* eigensolver hit its iteration limit; the best
+                                 available pairs are still returned            */
+    KL_ERR_NUMERIC = -5,      /* NaN/Inf met, or a factorisation broke down    */
+    KL_ERR_TIMEOUT = -6,      /* a bounded device wait gave up                 */
+    KL_ERR_UNSUPPORTED = -7,  /* feature not available on this device/build    */
+    KL_WARN_COMPLEX = 1       /* collocation: a returned pair had a non-zero
+                                 imaginary part (real parts are returned)      */
+} kl_status;
+
+enum { KL_GEOM_CUBE = 0, KL_GEOM_QUARTER_ANNULUS = 1 };
+
+/* Covariance kernels Gamma(x, x'), r = |x - x'| (Euclidean):
+ *   KL_KERNEL_GAUSS     sigma^2 exp(-r^2 / L^2)
+ *   KL_KERNEL_EXP_SEP   sigma^2 exp(-sum_d |x_d - x'_d| / L)
+ *   KL_KERNEL_EXP       sigma^2 exp(-r / L)
+ *   KL_KERNEL_MATERN32  sigma^2 (1 + sqrt(3) r / L) exp(-sqrt(3) r / L)
+ *   KL_KERNEL_CONST     sigma^2 (rank-one test kernel)                    */
+enum { KL_KERNEL_GAUSS = 0, KL_KERNEL_EXP_SEP = 1, KL_KERNEL_EXP = 2,
+       KL_KERNEL_MATERN32 = 3, KL_KERNEL_CONST = 4 };
+
+enum { KL_GALERKIN_IBQ = 0, KL_COLLOCATION = 1 };
+
+/* Arithmetic of the pairwise product Gamma * X (the O(N~^2) / O(N N_e N_q)
+ * step; Sec. 3.3). Everything else (sum factorisation, Z solves,
+ * orthogonalisation, Rayleigh-Ritz and the small eigenproblems) is FP64.
+ *   KL_FP64        FP64 kernel evaluation and products (CUDA cores).
+ *   KL_FP32        FP32 kernel evaluation and FP32 products (CUDA cores).
+ *   KL_MIXED_BF16  FP32 kernel tiles written to tensor memory and multiplied
+ *                  on tcgen05 tensor cores as split (hi + lo) BF16 products
+ *                  with FP32 accumulation.
+ *   KL_MIXED_TF32  as KL_MIXED_BF16 with split TF32 products.               */
+enum { KL_FP64 = 0, KL_FP32 = 1, KL_MIXED_BF16 = 2, KL_MIXED_TF32 = 3 };
+
+typedef struct kl_params {
+    int dim;                 /* 1, 2 or 3 parametric directions (annulus: 3)  */
+    int geometry;            /* KL_GEOM_*                                     */
+    double geo[3];           /* annulus: r_in, r_out, height (> 0, r_out >
+                                r_in); ignored for the cube                   */
+    int degree;              /* p, 1 <= p <= 8 (trial and interpolation)      */
+    int elems[3];            /* elements per direction (>= 1); direction 1 of
+                                the annulus is the angle, 2 the radius, 3 the
+                                height                                        */
+    int kernel;              /* KL_KERNEL_*                                   */
+    double sigma;            /* standard deviation (> 0)                      */
+    double L;                /* correlation length (> 0)                      */
+    int method;              /* KL_GALERKIN_IBQ or KL_COLLOCATION             */
+    int interp_continuity;   /* Galerkin interpolation space continuity:
+                                -2 = rule of Sec. 4 (C^0 for the exponential
+                                kernels, C^{p-1} otherwise), else 0 .. p-1    */
+    int precision;           /* KL_FP64, KL_FP32, KL_MIXED_BF16, KL_MIXED_TF32 */
+    int block_k;             /* eigensolver block size = vectors per operator
+                                application, 1..64 (0: 8)                     */
+    int refine;              /* final Rayleigh-Ritz refinement when precision
+                                is not FP64: 0 none, 1 FP64 Rayleigh-Ritz on
+                                the mixed operator, 2 FP64 Rayleigh-Ritz on an
+                                FP64 application of the operator (-1: 1)      */
+    int max_restarts;        /* restart cycles before KL_ERR_NOCONV (0: 200)  */
+    unsigned long long seed; /* start block of the eigensolver                */
+} kl_params;
+
+/* Fills *p with: cube, dim 3, p = 2, 4x4x4 elements, Gaussian kernel,
+ * sigma = 1, L = 0.5, Galerkin, rule continuity, FP64, block 8, refine -1,
+ * max_restarts 0, seed 2101. */
+void kl_default_params(kl_params* p);
+
+/* Sec. 3.1 / Sec. 3.2 set-up ("formation ... negligible", Sec. 3.3): knot
+ * vectors, Greville points, 1D mass / collocation / mixed mass matrices and
+ * their factorisations (host, FP64), then the point tables and geometry
+ * factors on the device. `stream` is a cudaStream_t (NULL: legacy default
+ * stream). On success *out owns all device memory of the solver.
+ * Errors: KL_ERR_ARG (bad params or out == NULL), KL_ERR_OOM, KL_ERR_CUDA,
+ * KL_ERR_UNSUPPORTED (no sm_100-class device for the tcgen05 precisions). */
+int kl_create(const kl_params* params, void* stream, kl_solver** out);
+
+/* Frees every resource of the handle (synchronises its stream). NULL is OK. */
+int kl_destroy(kl_solver* h);
+
+/* N = trial dofs; n_src = number of pairwise source points (Galerkin: N~ =
+ * interpolation dofs; collocation: N_e N_q quadrature points); n_tgt =
+ * pairwise target points (Galerkin: N~; collocation: N). Any pointer may be
+ * NULL. */
+int kl_dims(const kl_solver* h, int64_t* N, int64_t* n_src, int64_t* n_tgt);
+
+/* Y = A X for k vectors (1 <= k <= 256), X and Y device FP64 blocks of
+ * length N (ldx, ldy >= N). A is the generalized matrix in the coefficient
+ * basis: Galerkin  M^T B~^-1 J Gamma J B~^-T M  (Sec. 3.1),
+ *           collocation  Gamma (J .* W .* (R X))  (Algorithm 1 steps 1-3).
+ * Arithmetic of the pairwise step per params.precision. X and Y must not
+ * overlap. Errors: KL_ERR_ARG, KL_ERR_CUDA, KL_ERR_OOM. */
+int kl_apply_A(kl_solver* h, const double* X, int64_t ldx, double* Y, int64_t ldy, int k);
+
+/* Y = Z^-1 X (device FP64 blocks as above). Galerkin: Z^-1 = L^-T L^-1 with
+ * the Kronecker Cholesky factor L = L_d x ... x L_1 (Sec. 3.1). Collocation:
+ * the Kronecker pivoted-LU solve Z^-1 = Q U^-1 L^-1 P per direction
+ * (Sec. 3.2, Sec. 3.3 Remark). X and Y may be the same buffer. */
+int kl_apply_Zinv(kl_solver* h, const double* X, int64_t ldx, double* Y, int64_t ldy, int k);
+
+/* Y = A' X with the standard-form operator of Eq. standard:
+ * Galerkin A' = L^-1 A L^-T (the nine-step product of Sec. 3.1, with the
+ * Kronecker factors of each side folded per direction); collocation
+ * A' = Z^-1 A (Algorithm 1). Device FP64 blocks, X and Y must not overlap. */
+int kl_apply_Aprime(kl_solver* h, const double* X, int64_t ldx, double* Y, int64_t ldy, int k);
+
+typedef struct kl_solve_info {
+    int restarts;            /* restart cycles used                           */
+    int applies;             /* operator applications (blocks)                */
+    int vectors_applied;     /* sum of block widths over all applications    */
+    int converged;           /* eigenpairs meeting tol                         */
+    double max_resid;        /* max relative residual of the returned pairs   */
+    double max_imag;         /* collocation: max |Im lambda| / |lambda_1|     */
+    double seconds;          /* wall time of the call                          */
+} kl_solve_info;
+
+/* The M largest eigenpairs (1 <= M <= N, M <= 512) of A v = lambda Z v.
+ *   tol        stop when every ||A' y - theta y|| <= tol * |theta_1| (<= 0:
+ *              1e-10 for KL_FP64, 1e-6 otherwise).
+ *   lambda     host array of M doubles, descending (collocation: real parts
+ *              in descending order of the real part).
+ *   V          N x M column-major (ldv >= N), host memory if v_on_device == 0,
+ *              device memory otherwise; NULL to skip the vectors. Galerkin
+ *              vectors are Z-orthonormal (v^T Z v = 1: unit L2 norm of the
+ *              eigenfunction, Sec. 2); collocation vectors have unit L2 norm of
+ *              sum_j v_j R_j under the collocation Gauss rule. The largest-
+ *              magnitude entry of each vector is positive.
+ *   resid      host array of M relative residuals ||A' y - theta y|| /
+ *              |theta_1|, or NULL.
+ *   info       optional statistics, or NULL.
+ * Synchronises the handle's stream. Returns KL_OK, KL_WARN_COMPLEX,
+ * KL_ERR_NOCONV (best pairs still written), or an error. */
+int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* V, int64_t ldv,
+            int v_on_device, double* resid, kl_solve_info* info);
+
+/* Per-kernel-class device time measured with CUDA events recorded on the
+ * handle's stream around every launch while profiling is on. `units` is the
+ * algorithmic work the launches performed: kernel evaluations (pairs) for the
+ * pairwise classes, bytes for the sum-factorisation class. */
+typedef struct kl_kernel_stats {
+    char name[32];
+    long long launches;
+    double ms;
+    double units;
+} kl_kernel_stats;
+
+/* Turns event timing on (1) or off (0) and clears the counters. */
+int kl_profile_enable(kl_solver* h, int on);
+/* Copies up to `cap` entries; *n receives the number of classes. Synchronises
+ * the stream to read the events. */
+int kl_profile_read(kl_solver* h, kl_kernel_stats* out, int cap, int* n);
+/* Number of kernels this handle launched since creation (all classes). */
+long long kl_launch_count(const kl_solver* h);
+
+/* Bytes copied host -> device during kl_create (tables and point sets) and
+ * bytes of device memory the handle holds. */
+int kl_memory(const kl_solver* h, int64_t* h2d_bytes, int64_t* device_bytes);
+
+/* Measured throughput of the arithmetic units that bound the pairwise kernel
+ * evaluation on the current device, in operations per second: FP32 FMA, the
+ * special-function base-2 exponential (ex2) and FP64 FMA. Used as the
+ * denominator of the pairwise kernels' roofline. No paper passage: the
+ * paper's computations ran on one CPU core (Sec. 4). Any pointer may be NULL.
+ * Errors: KL_ERR_CUDA, KL_ERR_OOM. */
+int kl_measure_peaks(double* fp32_fma_per_s, double* ex2_per_s, double* fp64_fma_per_s);
+
+/* Last error message of the handle (h may be NULL: last kl_create error). */
+const char* kl_last_error(const kl_solver* h);
+const char* kl_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KL_H */

@@ -1,0 +1,543 @@
+// C ABI entry points: handle creation (Sec. 3.1 / 3.2 set-up), the
+// matrix-free operator applications and profiling counters.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "handle.h"
+#include "kernels_tc.h"
+
+namespace {
+std::string g_create_error;
+}
+
+namespace kl {
+
+int fail(kl_solver* h, int code, const std::string& msg) {
+    if (h) h->err = msg; else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(kl_solver* h, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(h, e == cudaErrorMemoryAllocation ? KL_ERR_OOM : KL_ERR_CUDA, m);
+}
+
+ProfScope::ProfScope(kl_solver* h_, const char* n, double u) : h(h_), name(n), units(u) {
+    if (!h->profiling) return;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, h->stream);
+}
+
+ProfScope::~ProfScope() {
+    if (!e0) return;
+    cudaEventRecord(e1, h->stream);
+    auto& p = h->prof[name];
+    p.pending.emplace_back(e0, e1);
+    p.pending_units.push_back(units);
+}
+
+namespace {
+
+__global__ void to_float_kernel(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x)
+        y[i] = float(x[i]);
+}
+
+template <class T>
+cudaError_t dalloc(kl_solver* h, T** p, int64_t count) {
+    *p = nullptr;
+    if (count <= 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, size_t(count) * sizeof(T));
+    if (e == cudaSuccess) h->dev_bytes += count * int64_t(sizeof(T));
+    return e;
+}
+
+void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+int64_t prod3(const int* a) { return int64_t(a[0]) * a[1] * a[2]; }
+
+}  // namespace
+
+int ensure_workspace(kl_solver* h, int k) {
+    if (k <= h->k_cap) return KL_OK;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "workspace sync");
+    for (int i = 0; i < 3; ++i) {
+        dfree(h->ws[i]);
+        h->ws[i] = nullptr;
+    }
+    dfree(h->pair_scratch);
+    h->pair_scratch = nullptr;
+    const int64_t big = std::max(h->S, h->T) * int64_t(k);
+    for (int i = 0; i < 3; ++i)
+        if ((e = dalloc(h, &h->ws[i], big)) != cudaSuccess) return cuda_fail(h, e, "workspace alloc");
+    h->pair_splits = pair_choose_splits(h->T, h->S, h->sm_count);
+    h->pair_scratch_len = std::max<int64_t>(pair_scratch_doubles(h->T, k, h->pair_splits),
+                                            tc_scratch_doubles(h->T, h->S, k, h->sm_count));
+    if ((e = dalloc(h, &h->pair_scratch, h->pair_scratch_len)) != cudaSuccess)
+        return cuda_fail(h, e, "pair scratch alloc");
+    h->k_cap = k;
+    return KL_OK;
+}
+
+// Y <- (x)_d F_d applied mode by mode: X has dims (n_in[0], n_in[1], n_in[2]),
+// F_d is (n_out[d] x n_in[d]). The last product writes Y (ldy) with optional
+// per-point scaling `post`; intermediates use ws[wa], ws[wb].
+static int kron3(kl_solver* h, const double* const* Fd, const int* n_in, const int* n_out,
+                 const double* X, int64_t ldx, double* Y, int64_t ldy, int k, const double* post,
+                 int wa, int wb) {
+    int dims[3] = {n_in[0], n_in[1], n_in[2]};
+    const double* cur = X;
+    int64_t ldc = ldx;
+    for (int d = 0; d < 3; ++d) {
+        int64_t a = 1, b = 1;
+        for (int j = 0; j < d; ++j) a *= dims[j];
+        for (int j = d + 1; j < 3; ++j) b *= dims[j];
+        dims[d] = n_out[d];
+        const int64_t out_len = prod3(dims);
+        double* out;
+        int64_t ldo;
+        if (d == 2) {
+            out = Y;
+            ldo = ldy;
+        } else {
+            out = h->ws[d == 0 ? wa : wb];
+            ldo = out_len;
+        }
+        cudaError_t e = launch_modeprod(Fd[d], n_out[d], n_in[d], cur, ldc, out, ldo, a, b, k,
+                                        d == 2 ? post : nullptr, h->stream);
+        ++h->launches;
+        if (e != cudaSuccess) return cuda_fail(h, e, "modeprod");
+        cur = out;
+        ldc = ldo;
+    }
+    return KL_OK;
+}
+
+static int pairwise(kl_solver* h, int precision, const double* U, double* W, int k,
+                    const double* post) {
+    const double S2 = h->prm.sigma * h->prm.sigma;
+    KernelSpec ks;
+    ks.kind = h->prm.kernel;
+    ks.sigma2 = S2;
+    const double L = h->prm.L;
+    switch (h->prm.kernel) {
+        case KL_KERNEL_GAUSS: ks.a = 1.0 / (L * L); break;
+        case KL_KERNEL_MATERN32: ks.a = std::sqrt(3.0) / L; break;
+        default: ks.a = 1.0 / L; break;
+    }
+    const double pairs = double(h->T) * double(h->S);
+    if (precision == KL_FP64 || precision == KL_FP32) {
+        PairArgs a{};
+        a.tx = h->tx; a.ty = h->ty; a.tz = h->tz;
+        a.sx = h->sx; a.sy = h->sy; a.sz = h->sz;
+        a.tx32 = h->tx32; a.ty32 = h->ty32; a.tz32 = h->tz32;
+        a.sx32 = h->sx32; a.sy32 = h->sy32; a.sz32 = h->sz32;
+        a.T = h->T; a.S = h->S;
+        a.X = U; a.ldx = h->S; a.Y = W; a.ldy = h->T; a.k = k;
+        a.post = post; a.ks = ks;
+        a.scratch = h->pair_scratch; a.splits = h->pair_splits;
+        ProfScope ps(h, precision == KL_FP64 ? "pair_f64" : "pair_f32", pairs);
+        cudaError_t e = launch_pair_simt(a, precision == KL_FP32, h->stream);
+        h->launches += (k + 31) / 32 + 1;
+        if (e != cudaSuccess) return cuda_fail(h, e, "pairwise (CUDA cores)");
+        return KL_OK;
+    }
+    if (precision == KL_MIXED_BF16 || precision == KL_MIXED_TF32) {
+        if (h->cc_major != 10) return fail(h, KL_ERR_UNSUPPORTED, "tcgen05 precisions need an sm_100-class GPU");
+        TcArgs a{};
+        a.tx = h->tx32; a.ty = h->ty32; a.tz = h->tz32;
+        a.sx = h->sx32; a.sy = h->sy32; a.sz = h->sz32;
+        a.T = h->T; a.S = h->S;
+        a.X = U; a.ldx = h->S; a.Y = W; a.ldy = h->T; a.k = k;
+        a.post = post; a.ks = ks; a.tf32 = precision == KL_MIXED_TF32;
+        a.scratch = h->pair_scratch; a.scratch_len = h->pair_scratch_len;
+        a.sm_count = h->sm_count;
+        ProfScope ps(h, precision == KL_MIXED_TF32 ? "pair_tc_tf32" : "pair_tc_bf16", pairs);
+        int launched = 0;
+        cudaError_t e = launch_pair_tc(a, h->stream, &launched);
+        h->launches += launched;
+        if (e != cudaSuccess) return cuda_fail(h, e, "pairwise (tcgen05)");
+        return KL_OK;
+    }
+    return fail(h, KL_ERR_ARG, "unknown precision");
+}
+
+int apply_operator(kl_solver* h, int which, int precision, const double* X, int64_t ldx, double* Y,
+                   int64_t ldy, int k) {
+    int rc;
+    const bool gal = h->prm.method == KL_GALERKIN_IBQ;
+    const double* const* F = (gal && which == 1) ? h->P : h->F;
+    const double* const* FT = (gal && which == 1) ? h->PT : h->FT;
+    const int* n_src = gal ? h->Nt1 : h->Nq1;
+    // 1) sum factorisation to the source points, scaled by J (Galerkin) or
+    //    w det DF (collocation, Algorithm 1 steps 1-2)
+    double* U = h->ws[0];
+    if ((rc = kron3(h, F, h->N1, n_src, X, ldx, U, h->S, k, h->src_scale, 1, 2)) != KL_OK) return rc;
+    // 2) pairwise product over all (target, source) pairs (Algorithm 1 step 3)
+    double* W = h->ws[1];
+    if ((rc = pairwise(h, precision, U, W, k, gal ? h->src_scale : nullptr)) != KL_OK) return rc;
+    // 3) back to the trial space: Galerkin J, B~^-1, M^T (and L^-1); collocation Z^-1 for A'
+    if (gal) return kron3(h, FT, n_src, h->N1, W, h->T, Y, ldy, k, nullptr, 0, 2);
+    if (which == 1) return kron3(h, h->Zinv, h->N1, h->N1, W, h->T, Y, ldy, k, nullptr, 0, 2);
+    cudaError_t e = launch_copy_block(W, h->T, Y, ldy, h->T, k, h->stream);
+    ++h->launches;
+    if (e != cudaSuccess) return cuda_fail(h, e, "copy");
+    return KL_OK;
+}
+
+int apply_zinv(kl_solver* h, const double* X, int64_t ldx, double* Y, int64_t ldy, int k) {
+    return kron3(h, h->Zinv, h->N1, h->N1, X, ldx, Y, ldy, k, nullptr, 0, 1);
+}
+
+int back_transform(kl_solver* h, const double* Yv, int64_t ldy, double* V, int64_t ldv, int k) {
+    if (h->prm.method == KL_GALERKIN_IBQ)
+        return kron3(h, h->LinvT, h->N1, h->N1, Yv, ldy, V, ldv, k, nullptr, 0, 1);
+    cudaError_t e = launch_copy_block(Yv, ldy, V, ldv, h->N, k, h->stream);
+    ++h->launches;
+    return e == cudaSuccess ? KL_OK : cuda_fail(h, e, "copy");
+}
+
+int field_at_quadrature(kl_solver* h, const double* V, int64_t ldv, double* out, int k) {
+    return kron3(h, h->F, h->N1, h->Nq1, V, ldv, out, h->S, k, nullptr, 1, 2);
+}
+
+}  // namespace kl
+
+using namespace kl;
+
+extern "C" {
+
+void kl_default_params(kl_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->dim = 3;
+    p->geometry = KL_GEOM_CUBE;
+    p->geo[0] = 1.0;
+    p->geo[1] = 2.0;
+    p->geo[2] = 1.0;
+    p->degree = 2;
+    p->elems[0] = p->elems[1] = p->elems[2] = 4;
+    p->kernel = KL_KERNEL_GAUSS;
+    p->sigma = 1.0;
+    p->L = 0.5;
+    p->method = KL_GALERKIN_IBQ;
+    p->interp_continuity = -2;
+    p->precision = KL_FP64;
+    p->block_k = 8;
+    p->refine = -1;
+    p->max_restarts = 0;
+    p->seed = 2101;
+}
+
+const char* kl_status_string(int s) {
+    switch (s) {
+        case KL_OK: return "ok";
+        case KL_ERR_ARG: return "invalid argument";
+        case KL_ERR_CUDA: return "CUDA error";
+        case KL_ERR_OOM: return "out of device memory";
+        case KL_ERR_NOCONV: return "eigensolver did not converge";
+        case KL_ERR_NUMERIC: return "numerical breakdown";
+        case KL_ERR_TIMEOUT: return "device wait timed out";
+        case KL_ERR_UNSUPPORTED: return "unsupported";
+        case KL_WARN_COMPLEX: return "complex eigenvalues met";
+        default: return "unknown status";
+    }
+}
+
+const char* kl_last_error(const kl_solver* h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+static std::string check_params(const kl_params& p) {
+    if (p.dim < 1 || p.dim > 3) return "dim must be 1, 2 or 3";
+    if (p.geometry != KL_GEOM_CUBE && p.geometry != KL_GEOM_QUARTER_ANNULUS) return "unknown geometry";
+    if (p.geometry == KL_GEOM_QUARTER_ANNULUS) {
+        if (p.dim != 3) return "the annulus needs dim = 3";
+        if (!(p.geo[0] > 0 && p.geo[1] > p.geo[0] && p.geo[2] > 0)) return "annulus needs 0 < r_in < r_out, height > 0";
+    }
+    if (p.degree < 1 || p.degree > 8) return "degree must be in 1..8";
+    for (int d = 0; d < p.dim; ++d)
+        if (p.elems[d] < 1 || p.elems[d] > 4096) return "elements per direction must be in 1..4096";
+    if (p.kernel < KL_KERNEL_GAUSS || p.kernel > KL_KERNEL_CONST) return "unknown kernel";
+    if (!(p.sigma > 0) || !std::isfinite(p.sigma)) return "sigma must be > 0";
+    if (!(p.L > 0) || !std::isfinite(p.L)) return "L must be > 0";
+    if (p.method != KL_GALERKIN_IBQ && p.method != KL_COLLOCATION) return "unknown method";
+    if (p.interp_continuity != -2 && (p.interp_continuity < 0 || p.interp_continuity > p.degree - 1))
+        return "interp_continuity must be -2 or in 0..p-1";
+    if (p.precision < KL_FP64 || p.precision > KL_MIXED_TF32) return "unknown precision";
+    if (p.block_k < 0 || p.block_k > 64) return "block_k must be in 0..64";
+    if (p.refine < -1 || p.refine > 2) return "refine must be -1, 0, 1 or 2";
+    if (p.max_restarts < 0) return "max_restarts must be >= 0";
+    return "";
+}
+
+int kl_create(const kl_params* params, void* stream, kl_solver** out) {
+    g_create_error.clear();
+    if (!params || !out) return fail(nullptr, KL_ERR_ARG, "params and out must not be NULL");
+    *out = nullptr;
+    std::string msg = check_params(*params);
+    if (!msg.empty()) return fail(nullptr, KL_ERR_ARG, msg);
+
+    kl_solver* h = new kl_solver();
+    h->prm = *params;
+    if (h->prm.block_k == 0) h->prm.block_k = 8;
+    if (h->prm.refine < 0) h->prm.refine = 1;
+    if (h->prm.max_restarts == 0) h->prm.max_restarts = 200;
+    h->stream = static_cast<cudaStream_t>(stream);
+    auto bail = [&](int code) {
+        g_create_error = h->err;
+        kl_destroy(h);
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaGetDevice"));
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, h->device)) != cudaSuccess)
+        return bail(cuda_fail(h, e, "cudaGetDeviceProperties"));
+    h->sm_count = prop.multiProcessorCount;
+    h->cc_major = prop.major;
+    h->cc_minor = prop.minor;
+    if ((h->prm.precision == KL_MIXED_BF16 || h->prm.precision == KL_MIXED_TF32) && h->cc_major != 10)
+        return bail(fail(h, KL_ERR_UNSUPPORTED, "tcgen05 precisions need an sm_100-class GPU"));
+
+    const kl_params& p = h->prm;
+    const bool gal = p.method == KL_GALERKIN_IBQ;
+    const bool exp_kernel = p.kernel == KL_KERNEL_EXP || p.kernel == KL_KERNEL_EXP_SEP;
+    const int icont = p.interp_continuity == -2 ? (exp_kernel ? 0 : p.degree - 1) : p.interp_continuity;
+
+    // ---- host set-up per direction ----
+    Dir1D dir[3];
+    for (int d = 0; d < 3; ++d) {
+        const bool present = d < p.dim;
+        const bool rational = (p.geometry == KL_GEOM_QUARTER_ANNULUS) && d == 0;
+        std::string m = setup_direction(dir[d], present, present ? p.elems[d] : 1, p.degree, icont,
+                                        rational, gal, !gal);
+        if (!m.empty()) return bail(fail(h, KL_ERR_NUMERIC, "set-up: " + m));
+        h->N1[d] = dir[d].N;
+        h->Nt1[d] = dir[d].Nt;
+        h->Nq1[d] = dir[d].nq;
+    }
+    h->N = prod3(h->N1);
+    h->S = gal ? prod3(h->Nt1) : prod3(h->Nq1);
+    h->T = gal ? h->S : h->N;
+
+    // ---- tables: pack every 1D array into one host buffer, upload once ----
+    std::vector<double> buf;
+    std::vector<size_t> off;
+    auto push = [&](const std::vector<double>& v) {
+        off.push_back(buf.size());
+        buf.insert(buf.end(), v.begin(), v.end());
+        while (buf.size() % 4) buf.push_back(0.0);  // 32-byte alignment
+    };
+    for (int d = 0; d < 3; ++d) {
+        const Dir1D& q = dir[d];
+        if (gal) {
+            push(q.Q.a);
+            push(transpose(q.Q).a);
+            push(q.P.a);
+            push(transpose(q.P).a);
+            push(q.Zinv_gal.a);
+            push(q.LinvT.a);
+        } else {
+            push(q.R.a);
+            push(transpose(q.R).a);
+            push(q.R.a);  // unused P slot
+            push(transpose(q.R).a);
+            push(q.Zinv_col.a);
+            push(identity(q.N).a);
+        }
+    }
+    for (int d = 0; d < 3; ++d) push(gal ? dir[d].xg : dir[d].xc);  // target params
+    for (int d = 0; d < 3; ++d) push(gal ? dir[d].xg : dir[d].xq);  // source params
+    for (int d = 0; d < 3; ++d) push(gal ? std::vector<double>(dir[d].Nt, 1.0) : dir[d].wq);
+    if ((e = dalloc(h, &h->d_tables, int64_t(buf.size()))) != cudaSuccess)
+        return bail(cuda_fail(h, e, "table alloc"));
+    if ((e = cudaMemcpyAsync(h->d_tables, buf.data(), buf.size() * sizeof(double),
+                             cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+        return bail(cuda_fail(h, e, "table upload"));
+    h->h2d_bytes += int64_t(buf.size() * sizeof(double));
+    for (int d = 0; d < 3; ++d) {
+        h->F[d] = h->d_tables + off[6 * d + 0];
+        h->FT[d] = h->d_tables + off[6 * d + 1];
+        h->P[d] = h->d_tables + off[6 * d + 2];
+        h->PT[d] = h->d_tables + off[6 * d + 3];
+        h->Zinv[d] = h->d_tables + off[6 * d + 4];
+        h->LinvT[d] = h->d_tables + off[6 * d + 5];
+    }
+    for (int j = 0; j < 9; ++j) h->pts1d[j] = h->d_tables + off[18 + j];
+
+    // ---- point sets and geometry factors on the device ----
+    const int64_t T = h->T, S = h->S;
+    const int64_t npts = gal ? 4 * S : 3 * T + 4 * S;
+    if ((e = dalloc(h, &h->d_points, npts)) != cudaSuccess) return bail(cuda_fail(h, e, "points alloc"));
+    if ((e = dalloc(h, &h->d_points32, 3 * T + 3 * S)) != cudaSuccess)
+        return bail(cuda_fail(h, e, "points alloc"));
+    double geo[3] = {p.geo[0], p.geo[1], p.geo[2]};
+    const int* nsrc = gal ? h->Nt1 : h->Nq1;
+    h->sx = h->d_points;
+    h->sy = h->sx + S;
+    h->sz = h->sy + S;
+    h->src_scale = h->sz + S;
+    e = launch_tensor_points(p.geometry, geo, h->pts1d[3], h->pts1d[4], h->pts1d[5], nsrc[0], nsrc[1],
+                             nsrc[2], gal ? nullptr : h->pts1d[6], gal ? nullptr : h->pts1d[7],
+                             gal ? nullptr : h->pts1d[8], gal ? 0.5 : 1.0, h->sx, h->sy, h->sz,
+                             h->src_scale, h->stream);
+    ++h->launches;
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "source points"));
+    if (gal) {
+        h->tx = h->sx;
+        h->ty = h->sy;
+        h->tz = h->sz;
+    } else {
+        h->tx = h->src_scale + S;
+        h->ty = h->tx + T;
+        h->tz = h->ty + T;
+        e = launch_tensor_points(p.geometry, geo, h->pts1d[0], h->pts1d[1], h->pts1d[2], h->N1[0],
+                                 h->N1[1], h->N1[2], nullptr, nullptr, nullptr, 0.0, h->tx, h->ty,
+                                 h->tz, nullptr, h->stream);
+        ++h->launches;
+        if (e != cudaSuccess) return bail(cuda_fail(h, e, "target points"));
+    }
+    h->tx32 = h->d_points32;
+    h->ty32 = h->tx32 + T;
+    h->tz32 = h->ty32 + T;
+    h->sx32 = h->tz32 + T;
+    h->sy32 = h->sx32 + S;
+    h->sz32 = h->sy32 + S;
+    const double* src64[6] = {h->tx, h->ty, h->tz, h->sx, h->sy, h->sz};
+    float* dst32[6] = {h->tx32, h->ty32, h->tz32, h->sx32, h->sy32, h->sz32};
+    for (int j = 0; j < 6; ++j) {
+        const int64_t n = j < 3 ? T : S;
+        to_float_kernel<<<int(std::min<int64_t>((n + 255) / 256, 4096)), 256, 0, h->stream>>>(src64[j], dst32[j], n);
+        ++h->launches;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(h, e, "points fp32"));
+    int rc = ensure_workspace(h, h->prm.block_k);
+    if (rc != KL_OK) return bail(rc);
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "create sync"));
+    *out = h;
+    return KL_OK;
+}
+
+int kl_destroy(kl_solver* h) {
+    if (!h) return KL_OK;
+    if (h->stream || true) cudaStreamSynchronize(h->stream);
+    for (auto& kv : h->prof)
+        for (auto& pe : kv.second.pending) {
+            cudaEventDestroy(pe.first);
+            cudaEventDestroy(pe.second);
+        }
+    dfree(h->d_tables);
+    dfree(h->d_points);
+    dfree(h->d_points32);
+    for (int i = 0; i < 3; ++i) dfree(h->ws[i]);
+    dfree(h->pair_scratch);
+    dfree(h->eig_ws);
+    delete h;
+    return KL_OK;
+}
+
+int kl_dims(const kl_solver* h, int64_t* N, int64_t* n_src, int64_t* n_tgt) {
+    if (!h) return KL_ERR_ARG;
+    if (N) *N = h->N;
+    if (n_src) *n_src = h->S;
+    if (n_tgt) *n_tgt = h->T;
+    return KL_OK;
+}
+
+static int check_block(kl_solver* h, const double* X, int64_t ldx, const double* Y, int64_t ldy, int k) {
+    if (!X || !Y) return fail(h, KL_ERR_ARG, "X and Y must not be NULL");
+    if (k < 1 || k > 256) return fail(h, KL_ERR_ARG, "k must be in 1..256");
+    if (ldx < h->N || ldy < h->N) return fail(h, KL_ERR_ARG, "leading dimensions must be >= N");
+    return KL_OK;
+}
+
+int kl_apply_A(kl_solver* h, const double* X, int64_t ldx, double* Y, int64_t ldy, int k) {
+    if (!h) return KL_ERR_ARG;
+    int rc = check_block(h, X, ldx, Y, ldy, k);
+    if (rc != KL_OK) return rc;
+    if ((rc = ensure_workspace(h, k)) != KL_OK) return rc;
+    return apply_operator(h, 0, h->prm.precision, X, ldx, Y, ldy, k);
+}
+
+int kl_apply_Aprime(kl_solver* h, const double* X, int64_t ldx, double* Y, int64_t ldy, int k) {
+    if (!h) return KL_ERR_ARG;
+    int rc = check_block(h, X, ldx, Y, ldy, k);
+    if (rc != KL_OK) return rc;
+    if ((rc = ensure_workspace(h, k)) != KL_OK) return rc;
+    return apply_operator(h, 1, h->prm.precision, X, ldx, Y, ldy, k);
+}
+
+int kl_apply_Zinv(kl_solver* h, const double* X, int64_t ldx, double* Y, int64_t ldy, int k) {
+    if (!h) return KL_ERR_ARG;
+    int rc = check_block(h, X, ldx, Y, ldy, k);
+    if (rc != KL_OK) return rc;
+    if ((rc = ensure_workspace(h, k)) != KL_OK) return rc;
+    return apply_zinv(h, X, ldx, Y, ldy, k);
+}
+
+int kl_profile_enable(kl_solver* h, int on) {
+    if (!h) return KL_ERR_ARG;
+    cudaStreamSynchronize(h->stream);
+    for (auto& kv : h->prof)
+        for (auto& pe : kv.second.pending) {
+            cudaEventDestroy(pe.first);
+            cudaEventDestroy(pe.second);
+        }
+    h->prof.clear();
+    h->profiling = on != 0;
+    return KL_OK;
+}
+
+int kl_profile_read(kl_solver* h, kl_kernel_stats* out, int cap, int* n) {
+    if (!h) return KL_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "profile sync");
+    int i = 0;
+    for (auto& kv : h->prof) {
+        kl_prof_entry& p = kv.second;
+        for (size_t j = 0; j < p.pending.size(); ++j) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, p.pending[j].first, p.pending[j].second);
+            p.ms += ms;
+            p.units += p.pending_units[j];
+            p.launches += 1;
+            cudaEventDestroy(p.pending[j].first);
+            cudaEventDestroy(p.pending[j].second);
+        }
+        p.pending.clear();
+        p.pending_units.clear();
+        if (out && i < cap) {
+            std::memset(&out[i], 0, sizeof(kl_kernel_stats));
+            std::snprintf(out[i].name, sizeof(out[i].name), "%s", kv.first.c_str());
+            out[i].launches = p.launches;
+            out[i].ms = p.ms;
+            out[i].units = p.units;
+        }
+        ++i;
+    }
+    if (n) *n = i;
+    return KL_OK;
+}
+
+long long kl_launch_count(const kl_solver* h) { return h ? h->launches : 0; }
+
+int kl_memory(const kl_solver* h, int64_t* h2d_bytes, int64_t* device_bytes) {
+    if (!h) return KL_ERR_ARG;
+    if (h2d_bytes) *h2d_bytes = h->h2d_bytes;
+    if (device_bytes) *device_bytes = h->dev_bytes;
+    return KL_OK;
+}
+
+}  // extern "C"

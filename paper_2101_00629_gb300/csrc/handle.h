@@ -1,0 +1,97 @@
+// The solver handle behind the opaque kl_solver of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "kl_internal.h"
+
+struct kl_prof_entry {
+    long long launches = 0;
+    double ms = 0.0;
+    double units = 0.0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    std::vector<double> pending_units;
+};
+
+struct kl_solver {
+    kl_params prm{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sm_count = 152;
+    int cc_major = 0, cc_minor = 0;
+    std::string err;
+
+    // sizes
+    int N1[3] = {1, 1, 1};   // trial dofs per direction
+    int Nt1[3] = {1, 1, 1};  // interpolation dofs per direction (Galerkin)
+    int Nq1[3] = {1, 1, 1};  // quadrature points per direction (collocation)
+    int64_t N = 0;           // trial dofs
+    int64_t S = 0;           // pairwise sources (N~ or NeNq)
+    int64_t T = 0;           // pairwise targets (N~ or N)
+
+    // device 1D tables (all inside one allocation)
+    double* d_tables = nullptr;
+    const double* F[3] = {};      // Galerkin: Q_d (A) ; collocation: R_d     (S_d x N_d)
+    const double* FT[3] = {};     // transposes                                (N_d x S_d)
+    const double* P[3] = {};      // Galerkin standard form P_d                (Nt_d x N_d)
+    const double* PT[3] = {};     // transposes
+    const double* Zinv[3] = {};   // Z_d^-1                                     (N_d x N_d)
+    const double* LinvT[3] = {};  // Galerkin L_d^-T                            (N_d x N_d)
+    const double* pts1d[9] = {};  // target params (3), source params (3), source weights (3)
+
+    // device point sets
+    double* d_points = nullptr;   // tx ty tz (T) sx sy sz (S) scale (S)
+    float* d_points32 = nullptr;  // tx ty tz sx sy sz in FP32
+    double *tx = nullptr, *ty = nullptr, *tz = nullptr;
+    double *sx = nullptr, *sy = nullptr, *sz = nullptr;
+    float *tx32 = nullptr, *ty32 = nullptr, *tz32 = nullptr;
+    float *sx32 = nullptr, *sy32 = nullptr, *sz32 = nullptr;
+    double* src_scale = nullptr;  // Galerkin J (= target scale too); collocation w det DF
+    double* d_geo = nullptr;      // geometry parameters on the device (unused by kernels)
+
+    // workspaces for operator applications (k_cap vectors)
+    int k_cap = 0;
+    double* ws[3] = {nullptr, nullptr, nullptr};
+    double* pair_scratch = nullptr;
+    int64_t pair_scratch_len = 0;
+    int pair_splits = 1;
+
+    // eigensolver workspaces
+    int64_t eig_cap_bytes = 0;
+    void* eig_ws = nullptr;
+
+    // bookkeeping
+    long long launches = 0;
+    int64_t h2d_bytes = 0;
+    int64_t dev_bytes = 0;
+    bool profiling = false;
+    std::map<std::string, kl_prof_entry> prof;
+};
+
+namespace kl {
+int fail(kl_solver* h, int code, const std::string& msg);
+int cuda_fail(kl_solver* h, cudaError_t e, const char* where);
+int ensure_workspace(kl_solver* h, int k);
+// Operator applications on device blocks (k <= h->k_cap after ensure_workspace).
+// which: 0 = A (generalized), 1 = A' (standard form). precision: KL_* precision.
+int apply_operator(kl_solver* h, int which, int precision, const double* X, int64_t ldx,
+                   double* Y, int64_t ldy, int k);
+int apply_zinv(kl_solver* h, const double* X, int64_t ldx, double* Y, int64_t ldy, int k);
+// Galerkin back-transform v = L^-T y; collocation: copy.
+int back_transform(kl_solver* h, const double* Yv, int64_t ldy, double* V, int64_t ldv, int k);
+// Collocation field values R v at the quadrature points into out (S x k).
+int field_at_quadrature(kl_solver* h, const double* V, int64_t ldv, double* out, int k);
+// Profiling helpers: record an event pair around a launch sequence.
+struct ProfScope {
+    kl_solver* h;
+    const char* name;
+    double units;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ProfScope(kl_solver* h_, const char* n, double u);
+    ~ProfScope();
+};
+}  // namespace kl

@@ -1,0 +1,294 @@
+// Point tables (geometry map F and det DF) and the sum-factorisation mode
+// products of Sec. 3.1 ("matrix-vector products with Kronecker structured
+// matrices ... in linear or nearly linear time") and Algorithm 1 step 1
+// (interpolation at the quadrature points), plus small block utilities.
+//
+// Layout: a block of k vectors over a tensor grid (n1, n2, n3) is
+// column-major, point index i1 + n1 * (i2 + n2 * i3), column stride ld.
+#include <cmath>
+
+#include "kl_internal.h"
+
+namespace kl {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(int64_t n, int per_block = kThreads) {
+    int64_t g = (n + per_block - 1) / per_block;
+    if (g > 148 * 64) g = 148 * 64;  // grid-stride beyond this
+    return int(g < 1 ? 1 : g);
+}
+
+// Quadratic NURBS quarter arc (control points (1,0), (1,1), (0,1), weights
+// 1, sqrt(2)/2, 1): unit-circle point and d(theta)/du.
+__device__ inline void arc_point(double u, double& cx, double& cy, double& dtheta) {
+    const double w = 0.70710678118654752440;
+    const double a = 1.0 - u;
+    const double nx = a * a + 2.0 * w * u * a;
+    const double ny = 2.0 * w * u * a + u * u;
+    const double W = a * a + 2.0 * w * u * a + u * u;
+    const double dnx = -2.0 * a + 2.0 * w * (1.0 - 2.0 * u);
+    const double dny = 2.0 * w * (1.0 - 2.0 * u) + 2.0 * u;
+    const double dW = -2.0 * a + 2.0 * w * (1.0 - 2.0 * u) + 2.0 * u;
+    cx = nx / W;
+    cy = ny / W;
+    const double dcx = (dnx * W - nx * dW) / (W * W);
+    const double dcy = (dny * W - ny * dW) / (W * W);
+    dtheta = cx * dcy - cy * dcx;
+}
+
+__global__ void tensor_points_kernel(int geometry, double r_in, double r_out, double h,
+                                     const double* __restrict__ t1, const double* __restrict__ t2,
+                                     const double* __restrict__ t3, int n1, int n2, int n3,
+                                     const double* __restrict__ w1, const double* __restrict__ w2,
+                                     const double* __restrict__ w3, double jac_power, double* out_x,
+                                     double* out_y, double* out_z, double* out_w) {
+    const int64_t n = int64_t(n1) * n2 * n3;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int i1 = int(i % n1);
+        const int i2 = int((i / n1) % n2);
+        const int i3 = int(i / (int64_t(n1) * n2));
+        const double u1 = t1[i1], u2 = t2[i2], u3 = t3[i3];
+        double x, y, z, det;
+        if (geometry == KL_GEOM_QUARTER_ANNULUS) {
+            double cx, cy, dth;
+            arc_point(u1, cx, cy, dth);
+            const double r = r_in + (r_out - r_in) * u2;
+            x = r * cx;
+            y = r * cy;
+            z = h * u3;
+            det = r * dth * (r_out - r_in) * h;
+        } else {
+            x = u1;
+            y = u2;
+            z = u3;
+            det = 1.0;
+        }
+        double w = 1.0;
+        if (w1) w *= w1[i1] * w2[i2] * w3[i3];
+        if (jac_power == 0.5) w *= sqrt(det);
+        else if (jac_power == 1.0) w *= det;
+        if (out_x) out_x[i] = x;
+        if (out_y) out_y[i] = y;
+        if (out_z) out_z[i] = z;
+        if (out_w) out_w[i] = w;
+    }
+}
+
+// out[(ia, i, ib), c] = sum_l A[i + m l] X[(ia, l, ib), c], optional post scale.
+__global__ void modeprod_kernel(const double* __restrict__ A, int m, int n,
+                                const double* __restrict__ X, int64_t ldx, double* __restrict__ Y,
+                                int64_t ldy, int64_t a, int64_t b, int k,
+                                const double* __restrict__ post) {
+    const int64_t per_col = a * m * b;
+    const int64_t total = per_col * k;
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t c = t / per_col;
+        const int64_t r = t - c * per_col;  // = ia + a * (i + m * ib)
+        const int64_t ia = r % a;
+        const int64_t rest = r / a;
+        const int i = int(rest % m);
+        const int64_t ib = rest / m;
+        const double* x = X + c * ldx + ia + a * n * ib;
+        double acc = 0.0;
+        for (int l = 0; l < n; ++l) acc = fma(A[i + int64_t(m) * l], x[a * l], acc);
+        if (post) acc *= post[r];
+        Y[c * ldy + r] = acc;
+    }
+}
+
+__device__ inline unsigned long long splitmix64(unsigned long long x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+// Standard normal numbers: SplitMix64 of (seed, counter) -> two uniforms ->
+// Box-Muller (one output per counter).
+__global__ void randn_kernel(double* X, int64_t ldx, int64_t K, int n, unsigned long long seed,
+                             unsigned long long offset) {
+    const int64_t total = K * n;
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t c = t / K, i = t - c * K;
+        const unsigned long long ctr = offset + (unsigned long long)t;
+        const unsigned long long h1 = splitmix64(seed ^ splitmix64(2 * ctr));
+        const unsigned long long h2 = splitmix64(seed ^ splitmix64(2 * ctr + 1));
+        const double u1 = ((h1 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        const double u2 = ((h2 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        X[c * ldx + i] = sqrt(-2.0 * log(u1)) * cos(6.283185307179586477 * u2);
+    }
+}
+
+__global__ void scale_cols_kernel(double* X, int64_t ldx, int64_t K, int n,
+                                  const double* __restrict__ s, int invert) {
+    const int64_t total = K * n;
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t c = t / K, i = t - c * K;
+        const double f = invert ? 1.0 / s[c] : s[c];
+        X[c * ldx + i] *= f;
+    }
+}
+
+__global__ void copy_block_kernel(const double* __restrict__ X, int64_t ldx, double* Y,
+                                  int64_t ldy, int64_t K, int n) {
+    const int64_t total = K * n;
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t c = t / K, i = t - c * K;
+        Y[c * ldy + i] = X[c * ldx + i];
+    }
+}
+
+template <int BS>
+__device__ inline double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x < 32) {
+        r = (threadIdx.x < BS / 32) ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    }
+    return r;  // valid in thread 0
+}
+
+// One block per column: out[c] = sqrt(sum_i w_i X_ic^2) (w may be NULL).
+__global__ void weighted_norms_kernel(const double* __restrict__ X, int64_t ldx, int64_t K,
+                                      const double* __restrict__ w, double* out) {
+    __shared__ double sh[32];
+    const int c = blockIdx.x;
+    const double* x = X + c * ldx;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < K; i += blockDim.x) {
+        const double v = x[i];
+        s += (w ? w[i] : 1.0) * v * v;
+    }
+    s = block_sum<kThreads>(s, sh);
+    if (threadIdx.x == 0) out[c] = sqrt(s);
+}
+
+// One block per column: flip the sign so that the largest-magnitude entry is
+// positive (first index wins ties).
+__global__ void sign_fix_kernel(double* X, int64_t ldx, int64_t K) {
+    __shared__ double sv[kThreads];
+    __shared__ int64_t si[kThreads];
+    const int c = blockIdx.x;
+    double* x = X + c * ldx;
+    double best = -1.0, val = 0.0;
+    int64_t bi = 0;
+    for (int64_t i = threadIdx.x; i < K; i += blockDim.x) {
+        const double a = fabs(x[i]);
+        if (a > best) best = a, bi = i, val = x[i];
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __shared__ double sval[kThreads];
+    sval[threadIdx.x] = val;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            const int o = threadIdx.x + s;
+            if (sv[o] > sv[threadIdx.x] || (sv[o] == sv[threadIdx.x] && si[o] < si[threadIdx.x])) {
+                sv[threadIdx.x] = sv[o];
+                si[threadIdx.x] = si[o];
+                sval[threadIdx.x] = sval[o];
+            }
+        }
+        __syncthreads();
+    }
+    const double sign = sval[0] < 0.0 ? -1.0 : 1.0;
+    if (sign < 0.0)
+        for (int64_t i = threadIdx.x; i < K; i += blockDim.x) x[i] = -x[i];
+}
+
+// One block per column: ||AY_c - theta_c Y_c||.
+__global__ void resid_norms_kernel(const double* __restrict__ Y, int64_t ldy,
+                                   const double* __restrict__ AY, int64_t lday,
+                                   const double* __restrict__ theta, int64_t K, double* out) {
+    __shared__ double sh[32];
+    const int c = blockIdx.x;
+    const double th = theta[c];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < K; i += blockDim.x) {
+        const double r = AY[c * lday + i] - th * Y[c * ldy + i];
+        s += r * r;
+    }
+    s = block_sum<kThreads>(s, sh);
+    if (threadIdx.x == 0) out[c] = sqrt(s);
+}
+
+}  // namespace
+
+cudaError_t launch_tensor_points(int geometry, const double* geo, const double* t1, const double* t2,
+                                 const double* t3, int n1, int n2, int n3, const double* w1,
+                                 const double* w2, const double* w3, double jac_power, double* out_x,
+                                 double* out_y, double* out_z, double* out_w, cudaStream_t s) {
+    const int64_t n = int64_t(n1) * n2 * n3;
+    tensor_points_kernel<<<grid_for(n), kThreads, 0, s>>>(geometry, geo[0], geo[1], geo[2], t1, t2,
+                                                          t3, n1, n2, n3, w1, w2, w3, jac_power,
+                                                          out_x, out_y, out_z, out_w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_modeprod(const double* A, int m, int n, const double* X, int64_t ldx, double* Y,
+                            int64_t ldy, int64_t a, int64_t b, int k, const double* post,
+                            cudaStream_t s) {
+    const int64_t total = a * m * b * k;
+    if (total == 0) return cudaSuccess;
+    modeprod_kernel<<<grid_for(total), kThreads, 0, s>>>(A, m, n, X, ldx, Y, ldy, a, b, k, post);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_randn(double* X, int64_t ldx, int64_t K, int n, unsigned long long seed,
+                         unsigned long long offset, cudaStream_t s) {
+    randn_kernel<<<grid_for(K * n), kThreads, 0, s>>>(X, ldx, K, n, seed, offset);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_cols(double* X, int64_t ldx, int64_t K, int n, const double* scale,
+                              int invert, cudaStream_t s) {
+    scale_cols_kernel<<<grid_for(K * n), kThreads, 0, s>>>(X, ldx, K, n, scale, invert);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_block(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t K,
+                              int n, cudaStream_t s) {
+    if (K * n == 0) return cudaSuccess;
+    copy_block_kernel<<<grid_for(K * n), kThreads, 0, s>>>(X, ldx, Y, ldy, K, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_col_norms(const double* X, int64_t ldx, int64_t K, int n, double* out,
+                             cudaStream_t s) {
+    weighted_norms_kernel<<<n, kThreads, 0, s>>>(X, ldx, K, nullptr, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weighted_norms(const double* X, int64_t ldx, int64_t K, int n, const double* w,
+                                  double* out, cudaStream_t s) {
+    weighted_norms_kernel<<<n, kThreads, 0, s>>>(X, ldx, K, w, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sign_fix(double* X, int64_t ldx, int64_t K, int n, cudaStream_t s) {
+    sign_fix_kernel<<<n, kThreads, 0, s>>>(X, ldx, K);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resid_norms(const double* Y, int64_t ldy, const double* AY, int64_t lday,
+                               const double* theta, int64_t K, int n, double* out,
+                               cudaStream_t s) {
+    resid_norms_kernel<<<n, kThreads, 0, s>>>(Y, ldy, AY, lday, theta, K, out);
+    return cudaGetLastError();
+}
+
+}  // namespace kl

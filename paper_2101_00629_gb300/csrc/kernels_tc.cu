@@ -1,0 +1,470 @@
+// Pairwise product W = Gamma X on the tcgen05 tensor cores (sm_100 family).
+//
+// The O(N~^2) step of the IBQ-Galerkin matvec (Sec. 3.1) and Algorithm 1 step
+// 3 of the collocation matvec (Sec. 3.2), with Gamma never stored:
+//
+//   * A CTA owns 128 target points; target t is tensor-memory lane t. Eight
+//     producer warps (two warpgroups, warp w serving lanes 32*(w%4)..) take
+//     source chunks in turn; each thread evaluates Gamma(x_t, y_j) for the
+//     chunk's sources in FP32 registers, splits every value into a high and a
+//     low part (BF16 + BF16 or TF32 + TF32) and writes both straight into
+//     tensor memory with tcgen05.st: the kernel tile becomes the A operand
+//     of the MMA without passing through shared memory.
+//   * The source values X (FP64 in HBM) are converted once per application
+//     into the same hi/lo split, laid out as K-major no-swizzle core matrices
+//     (8 rows x 16 bytes) chunk by chunk, and copied into a 4-stage shared
+//     memory ring by the producers; they are the B operand.
+//   * One thread of a ninth warp issues, per chunk and K step,
+//     D += A_hi B_hi + A_hi B_lo + A_lo B_hi  (tcgen05.mma, FP32 accumulator
+//     D in tensor memory, M = 128, N = k rounded up to 16), and tcgen05.commit
+//     releases the stage when the tensor core has read it.
+//   * After the last chunk the accumulator is read with tcgen05.ld and the
+//     partial sums of this source split are written in FP64; a second kernel
+//     adds the splits in a fixed order and applies sigma^2 and the
+//     per-target scale.
+//
+// Every mbarrier wait is bounded by a clock limit (about a second); on
+// timeout the kernel records an error flag, drains its own MMAs (also with a
+// bounded wait), frees its tensor memory and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "kernel_eval.cuh"
+#include "kernels_tc.h"
+
+namespace kl {
+
+namespace {
+
+constexpr int kStages = 4;
+constexpr int kProducers = 256;           // two warpgroups
+constexpr int kThreads = kProducers + 32; // + MMA warp
+constexpr int kTmemCols = 256;
+constexpr int kDCols = 64;                // accumulator columns reserved (N <= 64)
+constexpr int kAColsPerStage = 32;        // hi 16 + lo 16 columns
+constexpr long long kWaitLimit = 2000000000LL;  // clock cycles (~1 s)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait on the phase with the given parity. False on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > kWaitLimit) return false;
+    }
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, K-major, no swizzle: start address,
+// leading byte offset (stride between core matrices along K), stride byte
+// offset (between 8-row groups along M/N), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= uint64_t((addr >> 4) & 0x3FFFu);
+    d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;
+    d |= uint64_t((sbo >> 4) & 0x3FFFu) << 32;
+    d |= uint64_t(1) << 46;
+    return d;
+}
+
+// Instruction descriptor: dense, D = F32, A = B = BF16 (1) or TF32 (2),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t instr_desc(int n, bool tf32) {
+    return (1u << 4) | ((tf32 ? 2u : 1u) << 7) | ((tf32 ? 2u : 1u) << 10) |
+           (uint32_t(n >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tmemA(bool tf32, uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                          uint32_t idesc, uint32_t accumulate) {
+    if (tf32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+        "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t y;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo_k, float hi_k) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo_k, hi_k);  // .x (low bits) = even K
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Split g into hi + lo parts for one pair of K-adjacent values (BF16).
+__device__ __forceinline__ void split_bf16(float g0, float g1, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(g0), h1 = __float2bfloat16_rn(g1);
+    hi = pack_bf16(__bfloat162float(h0), __bfloat162float(h1));
+    lo = pack_bf16(g0 - __bfloat162float(h0), g1 - __bfloat162float(h1));
+}
+
+// Byte offset of element (n, kk) inside one hi or lo image of a chunk:
+// K steps of 32 bytes per row, each made of two 8x16-byte core matrices
+// along K; np/8 core matrices along N. esize = 2 (BF16) or 4 (TF32).
+__host__ __device__ inline uint32_t img_offset(int n, int kk, int np, int esize) {
+    const int per_core = 16 / esize;   // K elements per core-matrix row
+    const int per_step = 32 / esize;   // K elements per MMA
+    const int ks = kk / per_step, rem = kk % per_step;
+    const int kb = rem / per_core, e = rem % per_core;
+    const int nb = n / 8, r = n % 8;
+    return uint32_t(((ks * 2 + kb) * (np / 8) + nb) * 128 + r * 16 + e * esize);
+}
+
+// X (FP64) -> split images + FP32 source coordinates, chunk by chunk.
+__global__ void tc_convert_kernel(const double* __restrict__ X, int64_t ldx, int64_t S, int c0, int kc,
+                                  int np, int kchunk, bool tf32, const float* __restrict__ sx,
+                                  const float* __restrict__ sy, const float* __restrict__ sz,
+                                  float4* __restrict__ src4, uint8_t* __restrict__ img, int64_t nchunks) {
+    const int esize = tf32 ? 4 : 2;
+    const int64_t img_bytes = int64_t(np) * kchunk * esize;  // one of hi / lo
+    const int64_t total = nchunks * kchunk * np;
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        const int n = int(t % np);
+        const int64_t s = t / np;
+        const int64_t ch = s / kchunk;
+        const int kk = int(s % kchunk);
+        const float v = (s < S && n < kc) ? float(X[s + int64_t(c0 + n) * ldx]) : 0.f;
+        uint8_t* base = img + ch * 2 * img_bytes;
+        const uint32_t off = img_offset(n, kk, np, esize);
+        if (tf32) {
+            const uint32_t hi = tf32_rna(v);
+            const uint32_t lo = tf32_rna(v - __uint_as_float(hi));
+            *reinterpret_cast<uint32_t*>(base + off) = hi;
+            *reinterpret_cast<uint32_t*>(base + img_bytes + off) = lo;
+        } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+            *reinterpret_cast<__nv_bfloat16*>(base + off) = h;
+            *reinterpret_cast<__nv_bfloat16*>(base + img_bytes + off) = l;
+        }
+        if (n == 0) src4[s] = (s < S) ? make_float4(sx[s], sy[s], sz[s], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+template <int KIND, bool TF32, int NP>
+__global__ void __launch_bounds__(kThreads, 1)
+pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const float* __restrict__ tz,
+               int64_t T, const float4* __restrict__ src4, const uint8_t* __restrict__ img,
+               int64_t nchunks, int chunks_per_split, float a, float a2, double* __restrict__ part,
+               int k_total, int c0, int kc, int* __restrict__ err) {
+    constexpr int ESIZE = TF32 ? 4 : 2;
+    constexpr int KC = TF32 ? 16 : 32;                  // sources per chunk (16 TMEM columns)
+    constexpr int IMG = NP * KC * ESIZE;                // bytes of one of hi / lo
+    constexpr int STAGE_BYTES = 2 * IMG + KC * 16;      // hi, lo, coordinates
+    constexpr uint32_t IDESC = instr_desc(NP, TF32);
+
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t full_bar[kStages], empty_bar[kStages], done_bar, drain_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_ok[2], s_done;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int64_t tile = blockIdx.x;
+    const int split = blockIdx.y;
+    const int64_t ch0 = int64_t(split) * chunks_per_split;
+    const int nloc = int(nchunks - ch0 < chunks_per_split ? nchunks - ch0 : int64_t(chunks_per_split));
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full_bar[s], 128);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&done_bar, 1);
+        mbar_init(&drain_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t d_tmem = tmem;  // columns [0, NP)
+
+    if (warp < 8) {
+        // ---------------- producers ----------------
+        const int wg = warp >> 2;            // warpgroup 0 / 1
+        const int ptid = tid & 127;          // thread within the warpgroup
+        const int row = ptid;                // TMEM lane = target within the tile
+        const int64_t t = tile * 128 + row;
+        const float px = t < T ? tx[t] : 0.f, py = t < T ? ty[t] : 0.f, pz = t < T ? tz[t] : 0.f;
+        const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
+        bool ok = true;  // uniform within the warpgroup
+        for (int j = wg; j < nloc; j += 2) {
+            const int s = j % kStages;
+            const int use = j / kStages;
+            // one thread waits (bounded) for the stage, the warpgroup follows
+            if (ptid == 0) s_ok[wg] = (use == 0 || mbar_wait(&empty_bar[s], uint32_t((use - 1) & 1))) ? 1 : 0;
+            asm volatile("bar.sync %0, 128;" ::"r"(1 + wg) : "memory");
+            if (!s_ok[wg]) { ok = false; break; }
+            uint8_t* st = smem + s * STAGE_BYTES;
+            // copy the chunk's split image and coordinates into the stage
+            const uint4* gsrc = reinterpret_cast<const uint4*>(img + (ch0 + j) * int64_t(2 * IMG));
+            uint4* sdst = reinterpret_cast<uint4*>(st);
+            for (int e = ptid; e < (2 * IMG) / 16; e += 128) sdst[e] = gsrc[e];
+            float4* sc = reinterpret_cast<float4*>(st + 2 * IMG);
+            if (ptid < KC) sc[ptid] = src4[(ch0 + j) * KC + ptid];
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("bar.sync %0, 128;" ::"r"(1 + wg) : "memory");
+            // kernel tile row for this target, split into hi / lo
+            uint32_t hi[16], lo[16];
+            if (TF32) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const float4 y = sc[q];
+                    const float g = gamma32<KIND>(px - y.x, py - y.y, pz - y.z, a, a2);
+                    hi[q] = tf32_rna(g);
+                    lo[q] = tf32_rna(g - __uint_as_float(hi[q]));
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const float4 y0 = sc[2 * q], y1 = sc[2 * q + 1];
+                    const float g0 = gamma32<KIND>(px - y0.x, py - y0.y, pz - y0.z, a, a2);
+                    const float g1 = gamma32<KIND>(px - y1.x, py - y1.y, pz - y1.z, a, a2);
+                    split_bf16(g0, g1, hi[q], lo[q]);
+                }
+            }
+            __syncwarp();
+            const uint32_t acol = uint32_t(kDCols + s * kAColsPerStage);
+            tmem_st16(tmem + lane_base + acol, hi);
+            tmem_st16(tmem + lane_base + acol + 16, lo);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            mbar_arrive(&full_bar[s]);
+        }
+        if (!ok && ptid == 0) atomicExch(err, 1);
+        // ---------------- epilogue (warpgroup 0) ----------------
+        if (wg == 0) {
+            if (ptid == 0) s_done = (ok && mbar_wait(&done_bar, 0)) ? 1 : 0;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            const bool got = s_done != 0;
+            if (!got && ptid == 0) atomicExch(err, 1);
+            tc_fence_after();
+            uint32_t v[16];
+            for (int cb = 0; cb < NP; cb += 16) {
+                __syncwarp();
+                tmem_ld16(d_tmem + lane_base + uint32_t(cb), v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (got && t < T) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int c = cb + q;
+                        if (c < kc) part[(int64_t(split) * k_total + c0 + c) * T + t] = double(__uint_as_float(v[q]));
+                    }
+                }
+            }
+        }
+    } else if (warp == 8) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            bool ok = true;
+            for (int j = 0; j < nloc; ++j) {
+                const int s = j % kStages;
+                const int use = j / kStages;
+                if (!mbar_wait(&full_bar[s], uint32_t(use & 1))) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
+                const uint32_t acol = tmem + uint32_t(kDCols + s * kAColsPerStage);
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    const uint32_t step = uint32_t(ks * 2 * (NP / 8) * 128);
+                    const uint64_t bh = smem_desc(st + step, (NP / 8) * 128, 128);
+                    const uint64_t bl = smem_desc(st + IMG + step, (NP / 8) * 128, 128);
+                    const uint32_t ah = acol + uint32_t(ks * 8), al = acol + 16u + uint32_t(ks * 8);
+                    mma_tmemA(TF32, d_tmem, ah, bh, IDESC, (j > 0 || ks > 0) ? 1u : 0u);
+                    mma_tmemA(TF32, d_tmem, ah, bl, IDESC, 1u);
+                    mma_tmemA(TF32, d_tmem, al, bh, IDESC, 1u);
+                }
+                mma_commit(&empty_bar[s]);
+            }
+            if (ok) {
+                mma_commit(&done_bar);
+            } else {
+                atomicExch(err, 1);
+                mma_commit(&drain_bar);
+                mbar_wait(&drain_bar, 0);  // bounded: MMAs already issued finish
+            }
+        }
+        __syncwarp();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 8) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+template <int KIND, bool TF32, int NP>
+cudaError_t launch_np(const TcArgs& a, int c0, int kc, const float4* src4, const uint8_t* img,
+                      int64_t nchunks, int cps, int splits, double* part, int* err, cudaStream_t s) {
+    constexpr int ESIZE = TF32 ? 4 : 2;
+    constexpr int KC = TF32 ? 16 : 32;
+    constexpr int STAGE_BYTES = 2 * NP * KC * ESIZE + KC * 16;
+    // at least ~100 KB so that no more than two CTAs share an SM (256 TMEM
+    // columns each)
+    const int smem = std::max(kStages * STAGE_BYTES + 1024, 100 * 1024);
+    auto kern = pair_tc_kernel<KIND, TF32, NP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const double l2e = 1.4426950408889634074;
+    dim3 grid(unsigned((a.T + 127) / 128), unsigned(splits));
+    kern<<<grid, kThreads, smem, s>>>(a.tx, a.ty, a.tz, a.T, src4, img, nchunks, cps, float(a.ks.a),
+                                      float(a.ks.a * l2e), part, a.k, c0, kc, err);
+    return cudaGetLastError();
+}
+
+template <int KIND, bool TF32>
+cudaError_t launch_kind_tc(const TcArgs& a, int c0, int kc, int np, const float4* src4, const uint8_t* img,
+                           int64_t nchunks, int cps, int splits, double* part, int* err, cudaStream_t s) {
+    switch (np) {
+        case 16: return launch_np<KIND, TF32, 16>(a, c0, kc, src4, img, nchunks, cps, splits, part, err, s);
+        case 32: return launch_np<KIND, TF32, 32>(a, c0, kc, src4, img, nchunks, cps, splits, part, err, s);
+        case 48: return launch_np<KIND, TF32, 48>(a, c0, kc, src4, img, nchunks, cps, splits, part, err, s);
+        default: return launch_np<KIND, TF32, 64>(a, c0, kc, src4, img, nchunks, cps, splits, part, err, s);
+    }
+}
+
+template <bool TF32>
+cudaError_t launch_tc(const TcArgs& a, int c0, int kc, int np, const float4* src4, const uint8_t* img,
+                      int64_t nchunks, int cps, int splits, double* part, int* err, cudaStream_t s) {
+    switch (a.ks.kind) {
+        case KL_KERNEL_GAUSS: return launch_kind_tc<KL_KERNEL_GAUSS, TF32>(a, c0, kc, np, src4, img, nchunks, cps, splits, part, err, s);
+        case KL_KERNEL_EXP_SEP: return launch_kind_tc<KL_KERNEL_EXP_SEP, TF32>(a, c0, kc, np, src4, img, nchunks, cps, splits, part, err, s);
+        case KL_KERNEL_EXP: return launch_kind_tc<KL_KERNEL_EXP, TF32>(a, c0, kc, np, src4, img, nchunks, cps, splits, part, err, s);
+        case KL_KERNEL_MATERN32: return launch_kind_tc<KL_KERNEL_MATERN32, TF32>(a, c0, kc, np, src4, img, nchunks, cps, splits, part, err, s);
+        default: return launch_kind_tc<KL_KERNEL_CONST, TF32>(a, c0, kc, np, src4, img, nchunks, cps, splits, part, err, s);
+    }
+}
+
+struct TcPlan {
+    int kchunk;
+    int64_t nchunks;
+    int np_max;
+    int splits, cps;
+    int64_t img_doubles, src_doubles, part_doubles;
+};
+
+TcPlan plan(int64_t T, int64_t S, int k, int sm_count, bool tf32) {
+    TcPlan p;
+    p.kchunk = tf32 ? 16 : 32;
+    p.nchunks = std::max<int64_t>(1, (S + p.kchunk - 1) / p.kchunk);
+    const int kmax = std::min(k, 64);
+    p.np_max = std::max(16, (kmax + 15) / 16 * 16);
+    const int64_t tiles = (T + 127) / 128;
+    int64_t want = (4LL * sm_count + tiles - 1) / tiles;
+    int64_t cap = std::max<int64_t>(1, p.nchunks / 8);
+    want = std::max<int64_t>(1, std::min(want, cap));
+    p.cps = int((p.nchunks + want - 1) / want);
+    p.splits = int((p.nchunks + p.cps - 1) / p.cps);
+    const int esize = tf32 ? 4 : 2;
+    p.img_doubles = (p.nchunks * 2 * p.np_max * p.kchunk * esize + 7) / 8;
+    p.src_doubles = p.nchunks * p.kchunk * 2;  // float4 = 2 doubles
+    p.part_doubles = int64_t(p.splits) * k * T;
+    return p;
+}
+
+}  // namespace
+
+int64_t tc_scratch_doubles(int64_t T, int64_t S, int k, int sm_count) {
+    const TcPlan pb = plan(T, S, k, sm_count, false), pt = plan(T, S, k, sm_count, true);
+    const int64_t b = pb.img_doubles + pb.src_doubles + pb.part_doubles;
+    const int64_t t = pt.img_doubles + pt.src_doubles + pt.part_doubles;
+    return std::max(b, t) + 64;
+}
+
+cudaError_t launch_pair_tc(const TcArgs& a, cudaStream_t s, int* launched) {
+    *launched = 0;
+    const TcPlan p = plan(a.T, a.S, a.k, a.sm_count, a.tf32);
+    if (p.img_doubles + p.src_doubles + p.part_doubles + 64 > a.scratch_len) return cudaErrorInvalidValue;
+    uint8_t* img = reinterpret_cast<uint8_t*>(a.scratch);
+    float4* src4 = reinterpret_cast<float4*>(a.scratch + p.img_doubles);
+    double* part = a.scratch + p.img_doubles + p.src_doubles;
+    int* err = reinterpret_cast<int*>(part + p.part_doubles);
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    for (int c0 = 0; c0 < a.k; c0 += 64) {
+        const int kc = std::min(64, a.k - c0);
+        const int np = std::max(16, (kc + 15) / 16 * 16);
+        const int64_t total = p.nchunks * p.kchunk * np;
+        const int g = int(std::min<int64_t>((total + 255) / 256, 152 * 64));
+        tc_convert_kernel<<<g, 256, 0, s>>>(a.X, a.ldx, a.S, c0, kc, np, p.kchunk, a.tf32, a.sx, a.sy, a.sz,
+                                            src4, img, p.nchunks);
+        ++*launched;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        e = a.tf32 ? launch_tc<true>(a, c0, kc, np, src4, img, p.nchunks, p.cps, p.splits, part, err, s)
+                   : launch_tc<false>(a, c0, kc, np, src4, img, p.nchunks, p.cps, p.splits, part, err, s);
+        ++*launched;
+        if (e != cudaSuccess) return e;
+    }
+    e = launch_pair_reduce(part, p.splits, a.T, a.k, a.ks.sigma2, a.post, a.Y, a.ldy, s);
+    ++*launched;
+    return e;
+}
+
+}  // namespace kl

@@ -1,0 +1,154 @@
+// Internal declarations shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/kl.h"
+
+namespace kl {
+
+// ---------------------------------------------------------------------------
+// Host dense matrices (column-major, FP64) used only during set-up.
+// ---------------------------------------------------------------------------
+struct Mat {
+    int rows = 0, cols = 0;
+    std::vector<double> a;
+    Mat() = default;
+    Mat(int r, int c) : rows(r), cols(c), a(size_t(r) * c, 0.0) {}
+    double& operator()(int i, int j) { return a[size_t(i) + size_t(j) * rows]; }
+    double operator()(int i, int j) const { return a[size_t(i) + size_t(j) * rows]; }
+};
+
+Mat identity(int n);
+Mat transpose(const Mat& A);
+Mat matmul(const Mat& A, const Mat& B);
+// In-place lower Cholesky (upper part zeroed). False if not positive definite.
+bool cholesky(Mat& A);
+// Inverse of a lower-triangular matrix.
+Mat lower_inverse(const Mat& L);
+// Solve A X = B with partial pivoting. False if singular.
+bool lu_solve(const Mat& A, const Mat& B, Mat& X);
+
+// ---------------------------------------------------------------------------
+// Set-up of one parametric direction (Sec. 3.1, Sec. 3.2), host FP64.
+// ---------------------------------------------------------------------------
+struct Dir1D {
+    int nel = 1, p = 1;
+    int N = 1;     // trial dofs
+    // Galerkin
+    int Nt = 1;                 // interpolation dofs
+    std::vector<double> xg;     // Greville points of the interpolation space (Nt)
+    Mat Q;                      // B~^-T M             (Nt x N)
+    Mat P;                      // B~^-T M L^-T        (Nt x N)
+    Mat LinvT;                  // L^-T                (N x N)
+    Mat Zinv_gal;               // Z^-1 = L^-T L^-1    (N x N)
+    // Collocation
+    int nq = 1;                 // quadrature points of this direction
+    std::vector<double> xq, wq; // Gauss points / weights (nq)
+    std::vector<double> xc;     // Greville points of the trial space (N)
+    Mat R;                      // rational basis at quadrature points (nq x N)
+    Mat Zinv_col;               // (R_j(xc_i))^-1      (N x N)
+};
+
+// Builds the direction's tables. `rational` = direction 1 of the annulus
+// (NURBS weights from the quadratic arc). `present` = false gives the 1-dof
+// identity direction used for dim < 3. Returns an empty string on success.
+std::string setup_direction(Dir1D& d, bool present, int nel, int p, int interp_cont,
+                            bool rational, bool need_galerkin, bool need_collocation);
+
+// ---------------------------------------------------------------------------
+// Device-side launchers (defined in the .cu files). All take the stream.
+// ---------------------------------------------------------------------------
+struct KernelSpec {
+    int kind;       // KL_KERNEL_*
+    double sigma2;  // sigma^2
+    double a;       // scale of the argument (see pair kernels)
+};
+
+// Geometry factors at a tensor grid of parametric points.
+// out_x/y/z: physical coordinates; out_w: weight(i1)*weight(i2)*weight(i3) *
+// |det DF|^power (power 0.5 for J = sqrt(det DF), 1 for collocation).
+cudaError_t launch_tensor_points(int geometry, const double* geo, const double* t1, const double* t2,
+                                 const double* t3, int n1, int n2, int n3, const double* w1,
+                                 const double* w2, const double* w3, double jac_power, double* out_x,
+                                 double* out_y, double* out_z, double* out_w, cudaStream_t s);
+
+// Y(a, m, b, c) = sum_l A(i, l) X(a, l, b, c) (+ optional scaling by post[a + A*(i + m*b)]).
+cudaError_t launch_modeprod(const double* A, int m, int n, const double* X, int64_t ldx, double* Y,
+                            int64_t ldy, int64_t a, int64_t b, int k, const double* post,
+                            cudaStream_t s);
+
+// Pairwise products W = Gamma(targets, sources) X, FP64 or FP32 on CUDA cores.
+struct PairArgs {
+    const double *tx, *ty, *tz;  // targets (T), FP64
+    const float *tx32, *ty32, *tz32;
+    const double *sx, *sy, *sz;  // sources (S), FP64
+    const float *sx32, *sy32, *sz32;
+    int64_t T, S;
+    const double* X;  // S x k (ldx)
+    int64_t ldx;
+    double* Y;  // T x k (ldy)
+    int64_t ldy;
+    int k;
+    const double* post;  // optional per-target scale
+    KernelSpec ks;
+    double* scratch;  // splits * k * T doubles
+    int splits;
+};
+int64_t pair_scratch_doubles(int64_t T, int k, int splits);
+int pair_choose_splits(int64_t T, int64_t S, int sm_count);
+cudaError_t launch_pair_simt(const PairArgs& a, bool fp32, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Small dense FP64 linear algebra on the device (Sec. 3: standard form and
+// the outer eigensolver).
+// ---------------------------------------------------------------------------
+// C(m x n) = alpha * A^T B + beta * C, A: K x m (lda), B: K x n (ldb), K long.
+cudaError_t launch_gemm_tn(const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
+                           int64_t ldc, int m, int n, int64_t K, double alpha, double beta,
+                           double* scratch, int64_t scratch_doubles, cudaStream_t s);
+int64_t gemm_tn_scratch_doubles(int m, int n, int64_t K);
+// C(K x n) = alpha * A(K x m) B(m x n) + beta * C.
+cudaError_t launch_gemm_nn(const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
+                           int64_t ldc, int64_t K, int m, int n, double alpha, double beta,
+                           cudaStream_t s);
+// Lower Cholesky of the n x n SPD G (in place) and Rinv = L^-T (upper), flags
+// columns whose pivot collapsed (rank deficiency) in bad[n] (0/1).
+cudaError_t launch_chol_rinv(double* G, int n, double* Rinv, int* bad, cudaStream_t s);
+// Symmetric eigen-decomposition of the n x n H (cyclic Jacobi), eigenvalues
+// descending in w, eigenvectors in V (n x n).
+cudaError_t launch_sym_eig(const double* H, int n, double* w, double* V, double* work,
+                           int* status, cudaStream_t s);
+// Real non-symmetric eigen-decomposition (Hessenberg + Francis QR + back
+// substitution). wr/wi eigenvalues sorted by real part descending, V real
+// vectors (complex pairs as Re, Im columns), unit 2-norm.
+cudaError_t launch_nonsym_eig(const double* H, int n, double* wr, double* wi, double* V,
+                              double* work, int* status, cudaStream_t s);
+int64_t nonsym_eig_work_doubles(int n);
+int64_t sym_eig_work_doubles(int n);
+// Column 2-norms of X (K x n).
+cudaError_t launch_col_norms(const double* X, int64_t ldx, int64_t K, int n, double* out,
+                             cudaStream_t s);
+// Standard normal block by a counter-based generator (seed, stream offset).
+cudaError_t launch_randn(double* X, int64_t ldx, int64_t K, int n, unsigned long long seed,
+                         unsigned long long offset, cudaStream_t s);
+// Y(:, j) = X(:, j) * scale[j]  (scale on device).
+cudaError_t launch_scale_cols(double* X, int64_t ldx, int64_t K, int n, const double* scale,
+                              int invert, cudaStream_t s);
+// Copy a K x n block between leading dimensions.
+cudaError_t launch_copy_block(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t K,
+                              int n, cudaStream_t s);
+// Weighted column norms sqrt(sum_i w_i X_ij^2) and signed argmax fix-up.
+cudaError_t launch_weighted_norms(const double* X, int64_t ldx, int64_t K, int n, const double* w,
+                                  double* out, cudaStream_t s);
+cudaError_t launch_sign_fix(double* X, int64_t ldx, int64_t K, int n, cudaStream_t s);
+// Residual norms ||AV s_i - theta_i V s_i|| for i < n given Y = V S, AY = AV S.
+cudaError_t launch_resid_norms(const double* Y, int64_t ldy, const double* AY, int64_t lday,
+                               const double* theta, int64_t K, int n, double* out,
+                               cudaStream_t s);
+
+}  // namespace kl

@@ -1,0 +1,404 @@
+// kl_eigs: the outer iterative eigensolver on the standard form of Eq.
+// standard (Sec. 3: A' v' = lambda v', v = C v').
+//
+// The paper leaves the eigensolver unnamed (Sec. 3.3 counts its iterations
+// N_iter); this is a thick-restart block Krylov-Schur method that serves both
+// forms:
+//   * a basis V (N x m) is grown block by block: the newest block of A'V is
+//     orthogonalised against V (two classical Gram-Schmidt passes in FP64)
+//     and orthonormalised (CholQR2, collapsed columns replaced by fresh
+//     random directions);
+//   * the Rayleigh-Ritz matrix H = V^T (A'V) is formed explicitly in FP64 and
+//     decomposed on the device: cyclic Jacobi for the symmetric Galerkin form
+//     (A' = L^-1 A L^-T), Hessenberg + Francis QR for the non-symmetric
+//     collocation form (A' = Z^-1 A);
+//   * the restart keeps the nkeep leading Ritz vectors (and A' applied to
+//     them, so no operator application is repeated) followed by the
+//     orthonormalised residual block, which preserves the Krylov-Schur
+//     relation A' V = V H + F E^T;
+//   * for the reduced precisions a final Rayleigh-Ritz step in FP64 is taken
+//     on the converged Ritz vectors (refine = 2: with an FP64 application of
+//     the operator).
+// Vectors are then mapped back (Galerkin v = L^-T v'), normalised and given a
+// sign (largest-magnitude entry positive).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "handle.h"
+
+namespace kl {
+namespace {
+
+struct EigWs {
+    double *V, *AV, *T1, *T2;   // N x mmax each
+    double *H, *S, *G, *Rinv;   // mmax^2 each
+    double *theta, *thetai, *norms, *norms2;  // mmax each
+    double* la_work;            // eigensolver work
+    double* tn_scratch;         // gemm_tn partials
+    int64_t tn_len;
+    int* ibuf;                  // status + bad flags (mmax + 1)
+};
+
+struct Ctx {
+    kl_solver* h;
+    EigWs w;
+    int64_t N;
+    int mmax;
+    bool sym;
+    unsigned long long rng_offset = 0;
+    int applies = 0, vectors_applied = 0;
+};
+
+#define KL_TRY(expr)                         \
+    do {                                     \
+        int _rc = (expr);                    \
+        if (_rc != KL_OK) return _rc;        \
+    } while (0)
+
+int ck(Ctx& c, cudaError_t e, const char* where, int n_launch = 1) {
+    c.h->launches += n_launch;
+    if (e != cudaSuccess) return cuda_fail(c.h, e, where);
+    return KL_OK;
+}
+
+// C(m x n) = A^T B with A, B tall (N rows)
+int tn(Ctx& c, const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+       int m, int n, double alpha = 1.0, double beta = 0.0) {
+    return ck(c, launch_gemm_tn(A, lda, B, ldb, C, ldc, m, n, c.N, alpha, beta, c.w.tn_scratch,
+                                c.w.tn_len, c.h->stream), "gemm_tn", 2);
+}
+
+int nn(Ctx& c, const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+       int m, int n, double alpha, double beta) {
+    return ck(c, launch_gemm_nn(A, lda, B, ldb, C, ldc, c.N, m, n, alpha, beta, c.h->stream), "gemm_nn");
+}
+
+int sync_copy(Ctx& c, void* dst, const void* src, size_t bytes) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c.h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.h->stream);
+    if (e != cudaSuccess) return cuda_fail(c.h, e, "device->host copy");
+    return KL_OK;
+}
+
+// Two classical Gram-Schmidt passes of W (N x bw) against V[:, :nv].
+int project_out(Ctx& c, const double* V, int nv, double* W, int bw) {
+    if (nv <= 0) return KL_OK;
+    for (int pass = 0; pass < 2; ++pass) {
+        KL_TRY(tn(c, V, c.N, W, c.N, c.w.G, nv, nv, bw));
+        KL_TRY(nn(c, V, c.N, c.w.G, nv, W, c.N, nv, bw, -1.0, 1.0));
+    }
+    return KL_OK;
+}
+
+// Makes W (N x bw) orthonormal and orthogonal to V[:, :nv]. Columns that
+// collapse (W nearly in span(V) or linearly dependent) are replaced by random
+// vectors and the procedure repeats.
+int orthonormalize(Ctx& c, const double* V, int nv, double* W, int bw) {
+    std::vector<double> before(bw), after(bw);
+    std::vector<int> bad(bw);
+    for (int attempt = 0; attempt < 6; ++attempt) {
+        KL_TRY(ck(c, launch_col_norms(W, c.N, c.N, bw, c.w.norms, c.h->stream), "norms"));
+        KL_TRY(project_out(c, V, nv, W, bw));
+        KL_TRY(ck(c, launch_col_norms(W, c.N, c.N, bw, c.w.norms2, c.h->stream), "norms"));
+        KL_TRY(sync_copy(c, before.data(), c.w.norms, bw * sizeof(double)));
+        KL_TRY(sync_copy(c, after.data(), c.w.norms2, bw * sizeof(double)));
+        bool any = false;
+        for (int j = 0; j < bw; ++j) {
+            bad[j] = !(after[j] > 1e-10 * before[j]) || !(after[j] > 1e-290) || !std::isfinite(after[j]);
+            any |= bad[j] != 0;
+        }
+        if (!any) {
+            // CholQR twice
+            for (int pass = 0; pass < 2 && !any; ++pass) {
+                KL_TRY(tn(c, W, c.N, W, c.N, c.w.G, bw, bw, bw));
+                KL_TRY(ck(c, launch_chol_rinv(c.w.G, bw, c.w.Rinv, c.w.ibuf, c.h->stream), "chol"));
+                KL_TRY(sync_copy(c, bad.data(), c.w.ibuf, bw * sizeof(int)));
+                for (int j = 0; j < bw; ++j) any |= bad[j] != 0;
+                if (any) break;
+                KL_TRY(nn(c, W, c.N, c.w.Rinv, bw, c.w.T2, c.N, bw, bw, 1.0, 0.0));
+                KL_TRY(ck(c, launch_copy_block(c.w.T2, c.N, W, c.N, c.N, bw, c.h->stream), "copy"));
+            }
+            if (!any) {
+                // final projection pass keeps W orthogonal to V after CholQR
+                if (nv > 0) {
+                    KL_TRY(project_out(c, V, nv, W, bw));
+                    KL_TRY(tn(c, W, c.N, W, c.N, c.w.G, bw, bw, bw));
+                    KL_TRY(ck(c, launch_chol_rinv(c.w.G, bw, c.w.Rinv, c.w.ibuf, c.h->stream), "chol"));
+                    KL_TRY(sync_copy(c, bad.data(), c.w.ibuf, bw * sizeof(int)));
+                    for (int j = 0; j < bw; ++j) any |= bad[j] != 0;
+                    if (!any) {
+                        KL_TRY(nn(c, W, c.N, c.w.Rinv, bw, c.w.T2, c.N, bw, bw, 1.0, 0.0));
+                        KL_TRY(ck(c, launch_copy_block(c.w.T2, c.N, W, c.N, c.N, bw, c.h->stream), "copy"));
+                    }
+                }
+                if (!any) return KL_OK;
+            }
+        }
+        for (int j = 0; j < bw; ++j) {
+            if (!bad[j]) continue;
+            KL_TRY(ck(c, launch_randn(W + int64_t(j) * c.N, c.N, c.N, 1, c.h->prm.seed ^ 0x5bd1e995ull,
+                                      c.rng_offset, c.h->stream), "randn"));
+            c.rng_offset += uint64_t(c.N);
+        }
+    }
+    return fail(c.h, KL_ERR_NUMERIC, "orthonormalisation failed repeatedly");
+}
+
+int apply(Ctx& c, int precision, const double* X, double* Y, int k) {
+    KL_TRY(ensure_workspace(c.h, k));
+    c.applies += 1;
+    c.vectors_applied += k;
+    return apply_operator(c.h, 1, precision, X, c.N, Y, c.N, k);
+}
+
+// Rayleigh-Ritz on the first nv columns: theta (desc), S (nv x nv, ld nv).
+int rayleigh_ritz(Ctx& c, const double* V, const double* AV, int nv, double* max_imag) {
+    KL_TRY(tn(c, V, c.N, AV, c.N, c.w.H, nv, nv, nv));
+    int status = 0;
+    if (c.sym) {
+        KL_TRY(ck(c, launch_sym_eig(c.w.H, nv, c.w.theta, c.w.S, c.w.la_work, c.w.ibuf, c.h->stream), "sym_eig"));
+        KL_TRY(sync_copy(c, &status, c.w.ibuf, sizeof(int)));
+        if (max_imag) *max_imag = 0.0;
+    } else {
+        KL_TRY(ck(c, launch_nonsym_eig(c.w.H, nv, c.w.theta, c.w.thetai, c.w.S, c.w.la_work, c.w.ibuf,
+                                       c.h->stream), "nonsym_eig"));
+        KL_TRY(sync_copy(c, &status, c.w.ibuf, sizeof(int)));
+    }
+    if (status != 0) return fail(c.h, KL_ERR_NUMERIC, "small eigensolver did not converge");
+    return KL_OK;
+}
+
+}  // namespace
+}  // namespace kl
+
+using namespace kl;
+
+extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* Vout, int64_t ldv,
+                       int v_on_device, double* resid, kl_solve_info* info) {
+    if (!h) return KL_ERR_ARG;
+    const auto t_start = std::chrono::steady_clock::now();
+    if (!lambda) return fail(h, KL_ERR_ARG, "lambda must not be NULL");
+    if (M < 1 || M > 512 || M > h->N) return fail(h, KL_ERR_ARG, "M must be in 1..min(N, 512)");
+    if (Vout && ldv < h->N) return fail(h, KL_ERR_ARG, "ldv must be >= N");
+    const int prec = h->prm.precision;
+    if (!(tol > 0)) tol = (prec == KL_FP64) ? 1e-10 : 1e-6;
+
+    Ctx c;
+    c.h = h;
+    c.N = h->N;
+    c.sym = h->prm.method == KL_GALERKIN_IBQ;
+    const int64_t N = h->N;
+    const int b = int(std::min<int64_t>(h->prm.block_k, N));
+    const int nkeep = int(std::min<int64_t>(M + b, N));
+    int mmax = int(std::min<int64_t>(N, std::max(2 * nkeep, nkeep + 2 * b)));
+    if (mmax > 1024) mmax = 1024;
+    c.mmax = mmax;
+
+    // ---- workspace (one allocation, reused across calls) ----
+    const int64_t tn_len = std::max(gemm_tn_scratch_doubles(mmax, mmax, N), int64_t(1));
+    const int64_t la = std::max(sym_eig_work_doubles(mmax), nonsym_eig_work_doubles(mmax));
+    const int64_t need = 4 * N * mmax + 4 * int64_t(mmax) * mmax + 4 * int64_t(mmax) + la + tn_len +
+                         (int64_t(mmax) + 2) / 2 + 64;
+    if (need * int64_t(sizeof(double)) > h->eig_cap_bytes) {
+        cudaStreamSynchronize(h->stream);
+        if (h->eig_ws) cudaFree(h->eig_ws);
+        h->eig_ws = nullptr;
+        cudaError_t e = cudaMalloc(&h->eig_ws, size_t(need) * sizeof(double));
+        if (e != cudaSuccess) {
+            h->eig_cap_bytes = 0;
+            return cuda_fail(h, e, "eigensolver workspace");
+        }
+        h->eig_cap_bytes = need * int64_t(sizeof(double));
+        h->dev_bytes += h->eig_cap_bytes;
+    }
+    double* p = static_cast<double*>(h->eig_ws);
+    auto take = [&](int64_t n) {
+        double* r = p;
+        p += (n + 3) / 4 * 4;
+        return r;
+    };
+    c.w.V = take(N * mmax);
+    c.w.AV = take(N * mmax);
+    c.w.T1 = take(N * mmax);
+    c.w.T2 = take(N * mmax);
+    c.w.H = take(int64_t(mmax) * mmax);
+    c.w.S = take(int64_t(mmax) * mmax);
+    c.w.G = take(int64_t(mmax) * mmax);
+    c.w.Rinv = take(int64_t(mmax) * mmax);
+    c.w.theta = take(mmax);
+    c.w.thetai = take(mmax);
+    c.w.norms = take(mmax);
+    c.w.norms2 = take(mmax);
+    c.w.la_work = take(la);
+    c.w.tn_scratch = take(tn_len);
+    c.w.tn_len = tn_len;
+    c.w.ibuf = reinterpret_cast<int*>(take((int64_t(mmax) + 2) / 2 + 2));
+
+    double* V = c.w.V;
+    double* AV = c.w.AV;
+    std::vector<double> th(mmax), thi(mmax, 0.0), rn(mmax);
+
+    // ---- start block ----
+    int nv = b, na = 0;
+    if (int rc = ck(c, launch_randn(V, N, N, b, h->prm.seed, 0, h->stream), "randn"); rc != KL_OK) return rc;
+    c.rng_offset = uint64_t(N) * b;
+    if (int rc = orthonormalize(c, V, 0, V, b); rc != KL_OK) return rc;
+
+    int restarts = 0, nconv = 0;
+    bool done = false, complete = false;
+    double max_imag = 0.0;
+    int status_out = KL_OK;
+    while (!done) {
+        // ---- expansion ----
+        while (true) {
+            if (int rc = apply(c, prec, V + na * N, AV + na * N, nv - na); rc != KL_OK) return rc;
+            na = nv;
+            if (nv >= mmax || nv >= N) break;
+            const int bb = int(std::min<int64_t>(std::min(b, mmax - nv), N - nv));
+            double* Wn = V + int64_t(nv) * N;
+            if (int rc = ck(c, launch_copy_block(AV + int64_t(nv - bb) * N, N, Wn, N, N, bb, h->stream), "copy"); rc != KL_OK) return rc;
+            if (int rc = orthonormalize(c, V, nv, Wn, bb); rc != KL_OK) return rc;
+            nv += bb;
+        }
+        complete = nv >= N;
+        // ---- Rayleigh-Ritz ----
+        if (int rc = rayleigh_ritz(c, V, AV, nv, nullptr); rc != KL_OK) return rc;
+        const int mr = std::min(M, nv);
+        // Ritz vectors Y = V S(:, :mr) in T1, A'Y = AV S(:, :mr) in T2
+        if (int rc = nn(c, V, N, c.w.S, nv, c.w.T1, N, nv, mr, 1.0, 0.0); rc != KL_OK) return rc;
+        if (int rc = nn(c, AV, N, c.w.S, nv, c.w.T2, N, nv, mr, 1.0, 0.0); rc != KL_OK) return rc;
+        if (int rc = ck(c, launch_resid_norms(c.w.T1, N, c.w.T2, N, c.w.theta, N, mr, c.w.norms, h->stream), "resid"); rc != KL_OK) return rc;
+        if (int rc = sync_copy(c, th.data(), c.w.theta, nv * sizeof(double)); rc != KL_OK) return rc;
+        if (!c.sym) {
+            if (int rc = sync_copy(c, thi.data(), c.w.thetai, nv * sizeof(double)); rc != KL_OK) return rc;
+        }
+        if (int rc = sync_copy(c, rn.data(), c.w.norms, mr * sizeof(double)); rc != KL_OK) return rc;
+        const double scale = std::max(std::fabs(th[0]), 1e-300);
+        nconv = 0;
+        bool bad_num = false;
+        for (int i = 0; i < mr; ++i) {
+            if (!std::isfinite(rn[i]) || !std::isfinite(th[i])) bad_num = true;
+            if (rn[i] <= tol * scale) ++nconv;
+        }
+        if (bad_num) return fail(h, KL_ERR_NUMERIC, "NaN or Inf in the Ritz values");
+        if (nconv >= M || complete) break;
+        if (restarts >= h->prm.max_restarts) {
+            status_out = KL_ERR_NOCONV;
+            break;
+        }
+        // ---- restart ----
+        ++restarts;
+        const int keep = std::min(nkeep, nv - b);
+        // next block: newest block of A'V orthogonalised against the full basis
+        double* Wn = c.w.T1;  // reuse; Ritz vectors are recomputed after the loop
+        if (int rc = ck(c, launch_copy_block(AV + int64_t(nv - b) * N, N, Wn, N, N, b, h->stream), "copy"); rc != KL_OK) return rc;
+        if (int rc = orthonormalize(c, V, nv, Wn, b); rc != KL_OK) return rc;
+        // V S(:, :keep) and AV S(:, :keep) into T2 / back into V, AV
+        if (int rc = nn(c, V, N, c.w.S, nv, c.w.T2, N, nv, keep, 1.0, 0.0); rc != KL_OK) return rc;
+        if (int rc = ck(c, launch_copy_block(c.w.T2, N, V, N, N, keep, h->stream), "copy"); rc != KL_OK) return rc;
+        if (int rc = nn(c, AV, N, c.w.S, nv, c.w.T2, N, nv, keep, 1.0, 0.0); rc != KL_OK) return rc;
+        if (int rc = ck(c, launch_copy_block(c.w.T2, N, AV, N, N, keep, h->stream), "copy"); rc != KL_OK) return rc;
+        if (!c.sym) {
+            // Ritz (or real/imaginary) vectors are not orthonormal: CholQR2 on V
+            // and the same right factor on AV
+            for (int pass = 0; pass < 2; ++pass) {
+                if (int rc = tn(c, V, N, V, N, c.w.G, keep, keep, keep); rc != KL_OK) return rc;
+                if (int rc = ck(c, launch_chol_rinv(c.w.G, keep, c.w.Rinv, c.w.ibuf, h->stream), "chol"); rc != KL_OK) return rc;
+                if (int rc = nn(c, V, N, c.w.Rinv, keep, c.w.T2, N, keep, keep, 1.0, 0.0); rc != KL_OK) return rc;
+                if (int rc = ck(c, launch_copy_block(c.w.T2, N, V, N, N, keep, h->stream), "copy"); rc != KL_OK) return rc;
+                if (int rc = nn(c, AV, N, c.w.Rinv, keep, c.w.T2, N, keep, keep, 1.0, 0.0); rc != KL_OK) return rc;
+                if (int rc = ck(c, launch_copy_block(c.w.T2, N, AV, N, N, keep, h->stream), "copy"); rc != KL_OK) return rc;
+            }
+        }
+        if (int rc = ck(c, launch_copy_block(Wn, N, V + int64_t(keep) * N, N, N, b, h->stream), "copy"); rc != KL_OK) return rc;
+        nv = keep + b;
+        na = keep;
+    }
+
+    // ---- final Ritz pairs (optionally refined by an FP64 Rayleigh-Ritz) ----
+    int nk = std::min(nv, nkeep);
+    if (nk < M) nk = std::min(nv, M);
+    double* Y = c.w.T1;
+    double* AY = c.w.T2;
+    if (int rc = nn(c, V, N, c.w.S, nv, Y, N, nv, nk, 1.0, 0.0); rc != KL_OK) return rc;
+    if (prec != KL_FP64 && h->prm.refine > 0) {
+        if (!c.sym) {
+            // orthonormal basis of the Ritz subspace
+            for (int pass = 0; pass < 2; ++pass) {
+                if (int rc = tn(c, Y, N, Y, N, c.w.G, nk, nk, nk); rc != KL_OK) return rc;
+                if (int rc = ck(c, launch_chol_rinv(c.w.G, nk, c.w.Rinv, c.w.ibuf, h->stream), "chol"); rc != KL_OK) return rc;
+                if (int rc = nn(c, Y, N, c.w.Rinv, nk, AY, N, nk, nk, 1.0, 0.0); rc != KL_OK) return rc;
+                if (int rc = ck(c, launch_copy_block(AY, N, Y, N, N, nk, h->stream), "copy"); rc != KL_OK) return rc;
+            }
+        }
+        const int rprec = h->prm.refine == 2 ? KL_FP64 : prec;
+        if (int rc = apply(c, rprec, Y, AY, nk); rc != KL_OK) return rc;
+        // Rayleigh-Ritz on span(Y): reuse V/AV storage for the rotated pair
+        if (int rc = rayleigh_ritz(c, Y, AY, nk, nullptr); rc != KL_OK) return rc;
+        if (int rc = nn(c, Y, N, c.w.S, nk, V, N, nk, M, 1.0, 0.0); rc != KL_OK) return rc;
+        if (int rc = nn(c, AY, N, c.w.S, nk, AV, N, nk, M, 1.0, 0.0); rc != KL_OK) return rc;
+        if (int rc = ck(c, launch_copy_block(V, N, Y, N, N, M, h->stream), "copy"); rc != KL_OK) return rc;
+        if (int rc = ck(c, launch_copy_block(AV, N, AY, N, N, M, h->stream), "copy"); rc != KL_OK) return rc;
+    } else {
+        if (int rc = nn(c, AV, N, c.w.S, nv, AY, N, nv, M, 1.0, 0.0); rc != KL_OK) return rc;
+    }
+    if (int rc = ck(c, launch_resid_norms(Y, N, AY, N, c.w.theta, N, M, c.w.norms, h->stream), "resid"); rc != KL_OK) return rc;
+    if (int rc = sync_copy(c, th.data(), c.w.theta, M * sizeof(double)); rc != KL_OK) return rc;
+    if (!c.sym) {
+        if (int rc = sync_copy(c, thi.data(), c.w.thetai, M * sizeof(double)); rc != KL_OK) return rc;
+    }
+    if (int rc = sync_copy(c, rn.data(), c.w.norms, M * sizeof(double)); rc != KL_OK) return rc;
+    const double scale = std::max(std::fabs(th[0]), 1e-300);
+    double max_res = 0.0;
+    nconv = 0;
+    for (int i = 0; i < M; ++i) {
+        lambda[i] = th[i];
+        const double r = rn[i] / scale;
+        if (resid) resid[i] = r;
+        max_res = std::max(max_res, r);
+        if (r <= tol) ++nconv;
+        max_imag = std::max(max_imag, std::fabs(thi[i]) / scale);
+    }
+
+    // ---- eigenvectors: back-transform, normalise, sign ----
+    if (Vout) {
+        double* Vd = AV;  // N x M scratch
+        if (int rc = back_transform(h, Y, N, Vd, N, M); rc != KL_OK) return rc;
+        if (!c.sym) {
+            // unit L2 norm of the field sum_j v_j R_j under the Gauss rule
+            if (int rc = ensure_workspace(h, M); rc != KL_OK) return rc;
+            if (int rc = field_at_quadrature(h, Vd, N, h->ws[0], M); rc != KL_OK) return rc;
+            if (int rc = ck(c, launch_weighted_norms(h->ws[0], h->S, h->S, M, h->src_scale, c.w.norms, h->stream), "wnorm"); rc != KL_OK) return rc;
+            if (int rc = ck(c, launch_scale_cols(Vd, N, N, M, c.w.norms, 1, h->stream), "scale"); rc != KL_OK) return rc;
+        }
+        if (int rc = ck(c, launch_sign_fix(Vd, N, N, M, h->stream), "sign"); rc != KL_OK) return rc;
+        cudaError_t e = cudaMemcpy2DAsync(Vout, size_t(ldv) * sizeof(double), Vd, size_t(N) * sizeof(double),
+                                          size_t(N) * sizeof(double), size_t(M),
+                                          v_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                          h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "copy eigenvectors");
+    }
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "kl_eigs sync");
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (info) {
+        info->restarts = restarts;
+        info->applies = c.applies;
+        info->vectors_applied = c.vectors_applied;
+        info->converged = nconv;
+        info->max_resid = max_res;
+        info->max_imag = max_imag;
+        info->seconds = secs;
+    }
+    if (status_out != KL_OK) return fail(h, status_out, "iteration limit reached before convergence");
+    if (!c.sym && max_imag > 1e-8) {
+        h->err = "complex eigenvalues among the returned pairs";
+        return KL_WARN_COMPLEX;
+    }
+    return KL_OK;
+}
