@@ -42,6 +42,8 @@ def _args():
     ap.add_argument("--precision", default=MIXED, choices=["bf16", "tf32", "fp32"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run exactly one untimed step (for ncu launch lists); prints nothing")
     return ap.parse_args()
 
 
@@ -209,6 +211,14 @@ def run_gpu(a):
         rc = kl.kl_eigs(h, M, 0.0, lam[method], Vd, N, 1, res[method], infos[method])
         if rc != 0:
             raise RuntimeError(f"{method} solve returned status {rc}")
+
+    if a.profile_step:
+        for m in METHODS:
+            solve(m, handles[m])
+        torch.cuda.synchronize()
+        for m in METHODS:
+            kl.kl_destroy(handles[m])
+        return
 
     for _ in range(max(3, a.warmup)):
         for m in METHODS:

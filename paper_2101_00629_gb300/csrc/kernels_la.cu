@@ -189,7 +189,6 @@ __global__ void __launch_bounds__(512) sym_eig_kernel(const double* __restrict__
     __shared__ double s_c[256], s_s[256];
     __shared__ int s_p[256], s_q[256];
     __shared__ double s_red[32];
-    __shared__ int s_done;
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int e = tid; e < n * n; e += nt) {
         A[e] = 0.5 * (H[e] + H[(e % n) * n + e / n]);
@@ -198,37 +197,31 @@ __global__ void __launch_bounds__(512) sym_eig_kernel(const double* __restrict__
     __syncthreads();
     const int m = n + (n & 1);
     const int npairs = m / 2;
+    // Frobenius norm of H (invariant under the rotations) for the absolute
+    // part of the threshold
+    __shared__ double s_norm;
+    __shared__ int s_rot;
+    {
+        double f = 0.0;
+        for (int e = tid; e < n * n; e += nt) f += A[e] * A[e];
+        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+        if ((tid & 31) == 0) s_red[tid >> 5] = f;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int i = 0; i < nt / 32; ++i) t += s_red[i];
+            s_norm = sqrt(t);
+        }
+        __syncthreads();
+    }
+    const double anorm = s_norm;
+    // threshold Jacobi: a rotation is skipped when the off-diagonal entry is
+    // negligible relative to its diagonal pair or to the matrix norm; the
+    // iteration stops after a sweep that applied no rotation
     int sweep = 0;
-    for (; sweep < 40; ++sweep) {
-        // convergence test: off-diagonal vs diagonal Frobenius norms
-        double off = 0.0, dia = 0.0;
-        for (int e = tid; e < n * n; e += nt) {
-            const double v = A[e];
-            if (e % n == e / n) dia += v * v; else off += v * v;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            off += __shfl_xor_sync(0xffffffffu, off, o);
-            dia += __shfl_xor_sync(0xffffffffu, dia, o);
-        }
-        if ((tid & 31) == 0) s_red[tid >> 5] = off;
+    for (; sweep < 60 && n > 1; ++sweep) {
+        if (tid == 0) s_rot = 0;
         __syncthreads();
-        if (tid == 0) {
-            double o2 = 0.0;
-            for (int i = 0; i < nt / 32; ++i) o2 += s_red[i];
-            s_red[31] = o2;
-        }
-        __syncthreads();
-        const double offt = s_red[31];
-        __syncthreads();
-        if ((tid & 31) == 0) s_red[tid >> 5] = dia;
-        __syncthreads();
-        if (tid == 0) {
-            double d2 = 0.0;
-            for (int i = 0; i < nt / 32; ++i) d2 += s_red[i];
-            s_done = (offt <= 1e-32 * d2) || n < 2;
-        }
-        __syncthreads();
-        if (s_done) break;
         for (int r = 0; r < m - 1; ++r) {
             for (int i = tid; i < npairs; i += nt) {
                 int p = rr_player(i, r, m), q = rr_player(m - 1 - i, r, m);
@@ -237,11 +230,12 @@ __global__ void __launch_bounds__(512) sym_eig_kernel(const double* __restrict__
                 if (q < n) {
                     const double apq = A[p + q * n];
                     const double app = A[p + p * n], aqq = A[q + q * n];
-                    if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
+                    if (fabs(apq) > 1e-15 * sqrt(fabs(app * aqq)) && fabs(apq) > 1e-17 * anorm) {
                         const double tau = (aqq - app) / (2.0 * apq);
                         const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
                         c = 1.0 / sqrt(1.0 + t * t);
                         s = t * c;
+                        atomicAdd(&s_rot, 1);
                     }
                 }
                 s_p[i] = p;
@@ -276,6 +270,8 @@ __global__ void __launch_bounds__(512) sym_eig_kernel(const double* __restrict__
             }
             __syncthreads();
         }
+        if (s_rot == 0) break;
+        __syncthreads();
     }
     // sort eigenvalues descending (rank sort, ties broken by index)
     for (int i = tid; i < n; i += nt) {
@@ -288,7 +284,7 @@ __global__ void __launch_bounds__(512) sym_eig_kernel(const double* __restrict__
         w[rank] = di;
         for (int r = 0; r < n; ++r) Vout[r + int64_t(rank) * n] = V[r + i * n];
     }
-    if (tid == 0) *status = (sweep >= 40) ? 1 : 0;
+    if (tid == 0) *status = (sweep >= 60) ? 1 : 0;
 }
 
 // ------------------------------ nonsym_eig --------------------------------
@@ -432,7 +428,25 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
                 for (l = u; l >= 1; --l) {
                     double s = fabs(A[(l - 1) + int64_t(l - 1) * n]) + fabs(A[l + int64_t(l) * n]);
                     if (s == 0.0) s = anorm;
-                    if (fabs(A[l + int64_t(l - 1) * n]) <= DBL_EPSILON * s) {
+                    // relative test, plus an absolute one at roundoff of the
+                    // whole matrix: next to eigenvalues that are themselves at
+                    // roundoff level the relative test can never be met
+                    const double sub = fabs(A[l + int64_t(l - 1) * n]);
+                    if (sub <= DBL_EPSILON * s || sub <= DBL_EPSILON * anorm) {
+                        A[l + int64_t(l - 1) * n] = 0.0;
+                        break;
+                    }
+                    // Ahues-Tisseur test: the product of the off-diagonal
+                    // pair against the gap of the diagonal pair; needed for
+                    // clusters of (nearly) equal eigenvalues, where the
+                    // subdiagonal alone stalls well above roundoff
+                    const double up = fabs(A[(l - 1) + int64_t(l) * n]);
+                    const double ab = fmax(sub, up), ba = fmin(sub, up);
+                    const double dd = fabs(A[(l - 1) + int64_t(l - 1) * n] - A[l + int64_t(l) * n]);
+                    const double aa = fmax(fabs(A[l + int64_t(l) * n]), dd);
+                    const double bb = fmin(fabs(A[l + int64_t(l) * n]), dd);
+                    const double ss = aa + ab;
+                    if (ba * (ab / ss) <= fmax(DBL_MIN, DBL_EPSILON * (bb * (aa / ss)))) {
                         A[l + int64_t(l - 1) * n] = 0.0;
                         break;
                     }

@@ -18,10 +18,17 @@
 //     D += A_hi B_hi + A_hi B_lo + A_lo B_hi  (tcgen05.mma, FP32 accumulator
 //     D in tensor memory, M = 128, N = k rounded up to 16), and tcgen05.commit
 //     releases the stage when the tensor core has read it.
-//   * After the last chunk the accumulator is read with tcgen05.ld and the
-//     partial sums of this source split are written in FP64; a second kernel
-//     adds the splits in a fixed order and applies sigma^2 and the
-//     per-target scale.
+//   * The FP32 accumulator is double-buffered in tensor memory and restarted
+//     every kGroup chunks: warpgroup 0 reads the finished buffer with
+//     tcgen05.ld and adds it into FP64 partial sums of its own rows while the
+//     tensor core fills the other buffer. Long FP32 accumulations on the
+//     tensor core drift (the error grows linearly with their length); the
+//     flush bounds every FP32 sum to kGroup chunks.
+//   * The partial sums of each source split are reduced by a second kernel in
+//     a fixed order, which also applies sigma^2 and the per-target scale.
+//   * Coordinates are pre-scaled so that the kernel argument needs no
+//     multiplication (see gamma_scaled), and the hi/lo splits cost three
+//     (BF16) or two (TF32) instructions per value.
 //
 // Every mbarrier wait is bounded by a clock limit (about a second); on
 // timeout the kernel records an error flag, drains its own MMAs (also with a
@@ -30,6 +37,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 
 #include "kernel_eval.cuh"
@@ -43,8 +51,10 @@ constexpr int kStages = 4;
 constexpr int kProducers = 256;           // two warpgroups
 constexpr int kThreads = kProducers + 32; // + MMA warp
 constexpr int kTmemCols = 256;
-constexpr int kDCols = 64;                // accumulator columns reserved (N <= 64)
+constexpr int kDCols = 64;                // columns of one accumulator buffer (N <= 64)
+constexpr int kAColBase = 2 * kDCols;     // two accumulator buffers, then the A stages
 constexpr int kAColsPerStage = 32;        // hi 16 + lo 16 columns
+constexpr int kGroup = 8;                 // chunks accumulated in FP32 before a flush
 constexpr long long kWaitLimit = 2000000000LL;  // clock cycles (~1 s)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -129,6 +139,12 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
         : "memory");
 }
 
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
@@ -144,16 +160,50 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
     return y;
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo_k, float hi_k) {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(lo_k, hi_k);  // .x (low bits) = even K
-    return *reinterpret_cast<const uint32_t*>(&v);
+// Two K-adjacent values -> packed BF16 pair (even K in the low half).
+__device__ __forceinline__ uint32_t cvt_bf16x2(float even_k, float odd_k) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(odd_k), "f"(even_k));
+    return r;
 }
 
-// Split g into hi + lo parts for one pair of K-adjacent values (BF16).
+// Split (g0, g1) into packed hi and lo BF16 pairs with g ~ hi + lo.
 __device__ __forceinline__ void split_bf16(float g0, float g1, uint32_t& hi, uint32_t& lo) {
-    const __nv_bfloat16 h0 = __float2bfloat16_rn(g0), h1 = __float2bfloat16_rn(g1);
-    hi = pack_bf16(__bfloat162float(h0), __bfloat162float(h1));
-    lo = pack_bf16(g0 - __bfloat162float(h0), g1 - __bfloat162float(h1));
+    hi = cvt_bf16x2(g0, g1);
+    const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xffff0000u);
+    lo = cvt_bf16x2(g0 - h0, g1 - h1);
+}
+
+// Split g into hi (mantissa truncated to the 10 bits a TF32 operand keeps)
+// and lo = g - hi (exact in FP32; the tensor core uses its leading 10 bits).
+__device__ __forceinline__ void split_tf32(float g, uint32_t& hi, uint32_t& lo) {
+    hi = __float_as_uint(g) & 0xffffe000u;
+    lo = __float_as_uint(g - __uint_as_float(hi));
+}
+
+// Kernel value without sigma^2 from pre-scaled coordinate differences: the
+// conversion multiplies every coordinate by c (c^2 = a log2(e) for the
+// Gaussian, c = a log2(e) otherwise), so the base-2 exponent is a plain sum.
+template <int KIND>
+__device__ __forceinline__ float gamma_scaled(float dx, float dy, float dz) {
+    if (KIND == KL_KERNEL_GAUSS) return ex2_approx(-fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    if (KIND == KL_KERNEL_EXP_SEP) return ex2_approx(-(fabsf(dx) + fabsf(dy) + fabsf(dz)));
+    if (KIND == KL_KERNEL_EXP) return ex2_approx(-sqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz))));
+    if (KIND == KL_KERNEL_MATERN32) {
+        // a r = r' ln 2 with r' = a log2(e) r
+        const float r = sqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        return fmaf(0.69314718055994531f, r, 1.0f) * ex2_approx(-r);
+    }
+    return 1.0f;
+}
+
+// Coordinate scale c of gamma_scaled: the argument a r^2 log2(e) (Gaussian) or
+// a r log2(e) (exponentials, Matern) becomes |c x - c y|^2 or |c x - c y|.
+float coord_scale(const KernelSpec& ks) {
+    const double l2e = 1.4426950408889634074;
+    if (ks.kind == KL_KERNEL_GAUSS) return float(std::sqrt(ks.a * l2e));
+    if (ks.kind == KL_KERNEL_CONST) return 1.0f;
+    return float(ks.a * l2e);
 }
 
 // Byte offset of element (n, kk) inside one hi or lo image of a chunk:
@@ -170,7 +220,7 @@ __host__ __device__ inline uint32_t img_offset(int n, int kk, int np, int esize)
 
 // X (FP64) -> split images + FP32 source coordinates, chunk by chunk.
 __global__ void tc_convert_kernel(const double* __restrict__ X, int64_t ldx, int64_t S, int c0, int kc,
-                                  int np, int kchunk, bool tf32, const float* __restrict__ sx,
+                                  int np, int kchunk, bool tf32, float cscale, const float* __restrict__ sx,
                                   const float* __restrict__ sy, const float* __restrict__ sz,
                                   float4* __restrict__ src4, uint8_t* __restrict__ img, int64_t nchunks) {
     const int esize = tf32 ? 4 : 2;
@@ -196,15 +246,17 @@ __global__ void tc_convert_kernel(const double* __restrict__ X, int64_t ldx, int
             *reinterpret_cast<__nv_bfloat16*>(base + off) = h;
             *reinterpret_cast<__nv_bfloat16*>(base + img_bytes + off) = l;
         }
-        if (n == 0) src4[s] = (s < S) ? make_float4(sx[s], sy[s], sz[s], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (n == 0)
+            src4[s] = (s < S) ? make_float4(cscale * sx[s], cscale * sy[s], cscale * sz[s], 0.f)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
 template <int KIND, bool TF32, int NP>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
 pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const float* __restrict__ tz,
                int64_t T, const float4* __restrict__ src4, const uint8_t* __restrict__ img,
-               int64_t nchunks, int chunks_per_split, float a, float a2, double* __restrict__ part,
+               int64_t nchunks, int chunks_per_split, float cscale, double* __restrict__ part,
                int k_total, int c0, int kc, int* __restrict__ err) {
     constexpr int ESIZE = TF32 ? 4 : 2;
     constexpr int KC = TF32 ? 16 : 32;                  // sources per chunk (16 TMEM columns)
@@ -213,9 +265,9 @@ pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const
     constexpr uint32_t IDESC = instr_desc(NP, TF32);
 
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ uint64_t full_bar[kStages], empty_bar[kStages], done_bar, drain_bar;
+    __shared__ uint64_t full_bar[kStages], empty_bar[kStages], dfull_bar[2], dfree_bar[2], drain_bar;
     __shared__ uint32_t tmem_slot;
-    __shared__ int s_ok[2], s_done;
+    __shared__ int s_ok[2], s_flush_ok;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -223,13 +275,17 @@ pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const
     const int split = blockIdx.y;
     const int64_t ch0 = int64_t(split) * chunks_per_split;
     const int nloc = int(nchunks - ch0 < chunks_per_split ? nchunks - ch0 : int64_t(chunks_per_split));
+    const int ngroups = (nloc + kGroup - 1) / kGroup;
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full_bar[s], 128);
             mbar_init(&empty_bar[s], 1);
         }
-        mbar_init(&done_bar, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&dfull_bar[b], 1);
+            mbar_init(&dfree_bar[b], 128);
+        }
         mbar_init(&drain_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -243,7 +299,6 @@ pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    const uint32_t d_tmem = tmem;  // columns [0, NP)
 
     if (warp < 8) {
         // ---------------- producers ----------------
@@ -251,12 +306,51 @@ pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const
         const int ptid = tid & 127;          // thread within the warpgroup
         const int row = ptid;                // TMEM lane = target within the tile
         const int64_t t = tile * 128 + row;
-        const float px = t < T ? tx[t] : 0.f, py = t < T ? ty[t] : 0.f, pz = t < T ? tz[t] : 0.f;
+        const float px = t < T ? cscale * tx[t] : 0.f;
+        const float py = t < T ? cscale * ty[t] : 0.f;
+        const float pz = t < T ? cscale * tz[t] : 0.f;
         const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
+        double* prow = part + (int64_t(split) * k_total + c0) * T + t;  // column c at prow[c * T]
         bool ok = true;  // uniform within the warpgroup
+        int flushed = 0; // groups already flushed (warpgroup 0)
+
+        // warpgroup 0: add accumulator buffer of group g into the FP64 partials
+        auto flush = [&](int g) {
+            if (ptid == 0) s_flush_ok = (ok && mbar_wait(&dfull_bar[g & 1], uint32_t((g >> 1) & 1))) ? 1 : 0;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            const bool got = s_flush_ok != 0;
+            if (!got) ok = false;
+            tc_fence_after();
+            uint32_t v[16];
+            const uint32_t dcol = uint32_t((g & 1) * kDCols);
+#pragma unroll 1
+            for (int cb = 0; cb < NP; cb += 16) {
+                __syncwarp();
+                tmem_ld16(tmem + lane_base + dcol + uint32_t(cb), v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (got && t < T) {
+#pragma unroll 4
+                    for (int q = 0; q < 16; ++q) {
+                        const int c = cb + q;
+                        if (c < kc) {
+                            const double x = double(__uint_as_float(v[q]));
+                            prow[int64_t(c) * T] = (g == 0) ? x : prow[int64_t(c) * T] + x;
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&dfree_bar[g & 1]);
+        };
+
         for (int j = wg; j < nloc; j += 2) {
             const int s = j % kStages;
             const int use = j / kStages;
+            // warpgroup 0 flushes every group older than the one it now fills
+            if (wg == 0) {
+                while (flushed < j / kGroup) flush(flushed++);
+                if (!ok) break;
+            }
             // one thread waits (bounded) for the stage, the warpgroup follows
             if (ptid == 0) s_ok[wg] = (use == 0 || mbar_wait(&empty_bar[s], uint32_t((use - 1) & 1))) ? 1 : 0;
             asm volatile("bar.sync %0, 128;" ::"r"(1 + wg) : "memory");
@@ -270,55 +364,38 @@ pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const
             if (ptid < KC) sc[ptid] = src4[(ch0 + j) * KC + ptid];
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("bar.sync %0, 128;" ::"r"(1 + wg) : "memory");
-            // kernel tile row for this target, split into hi / lo
-            uint32_t hi[16], lo[16];
-            if (TF32) {
+            // kernel tile row for this target, split into hi / lo, written to
+            // tensor memory in two halves of 8 columns each
+            const uint32_t acol = uint32_t(kAColBase + s * kAColsPerStage);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const float4 y = sc[q];
-                    const float g = gamma32<KIND>(px - y.x, py - y.y, pz - y.z, a, a2);
-                    hi[q] = tf32_rna(g);
-                    lo[q] = tf32_rna(g - __uint_as_float(hi[q]));
-                }
-            } else {
+            for (int half = 0; half < 2; ++half) {
+                uint32_t hi[8], lo[8];
+                if (TF32) {
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const float4 y0 = sc[2 * q], y1 = sc[2 * q + 1];
-                    const float g0 = gamma32<KIND>(px - y0.x, py - y0.y, pz - y0.z, a, a2);
-                    const float g1 = gamma32<KIND>(px - y1.x, py - y1.y, pz - y1.z, a, a2);
-                    split_bf16(g0, g1, hi[q], lo[q]);
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 y = sc[8 * half + q];
+                        split_tf32(gamma_scaled<KIND>(px - y.x, py - y.y, pz - y.z), hi[q], lo[q]);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 y0 = sc[16 * half + 2 * q], y1 = sc[16 * half + 2 * q + 1];
+                        split_bf16(gamma_scaled<KIND>(px - y0.x, py - y0.y, pz - y0.z),
+                                   gamma_scaled<KIND>(px - y1.x, py - y1.y, pz - y1.z), hi[q], lo[q]);
+                    }
                 }
+                __syncwarp();
+                tmem_st8(tmem + lane_base + acol + uint32_t(8 * half), hi);
+                tmem_st8(tmem + lane_base + acol + 16u + uint32_t(8 * half), lo);
             }
-            __syncwarp();
-            const uint32_t acol = uint32_t(kDCols + s * kAColsPerStage);
-            tmem_st16(tmem + lane_base + acol, hi);
-            tmem_st16(tmem + lane_base + acol + 16, lo);
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
             mbar_arrive(&full_bar[s]);
         }
-        if (!ok && ptid == 0) atomicExch(err, 1);
-        // ---------------- epilogue (warpgroup 0) ----------------
         if (wg == 0) {
-            if (ptid == 0) s_done = (ok && mbar_wait(&done_bar, 0)) ? 1 : 0;
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            const bool got = s_done != 0;
-            if (!got && ptid == 0) atomicExch(err, 1);
-            tc_fence_after();
-            uint32_t v[16];
-            for (int cb = 0; cb < NP; cb += 16) {
-                __syncwarp();
-                tmem_ld16(d_tmem + lane_base + uint32_t(cb), v);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (got && t < T) {
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const int c = cb + q;
-                        if (c < kc) part[(int64_t(split) * k_total + c0 + c) * T + t] = double(__uint_as_float(v[q]));
-                    }
-                }
-            }
+            while (ok && flushed < ngroups) flush(flushed++);
         }
+        if (!ok && ptid == 0) atomicExch(err, 1);
     } else if (warp == 8) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
@@ -326,25 +403,28 @@ pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const
             for (int j = 0; j < nloc; ++j) {
                 const int s = j % kStages;
                 const int use = j / kStages;
+                const int g = j / kGroup;
+                const bool first = (j % kGroup) == 0;
+                const uint32_t d_tmem = tmem + uint32_t((g & 1) * kDCols);
+                if (first && g >= 2 && !mbar_wait(&dfree_bar[g & 1], uint32_t(((g >> 1) - 1) & 1))) { ok = false; break; }
                 if (!mbar_wait(&full_bar[s], uint32_t(use & 1))) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
-                const uint32_t acol = tmem + uint32_t(kDCols + s * kAColsPerStage);
+                const uint32_t acol = tmem + uint32_t(kAColBase + s * kAColsPerStage);
 #pragma unroll
                 for (int ks = 0; ks < 2; ++ks) {
                     const uint32_t step = uint32_t(ks * 2 * (NP / 8) * 128);
                     const uint64_t bh = smem_desc(st + step, (NP / 8) * 128, 128);
                     const uint64_t bl = smem_desc(st + IMG + step, (NP / 8) * 128, 128);
                     const uint32_t ah = acol + uint32_t(ks * 8), al = acol + 16u + uint32_t(ks * 8);
-                    mma_tmemA(TF32, d_tmem, ah, bh, IDESC, (j > 0 || ks > 0) ? 1u : 0u);
+                    mma_tmemA(TF32, d_tmem, ah, bh, IDESC, (first && ks == 0) ? 0u : 1u);
                     mma_tmemA(TF32, d_tmem, ah, bl, IDESC, 1u);
                     mma_tmemA(TF32, d_tmem, al, bh, IDESC, 1u);
                 }
                 mma_commit(&empty_bar[s]);
+                if ((j % kGroup) == kGroup - 1 || j == nloc - 1) mma_commit(&dfull_bar[g & 1]);
             }
-            if (ok) {
-                mma_commit(&done_bar);
-            } else {
+            if (!ok) {
                 atomicExch(err, 1);
                 mma_commit(&drain_bar);
                 mbar_wait(&drain_bar, 0);  // bounded: MMAs already issued finish
@@ -372,10 +452,9 @@ cudaError_t launch_np(const TcArgs& a, int c0, int kc, const float4* src4, const
     auto kern = pair_tc_kernel<KIND, TF32, NP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const double l2e = 1.4426950408889634074;
     dim3 grid(unsigned((a.T + 127) / 128), unsigned(splits));
-    kern<<<grid, kThreads, smem, s>>>(a.tx, a.ty, a.tz, a.T, src4, img, nchunks, cps, float(a.ks.a),
-                                      float(a.ks.a * l2e), part, a.k, c0, kc, err);
+    kern<<<grid, kThreads, smem, s>>>(a.tx, a.ty, a.tz, a.T, src4, img, nchunks, cps, coord_scale(a.ks), part,
+                                      a.k, c0, kc, err);
     return cudaGetLastError();
 }
 
@@ -453,8 +532,8 @@ cudaError_t launch_pair_tc(const TcArgs& a, cudaStream_t s, int* launched) {
         const int np = std::max(16, (kc + 15) / 16 * 16);
         const int64_t total = p.nchunks * p.kchunk * np;
         const int g = int(std::min<int64_t>((total + 255) / 256, 152 * 64));
-        tc_convert_kernel<<<g, 256, 0, s>>>(a.X, a.ldx, a.S, c0, kc, np, p.kchunk, a.tf32, a.sx, a.sy, a.sz,
-                                            src4, img, p.nchunks);
+        tc_convert_kernel<<<g, 256, 0, s>>>(a.X, a.ldx, a.S, c0, kc, np, p.kchunk, a.tf32, coord_scale(a.ks),
+                                            a.sx, a.sy, a.sz, src4, img, p.nchunks);
         ++*launched;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         e = a.tf32 ? launch_tc<true>(a, c0, kc, np, src4, img, p.nchunks, p.cps, p.splits, part, err, s)

@@ -194,9 +194,14 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
     c.sym = h->prm.method == KL_GALERKIN_IBQ;
     const int64_t N = h->N;
     const int b = int(std::min<int64_t>(h->prm.block_k, N));
-    const int nkeep = int(std::min<int64_t>(M + b, N));
-    int mmax = int(std::min<int64_t>(N, std::max(2 * nkeep, nkeep + 2 * b)));
-    if (mmax > 1024) mmax = 1024;
+    // nkeep and mmax are multiples of b so that every expansion step takes the
+    // images of a full block (the Krylov-Schur relation needs the whole
+    // residual of the last block); a basis of N vectors is complete instead
+    const int nkeep_full = (M + b + b - 1) / b * b;
+    const int mmax_full = std::max(2 * nkeep_full, nkeep_full + 2 * b);
+    if (mmax_full > 512 && mmax_full < N) return fail(h, KL_ERR_ARG, "M + 2 block_k too large for the basis limit 512");
+    const int nkeep = int(std::min<int64_t>(nkeep_full, N));
+    const int mmax = int(std::min<int64_t>(mmax_full, N));
     c.mmax = mmax;
 
     // ---- workspace (one allocation, reused across calls) ----
