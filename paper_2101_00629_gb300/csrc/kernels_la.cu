@@ -342,7 +342,8 @@ __device__ inline void house(const double* x, int len, double* v, double& beta) 
 
 __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restrict__ H, int n,
                                                          double* wr_out, double* wi_out,
-                                                         double* Vout, double* work, int* status) {
+                                                         double* Vout, double* Qout, double* work,
+                                                         int* status) {
     double* A = work;                        // n x n (Schur form)
     double* Z = A + int64_t(n) * n;          // n x n (Schur vectors)
     double* X = Z + int64_t(n) * n;          // n x n (eigenvectors of T, real/imag)
@@ -428,27 +429,28 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
                 for (l = u; l >= 1; --l) {
                     double s = fabs(A[(l - 1) + int64_t(l - 1) * n]) + fabs(A[l + int64_t(l) * n]);
                     if (s == 0.0) s = anorm;
-                    // relative test, plus an absolute one at roundoff of the
-                    // whole matrix: next to eigenvalues that are themselves at
-                    // roundoff level the relative test can never be met
                     const double sub = fabs(A[l + int64_t(l - 1) * n]);
-                    if (sub <= DBL_EPSILON * s || sub <= DBL_EPSILON * anorm) {
+                    // absolute test at roundoff of the whole matrix: next to
+                    // eigenvalues that are themselves at roundoff level a
+                    // relative test can never be met
+                    if (sub <= double(n) * DBL_EPSILON * anorm) {
                         A[l + int64_t(l - 1) * n] = 0.0;
                         break;
                     }
-                    // Ahues-Tisseur test: the product of the off-diagonal
-                    // pair against the gap of the diagonal pair; needed for
-                    // clusters of (nearly) equal eigenvalues, where the
-                    // subdiagonal alone stalls well above roundoff
-                    const double up = fabs(A[(l - 1) + int64_t(l) * n]);
-                    const double ab = fmax(sub, up), ba = fmin(sub, up);
-                    const double dd = fabs(A[(l - 1) + int64_t(l - 1) * n] - A[l + int64_t(l) * n]);
-                    const double aa = fmax(fabs(A[l + int64_t(l) * n]), dd);
-                    const double bb = fmin(fabs(A[l + int64_t(l) * n]), dd);
-                    const double ss = aa + ab;
-                    if (ba * (ab / ss) <= fmax(DBL_MIN, DBL_EPSILON * (bb * (aa / ss)))) {
-                        A[l + int64_t(l - 1) * n] = 0.0;
-                        break;
+                    // relative test, confirmed by the more conservative
+                    // Ahues-Kressner criterion (off-diagonal product against
+                    // the gap of the diagonal pair)
+                    if (sub <= DBL_EPSILON * s) {
+                        const double up = fabs(A[(l - 1) + int64_t(l) * n]);
+                        const double ab = fmax(sub, up), ba = fmin(sub, up);
+                        const double dd = fabs(A[(l - 1) + int64_t(l - 1) * n] - A[l + int64_t(l) * n]);
+                        const double aa = fmax(fabs(A[l + int64_t(l) * n]), dd);
+                        const double bb = fmin(fabs(A[l + int64_t(l) * n]), dd);
+                        const double ss = aa + ab;
+                        if (ba * (ab / ss) <= fmax(DBL_MIN, DBL_EPSILON * (bb * (aa / ss)))) {
+                            A[l + int64_t(l - 1) * n] = 0.0;
+                            break;
+                        }
                     }
                 }
                 if (l < 0) l = 0;
@@ -459,12 +461,12 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
             s_l = l;
             s_action = action;
             if (action == 3) {
-                if (s_its >= 60 || total_its > 40 * n) {
+                if (s_its >= 300 || total_its > 120 * max(10, n)) {
                     s_fail = 1;
                     s_action = 4;
                 } else {
                     double sh, th;
-                    if (s_its == 10 || s_its == 25) {
+                    if (s_its > 0 && s_its % 10 == 0) {  // exceptional shift
                         const double ex = fabs(A[u + int64_t(u - 1) * n]) + fabs(A[(u - 1) + int64_t(u - 2) * n]);
                         const double c = A[u + int64_t(u) * n] + 0.75 * ex;
                         sh = 2.0 * c;
@@ -612,8 +614,184 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
         }
     }
     __syncthreads();
+    // ---- reorder the real Schur form: eigenvalues by decreasing real part ----
+    // Selection sort over the diagonal blocks (1x1 real eigenvalues, 2x2
+    // complex pairs). Adjacent blocks A (n1 x n1) and B (n2 x n2) with
+    // coupling C are exchanged by the direct swap: solve A X - X B = C, the
+    // columns of [X; -I] span the B-invariant subspace, and the orthogonal
+    // factor Q of their QR factorisation gives Q^T [A C; 0 B] Q = [B' *; 0 A'].
+    // The leading Schur vectors then span the invariant subspace of the
+    // largest eigenvalues, which is what a Krylov-Schur restart keeps.
+    __shared__ double s_q[16];
+    __shared__ int s_k, s_m, s_n2, s_act, s_pos;
+    if (tid == 0) s_pos = 0;
+    __syncthreads();
+    while (!s_fail) {
+        if (tid == 0) {
+            const int pos = s_pos;
+            s_act = 0;
+            if (pos < n) {
+                // best block at or after pos (max real part, earliest on ties)
+                int best = -1, bsz = 1, prev = -1, psz = 1, before_best = -1, before_sz = 1;
+                double bkey = -DBL_MAX;
+                for (int i = pos; i < n;) {
+                    const int sz = (i + 1 < n && A[(i + 1) + int64_t(i) * n] != 0.0) ? 2 : 1;
+                    const double key = sz == 1 ? A[i + int64_t(i) * n]
+                                               : 0.5 * (A[i + int64_t(i) * n] + A[(i + 1) + int64_t(i + 1) * n]);
+                    if (key > bkey) {
+                        bkey = key;
+                        best = i;
+                        bsz = sz;
+                        before_best = prev;
+                        before_sz = psz;
+                    }
+                    prev = i;
+                    psz = sz;
+                    i += sz;
+                }
+                if (best == pos) {
+                    s_pos = pos + bsz;
+                    s_act = 2;
+                } else {
+                    // swap the block before `best` (k, n1) with best (n2)
+                    const int k = before_best, n1 = before_sz, n2 = bsz, m = n1 + n2;
+                    double K[16], x[4], W[8], Qm[16];
+                    const int pdim = n1 * n2;
+                    for (int r = 0; r < pdim * pdim; ++r) K[r] = 0.0;
+                    // K = I_{n2} (x) A - B^T (x) I_{n1}, x = vec(X) column-major
+                    for (int j = 0; j < n2; ++j)
+                        for (int i = 0; i < n1; ++i) {
+                            const int row = i + n1 * j;
+                            for (int i2 = 0; i2 < n1; ++i2)
+                                K[row + pdim * (i2 + n1 * j)] += A[(k + i) + int64_t(k + i2) * n];
+                            for (int j2 = 0; j2 < n2; ++j2)
+                                K[row + pdim * (i + n1 * j2)] -= A[(k + n1 + j2) + int64_t(k + n1 + j) * n];
+                            x[row] = A[(k + i) + int64_t(k + n1 + j) * n];
+                        }
+                    // Gaussian elimination with partial pivoting (pdim <= 4)
+                    double kn = 0.0;
+                    for (int r = 0; r < pdim * pdim; ++r) kn = fmax(kn, fabs(K[r]));
+                    const double tiny = DBL_EPSILON * fmax(kn, anorm);
+                    for (int c = 0; c < pdim; ++c) {
+                        int pr = c;
+                        for (int r = c + 1; r < pdim; ++r)
+                            if (fabs(K[r + pdim * c]) > fabs(K[pr + pdim * c])) pr = r;
+                        if (pr != c) {
+                            for (int cc = 0; cc < pdim; ++cc) {
+                                const double t = K[c + pdim * cc]; K[c + pdim * cc] = K[pr + pdim * cc]; K[pr + pdim * cc] = t;
+                            }
+                            const double t = x[c]; x[c] = x[pr]; x[pr] = t;
+                        }
+                        if (fabs(K[c + pdim * c]) < tiny) K[c + pdim * c] = K[c + pdim * c] >= 0.0 ? tiny : -tiny;
+                        for (int r = c + 1; r < pdim; ++r) {
+                            const double f = K[r + pdim * c] / K[c + pdim * c];
+                            for (int cc = c; cc < pdim; ++cc) K[r + pdim * cc] -= f * K[c + pdim * cc];
+                            x[r] -= f * x[c];
+                        }
+                    }
+                    for (int r = pdim - 1; r >= 0; --r) {
+                        double t = x[r];
+                        for (int cc = r + 1; cc < pdim; ++cc) t -= K[r + pdim * cc] * x[cc];
+                        x[r] = t / K[r + pdim * r];
+                    }
+                    // W = [X; -I] (m x n2), Householder QR, Q accumulated
+                    for (int j = 0; j < n2; ++j)
+                        for (int i = 0; i < m; ++i) W[i + m * j] = (i < n1) ? x[i + n1 * j] : (i - n1 == j ? -1.0 : 0.0);
+                    for (int r = 0; r < m * m; ++r) Qm[r] = (r % m == r / m) ? 1.0 : 0.0;
+                    for (int j = 0; j < n2; ++j) {
+                        double v[4], beta, xx[4];
+                        const int len = m - j;
+                        for (int t = 0; t < len; ++t) xx[t] = W[(j + t) + m * j];
+                        house(xx, len, v, beta);
+                        for (int c = j; c < n2; ++c) {
+                            double sdot = 0.0;
+                            for (int t = 0; t < len; ++t) sdot += v[t] * W[(j + t) + m * c];
+                            for (int t = 0; t < len; ++t) W[(j + t) + m * c] -= beta * sdot * v[t];
+                        }
+                        for (int r = 0; r < m; ++r) {
+                            double sdot = 0.0;
+                            for (int t = 0; t < len; ++t) sdot += Qm[r + m * (j + t)] * v[t];
+                            for (int t = 0; t < len; ++t) Qm[r + m * (j + t)] -= beta * sdot * v[t];
+                        }
+                    }
+                    for (int r = 0; r < m * m; ++r) s_q[r] = Qm[r];
+                    s_k = k;
+                    s_m = m;
+                    s_n2 = n2;
+                    s_act = 1;
+                }
+            }
+        }
+        __syncthreads();
+        const int act = s_act;
+        if (act == 0) break;
+        if (act == 1) {
+            const int k = s_k, m = s_m;
+            // rows k..k+m-1 <- Q^T rows (columns k..n-1)
+            for (int j = k + tid; j < n; j += nt) {
+                double old[4];
+                for (int t = 0; t < m; ++t) old[t] = A[(k + t) + int64_t(j) * n];
+                for (int t = 0; t < m; ++t) {
+                    double acc = 0.0;
+                    for (int u2 = 0; u2 < m; ++u2) acc += s_q[u2 + m * t] * old[u2];
+                    A[(k + t) + int64_t(j) * n] = acc;
+                }
+            }
+            __syncthreads();
+            // columns k..k+m-1 <- columns Q (rows 0..k+m-1), and Z (all rows)
+            for (int r = tid; r < n; r += nt) {
+                double old[4], oz[4];
+                for (int t = 0; t < m; ++t) {
+                    old[t] = A[r + int64_t(k + t) * n];
+                    oz[t] = Z[r + int64_t(k + t) * n];
+                }
+                for (int t = 0; t < m; ++t) {
+                    double acc = 0.0, accz = 0.0;
+                    for (int u2 = 0; u2 < m; ++u2) {
+                        acc += old[u2] * s_q[u2 + m * t];
+                        accz += oz[u2] * s_q[u2 + m * t];
+                    }
+                    if (r < k + m) A[r + int64_t(k + t) * n] = acc;
+                    Z[r + int64_t(k + t) * n] = accz;
+                }
+            }
+            __syncthreads();
+            if (tid == 0) {
+                // the exchanged blocks: zero the new (2,1) block
+                const int n2 = s_n2;
+                for (int i = k + n2; i < k + m; ++i)
+                    for (int j = k; j < k + n2; ++j) A[i + int64_t(j) * n] = 0.0;
+            }
+            __syncthreads();
+        }
+    }
+    // eigenvalues from the (re)ordered blocks
+    if (tid == 0 && !s_fail) {
+        for (int i = 0; i < n;) {
+            if (i + 1 < n && A[(i + 1) + int64_t(i) * n] != 0.0) {
+                const double a = A[i + int64_t(i) * n], b = A[i + int64_t(i + 1) * n];
+                const double c = A[(i + 1) + int64_t(i) * n], d = A[(i + 1) + int64_t(i + 1) * n];
+                const double pp = 0.5 * (a - d), q = pp * pp + b * c;
+                wr[i] = wr[i + 1] = d + pp;
+                const double im = q < 0.0 ? sqrt(-q) : 0.0;
+                wi[i] = im;
+                wi[i + 1] = -im;
+                i += 2;
+            } else {
+                wr[i] = A[i + int64_t(i) * n];
+                wi[i] = 0.0;
+                i += 1;
+            }
+        }
+    }
+    __syncthreads();
     // ---- eigenvectors of the quasi-triangular T by back substitution ----
+    // Diagonal entries within 1e-10 ||T|| of the eigenvalue belong to its
+    // cluster; their components are set to zero instead of dividing by a
+    // vanishing pivot, so the vectors of a (numerically) multiple eigenvalue
+    // stay independent (its invariant subspace is spanned by Schur vectors).
     const double small = DBL_EPSILON * fmax(anorm, DBL_MIN);
+    const double clus = 1e-10 * anorm;
     for (int col = tid; col < n; col += nt) {
         double* xr = X + int64_t(col) * n;
         if (wi[col] == 0.0) {
@@ -626,6 +804,10 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
                     double s = 0.0;
                     for (int l2 = j + 1; l2 <= col; ++l2) s += A[j + int64_t(l2) * n] * xr[l2];
                     double den = A[j + int64_t(j) * n] - lam;
+                    if (fabs(den) <= clus) {
+                        xr[j] = 0.0;
+                        continue;
+                    }
                     if (fabs(den) < small) den = small;
                     xr[j] = -s / den;
                 } else {
@@ -729,7 +911,10 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
         wi_out[rank] = wi[i];
         for (int r = 0; r < n; ++r) Vout[r + int64_t(rank) * n] = Vt[r + int64_t(i) * n];
     }
-    if (tid == 0) *status = s_fail;
+    if (Qout) {
+        for (int e = tid; e < n * n; e += nt) Qout[e] = Z[e];
+    }
+    if (tid == 0) *status = s_fail ? 1 : 0;
 }
 
 }  // namespace
@@ -784,9 +969,9 @@ cudaError_t launch_sym_eig(const double* H, int n, double* w, double* V, double*
 
 int64_t nonsym_eig_work_doubles(int n) { return 3 * int64_t(n) * n + 3 * int64_t(n); }
 
-cudaError_t launch_nonsym_eig(const double* H, int n, double* wr, double* wi, double* V,
+cudaError_t launch_nonsym_eig(const double* H, int n, double* wr, double* wi, double* V, double* Q,
                               double* work, int* status, cudaStream_t s) {
-    nonsym_eig_kernel<<<1, 256, 0, s>>>(H, n, wr, wi, V, work, status);
+    nonsym_eig_kernel<<<1, 256, 0, s>>>(H, n, wr, wi, V, Q, work, status);
     return cudaGetLastError();
 }
 

@@ -125,8 +125,11 @@ cudaError_t launch_sym_eig(const double* H, int n, double* w, double* V, double*
                            int* status, cudaStream_t s);
 // Real non-symmetric eigen-decomposition (Hessenberg + Francis QR + back
 // substitution). wr/wi eigenvalues sorted by real part descending, V real
-// vectors (complex pairs as Re, Im columns), unit 2-norm.
-cudaError_t launch_nonsym_eig(const double* H, int n, double* wr, double* wi, double* V,
+// vectors (complex pairs as Re, Im columns), unit 2-norm. When every
+// eigenvalue is real the Schur form is reordered and Q (optional) receives
+// the Schur vectors in the same order (status 0); status 2 means complex
+// pairs were met and Q is not ordered; status 1 means no convergence.
+cudaError_t launch_nonsym_eig(const double* H, int n, double* wr, double* wi, double* V, double* Q,
                               double* work, int* status, cudaStream_t s);
 int64_t nonsym_eig_work_doubles(int n);
 int64_t sym_eig_work_doubles(int n);

@@ -37,6 +37,7 @@ namespace {
 struct EigWs {
     double *V, *AV, *T1, *T2;   // N x mmax each
     double *H, *S, *G, *Rinv;   // mmax^2 each
+    double* Q;                  // ordered Schur vectors (non-symmetric), mmax^2
     double *theta, *thetai, *norms, *norms2;  // mmax each
     double* la_work;            // eigensolver work
     double* tn_scratch;         // gemm_tn partials
@@ -50,6 +51,7 @@ struct Ctx {
     int64_t N;
     int mmax;
     bool sym;
+    bool schur_ok = false;      // Q holds ordered Schur vectors of the last H
     unsigned long long rng_offset = 0;
     int applies = 0, vectors_applied = 0;
 };
@@ -165,9 +167,11 @@ int rayleigh_ritz(Ctx& c, const double* V, const double* AV, int nv, double* max
         KL_TRY(sync_copy(c, &status, c.w.ibuf, sizeof(int)));
         if (max_imag) *max_imag = 0.0;
     } else {
-        KL_TRY(ck(c, launch_nonsym_eig(c.w.H, nv, c.w.theta, c.w.thetai, c.w.S, c.w.la_work, c.w.ibuf,
-                                       c.h->stream), "nonsym_eig"));
+        KL_TRY(ck(c, launch_nonsym_eig(c.w.H, nv, c.w.theta, c.w.thetai, c.w.S, c.w.Q, c.w.la_work,
+                                       c.w.ibuf, c.h->stream), "nonsym_eig"));
         KL_TRY(sync_copy(c, &status, c.w.ibuf, sizeof(int)));
+        c.schur_ok = status == 0;
+        if (status == 2) status = 0;  // complex pairs: eigenvectors valid, Schur order not
     }
     if (status != 0) return fail(c.h, KL_ERR_NUMERIC, "small eigensolver did not converge");
     return KL_OK;
@@ -199,16 +203,19 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
     // residual of the last block); a basis of N vectors is complete instead
     const int nkeep_full = (M + b + b - 1) / b * b;
     const int mmax_full = std::max(2 * nkeep_full, nkeep_full + 2 * b);
-    if (mmax_full > 512 && mmax_full < N) return fail(h, KL_ERR_ARG, "M + 2 block_k too large for the basis limit 512");
+    if (mmax_full + b > 512 && mmax_full < N) return fail(h, KL_ERR_ARG, "M + 3 block_k too large for the basis limit 512");
     const int nkeep = int(std::min<int64_t>(nkeep_full, N));
     const int mmax = int(std::min<int64_t>(mmax_full, N));
-    c.mmax = mmax;
+    // a restart keeps one extra vector rather than split a complex pair, so
+    // the basis may grow to mmax + b - 1 columns
+    const int mcap = int(std::min<int64_t>(int64_t(mmax) + b, N));
+    c.mmax = mcap;
 
     // ---- workspace (one allocation, reused across calls) ----
-    const int64_t tn_len = std::max(gemm_tn_scratch_doubles(mmax, mmax, N), int64_t(1));
-    const int64_t la = std::max(sym_eig_work_doubles(mmax), nonsym_eig_work_doubles(mmax));
-    const int64_t need = 4 * N * mmax + 4 * int64_t(mmax) * mmax + 4 * int64_t(mmax) + la + tn_len +
-                         (int64_t(mmax) + 2) / 2 + 64;
+    const int64_t tn_len = std::max(gemm_tn_scratch_doubles(mcap, mcap, N), int64_t(1));
+    const int64_t la = std::max(sym_eig_work_doubles(mcap), nonsym_eig_work_doubles(mcap));
+    const int64_t need = 4 * N * mcap + 5 * int64_t(mcap) * mcap + 4 * int64_t(mcap) + la + tn_len +
+                         (int64_t(mcap) + 2) / 2 + 64;
     if (need * int64_t(sizeof(double)) > h->eig_cap_bytes) {
         cudaStreamSynchronize(h->stream);
         if (h->eig_ws) cudaFree(h->eig_ws);
@@ -227,26 +234,27 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
         p += (n + 3) / 4 * 4;
         return r;
     };
-    c.w.V = take(N * mmax);
-    c.w.AV = take(N * mmax);
-    c.w.T1 = take(N * mmax);
-    c.w.T2 = take(N * mmax);
-    c.w.H = take(int64_t(mmax) * mmax);
-    c.w.S = take(int64_t(mmax) * mmax);
-    c.w.G = take(int64_t(mmax) * mmax);
-    c.w.Rinv = take(int64_t(mmax) * mmax);
-    c.w.theta = take(mmax);
-    c.w.thetai = take(mmax);
-    c.w.norms = take(mmax);
-    c.w.norms2 = take(mmax);
+    c.w.V = take(N * mcap);
+    c.w.AV = take(N * mcap);
+    c.w.T1 = take(N * mcap);
+    c.w.T2 = take(N * mcap);
+    c.w.H = take(int64_t(mcap) * mcap);
+    c.w.S = take(int64_t(mcap) * mcap);
+    c.w.G = take(int64_t(mcap) * mcap);
+    c.w.Rinv = take(int64_t(mcap) * mcap);
+    c.w.Q = take(int64_t(mcap) * mcap);
+    c.w.theta = take(mcap);
+    c.w.thetai = take(mcap);
+    c.w.norms = take(mcap);
+    c.w.norms2 = take(mcap);
     c.w.la_work = take(la);
     c.w.tn_scratch = take(tn_len);
     c.w.tn_len = tn_len;
-    c.w.ibuf = reinterpret_cast<int*>(take((int64_t(mmax) + 2) / 2 + 2));
+    c.w.ibuf = reinterpret_cast<int*>(take((int64_t(mcap) + 2) / 2 + 2));
 
     double* V = c.w.V;
     double* AV = c.w.AV;
-    std::vector<double> th(mmax), thi(mmax, 0.0), rn(mmax);
+    std::vector<double> th(mcap), thi(mcap, 0.0), rn(mcap);
 
     // ---- start block ----
     int nv = b, na = 0;
@@ -264,7 +272,7 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
             if (int rc = apply(c, prec, V + na * N, AV + na * N, nv - na); rc != KL_OK) return rc;
             na = nv;
             if (nv >= mmax || nv >= N) break;
-            const int bb = int(std::min<int64_t>(std::min(b, mmax - nv), N - nv));
+            const int bb = int(std::min<int64_t>(b, N - nv));
             double* Wn = V + int64_t(nv) * N;
             if (int rc = ck(c, launch_copy_block(AV + int64_t(nv - bb) * N, N, Wn, N, N, bb, h->stream), "copy"); rc != KL_OK) return rc;
             if (int rc = orthonormalize(c, V, nv, Wn, bb); rc != KL_OK) return rc;
@@ -298,17 +306,23 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
         }
         // ---- restart ----
         ++restarts;
-        const int keep = std::min(nkeep, nv - b);
+        int keep = std::min(nkeep, nv - b);
+        if (!c.sym && thi[keep - 1] > 0.0) ++keep;  // do not split a complex pair
         // next block: newest block of A'V orthogonalised against the full basis
         double* Wn = c.w.T1;  // reuse; Ritz vectors are recomputed after the loop
         if (int rc = ck(c, launch_copy_block(AV + int64_t(nv - b) * N, N, Wn, N, N, b, h->stream), "copy"); rc != KL_OK) return rc;
         if (int rc = orthonormalize(c, V, nv, Wn, b); rc != KL_OK) return rc;
-        // V S(:, :keep) and AV S(:, :keep) into T2 / back into V, AV
-        if (int rc = nn(c, V, N, c.w.S, nv, c.w.T2, N, nv, keep, 1.0, 0.0); rc != KL_OK) return rc;
+        // Symmetric: the leading Ritz vectors (orthonormal). Non-symmetric:
+        // the leading ordered Schur vectors (orthonormal, spanning the
+        // invariant subspace of the wanted Ritz values, also for clusters
+        // of equal eigenvalues); Ritz vectors only if complex pairs stopped
+        // the ordering. V R(:, :keep) and AV R(:, :keep) go back into V, AV.
+        const double* Rk = (c.sym || !c.schur_ok) ? c.w.S : c.w.Q;
+        if (int rc = nn(c, V, N, Rk, nv, c.w.T2, N, nv, keep, 1.0, 0.0); rc != KL_OK) return rc;
         if (int rc = ck(c, launch_copy_block(c.w.T2, N, V, N, N, keep, h->stream), "copy"); rc != KL_OK) return rc;
-        if (int rc = nn(c, AV, N, c.w.S, nv, c.w.T2, N, nv, keep, 1.0, 0.0); rc != KL_OK) return rc;
+        if (int rc = nn(c, AV, N, Rk, nv, c.w.T2, N, nv, keep, 1.0, 0.0); rc != KL_OK) return rc;
         if (int rc = ck(c, launch_copy_block(c.w.T2, N, AV, N, N, keep, h->stream), "copy"); rc != KL_OK) return rc;
-        if (!c.sym) {
+        if (!c.sym && !c.schur_ok) {
             // Ritz (or real/imaginary) vectors are not orthonormal: CholQR2 on V
             // and the same right factor on AV
             for (int pass = 0; pass < 2; ++pass) {
@@ -328,11 +342,13 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
     // ---- final Ritz pairs (optionally refined by an FP64 Rayleigh-Ritz) ----
     int nk = std::min(nv, nkeep);
     if (nk < M) nk = std::min(nv, M);
+    if (!c.sym && nk < nv && thi[nk - 1] > 0.0) ++nk;  // keep complex pairs whole
     double* Y = c.w.T1;
     double* AY = c.w.T2;
-    if (int rc = nn(c, V, N, c.w.S, nv, Y, N, nv, nk, 1.0, 0.0); rc != KL_OK) return rc;
+    const bool use_schur = !c.sym && c.schur_ok && prec != KL_FP64 && h->prm.refine > 0;
+    if (int rc = nn(c, V, N, use_schur ? c.w.Q : c.w.S, nv, Y, N, nv, nk, 1.0, 0.0); rc != KL_OK) return rc;
     if (prec != KL_FP64 && h->prm.refine > 0) {
-        if (!c.sym) {
+        if (!c.sym && !use_schur) {
             // orthonormal basis of the Ritz subspace
             for (int pass = 0; pass < 2; ++pass) {
                 if (int rc = tn(c, Y, N, Y, N, c.w.G, nk, nk, nk); rc != KL_OK) return rc;
