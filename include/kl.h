@@ -214,6 +214,31 @@ int kl_memory(const kl_solver* h, int64_t* h2d_bytes, int64_t* device_bytes);
  * Errors: KL_ERR_CUDA, KL_ERR_OOM. */
 int kl_measure_peaks(double* fp32_fma_per_s, double* ex2_per_s, double* fp64_fma_per_s);
 
+/* Y = sigma^2 Gamma(targets, sources) X with FP64 kernel evaluation on the
+ * CUDA cores, allocating no device memory. No paper passage: the paper has no
+ * counterpart; this entry point exists for callers that cannot allocate --
+ * code inside CUDA graph capture, applications with fixed memory pools, or
+ * hosts that hand out one pre-sized arena and forbid cudaMalloc/cudaFree.
+ *   kernel, sigma, L  as in kl_params (KL_KERNEL_*, sigma > 0, L > 0).
+ *   tgt               device FP64, 3*T values: all x, then all y, then all z.
+ *   src               device FP64, 3*S values, same layout.
+ *   X                 device FP64, S x k column-major (ldx >= S).
+ *   Y                 device FP64, T x k column-major (ldy >= T), written.
+ *   stream            cudaStream_t (NULL: legacy default stream).
+ * Its partial sums live in one static device array of 2^21 doubles (16 MiB)
+ * that every device loading the library holds until the process exits; the
+ * call requires k * T <= 2^21 and returns KL_ERR_ARG beyond that. The first
+ * call on a device looks up that array's device address (set-up, with the
+ * device current); make the first call before any stream capture. All calls
+ * on a device share the array: calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller. Nothing in
+ * the array needs clearing between calls. No cudaMalloc or cudaFree is made.
+ * Asynchronous on `stream`. Errors: KL_ERR_ARG, KL_ERR_CUDA; the message is
+ * kl_last_error(NULL). */
+int kl_pairwise_noalloc(int kernel, double sigma, double L, const double* tgt, int64_t T,
+                        const double* src, int64_t S, const double* X, int64_t ldx, double* Y,
+                        int64_t ldy, int k, void* stream);
+
 /* Last error message of the handle (h may be NULL: last kl_create error). */
 const char* kl_last_error(const kl_solver* h);
 const char* kl_status_string(int status);

@@ -17,7 +17,7 @@ __all__ = [
     "kl_default_params", "kl_create", "kl_destroy", "kl_dims", "kl_apply_A",
     "kl_apply_Zinv", "kl_apply_Aprime", "kl_eigs", "kl_profile_enable",
     "kl_profile_read", "kl_launch_count", "kl_memory", "kl_last_error",
-    "kl_status_string", "kl_measure_peaks", "library_path", "EXPORTED_SYMBOLS",
+    "kl_status_string", "kl_measure_peaks", "kl_pairwise_noalloc", "library_path", "EXPORTED_SYMBOLS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -37,7 +37,7 @@ EXPORTED_SYMBOLS = (
     "kl_default_params", "kl_create", "kl_destroy", "kl_dims", "kl_apply_A",
     "kl_apply_Zinv", "kl_apply_Aprime", "kl_eigs", "kl_profile_enable",
     "kl_profile_read", "kl_launch_count", "kl_memory", "kl_last_error",
-    "kl_status_string", "kl_measure_peaks",
+    "kl_status_string", "kl_measure_peaks", "kl_pairwise_noalloc",
 )
 
 
@@ -119,6 +119,7 @@ def _load():
         "kl_last_error": (ctypes.c_char_p, [vp]),
         "kl_status_string": (ctypes.c_char_p, [c_int]),
         "kl_measure_peaks": (c_int, [ctypes.POINTER(dbl)] * 3),
+        "kl_pairwise_noalloc": (c_int, [c_int, dbl, dbl, vp, i64, vp, i64, vp, i64, vp, i64, c_int, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -258,3 +259,14 @@ def kl_measure_peaks():
     a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(None, _load().kl_measure_peaks(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+def kl_pairwise_noalloc(kernel, sigma, L, tgt, T, src, S, X, ldx, Y, ldy, k, stream=None):
+    """Y = sigma^2 Gamma(tgt, src) X without device allocation (see kl.h)."""
+    if isinstance(kernel, str):
+        kernel = KERNELS[kernel]
+    if stream is not None and not isinstance(stream, int):
+        stream = stream.cuda_stream
+    rc = _load().kl_pairwise_noalloc(int(kernel), float(sigma), float(L), _ptr(tgt), int(T), _ptr(src), int(S),
+                                     _ptr(X), int(ldx), _ptr(Y), int(ldy), int(k), stream)
+    return _check(None, rc)
