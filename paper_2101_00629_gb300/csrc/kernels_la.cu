@@ -7,10 +7,13 @@
 //   gemm_nn    C = alpha A B + beta C for tall A and small B (basis updates).
 //   chol_rinv  Cholesky of a small SPD Gram matrix and the inverse of its
 //              transpose (CholQR), flagging collapsed pivots.
-//   sym_eig    cyclic Jacobi with a round-robin parallel ordering (one CTA).
 //   nonsym_eig Householder reduction to Hessenberg form, Francis double-shift
-//              QR to real Schur form with accumulated Schur vectors, and
-//              eigenvectors by back substitution (one CTA).
+//              QR to real Schur form with accumulated Schur vectors, ordering
+//              of the Schur form, and eigenvectors by back substitution (one
+//              warp: the bulge chase is a serial chain of small updates, so
+//              warp-level synchronisation is what keeps it fast).
+//   sym_eig    the same kernel for a symmetric matrix (ordered Schur vectors
+//              are its eigenvectors).
 #include <cfloat>
 #include <cmath>
 
@@ -24,8 +27,10 @@ namespace {
 constexpr int TN_T = 32;
 
 inline int tn_splits(int m, int n, int64_t K) {
+    // the long dimension is cut into chunks of >= 256 rows until about eight
+    // CTAs per SM exist (FP64 work is the limit: ~2 DFMA/clock/SM on GB300)
     const int tiles = ((m + TN_T - 1) / TN_T) * ((n + TN_T - 1) / TN_T);
-    int64_t s = (K + 1023) / 1024;
+    int64_t s = (K + 255) / 256;
     int64_t cap = (8 * 152) / tiles;
     if (cap < 1) cap = 1;
     if (s > cap) s = cap;
@@ -172,121 +177,6 @@ __global__ void __launch_bounds__(256) chol_rinv_kernel(double* G, int n, double
     }
 }
 
-// ------------------------------- sym_eig ----------------------------------
-// Round-robin ordering: player 0 fixed, players 1..m-1 rotate. In round r the
-// player at position j >= 1 is ((j - 1 + r) mod (m - 1)) + 1; position i is
-// paired with position m - 1 - i.
-__device__ inline int rr_player(int pos, int r, int m) {
-    return pos == 0 ? 0 : ((pos - 1 + r) % (m - 1)) + 1;
-}
-
-__global__ void __launch_bounds__(512) sym_eig_kernel(const double* __restrict__ H, int n,
-                                                      double* w, double* Vout, double* work,
-                                                      int* status, int use_smem) {
-    extern __shared__ double smem[];
-    double* A = use_smem ? smem : work + int64_t(n) * n;  // n x n
-    double* V = work;                                      // n x n
-    __shared__ double s_c[256], s_s[256];
-    __shared__ int s_p[256], s_q[256];
-    __shared__ double s_red[32];
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < n * n; e += nt) {
-        A[e] = 0.5 * (H[e] + H[(e % n) * n + e / n]);
-        V[e] = (e % n == e / n) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    const int m = n + (n & 1);
-    const int npairs = m / 2;
-    // Frobenius norm of H (invariant under the rotations) for the absolute
-    // part of the threshold
-    __shared__ double s_norm;
-    __shared__ int s_rot;
-    {
-        double f = 0.0;
-        for (int e = tid; e < n * n; e += nt) f += A[e] * A[e];
-        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
-        if ((tid & 31) == 0) s_red[tid >> 5] = f;
-        __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int i = 0; i < nt / 32; ++i) t += s_red[i];
-            s_norm = sqrt(t);
-        }
-        __syncthreads();
-    }
-    const double anorm = s_norm;
-    // threshold Jacobi: a rotation is skipped when the off-diagonal entry is
-    // negligible relative to its diagonal pair or to the matrix norm; the
-    // iteration stops after a sweep that applied no rotation
-    int sweep = 0;
-    for (; sweep < 60 && n > 1; ++sweep) {
-        if (tid == 0) s_rot = 0;
-        __syncthreads();
-        for (int r = 0; r < m - 1; ++r) {
-            for (int i = tid; i < npairs; i += nt) {
-                int p = rr_player(i, r, m), q = rr_player(m - 1 - i, r, m);
-                if (p > q) { const int t = p; p = q; q = t; }
-                double c = 1.0, s = 0.0;
-                if (q < n) {
-                    const double apq = A[p + q * n];
-                    const double app = A[p + p * n], aqq = A[q + q * n];
-                    if (fabs(apq) > 1e-15 * sqrt(fabs(app * aqq)) && fabs(apq) > 1e-17 * anorm) {
-                        const double tau = (aqq - app) / (2.0 * apq);
-                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                        c = 1.0 / sqrt(1.0 + t * t);
-                        s = t * c;
-                        atomicAdd(&s_rot, 1);
-                    }
-                }
-                s_p[i] = p;
-                s_q[i] = q;
-                s_c[i] = c;
-                s_s[i] = s;
-            }
-            __syncthreads();
-            // rows: row p <- c row p - s row q ; row q <- s row p + c row q
-            for (int e = tid; e < npairs * n; e += nt) {
-                const int i = e / n, j = e % n;
-                const int p = s_p[i], q = s_q[i];
-                if (q >= n || s_s[i] == 0.0) continue;
-                const double c = s_c[i], s = s_s[i];
-                const double ap = A[p + j * n], aq = A[q + j * n];
-                A[p + j * n] = c * ap - s * aq;
-                A[q + j * n] = s * ap + c * aq;
-            }
-            __syncthreads();
-            // columns of A and V
-            for (int e = tid; e < npairs * n; e += nt) {
-                const int i = e / n, j = e % n;
-                const int p = s_p[i], q = s_q[i];
-                if (q >= n || s_s[i] == 0.0) continue;
-                const double c = s_c[i], s = s_s[i];
-                const double ap = A[j + p * n], aq = A[j + q * n];
-                A[j + p * n] = c * ap - s * aq;
-                A[j + q * n] = s * ap + c * aq;
-                const double vp = V[j + p * n], vq = V[j + q * n];
-                V[j + p * n] = c * vp - s * vq;
-                V[j + q * n] = s * vp + c * vq;
-            }
-            __syncthreads();
-        }
-        if (s_rot == 0) break;
-        __syncthreads();
-    }
-    // sort eigenvalues descending (rank sort, ties broken by index)
-    for (int i = tid; i < n; i += nt) {
-        const double di = A[i + i * n];
-        int rank = 0;
-        for (int j = 0; j < n; ++j) {
-            const double dj = A[j + j * n];
-            if (dj > di || (dj == di && j < i)) ++rank;
-        }
-        w[rank] = di;
-        for (int r = 0; r < n; ++r) Vout[r + int64_t(rank) * n] = V[r + i * n];
-    }
-    if (tid == 0) *status = (sweep >= 60) ? 1 : 0;
-}
-
 // ------------------------------ nonsym_eig --------------------------------
 struct cplx {
     double re, im;
@@ -340,12 +230,16 @@ __device__ inline void house(const double* x, int len, double* v, double& beta) 
     beta = vv > 0.0 ? 2.0 / vv : 0.0;
 }
 
-__global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restrict__ H, int n,
-                                                         double* wr_out, double* wi_out,
-                                                         double* Vout, double* Qout, double* work,
-                                                         int* status) {
-    double* A = work;                        // n x n (Schur form)
-    double* Z = A + int64_t(n) * n;          // n x n (Schur vectors)
+__global__ void __launch_bounds__(32) nonsym_eig_kernel(const double* __restrict__ H, int n,
+                                                        double* wr_out, double* wi_out,
+                                                        double* Vout, double* Qout, double* work,
+                                                        int* status, int use_smem, int sym) {
+    extern __shared__ double smem_a[];
+    // the Schur form lives in shared memory when it fits: thread 0's serial
+    // scans (deflation, block search) then cost shared- not global-memory
+    // latency
+    double* A = use_smem ? smem_a : work;    // n x n (Schur form)
+    double* Z = work + int64_t(n) * n;       // n x n (Schur vectors), always global
     double* X = Z + int64_t(n) * n;          // n x n (eigenvectors of T, real/imag)
     double* wr = X + int64_t(n) * n;         // n
     double* wi = wr + n;                     // n
@@ -356,10 +250,10 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
     __shared__ double s_sh, s_th;
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int e = tid; e < n * n; e += nt) {
-        A[e] = H[e];
+        A[e] = sym ? 0.5 * (H[e] + H[(e % n) * n + e / n]) : H[e];
         Z[e] = (e % n == e / n) ? 1.0 : 0.0;
     }
-    __syncthreads();
+    __syncwarp();
     // ---- Hessenberg reduction ----
     for (int k = 0; k + 2 < n; ++k) {
         const int len = n - k - 1;
@@ -377,7 +271,7 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
             }
             s_beta = beta;
         }
-        __syncthreads();
+        __syncwarp();
         const double beta = s_beta;
         if (beta != 0.0) {
             // left: rows k+1..n-1, columns k..n-1
@@ -387,7 +281,7 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
                 s *= beta;
                 for (int t = 0; t < len; ++t) A[(k + 1 + t) + int64_t(j) * n] -= s * hv[t];
             }
-            __syncthreads();
+            __syncwarp();
             // right: all rows, columns k+1..n-1 ; and Z
             for (int i = tid; i < n; i += nt) {
                 double s = 0.0, sz = 0.0;
@@ -403,9 +297,9 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
                 }
             }
         }
-        __syncthreads();
+        __syncwarp();
         for (int i = k + 2 + tid; i < n; i += nt) A[i + int64_t(k) * n] = 0.0;
-        __syncthreads();
+        __syncwarp();
     }
     // ---- Francis double-shift QR to real Schur form ----
     double anorm = 0.0;
@@ -415,14 +309,14 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
         s_its = 0;
         s_fail = 0;
     }
-    __syncthreads();
+    __syncwarp();
     int total_its = 0;
     while (true) {
-        __syncthreads();
+        __syncwarp();
         if (tid == 0) {
             const int u = s_u;
             int l = 0;
-            int action = 0;  // 1: one root, 2: two roots, 3: Francis step, 4: done
+            int action = 0;  // 1: one root, 2: two roots, 3: Francis step, 4: done, 5: split
             if (u < 0) {
                 action = 4;
             } else {
@@ -458,6 +352,24 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
                 else if (l == u - 1) action = 2;
                 else action = 3;
             }
+            if (action == 3 && s_its >= 30 && s_its % 10 == 5) {
+                // A window that resists the shifts for 30 iterations is a
+                // cluster of (numerically) equal eigenvalues perturbed into a
+                // near-Jordan block. The window is already decoupled from its
+                // neighbours, so zeroing its smallest subdiagonal leaves every
+                // other eigenvalue and the window's invariant subspace as
+                // they are; it only splits the cluster (by about
+                // sqrt(|sub * super|)).
+                // Only a subdiagonal far below any tolerance of the outer
+                // solver is dropped (backward error 1e-10 * ||H||).
+                int m = l + 1;
+                for (int i = l + 2; i <= u; ++i)
+                    if (fabs(A[i + int64_t(i - 1) * n]) < fabs(A[m + int64_t(m - 1) * n])) m = i;
+                if (fabs(A[m + int64_t(m - 1) * n]) <= 1e-10 * anorm) {
+                    A[m + int64_t(m - 1) * n] = 0.0;
+                    action = 5;
+                }
+            }
             s_l = l;
             s_action = action;
             if (action == 3) {
@@ -483,10 +395,15 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
                 }
             }
         }
-        __syncthreads();
+        __syncwarp();
         const int action = s_action;
         const int u = s_u, l = s_l;
         if (action == 4) break;
+        if (action == 5) {
+            // a stalled window was split; look for deflations again
+            if (tid == 0) s_its = s_its + 1;
+            continue;
+        }
         if (action == 1) {
             if (tid == 0) {
                 wr[u] = A[u + int64_t(u) * n];
@@ -503,7 +420,10 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
             if (tid == 0) {
                 const double a = A[(u - 1) + int64_t(u - 1) * n], b = A[(u - 1) + int64_t(u) * n];
                 const double c = A[u + int64_t(u - 1) * n], d = A[u + int64_t(u) * n];
-                const double p = 0.5 * (a - d), q = p * p + b * c;
+                const double p = 0.5 * (a - d);
+                // a symmetric matrix has real eigenvalues: rounding may leave
+                // b c slightly negative, which must not create a complex pair
+                const double q = sym ? fmax(p * p + b * c, 0.0) : p * p + b * c;
                 s_rot = 0;
                 if (q >= 0.0) {
                     const double zz = p + (p >= 0.0 ? sqrt(q) : -sqrt(q));
@@ -522,7 +442,7 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
                     wi[u] = -sqrt(-q);
                 }
             }
-            __syncthreads();
+            __syncwarp();
             if (s_rot) {
                 const double cs = s_cs, sn = s_sn;
                 for (int j = u - 1 + tid; j < n; j += nt) {
@@ -530,7 +450,7 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
                     A[(u - 1) + int64_t(j) * n] = cs * x1 + sn * x2;
                     A[u + int64_t(j) * n] = -sn * x1 + cs * x2;
                 }
-                __syncthreads();
+                __syncwarp();
                 for (int i = tid; i < n; i += nt) {
                     if (i <= u) {
                         const double x1 = A[i + int64_t(u - 1) * n], x2 = A[i + int64_t(u) * n];
@@ -541,7 +461,7 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
                     Z[i + int64_t(u - 1) * n] = cs * z1 + sn * z2;
                     Z[i + int64_t(u) * n] = -sn * z1 + cs * z2;
                 }
-                __syncthreads();
+                __syncwarp();
                 if (tid == 0) {
                     A[u + int64_t(u - 1) * n] = 0.0;
                     // diagonal entries now hold the two real eigenvalues
@@ -549,7 +469,7 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
                     wr[u] = A[u + int64_t(u) * n];
                 }
             }
-            __syncthreads();
+            __syncwarp();
             if (tid == 0) {
                 s_u = u - 2;
                 s_its = 0;
@@ -568,7 +488,7 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
             s_x[1] = h21 * (h11 + h22 - s_sh);
             s_x[2] = h21 * h32;
         }
-        __syncthreads();
+        __syncwarp();
         for (int kk = 0; kk <= ns - 3; ++kk) {
             if (tid == 0) {
                 double v[3], beta;
@@ -578,21 +498,21 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
                 s_v[2] = v[2];
                 s_beta = beta;
             }
-            __syncthreads();
+            __syncwarp();
             const int r0 = l + kk;
             const int c0 = l + (kk > 0 ? kk - 1 : 0);
             refl_rows(A, n, r0, 3, c0, n, s_v, s_beta);
-            __syncthreads();
+            __syncwarp();
             const int rmax = min(l + kk + 3, u);  // last row touched (inclusive)
             refl_cols(A, n, r0, 3, 0, rmax + 1, s_v, s_beta);
             refl_cols(Z, n, r0, 3, 0, n, s_v, s_beta);
-            __syncthreads();
+            __syncwarp();
             if (tid == 0) {
                 s_x[0] = A[(r0 + 1) + int64_t(r0) * n];
                 s_x[1] = A[(r0 + 2) + int64_t(r0) * n];
                 s_x[2] = (kk < ns - 3) ? A[(r0 + 3) + int64_t(r0) * n] : 0.0;
             }
-            __syncthreads();
+            __syncwarp();
         }
         if (tid == 0) {
             double v[3], beta;
@@ -601,19 +521,19 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
             s_v[1] = v[1];
             s_beta = beta;
         }
-        __syncthreads();
+        __syncwarp();
         refl_rows(A, n, u - 1, 2, u - 2, n, s_v, s_beta);
-        __syncthreads();
+        __syncwarp();
         refl_cols(A, n, u - 1, 2, 0, u + 1, s_v, s_beta);
         refl_cols(Z, n, u - 1, 2, 0, n, s_v, s_beta);
-        __syncthreads();
+        __syncwarp();
         // clean the bulge remnants below the subdiagonal of the window
         for (int e = tid; e < ns * ns; e += nt) {
             const int i = l + e % ns, j = l + e / ns;
             if (i > j + 1) A[i + int64_t(j) * n] = 0.0;
         }
     }
-    __syncthreads();
+    __syncwarp();
     // ---- reorder the real Schur form: eigenvalues by decreasing real part ----
     // Selection sort over the diagonal blocks (1x1 real eigenvalues, 2x2
     // complex pairs). Adjacent blocks A (n1 x n1) and B (n2 x n2) with
@@ -625,8 +545,9 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
     __shared__ double s_q[16];
     __shared__ int s_k, s_m, s_n2, s_act, s_pos;
     if (tid == 0) s_pos = 0;
-    __syncthreads();
     while (!s_fail) {
+        // every lane has read the previous decision before lane 0 rewrites it
+        __syncwarp();
         if (tid == 0) {
             const int pos = s_pos;
             s_act = 0;
@@ -722,7 +643,7 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
                 }
             }
         }
-        __syncthreads();
+        __syncwarp();
         const int act = s_act;
         if (act == 0) break;
         if (act == 1) {
@@ -737,7 +658,7 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
                     A[(k + t) + int64_t(j) * n] = acc;
                 }
             }
-            __syncthreads();
+            __syncwarp();
             // columns k..k+m-1 <- columns Q (rows 0..k+m-1), and Z (all rows)
             for (int r = tid; r < n; r += nt) {
                 double old[4], oz[4];
@@ -755,14 +676,14 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
                     Z[r + int64_t(k + t) * n] = accz;
                 }
             }
-            __syncthreads();
+            __syncwarp();
             if (tid == 0) {
                 // the exchanged blocks: zero the new (2,1) block
                 const int n2 = s_n2;
                 for (int i = k + n2; i < k + m; ++i)
                     for (int j = k; j < k + n2; ++j) A[i + int64_t(j) * n] = 0.0;
             }
-            __syncthreads();
+            __syncwarp();
         }
     }
     // eigenvalues from the (re)ordered blocks
@@ -784,7 +705,7 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
             }
         }
     }
-    __syncthreads();
+    __syncwarp();
     // ---- eigenvectors of the quasi-triangular T by back substitution ----
     // Diagonal entries within 1e-10 ||T|| of the eigenvalue belong to its
     // cluster; their components are set to zero instead of dividing by a
@@ -792,7 +713,7 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
     // stay independent (its invariant subspace is spanned by Schur vectors).
     const double small = DBL_EPSILON * fmax(anorm, DBL_MIN);
     const double clus = 1e-10 * anorm;
-    for (int col = tid; col < n; col += nt) {
+    for (int col = tid; col < n && !sym; col += nt) {
         double* xr = X + int64_t(col) * n;
         if (wi[col] == 0.0) {
             const double lam = wr[col];
@@ -880,18 +801,19 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
         }
         // wi < 0: second member of a pair, written by its partner
     }
-    __syncthreads();
-    // V = Z X (each thread one row), then normalise columns (pairs jointly)
+    __syncwarp();
+    // V = Z X (each thread one row), then normalise columns (pairs jointly);
+    // the symmetric mode returns the ordered Schur vectors instead
     double* Vt = A;  // reuse (Schur form no longer needed)
-    for (int i = tid; i < n; i += nt) {
+    for (int i = tid; i < n && !sym; i += nt) {
         for (int c = 0; c < n; ++c) {
             double s = 0.0;
             for (int l2 = 0; l2 < n; ++l2) s += Z[i + int64_t(l2) * n] * X[l2 + int64_t(c) * n];
             Vt[i + int64_t(c) * n] = s;
         }
     }
-    __syncthreads();
-    for (int c = tid; c < n; c += nt) {
+    __syncwarp();
+    for (int c = tid; c < n && !sym; c += nt) {
         if (wi[c] < 0.0) continue;
         double s = 0.0;
         const int w2 = (wi[c] > 0.0) ? 2 : 1;
@@ -901,20 +823,28 @@ __global__ void __launch_bounds__(256) nonsym_eig_kernel(const double* __restric
         for (int t = 0; t < w2; ++t)
             for (int i = 0; i < n; ++i) Vt[i + int64_t(c + t) * n] *= s;
     }
-    __syncthreads();
+    __syncwarp();
     // sort by real part descending; a complex pair keeps its (+, -) order
     for (int i = tid; i < n; i += nt) {
         int rank = 0;
         for (int j = 0; j < n; ++j)
             if (wr[j] > wr[i] || (wr[j] == wr[i] && j < i)) ++rank;
         wr_out[rank] = wr[i];
-        wi_out[rank] = wi[i];
-        for (int r = 0; r < n; ++r) Vout[r + int64_t(rank) * n] = Vt[r + int64_t(i) * n];
+        if (wi_out) wi_out[rank] = wi[i];
+        if (Vout && !sym)
+            for (int r = 0; r < n; ++r) Vout[r + int64_t(rank) * n] = Vt[r + int64_t(i) * n];
     }
     if (Qout) {
         for (int e = tid; e < n * n; e += nt) Qout[e] = Z[e];
     }
-    if (tid == 0) *status = s_fail ? 1 : 0;
+    if (tid == 0) {
+        status[0] = s_fail ? 1 : 0;
+        // diagnostics after the status word: QR iterations, last window end,
+        // iterations spent on it
+        status[1] = total_its;
+        status[2] = s_u;
+        status[3] = s_its;
+    }
 }
 
 }  // namespace
@@ -953,17 +883,20 @@ cudaError_t launch_chol_rinv(double* G, int n, double* Rinv, int* bad, cudaStrea
     return cudaGetLastError();
 }
 
-int64_t sym_eig_work_doubles(int n) { return 2 * int64_t(n) * n; }
+int64_t sym_eig_work_doubles(int n) { return nonsym_eig_work_doubles(n); }
 
+// Symmetric eigenproblem: the same Hessenberg (here tridiagonal) reduction and
+// Francis QR; the ordered real Schur form of a symmetric matrix is diagonal,
+// so the ordered Schur vectors are orthonormal eigenvectors.
 cudaError_t launch_sym_eig(const double* H, int n, double* w, double* V, double* work, int* status,
                            cudaStream_t s) {
     const size_t smem = size_t(n) * n * sizeof(double);
     const int use_smem = smem <= 200 * 1024;
     if (use_smem) {
-        cudaError_t e = cudaFuncSetAttribute(sym_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        cudaError_t e = cudaFuncSetAttribute(nonsym_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
     }
-    sym_eig_kernel<<<1, 512, use_smem ? smem : 0, s>>>(H, n, w, V, work, status, use_smem);
+    nonsym_eig_kernel<<<1, 32, use_smem ? smem : 0, s>>>(H, n, w, nullptr, nullptr, V, work, status, use_smem, 1);
     return cudaGetLastError();
 }
 
@@ -971,7 +904,13 @@ int64_t nonsym_eig_work_doubles(int n) { return 3 * int64_t(n) * n + 3 * int64_t
 
 cudaError_t launch_nonsym_eig(const double* H, int n, double* wr, double* wi, double* V, double* Q,
                               double* work, int* status, cudaStream_t s) {
-    nonsym_eig_kernel<<<1, 256, 0, s>>>(H, n, wr, wi, V, Q, work, status);
+    const size_t smem = size_t(n) * n * sizeof(double);
+    const int use_smem = smem <= 200 * 1024;
+    if (use_smem) {
+        cudaError_t e = cudaFuncSetAttribute(nonsym_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+    }
+    nonsym_eig_kernel<<<1, 32, use_smem ? smem : 0, s>>>(H, n, wr, wi, V, Q, work, status, use_smem, 0);
     return cudaGetLastError();
 }
 

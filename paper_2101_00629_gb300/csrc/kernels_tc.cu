@@ -47,9 +47,9 @@ namespace kl {
 
 namespace {
 
-constexpr int kStages = 4;
+constexpr int kStages = 4;                // TMEM A-operand ring (kernel tiles)
 constexpr int kProducers = 256;           // two warpgroups
-constexpr int kThreads = kProducers + 32; // + MMA warp
+constexpr int kThreads = kProducers + 64; // + MMA warp + loader warp
 constexpr int kTmemCols = 256;
 constexpr int kDCols = 64;                // columns of one accumulator buffer (N <= 64)
 constexpr int kAColBase = 2 * kDCols;     // two accumulator buffers, then the A stages
@@ -206,6 +206,13 @@ float coord_scale(const KernelSpec& ks) {
     return float(ks.a * l2e);
 }
 
+// Depth of the shared-memory stage ring: as many stages as fit in ~100 KB
+// (two CTAs per SM), at most 16, at least the TMEM ring depth.
+__host__ __device__ constexpr int smem_stages(int stage_bytes) {
+    return (99 * 1024) / stage_bytes >= 16 ? 16
+         : ((99 * 1024) / stage_bytes < kStages ? kStages : (99 * 1024) / stage_bytes);
+}
+
 // Byte offset of element (n, kk) inside one hi or lo image of a chunk:
 // K steps of 32 bytes per row, each made of two 8x16-byte core matrices
 // along K; np/8 core matrices along N. esize = 2 (BF16) or 4 (TF32).
@@ -252,35 +259,74 @@ __global__ void tc_convert_kernel(const double* __restrict__ X, int64_t ldx, int
     }
 }
 
+// Bulk asynchronous copy global -> shared memory, completion counted in bytes
+// on an mbarrier (both addresses 16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Bounded wait by every lane of a warp, then a warp-uniform verdict.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity) {
+    const bool ok = mbar_wait(bar, parity);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Work unit u of the persistent schedule: target tile u / splits, source
+// chunk range [c0, c1) of split u % splits.
+struct Unit {
+    int64_t tile;
+    int split;
+    int64_t c0;
+    int nloc;
+};
+__device__ __forceinline__ Unit unit_of(int64_t u, int splits, int64_t nchunks, int cps) {
+    Unit r;
+    r.tile = u / splits;
+    r.split = int(u % splits);
+    r.c0 = int64_t(r.split) * cps;
+    const int64_t left = nchunks - r.c0;
+    r.nloc = int(left < cps ? left : int64_t(cps));
+    return r;
+}
+
 template <int KIND, bool TF32, int NP>
 __global__ void __launch_bounds__(kThreads, 2)
 pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const float* __restrict__ tz,
                int64_t T, const float4* __restrict__ src4, const uint8_t* __restrict__ img,
-               int64_t nchunks, int chunks_per_split, float cscale, double* __restrict__ part,
-               int k_total, int c0, int kc, int* __restrict__ err) {
+               int64_t nchunks, int cps, int splits, int64_t nunits, float cscale,
+               double* __restrict__ part, int k_total, int c0, int kc, int* __restrict__ err) {
     constexpr int ESIZE = TF32 ? 4 : 2;
     constexpr int KC = TF32 ? 16 : 32;                  // sources per chunk (16 TMEM columns)
     constexpr int IMG = NP * KC * ESIZE;                // bytes of one of hi / lo
     constexpr int STAGE_BYTES = 2 * IMG + KC * 16;      // hi, lo, coordinates
+    constexpr int SSTAGES = smem_stages(STAGE_BYTES);   // shared-memory ring (>= kStages)
     constexpr uint32_t IDESC = instr_desc(NP, TF32);
 
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ uint64_t full_bar[kStages], empty_bar[kStages], dfull_bar[2], dfree_bar[2], drain_bar;
+    // loaded/sempty: shared-memory ring (bulk copies ahead of use);
+    // full/tfree: TMEM ring of kernel tiles; dfull/dfree: accumulators
+    __shared__ uint64_t loaded_bar[SSTAGES], sempty_bar[SSTAGES], full_bar[kStages], tfree_bar[kStages];
+    __shared__ uint64_t dfull_bar[2], dfree_bar[2], drain_bar;
     __shared__ uint32_t tmem_slot;
-    __shared__ int s_ok[2], s_flush_ok;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int64_t tile = blockIdx.x;
-    const int split = blockIdx.y;
-    const int64_t ch0 = int64_t(split) * chunks_per_split;
-    const int nloc = int(nchunks - ch0 < chunks_per_split ? nchunks - ch0 : int64_t(chunks_per_split));
-    const int ngroups = (nloc + kGroup - 1) / kGroup;
 
     if (tid == 0) {
+        for (int s = 0; s < SSTAGES; ++s) {
+            mbar_init(&loaded_bar[s], 1);
+            mbar_init(&sempty_bar[s], 1);
+        }
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full_bar[s], 128);
-            mbar_init(&empty_bar[s], 1);
+            mbar_init(&tfree_bar[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&dfull_bar[b], 1);
@@ -301,134 +347,162 @@ pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const
     const uint32_t tmem = tmem_slot;
 
     if (warp < 8) {
-        // ---------------- producers ----------------
-        const int wg = warp >> 2;            // warpgroup 0 / 1
-        const int ptid = tid & 127;          // thread within the warpgroup
-        const int row = ptid;                // TMEM lane = target within the tile
-        const int64_t t = tile * 128 + row;
-        const float px = t < T ? cscale * tx[t] : 0.f;
-        const float py = t < T ? cscale * ty[t] : 0.f;
-        const float pz = t < T ? cscale * tz[t] : 0.f;
+        // ---------------- producers (two warpgroups, alternate chunks) ----------------
+        const int wg = warp >> 2;
+        const int ptid = tid & 127;
         const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
-        double* prow = part + (int64_t(split) * k_total + c0) * T + t;  // column c at prow[c * T]
-        bool ok = true;  // uniform within the warpgroup
-        int flushed = 0; // groups already flushed (warpgroup 0)
-
-        // warpgroup 0: add accumulator buffer of group g into the FP64 partials
-        auto flush = [&](int g) {
-            if (ptid == 0) s_flush_ok = (ok && mbar_wait(&dfull_bar[g & 1], uint32_t((g >> 1) & 1))) ? 1 : 0;
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            const bool got = s_flush_ok != 0;
-            if (!got) ok = false;
-            tc_fence_after();
-            uint32_t v[16];
-            const uint32_t dcol = uint32_t((g & 1) * kDCols);
+        bool ok = true;
+        int64_t jbase = 0;   // chunks of earlier units (stage ring position)
+        int64_t gbase = 0;   // accumulator groups of earlier units
+        for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+            const Unit un = unit_of(u, splits, nchunks, cps);
+            const int64_t t = un.tile * 128 + ptid;
+            const float px = t < T ? cscale * tx[t] : 0.f;
+            const float py = t < T ? cscale * ty[t] : 0.f;
+            const float pz = t < T ? cscale * tz[t] : 0.f;
+            double* prow = part + (int64_t(un.split) * k_total + c0) * T + t;
+            const int ngroups = (un.nloc + kGroup - 1) / kGroup;
+            int flushed = 0;
+            // warpgroup 0 adds the finished accumulator of local group g into
+            // this unit's FP64 partial sums (rows owned by this thread)
+            auto flush = [&](int g) {
+                const int64_t gg = gbase + g;
+                const bool got = ok && warp_wait(&dfull_bar[gg & 1], uint32_t((gg >> 1) & 1));
+                if (!got) ok = false;
+                tc_fence_after();
+                uint32_t v[16];
+                const uint32_t dcol = uint32_t((gg & 1) * kDCols);
 #pragma unroll 1
-            for (int cb = 0; cb < NP; cb += 16) {
-                __syncwarp();
-                tmem_ld16(tmem + lane_base + dcol + uint32_t(cb), v);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (got && t < T) {
-#pragma unroll 4
-                    for (int q = 0; q < 16; ++q) {
-                        const int c = cb + q;
-                        if (c < kc) {
-                            const double x = double(__uint_as_float(v[q]));
-                            prow[int64_t(c) * T] = (g == 0) ? x : prow[int64_t(c) * T] + x;
+                for (int cb = 0; cb < NP; cb += 16) {
+                    __syncwarp();
+                    tmem_ld16(tmem + lane_base + dcol + uint32_t(cb), v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (got && t < T) {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const int c = cb + q;
+                            if (c < kc) {
+                                const double x = double(__uint_as_float(v[q]));
+                                prow[int64_t(c) * T] = (g == 0) ? x : prow[int64_t(c) * T] + x;
+                            }
                         }
                     }
                 }
-            }
-            tc_fence_before();
-            mbar_arrive(&dfree_bar[g & 1]);
-        };
-
-        for (int j = wg; j < nloc; j += 2) {
-            const int s = j % kStages;
-            const int use = j / kStages;
-            // warpgroup 0 flushes every group older than the one it now fills
-            if (wg == 0) {
-                while (flushed < j / kGroup) flush(flushed++);
-                if (!ok) break;
-            }
-            // one thread waits (bounded) for the stage, the warpgroup follows
-            if (ptid == 0) s_ok[wg] = (use == 0 || mbar_wait(&empty_bar[s], uint32_t((use - 1) & 1))) ? 1 : 0;
-            asm volatile("bar.sync %0, 128;" ::"r"(1 + wg) : "memory");
-            if (!s_ok[wg]) { ok = false; break; }
-            uint8_t* st = smem + s * STAGE_BYTES;
-            // copy the chunk's split image and coordinates into the stage
-            const uint4* gsrc = reinterpret_cast<const uint4*>(img + (ch0 + j) * int64_t(2 * IMG));
-            uint4* sdst = reinterpret_cast<uint4*>(st);
-            for (int e = ptid; e < (2 * IMG) / 16; e += 128) sdst[e] = gsrc[e];
-            float4* sc = reinterpret_cast<float4*>(st + 2 * IMG);
-            if (ptid < KC) sc[ptid] = src4[(ch0 + j) * KC + ptid];
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("bar.sync %0, 128;" ::"r"(1 + wg) : "memory");
-            // kernel tile row for this target, split into hi / lo, written to
-            // tensor memory in two halves of 8 columns each
-            const uint32_t acol = uint32_t(kAColBase + s * kAColsPerStage);
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                uint32_t hi[8], lo[8];
-                if (TF32) {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float4 y = sc[8 * half + q];
-                        split_tf32(gamma_scaled<KIND>(px - y.x, py - y.y, pz - y.z), hi[q], lo[q]);
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float4 y0 = sc[16 * half + 2 * q], y1 = sc[16 * half + 2 * q + 1];
-                        split_bf16(gamma_scaled<KIND>(px - y0.x, py - y0.y, pz - y0.z),
-                                   gamma_scaled<KIND>(px - y1.x, py - y1.y, pz - y1.z), hi[q], lo[q]);
-                    }
+                tc_fence_before();
+                mbar_arrive(&dfree_bar[gg & 1]);
+            };
+            for (int jl = wg; jl < un.nloc; jl += 2) {
+                if (wg == 0) {
+                    while (ok && flushed < jl / kGroup) flush(flushed++);
+                    if (!ok) break;
                 }
-                __syncwarp();
-                tmem_st8(tmem + lane_base + acol + uint32_t(8 * half), hi);
-                tmem_st8(tmem + lane_base + acol + 16u + uint32_t(8 * half), lo);
+                const int64_t jg = jbase + jl;
+                const int ss = int(jg % SSTAGES), s = int(jg % kStages);
+                if (!warp_wait(&loaded_bar[ss], uint32_t((jg / SSTAGES) & 1))) { ok = false; break; }
+                if (jg >= kStages && !warp_wait(&tfree_bar[s], uint32_t(((jg / kStages) - 1) & 1))) { ok = false; break; }
+                const float4* sc = reinterpret_cast<const float4*>(smem + ss * STAGE_BYTES + 2 * IMG);
+                const uint32_t acol = uint32_t(kAColBase + s * kAColsPerStage);
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    uint32_t hi[8], lo[8];
+                    if (TF32) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const float4 y = sc[8 * half + q];
+                            split_tf32(gamma_scaled<KIND>(px - y.x, py - y.y, pz - y.z), hi[q], lo[q]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const float4 y0 = sc[16 * half + 2 * q], y1 = sc[16 * half + 2 * q + 1];
+                            split_bf16(gamma_scaled<KIND>(px - y0.x, py - y0.y, pz - y0.z),
+                                       gamma_scaled<KIND>(px - y1.x, py - y1.y, pz - y1.z), hi[q], lo[q]);
+                        }
+                    }
+                    __syncwarp();
+                    tmem_st8(tmem + lane_base + acol + uint32_t(8 * half), hi);
+                    tmem_st8(tmem + lane_base + acol + 16u + uint32_t(8 * half), lo);
+                }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                tc_fence_before();
+                mbar_arrive(&full_bar[s]);
             }
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-            tc_fence_before();
-            mbar_arrive(&full_bar[s]);
+            if (wg == 0) {
+                while (ok && flushed < ngroups) flush(flushed++);
+            }
+            jbase += un.nloc;
+            gbase += ngroups;
         }
-        if (wg == 0) {
-            while (ok && flushed < ngroups) flush(flushed++);
-        }
-        if (!ok && ptid == 0) atomicExch(err, 1);
+        if (!ok && lane == 0) atomicExch(err, 1);
     } else if (warp == 8) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             bool ok = true;
-            for (int j = 0; j < nloc; ++j) {
-                const int s = j % kStages;
-                const int use = j / kStages;
-                const int g = j / kGroup;
-                const bool first = (j % kGroup) == 0;
-                const uint32_t d_tmem = tmem + uint32_t((g & 1) * kDCols);
-                if (first && g >= 2 && !mbar_wait(&dfree_bar[g & 1], uint32_t(((g >> 1) - 1) & 1))) { ok = false; break; }
-                if (!mbar_wait(&full_bar[s], uint32_t(use & 1))) { ok = false; break; }
-                tc_fence_after();
-                const uint32_t st = smem_u32(smem + s * STAGE_BYTES);
-                const uint32_t acol = tmem + uint32_t(kAColBase + s * kAColsPerStage);
+            int64_t jbase = 0, gbase = 0;
+            for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+                const Unit un = unit_of(u, splits, nchunks, cps);
+                for (int jl = 0; jl < un.nloc; ++jl) {
+                    const int64_t jg = jbase + jl;
+                    const int s = int(jg % kStages), ss = int(jg % SSTAGES);
+                    const int64_t gg = gbase + jl / kGroup;
+                    const bool first = (jl % kGroup) == 0;
+                    const uint32_t d_tmem = tmem + uint32_t((gg & 1) * kDCols);
+                    if (first && gg >= 2 && !mbar_wait(&dfree_bar[gg & 1], uint32_t(((gg >> 1) - 1) & 1))) { ok = false; break; }
+                    if (!mbar_wait(&full_bar[s], uint32_t((jg / kStages) & 1))) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t st = smem_u32(smem + ss * STAGE_BYTES);
+                    const uint32_t acol = tmem + uint32_t(kAColBase + s * kAColsPerStage);
 #pragma unroll
-                for (int ks = 0; ks < 2; ++ks) {
-                    const uint32_t step = uint32_t(ks * 2 * (NP / 8) * 128);
-                    const uint64_t bh = smem_desc(st + step, (NP / 8) * 128, 128);
-                    const uint64_t bl = smem_desc(st + IMG + step, (NP / 8) * 128, 128);
-                    const uint32_t ah = acol + uint32_t(ks * 8), al = acol + 16u + uint32_t(ks * 8);
-                    mma_tmemA(TF32, d_tmem, ah, bh, IDESC, (first && ks == 0) ? 0u : 1u);
-                    mma_tmemA(TF32, d_tmem, ah, bl, IDESC, 1u);
-                    mma_tmemA(TF32, d_tmem, al, bh, IDESC, 1u);
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint32_t step = uint32_t(ks * 2 * (NP / 8) * 128);
+                        const uint64_t bh = smem_desc(st + step, (NP / 8) * 128, 128);
+                        const uint64_t bl = smem_desc(st + IMG + step, (NP / 8) * 128, 128);
+                        const uint32_t ah = acol + uint32_t(ks * 8), al = acol + 16u + uint32_t(ks * 8);
+                        mma_tmemA(TF32, d_tmem, ah, bh, IDESC, (first && ks == 0) ? 0u : 1u);
+                        mma_tmemA(TF32, d_tmem, ah, bl, IDESC, 1u);
+                        mma_tmemA(TF32, d_tmem, al, bh, IDESC, 1u);
+                    }
+                    mma_commit(&sempty_bar[ss]);
+                    mma_commit(&tfree_bar[s]);
+                    if ((jl % kGroup) == kGroup - 1 || jl == un.nloc - 1) mma_commit(&dfull_bar[gg & 1]);
                 }
-                mma_commit(&empty_bar[s]);
-                if ((j % kGroup) == kGroup - 1 || j == nloc - 1) mma_commit(&dfull_bar[g & 1]);
+                jbase += un.nloc;
+                gbase += (un.nloc + kGroup - 1) / kGroup;
             }
             if (!ok) {
                 atomicExch(err, 1);
                 mma_commit(&drain_bar);
                 mbar_wait(&drain_bar, 0);  // bounded: MMAs already issued finish
             }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- loader: stage images and coordinates ahead ----------------
+        if (lane == 0) {
+            bool ok = true;
+            int64_t jbase = 0, issued = 0;
+            for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+                const Unit un = unit_of(u, splits, nchunks, cps);
+                for (int jl = 0; jl < un.nloc; ++jl) {
+                    const int64_t jg = jbase + jl;
+                    const int ss = int(jg % SSTAGES);
+                    const int64_t use = jg / SSTAGES;
+                    if (use > 0 && !mbar_wait(&sempty_bar[ss], uint32_t((use - 1) & 1))) { ok = false; break; }
+                    issued = jg + 1;
+                    uint8_t* st = smem + ss * STAGE_BYTES;
+                    const int64_t ch = un.c0 + jl;
+                    mbar_arrive_expect_tx(&loaded_bar[ss], uint32_t(STAGE_BYTES));
+                    bulk_g2s(st, img + ch * int64_t(2 * IMG), uint32_t(2 * IMG), &loaded_bar[ss]);
+                    bulk_g2s(st + 2 * IMG, src4 + ch * KC, uint32_t(KC * 16), &loaded_bar[ss]);
+                }
+                jbase += un.nloc;
+            }
+            if (!ok) atomicExch(err, 1);
+            // every copy issued here lands before the CTA exits: wait for the
+            // last use of each stage (already complete unless an error cut
+            // the pipeline short; bounded in any case)
+            for (int64_t jg = issued - 1; jg >= 0 && jg >= issued - SSTAGES; --jg)
+                mbar_wait(&loaded_bar[jg % SSTAGES], uint32_t((jg / SSTAGES) & 1));
         }
         __syncwarp();
     }
@@ -448,13 +522,15 @@ cudaError_t launch_np(const TcArgs& a, int c0, int kc, const float4* src4, const
     constexpr int STAGE_BYTES = 2 * NP * KC * ESIZE + KC * 16;
     // at least ~100 KB so that no more than two CTAs share an SM (256 TMEM
     // columns each)
-    const int smem = std::max(kStages * STAGE_BYTES + 1024, 100 * 1024);
+    const int smem = std::max(smem_stages(STAGE_BYTES) * STAGE_BYTES + 1024, 100 * 1024);
     auto kern = pair_tc_kernel<KIND, TF32, NP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    dim3 grid(unsigned((a.T + 127) / 128), unsigned(splits));
-    kern<<<grid, kThreads, smem, s>>>(a.tx, a.ty, a.tz, a.T, src4, img, nchunks, cps, coord_scale(a.ks), part,
-                                      a.k, c0, kc, err);
+    const int64_t tiles = (a.T + 127) / 128;
+    const int64_t nunits = tiles * splits;
+    const int64_t grid = std::min<int64_t>(nunits, 2LL * a.sm_count);
+    kern<<<unsigned(grid), kThreads, smem, s>>>(a.tx, a.ty, a.tz, a.T, src4, img, nchunks, cps, splits, nunits,
+                                                coord_scale(a.ks), part, a.k, c0, kc, err);
     return cudaGetLastError();
 }
 
@@ -489,6 +565,10 @@ struct TcPlan {
     int64_t img_doubles, src_doubles, part_doubles;
 };
 
+// Persistent schedule: 2 CTAs per SM walk the units (tile, source range)
+// round-robin. Splitting every tile's sources into `splits` ranges of equal
+// length gives about 16 units per CTA (load imbalance <= 1/16) while keeping
+// ranges >= 24 chunks long and the FP64 partial sums <= 64 MiB.
 TcPlan plan(int64_t T, int64_t S, int k, int sm_count, bool tf32) {
     TcPlan p;
     p.kchunk = tf32 ? 16 : 32;
@@ -496,9 +576,11 @@ TcPlan plan(int64_t T, int64_t S, int k, int sm_count, bool tf32) {
     const int kmax = std::min(k, 64);
     p.np_max = std::max(16, (kmax + 15) / 16 * 16);
     const int64_t tiles = (T + 127) / 128;
-    int64_t want = (4LL * sm_count + tiles - 1) / tiles;
-    int64_t cap = std::max<int64_t>(1, p.nchunks / 8);
-    want = std::max<int64_t>(1, std::min(want, cap));
+    const int64_t grid = 2LL * sm_count;
+    int64_t want = (16 * grid + tiles - 1) / tiles;
+    want = std::min(want, std::max<int64_t>(1, p.nchunks / 24));
+    want = std::min(want, std::max<int64_t>(1, (int64_t(8) << 20) / (int64_t(k) * T)));
+    want = std::max<int64_t>(1, want);
     p.cps = int((p.nchunks + want - 1) / want);
     p.splits = int((p.nchunks + p.cps - 1) / p.cps);
     const int esize = tf32 ? 4 : 2;

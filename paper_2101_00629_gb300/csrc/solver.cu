@@ -26,7 +26,10 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "handle.h"
@@ -38,7 +41,7 @@ struct EigWs {
     double *V, *AV, *T1, *T2;   // N x mmax each
     double *H, *S, *G, *Rinv;   // mmax^2 each
     double* Q;                  // ordered Schur vectors (non-symmetric), mmax^2
-    double *theta, *thetai, *norms, *norms2;  // mmax each
+    double *theta, *thetai, *norms, *norms2;  // mmax each (norms: 2 mmax)
     double* la_work;            // eigensolver work
     double* tn_scratch;         // gemm_tn partials
     int64_t tn_len;
@@ -101,46 +104,32 @@ int project_out(Ctx& c, const double* V, int nv, double* W, int bw) {
 // collapse (W nearly in span(V) or linearly dependent) are replaced by random
 // vectors and the procedure repeats.
 int orthonormalize(Ctx& c, const double* V, int nv, double* W, int bw) {
-    std::vector<double> before(bw), after(bw);
+    std::vector<double> norms(2 * bw);
     std::vector<int> bad(bw);
     for (int attempt = 0; attempt < 6; ++attempt) {
+        // column norms before and after two Gram-Schmidt passes (one sync)
         KL_TRY(ck(c, launch_col_norms(W, c.N, c.N, bw, c.w.norms, c.h->stream), "norms"));
         KL_TRY(project_out(c, V, nv, W, bw));
-        KL_TRY(ck(c, launch_col_norms(W, c.N, c.N, bw, c.w.norms2, c.h->stream), "norms"));
-        KL_TRY(sync_copy(c, before.data(), c.w.norms, bw * sizeof(double)));
-        KL_TRY(sync_copy(c, after.data(), c.w.norms2, bw * sizeof(double)));
+        KL_TRY(ck(c, launch_col_norms(W, c.N, c.N, bw, c.w.norms + bw, c.h->stream), "norms"));
+        KL_TRY(sync_copy(c, norms.data(), c.w.norms, 2 * bw * sizeof(double)));
         bool any = false;
         for (int j = 0; j < bw; ++j) {
-            bad[j] = !(after[j] > 1e-10 * before[j]) || !(after[j] > 1e-290) || !std::isfinite(after[j]);
+            const double before = norms[j], after = norms[bw + j];
+            bad[j] = !(after > 1e-10 * before) || !(after > 1e-290) || !std::isfinite(after);
             any |= bad[j] != 0;
         }
-        if (!any) {
-            // CholQR twice
-            for (int pass = 0; pass < 2 && !any; ++pass) {
-                KL_TRY(tn(c, W, c.N, W, c.N, c.w.G, bw, bw, bw));
-                KL_TRY(ck(c, launch_chol_rinv(c.w.G, bw, c.w.Rinv, c.w.ibuf, c.h->stream), "chol"));
-                KL_TRY(sync_copy(c, bad.data(), c.w.ibuf, bw * sizeof(int)));
-                for (int j = 0; j < bw; ++j) any |= bad[j] != 0;
-                if (any) break;
-                KL_TRY(nn(c, W, c.N, c.w.Rinv, bw, c.w.T2, c.N, bw, bw, 1.0, 0.0));
-                KL_TRY(ck(c, launch_copy_block(c.w.T2, c.N, W, c.N, c.N, bw, c.h->stream), "copy"));
-            }
-            if (!any) {
-                // final projection pass keeps W orthogonal to V after CholQR
-                if (nv > 0) {
-                    KL_TRY(project_out(c, V, nv, W, bw));
-                    KL_TRY(tn(c, W, c.N, W, c.N, c.w.G, bw, bw, bw));
-                    KL_TRY(ck(c, launch_chol_rinv(c.w.G, bw, c.w.Rinv, c.w.ibuf, c.h->stream), "chol"));
-                    KL_TRY(sync_copy(c, bad.data(), c.w.ibuf, bw * sizeof(int)));
-                    for (int j = 0; j < bw; ++j) any |= bad[j] != 0;
-                    if (!any) {
-                        KL_TRY(nn(c, W, c.N, c.w.Rinv, bw, c.w.T2, c.N, bw, bw, 1.0, 0.0));
-                        KL_TRY(ck(c, launch_copy_block(c.w.T2, c.N, W, c.N, c.N, bw, c.h->stream), "copy"));
-                    }
-                }
-                if (!any) return KL_OK;
-            }
+        // CholQR twice; W R^-1 stays orthogonal to V because it only mixes
+        // columns of W
+        for (int pass = 0; pass < 2 && !any; ++pass) {
+            KL_TRY(tn(c, W, c.N, W, c.N, c.w.G, bw, bw, bw));
+            KL_TRY(ck(c, launch_chol_rinv(c.w.G, bw, c.w.Rinv, c.w.ibuf, c.h->stream), "chol"));
+            KL_TRY(sync_copy(c, bad.data(), c.w.ibuf, bw * sizeof(int)));
+            for (int j = 0; j < bw; ++j) any |= bad[j] != 0;
+            if (any) break;
+            KL_TRY(nn(c, W, c.N, c.w.Rinv, bw, c.w.T2, c.N, bw, bw, 1.0, 0.0));
+            KL_TRY(ck(c, launch_copy_block(c.w.T2, c.N, W, c.N, c.N, bw, c.h->stream), "copy"));
         }
+        if (!any) return KL_OK;
         for (int j = 0; j < bw; ++j) {
             if (!bad[j]) continue;
             KL_TRY(ck(c, launch_randn(W + int64_t(j) * c.N, c.N, c.N, 1, c.h->prm.seed ^ 0x5bd1e995ull,
@@ -173,7 +162,20 @@ int rayleigh_ritz(Ctx& c, const double* V, const double* AV, int nv, double* max
         c.schur_ok = status == 0;
         if (status == 2) status = 0;  // complex pairs: eigenvectors valid, Schur order not
     }
-    if (status != 0) return fail(c.h, KL_ERR_NUMERIC, "small eigensolver did not converge");
+    if (status != 0) {
+        // diagnostics: with KL_DUMP_DIR set, keep the matrix that failed
+        if (const char* dir = std::getenv("KL_DUMP_DIR")) {
+            std::vector<double> Hh(size_t(nv) * nv);
+            if (cudaMemcpy(Hh.data(), c.w.H, Hh.size() * sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess) {
+                const std::string path = std::string(dir) + "/kl_rr_failed_" + std::to_string(nv) + ".f64";
+                if (FILE* f = std::fopen(path.c_str(), "wb")) {
+                    std::fwrite(Hh.data(), sizeof(double), Hh.size(), f);
+                    std::fclose(f);
+                }
+            }
+        }
+        return fail(c.h, KL_ERR_NUMERIC, "small eigensolver did not converge");
+    }
     return KL_OK;
 }
 
@@ -190,7 +192,11 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
     if (M < 1 || M > 512 || M > h->N) return fail(h, KL_ERR_ARG, "M must be in 1..min(N, 512)");
     if (Vout && ldv < h->N) return fail(h, KL_ERR_ARG, "ldv must be >= N");
     const int prec = h->prm.precision;
-    if (!(tol > 0)) tol = (prec == KL_FP64) ? 1e-10 : 1e-6;
+    // Default tolerances: the eigenvalue error of the symmetric Galerkin form
+    // is quadratic in the residual, that of the non-symmetric collocation form
+    // only linear, hence the tighter FP64 default there.
+    if (!(tol > 0))
+        tol = (prec == KL_FP64) ? (h->prm.method == KL_GALERKIN_IBQ ? 1e-10 : 1e-12) : 1e-6;
 
     Ctx c;
     c.h = h;
@@ -214,7 +220,7 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
     // ---- workspace (one allocation, reused across calls) ----
     const int64_t tn_len = std::max(gemm_tn_scratch_doubles(mcap, mcap, N), int64_t(1));
     const int64_t la = std::max(sym_eig_work_doubles(mcap), nonsym_eig_work_doubles(mcap));
-    const int64_t need = 4 * N * mcap + 5 * int64_t(mcap) * mcap + 4 * int64_t(mcap) + la + tn_len +
+    const int64_t need = 4 * N * mcap + 5 * int64_t(mcap) * mcap + 8 * int64_t(mcap) + la + tn_len +
                          (int64_t(mcap) + 2) / 2 + 64;
     if (need * int64_t(sizeof(double)) > h->eig_cap_bytes) {
         cudaStreamSynchronize(h->stream);
@@ -245,7 +251,7 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
     c.w.Q = take(int64_t(mcap) * mcap);
     c.w.theta = take(mcap);
     c.w.thetai = take(mcap);
-    c.w.norms = take(mcap);
+    c.w.norms = take(2 * int64_t(mcap));
     c.w.norms2 = take(mcap);
     c.w.la_work = take(la);
     c.w.tn_scratch = take(tn_len);
