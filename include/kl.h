@@ -56,8 +56,9 @@ typedef enum {
     KL_ERR_NUMERIC = -5,      /* NaN/Inf met, or a factorisation broke down    */
     KL_ERR_TIMEOUT = -6,      /* a bounded device wait gave up                 */
     KL_ERR_UNSUPPORTED = -7,  /* feature not available on this device/build    */
-    KL_WARN_COMPLEX = 1       /* collocation: a returned pair had a non-zero
-                                 imaginary part (real parts are returned)      */
+    KL_WARN_COMPLEX = 1       /* collocation: a returned pair had an imaginary
+                                 part above max(1e-8, tol) |lambda_1| (real
+                                 parts are returned)                           */
 } kl_status;
 
 enum { KL_GEOM_CUBE = 0, KL_GEOM_QUARTER_ANNULUS = 1 };

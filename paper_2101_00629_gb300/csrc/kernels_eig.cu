@@ -1,0 +1,888 @@
+// Small dense FP64 eigenproblems of the Rayleigh-Ritz step (Sec. 3: the
+// standard form A' v' = lambda v' is solved by an iterative projection
+// method, whose projected matrix H = V^T A' V is decomposed here).
+//
+// One CTA of four warps per matrix: Householder reduction to Hessenberg form,
+// Francis double-shift QR to real Schur form with accumulated Schur vectors,
+// ordering of the Schur form by decreasing real part, and eigenvectors of the
+// leading columns by back substitution.
+//
+// GB300 has a small FP64 unit: one warp-wide FP64 instruction issues every
+// 64 cycles per SM sub-partition, and a dependent FP64 FMA waits 63 cycles
+// (square root and division take about 650). The kernel is therefore laid
+// out so that every FP64 operation that can run in parallel does (four warps
+// on the four sub-partitions, reductions by shuffles, deflation and ordering
+// decisions evaluated by all threads at once) and only the Householder vector
+// of the bulge chase is a one-thread chain.
+#include <cfloat>
+#include <cmath>
+
+#include "kl_internal.h"
+
+namespace kl {
+
+namespace {
+
+constexpr int kEigThreads = 128;
+constexpr int kEigWarps = kEigThreads / 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct cplx {
+    double re, im;
+};
+__device__ inline cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ inline cplx cdiv(cplx a, cplx b) {
+    // Smith's algorithm
+    if (fabs(b.re) >= fabs(b.im)) {
+        const double r = b.im / b.re, d = b.re + b.im * r;
+        return {(a.re + a.im * r) / d, (a.im - a.re * r) / d};
+    }
+    const double r = b.re / b.im, d = b.re * r + b.im;
+    return {(a.re * r + a.im) / d, (a.im * r - a.re) / d};
+}
+
+__device__ inline double blk_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < kEigWarps; ++w) s += red[w];
+    __syncthreads();
+    return s;
+}
+__device__ inline double blk_max(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = red[0];
+    for (int w = 1; w < kEigWarps; ++w) s = fmax(s, red[w]);
+    __syncthreads();
+    return s;
+}
+__device__ inline int blk_max_int(int v, int* red) {
+    v = __reduce_max_sync(kFull, v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int s = red[0];
+    for (int w = 1; w < kEigWarps; ++w) s = max(s, red[w]);
+    __syncthreads();
+    return s;
+}
+
+// Householder vector for x (len 2 or 3): (I - beta v v^T) x = -sign(x0)|x| e1.
+// v^T v = 2 |x| (|x| + |x0|), so beta needs one division and no second sum.
+__device__ inline void house(const double* x, int len, double* v, double& beta) {
+    double ss = x[0] * x[0];
+    for (int t = 1; t < len; ++t) ss = fma(x[t], x[t], ss);
+    for (int t = 0; t < len; ++t) v[t] = x[t];
+    if (ss == 0.0) {
+        beta = 0.0;
+        return;
+    }
+    const double nrm = sqrt(ss);
+    v[0] += (x[0] >= 0.0 ? nrm : -nrm);
+    beta = 1.0 / (nrm * (nrm + fabs(x[0])));
+}
+
+// Deflation test for the subdiagonal entry (l, l-1).
+__device__ inline bool deflatable(const double* A, int n, int l, double anorm) {
+    double s = fabs(A[(l - 1) + int64_t(l - 1) * n]) + fabs(A[l + int64_t(l) * n]);
+    if (s == 0.0) s = anorm;
+    const double sub = fabs(A[l + int64_t(l - 1) * n]);
+    // absolute test at roundoff of the whole matrix: next to eigenvalues that
+    // are themselves at roundoff level a relative test can never be met
+    if (sub <= double(n) * DBL_EPSILON * anorm) return true;
+    // relative test, confirmed by the more conservative Ahues-Kressner
+    // criterion (off-diagonal product against the gap of the diagonal pair)
+    if (sub <= DBL_EPSILON * s) {
+        const double up = fabs(A[(l - 1) + int64_t(l) * n]);
+        const double ab = fmax(sub, up), ba = fmin(sub, up);
+        const double dd = fabs(A[(l - 1) + int64_t(l - 1) * n] - A[l + int64_t(l) * n]);
+        const double aa = fmax(fabs(A[l + int64_t(l) * n]), dd);
+        const double bb = fmin(fabs(A[l + int64_t(l) * n]), dd);
+        const double ss = aa + ab;
+        return ba * (ab / ss) <= fmax(DBL_MIN, DBL_EPSILON * (bb * (aa / ss)));
+    }
+    return false;
+}
+
+// Largest power of two g <= 32 with items * g <= kEigThreads (at least 1):
+// g threads share one dot product and combine it by shuffles.
+__device__ inline int group_size(int items) {
+    int g = 1;
+    while (g < 32 && items * (g * 2) <= kEigThreads) g *= 2;
+    return g;
+}
+
+// Orthogonal Q (m x m, m = n1 + n2 <= 4, column-major) exchanging the adjacent
+// diagonal blocks T11 (n1 x n1, at row/column k) and T22 (n2 x n2) of the
+// quasi-triangular T: Q^T [T11 T12; 0 T22] Q = [T22' *; 0 T11'].
+// 1x1 with 1x1: the Givens rotation whose first column is the eigenvector
+// (t12, t22 - t11) of t22. Otherwise the direct swap: solve the Sylvester
+// equation T11 X - X T22 = T12; the columns of [X; -I] span the
+// T22-invariant subspace and Q is the orthogonal factor of their QR
+// factorisation (Householder).
+__device__ void swap_transform(const double* A, int n, int k, int n1, int n2, double anorm, double* Qm) {
+    const int m = n1 + n2;
+    if (n1 == 1 && n2 == 1) {
+        const double a = A[k + int64_t(k) * n], d = A[(k + 1) + int64_t(k + 1) * n];
+        const double b = A[k + int64_t(k + 1) * n];
+        const double r = hypot(b, d - a);
+        const double c = r > 0.0 ? b / r : 1.0, sn = r > 0.0 ? (d - a) / r : 0.0;
+        Qm[0] = c;
+        Qm[1] = sn;
+        Qm[2] = -sn;
+        Qm[3] = c;
+        return;
+    }
+    double K[16], x[4], W[8];
+    const int pdim = n1 * n2;
+    for (int r = 0; r < pdim * pdim; ++r) K[r] = 0.0;
+    // K = I_{n2} (x) T11 - T22^T (x) I_{n1}, x = vec(X) column-major
+    for (int j = 0; j < n2; ++j)
+        for (int i = 0; i < n1; ++i) {
+            const int row = i + n1 * j;
+            for (int i2 = 0; i2 < n1; ++i2) K[row + pdim * (i2 + n1 * j)] += A[(k + i) + int64_t(k + i2) * n];
+            for (int j2 = 0; j2 < n2; ++j2) K[row + pdim * (i + n1 * j2)] -= A[(k + n1 + j2) + int64_t(k + n1 + j) * n];
+            x[row] = A[(k + i) + int64_t(k + n1 + j) * n];
+        }
+    // Gaussian elimination with partial pivoting; a pivot below eps ||T|| is
+    // replaced by that bound (the blocks have close eigenvalues)
+    double kn = 0.0;
+    for (int r = 0; r < pdim * pdim; ++r) kn = fmax(kn, fabs(K[r]));
+    const double tiny = DBL_EPSILON * fmax(kn, anorm);
+    for (int c = 0; c < pdim; ++c) {
+        int pr = c;
+        for (int r = c + 1; r < pdim; ++r)
+            if (fabs(K[r + pdim * c]) > fabs(K[pr + pdim * c])) pr = r;
+        if (pr != c) {
+            for (int cc = 0; cc < pdim; ++cc) {
+                const double t = K[c + pdim * cc];
+                K[c + pdim * cc] = K[pr + pdim * cc];
+                K[pr + pdim * cc] = t;
+            }
+            const double t = x[c];
+            x[c] = x[pr];
+            x[pr] = t;
+        }
+        if (fabs(K[c + pdim * c]) < tiny) K[c + pdim * c] = K[c + pdim * c] >= 0.0 ? tiny : -tiny;
+        for (int r = c + 1; r < pdim; ++r) {
+            const double f = K[r + pdim * c] / K[c + pdim * c];
+            for (int cc = c; cc < pdim; ++cc) K[r + pdim * cc] -= f * K[c + pdim * cc];
+            x[r] -= f * x[c];
+        }
+    }
+    for (int r = pdim - 1; r >= 0; --r) {
+        double t = x[r];
+        for (int cc = r + 1; cc < pdim; ++cc) t -= K[r + pdim * cc] * x[cc];
+        x[r] = t / K[r + pdim * r];
+    }
+    // W = [X; -I] (m x n2), Householder QR with Q accumulated
+    for (int j = 0; j < n2; ++j)
+        for (int i = 0; i < m; ++i) W[i + m * j] = (i < n1) ? x[i + n1 * j] : (i - n1 == j ? -1.0 : 0.0);
+    for (int r = 0; r < m * m; ++r) Qm[r] = (r % m == r / m) ? 1.0 : 0.0;
+    for (int j = 0; j < n2; ++j) {
+        double v[4];
+        const int len = m - j;
+        double ss = 0.0;
+        for (int t = 0; t < len; ++t) {
+            v[t] = W[(j + t) + m * j];
+            ss += v[t] * v[t];
+        }
+        if (ss == 0.0) continue;
+        const double x0 = v[0], nrm = sqrt(ss);
+        v[0] += (x0 >= 0.0 ? nrm : -nrm);
+        const double beta = 1.0 / (nrm * (nrm + fabs(x0)));
+        for (int c = j; c < n2; ++c) {
+            double sdot = 0.0;
+            for (int t = 0; t < len; ++t) sdot += v[t] * W[(j + t) + m * c];
+            for (int t = 0; t < len; ++t) W[(j + t) + m * c] -= beta * sdot * v[t];
+        }
+        for (int r = 0; r < m; ++r) {
+            double sdot = 0.0;
+            for (int t = 0; t < len; ++t) sdot += Qm[r + m * (j + t)] * v[t];
+            for (int t = 0; t < len; ++t) Qm[r + m * (j + t)] -= beta * sdot * v[t];
+        }
+    }
+}
+
+// Orders the diagonal blocks (1x1 real eigenvalues, 2x2 complex pairs) of the
+// quasi-triangular A by decreasing real part, updating the Schur vectors Z:
+// odd-even transposition sort over the blocks. In a round, blocks 2p + par
+// and 2p + par + 1 are exchanged where the second has the larger real part;
+// the exchanges act on disjoint row/column ranges and commute, so a round is
+// applied as one two-sided update (all rows, then all columns and Z). Each
+// exchange is computed by its own thread.
+// ints: 2n ints of scratch (block starts, pair positions, pair sizes/flags);
+// ord: 8n doubles (a 4 x 4 transform per pair).
+__device__ void order_schur(double* A, double* Z, int n, double anorm, double* ints_d, double* ord) {
+    constexpr int NT = kEigThreads;
+    __shared__ int s_wsum[kEigWarps];
+    int* bstart = reinterpret_cast<int*>(ints_d);  // n
+    int* pk = bstart + n;                           // n / 2 (pairs <= blocks / 2)
+    int* pinfo = pk + n / 2;                        // n / 2
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ipt = (n + NT - 1) / NT;
+    int quiet = 0;
+    for (int round = 0; round < 2 * n + 4 && quiet < 2; ++round) {
+        // block starts: i = 0 or a zero subdiagonal entry (i, i-1)
+        int cnt = 0;
+        for (int i = tid * ipt; i < min(n, (tid + 1) * ipt); ++i)
+            cnt += (i == 0 || A[i + int64_t(i - 1) * n] == 0.0);
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        int pos = incl - cnt, nb = 0;
+        for (int w = 0; w < kEigWarps; ++w) {
+            if (w < warp) pos += s_wsum[w];
+            nb += s_wsum[w];
+        }
+        for (int i = tid * ipt; i < min(n, (tid + 1) * ipt); ++i)
+            if (i == 0 || A[i + int64_t(i - 1) * n] == 0.0) bstart[pos++] = i;
+        __syncthreads();
+        const int par = round & 1;
+        const int npairs = max(0, (nb - par) / 2);
+        int any = 0;
+        for (int p = tid; p < npairs; p += NT) {
+            const int b0 = par + 2 * p;
+            const int k = bstart[b0], k2 = bstart[b0 + 1];
+            const int k3 = (b0 + 2 < nb) ? bstart[b0 + 2] : n;
+            const int n1 = k2 - k, n2 = k3 - k2;
+            const double key1 = n1 == 1 ? A[k + int64_t(k) * n] : 0.5 * (A[k + int64_t(k) * n] + A[(k + 1) + int64_t(k + 1) * n]);
+            const double key2 = n2 == 1 ? A[k2 + int64_t(k2) * n]
+                                        : 0.5 * (A[k2 + int64_t(k2) * n] + A[(k2 + 1) + int64_t(k2 + 1) * n]);
+            const int f = key2 > key1;
+            if (f) {
+                swap_transform(A, n, k, n1, n2, anorm, ord + 16 * int64_t(p));
+                if (n1 == 1 && n2 == 1) {
+                    // exact exchange of the diagonal pair
+                    ord[16 * int64_t(p) + 4] = A[k + int64_t(k) * n];
+                    ord[16 * int64_t(p) + 5] = A[k2 + int64_t(k2) * n];
+                }
+            }
+            pk[p] = k;
+            pinfo[p] = f | (n1 << 1) | (n2 << 3);
+            any |= f;
+        }
+        any = __syncthreads_or(any);
+        if (!any) {
+            ++quiet;
+            continue;
+        }
+        quiet = 0;
+        // rows of each exchanged span <- Q^T rows (columns k..n-1)
+        for (int64_t e = tid; e < int64_t(npairs) * n; e += NT) {
+            const int p = int(e / n), j = int(e % n);
+            const int info = pinfo[p];
+            if (!(info & 1)) continue;
+            const int k = pk[p], m = ((info >> 1) & 3) + ((info >> 3) & 3);
+            if (j < k) continue;
+            const double* Qm = ord + 16 * int64_t(p);
+            double old[4];
+            for (int t = 0; t < m; ++t) old[t] = A[(k + t) + int64_t(j) * n];
+            for (int t = 0; t < m; ++t) {
+                double acc = 0.0;
+                for (int u2 = 0; u2 < m; ++u2) acc = fma(Qm[u2 + m * t], old[u2], acc);
+                A[(k + t) + int64_t(j) * n] = acc;
+            }
+        }
+        __syncthreads();
+        // columns of each exchanged span <- columns Q (rows of A above the
+        // span's end, all rows of Z)
+        for (int64_t e = tid; e < int64_t(npairs) * 2 * n; e += NT) {
+            const int p = int(e / (2 * n)), i2 = int(e % (2 * n));
+            const int info = pinfo[p];
+            if (!(info & 1)) continue;
+            const int k = pk[p], m = ((info >> 1) & 3) + ((info >> 3) & 3);
+            double* M = i2 < n ? A : Z;
+            const int r = i2 < n ? i2 : i2 - n;
+            if (i2 < n && r >= k + m) continue;
+            const double* Qm = ord + 16 * int64_t(p);
+            double old[4];
+            for (int t = 0; t < m; ++t) old[t] = M[r + int64_t(k + t) * n];
+            for (int t = 0; t < m; ++t) {
+                double acc = 0.0;
+                for (int u2 = 0; u2 < m; ++u2) acc = fma(old[u2], Qm[u2 + m * t], acc);
+                M[r + int64_t(k + t) * n] = acc;
+            }
+        }
+        __syncthreads();
+        // the exchanged blocks: zero the new (2,1) block; 1x1 pairs take
+        // their exchanged diagonal exactly
+        for (int p = tid; p < npairs; p += NT) {
+            const int info = pinfo[p];
+            if (!(info & 1)) continue;
+            const int k = pk[p], n1 = (info >> 1) & 3, n2 = (info >> 3) & 3, m = n1 + n2;
+            for (int i = k + n2; i < k + m; ++i)
+                for (int j = k; j < k + n2; ++j) A[i + int64_t(j) * n] = 0.0;
+            if (n1 == 1 && n2 == 1) {
+                A[k + int64_t(k) * n] = ord[16 * int64_t(p) + 5];
+                A[(k + 1) + int64_t(k + 1) * n] = ord[16 * int64_t(p) + 4];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// smem_level: 2 = A, Z, X, the Householder vector and the ordering scratch in
+// shared memory, 1 = A and the Householder vector, 0 = everything in the
+// global work array.
+// nvec: eigenvectors wanted for the leading nvec ordered eigenvalues
+// (non-symmetric mode); the symmetric mode returns all ordered Schur vectors.
+__global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* __restrict__ H, int n,
+                                                                 double* wr_out, double* wi_out,
+                                                                 double* Vout, double* Qout, double* work,
+                                                                 int* status, int smem_level, int sym,
+                                                                 int nvec) {
+    extern __shared__ double smem_a[];
+    const int64_t nn = int64_t(n) * n;
+    double* A = smem_level >= 1 ? smem_a : work;
+    double* Z = smem_level == 2 ? smem_a + nn : work + nn;
+    double* X = smem_level == 2 ? smem_a + 2 * nn : work + 2 * nn;
+    double* hv = smem_level == 2 ? smem_a + 3 * nn : (smem_level == 1 ? smem_a + nn : work + 3 * nn + 2 * n);
+    double* wr = work + 3 * nn;
+    double* wi = wr + n;
+    double* ord = smem_level == 2 ? smem_a + 3 * nn + n : work + 3 * nn + 3 * n;  // 8n
+    __shared__ double s_red[kEigWarps];
+    __shared__ int s_redi[kEigWarps];
+    __shared__ double s_v[3], s_x[3];
+    __shared__ double s_beta, s_sh, s_th;
+    __shared__ int s_l, s_u, s_its, s_fail, s_action;
+    const int tid = threadIdx.x;
+    constexpr int NT = kEigThreads;
+
+    double amax = 0.0;
+    for (int64_t e = tid; e < nn; e += NT) {
+        const int i = int(e % n), j = int(e / n);
+        const double a = sym ? 0.5 * (H[e] + H[j + int64_t(i) * n]) : H[e];
+        A[e] = a;
+        Z[e] = (i == j) ? 1.0 : 0.0;
+        amax = fmax(amax, fabs(a));
+    }
+    const double anorm = blk_max(amax, s_red);  // also orders the stores above
+
+    // ---- Householder reduction to Hessenberg form ----
+    for (int k = 0; k + 2 < n; ++k) {
+        const int len = n - k - 1;
+        double ss = 0.0;
+        for (int t = tid; t < len; t += NT) {
+            const double x = A[(k + 1 + t) + int64_t(k) * n];
+            hv[t] = x;
+            ss = fma(x, x, ss);
+        }
+        ss = blk_sum(ss, s_red);
+        if (tid == 0) {
+            double beta = 0.0;
+            if (ss > 0.0) {
+                const double x0 = hv[0], nrm = sqrt(ss);
+                hv[0] = x0 + (x0 >= 0.0 ? nrm : -nrm);
+                beta = 1.0 / (nrm * (nrm + fabs(x0)));
+            }
+            s_beta = beta;
+        }
+        __syncthreads();
+        const double beta = s_beta;
+        if (beta != 0.0) {
+            // left: rows k+1..n-1 of columns k..n-1
+            const int ncols = n - k;
+            const int g = group_size(ncols), per = NT / g;
+            for (int base = 0; base < ncols; base += per) {
+                const int c = base + tid / g, p = tid % g;
+                double s = 0.0;
+                if (c < ncols)
+                    for (int t = p; t < len; t += g) s = fma(hv[t], A[(k + 1 + t) + int64_t(k + c) * n], s);
+                for (int o = g / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+                s *= beta;
+                if (c < ncols)
+                    for (int t = p; t < len; t += g) A[(k + 1 + t) + int64_t(k + c) * n] -= s * hv[t];
+            }
+            __syncthreads();
+            // right: all rows of A and of Z, columns k+1..n-1
+            const int items = 2 * n;
+            const int g2 = group_size(items), per2 = NT / g2;
+            for (int base = 0; base < items; base += per2) {
+                const int it = base + tid / g2, p = tid % g2;
+                double* M = it < n ? A : Z;
+                const int i = it < n ? it : it - n;
+                double s = 0.0;
+                if (it < items)
+                    for (int t = p; t < len; t += g2) s = fma(M[i + int64_t(k + 1 + t) * n], hv[t], s);
+                for (int o = g2 / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+                s *= beta;
+                if (it < items)
+                    for (int t = p; t < len; t += g2) M[i + int64_t(k + 1 + t) * n] -= s * hv[t];
+            }
+        }
+        __syncthreads();
+        for (int i = k + 2 + tid; i < n; i += NT) A[i + int64_t(k) * n] = 0.0;
+        __syncthreads();
+    }
+
+    // ---- Francis double-shift QR to real Schur form ----
+    if (tid == 0) {
+        s_u = n - 1;
+        s_its = 0;
+        s_fail = 0;
+    }
+    __syncthreads();
+    int total_its = 0;
+    while (true) {
+        const int u0 = s_u;
+        if (u0 < 0) break;
+        // largest l <= u with a negligible subdiagonal (l, l-1); 0 if none
+        int cand = 0;
+        for (int l = u0 - tid; l >= 1; l -= NT)
+            if (deflatable(A, n, l, anorm)) {
+                cand = l;
+                break;
+            }
+        cand = blk_max_int(cand, s_redi);
+        if (tid == 0) {
+            const int u = u0;
+            int l = cand;
+            if (l >= 1) A[l + int64_t(l - 1) * n] = 0.0;
+            int action = (l == u) ? 1 : (l == u - 1) ? 2 : 3;  // 1: one root, 2: 2x2 block, 3: Francis step
+            if (action == 3 && s_its >= 30 && s_its % 10 == 5) {
+                // A window that resists the shifts for 30 iterations is a
+                // cluster of (numerically) equal eigenvalues perturbed into a
+                // near-Jordan block. The window is already decoupled from its
+                // neighbours, so zeroing its smallest subdiagonal leaves every
+                // other eigenvalue and the window's invariant subspace as
+                // they are; it only splits the cluster (by about
+                // sqrt(|sub * super|)). Only a subdiagonal far below any
+                // tolerance of the outer solver is dropped (backward error
+                // 1e-10 * ||H||).
+                int m = l + 1;
+                for (int i = l + 2; i <= u; ++i)
+                    if (fabs(A[i + int64_t(i - 1) * n]) < fabs(A[m + int64_t(m - 1) * n])) m = i;
+                if (fabs(A[m + int64_t(m - 1) * n]) <= 1e-10 * anorm) {
+                    A[m + int64_t(m - 1) * n] = 0.0;
+                    action = 5;  // split: look for deflations again
+                    s_its = s_its + 1;
+                }
+            }
+            if (action == 3) {
+                if (s_its >= 300 || total_its > 120 * max(10, n)) {
+                    s_fail = 1;
+                    action = 4;
+                } else {
+                    double sh, th;
+                    if (s_its > 0 && s_its % 10 == 0) {  // exceptional shift
+                        const double ex = fabs(A[u + int64_t(u - 1) * n]) + fabs(A[(u - 1) + int64_t(u - 2) * n]);
+                        const double c = A[u + int64_t(u) * n] + 0.75 * ex;
+                        sh = 2.0 * c;
+                        th = c * c + 0.4375 * ex * ex;
+                    } else {
+                        const double a = A[(u - 1) + int64_t(u - 1) * n], b = A[(u - 1) + int64_t(u) * n];
+                        const double c = A[u + int64_t(u - 1) * n], d = A[u + int64_t(u) * n];
+                        sh = a + d;
+                        th = a * d - b * c;
+                    }
+                    s_its = s_its + 1;
+                    // first column of (H - s1)(H - s2) restricted to the window
+                    const double h11 = A[l + int64_t(l) * n], h12 = A[l + int64_t(l + 1) * n];
+                    const double h21 = A[(l + 1) + int64_t(l) * n], h22 = A[(l + 1) + int64_t(l + 1) * n];
+                    const double h32 = A[(l + 2) + int64_t(l + 1) * n];
+                    s_x[0] = h11 * h11 + h12 * h21 - sh * h11 + th;
+                    s_x[1] = h21 * (h11 + h22 - sh);
+                    s_x[2] = h21 * h32;
+                }
+            }
+            if (action == 1) {
+                wr[u] = A[u + int64_t(u) * n];
+                wi[u] = 0.0;
+            }
+            s_l = l;
+            s_action = action;
+        }
+        __syncthreads();
+        const int action = s_action;
+        const int u = u0, l = s_l;
+        if (action == 4) break;
+        if (action == 5) continue;
+        if (action == 1) {
+            if (tid == 0) {
+                s_u = u - 1;
+                s_its = 0;
+            }
+            __syncthreads();
+            continue;
+        }
+        if (action == 2) {
+            // 2x2 block at (u-1, u): triangularise if its eigenvalues are real
+            __shared__ double s_cs, s_sn;
+            __shared__ int s_rot;
+            if (tid == 0) {
+                const double a = A[(u - 1) + int64_t(u - 1) * n], b = A[(u - 1) + int64_t(u) * n];
+                const double c = A[u + int64_t(u - 1) * n], d = A[u + int64_t(u) * n];
+                const double p = 0.5 * (a - d);
+                // a symmetric matrix has real eigenvalues: rounding may leave
+                // b c slightly negative, which must not create a complex pair
+                const double q = sym ? fmax(p * p + b * c, 0.0) : p * p + b * c;
+                s_rot = 0;
+                if (q >= 0.0) {
+                    const double zz = p + (p >= 0.0 ? sqrt(q) : -sqrt(q));
+                    const double r = hypot(zz, c);
+                    if (r > 0.0) {
+                        s_cs = zz / r;
+                        s_sn = c / r;
+                        s_rot = 1;
+                    }
+                    wr[u - 1] = d + zz;
+                    wr[u] = (zz != 0.0) ? d - b * c / zz : d + zz;
+                    wi[u - 1] = wi[u] = 0.0;
+                } else {
+                    wr[u - 1] = wr[u] = d + p;
+                    wi[u - 1] = sqrt(-q);
+                    wi[u] = -sqrt(-q);
+                }
+            }
+            __syncthreads();
+            if (s_rot) {
+                const double cs = s_cs, sn = s_sn;
+                for (int j = u - 1 + tid; j < n; j += NT) {
+                    const double x1 = A[(u - 1) + int64_t(j) * n], x2 = A[u + int64_t(j) * n];
+                    A[(u - 1) + int64_t(j) * n] = cs * x1 + sn * x2;
+                    A[u + int64_t(j) * n] = -sn * x1 + cs * x2;
+                }
+                __syncthreads();
+                for (int e = tid; e < u + 1 + n; e += NT) {
+                    double* M = e <= u ? A : Z;
+                    const int i = e <= u ? e : e - u - 1;
+                    const double x1 = M[i + int64_t(u - 1) * n], x2 = M[i + int64_t(u) * n];
+                    M[i + int64_t(u - 1) * n] = cs * x1 + sn * x2;
+                    M[i + int64_t(u) * n] = -sn * x1 + cs * x2;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    A[u + int64_t(u - 1) * n] = 0.0;
+                    // diagonal entries now hold the two real eigenvalues
+                    wr[u - 1] = A[(u - 1) + int64_t(u - 1) * n];
+                    wr[u] = A[u + int64_t(u) * n];
+                }
+            }
+            if (tid == 0) {
+                s_u = u - 2;
+                s_its = 0;
+            }
+            __syncthreads();
+            continue;
+        }
+        // Francis double-shift step on the window [l, u] (size ns >= 3)
+        ++total_its;
+        const int ns = u - l + 1;
+        for (int kk = 0; kk <= ns - 3; ++kk) {
+            if (tid == 0) {
+                double v[3], beta;
+                house(s_x, 3, v, beta);
+                s_v[0] = v[0];
+                s_v[1] = v[1];
+                s_v[2] = v[2];
+                s_beta = beta;
+            }
+            __syncthreads();
+            const double v0 = s_v[0], v1 = s_v[1], v2 = s_v[2], beta = s_beta;
+            const int r0 = l + kk;
+            const int c0 = l + (kk > 0 ? kk - 1 : 0);
+            for (int j = c0 + tid; j < n; j += NT) {
+                double* col = A + int64_t(j) * n + r0;
+                const double a0 = col[0], a1 = col[1], a2 = col[2];
+                const double s = beta * fma(v2, a2, fma(v1, a1, v0 * a0));
+                col[0] = a0 - s * v0;
+                col[1] = a1 - s * v1;
+                col[2] = a2 - s * v2;
+            }
+            __syncthreads();
+            const int rmax = min(l + kk + 3, u);  // last row of A touched (inclusive)
+            for (int e = tid; e < rmax + 1 + n; e += NT) {
+                double* M = e <= rmax ? A : Z;
+                const int i = e <= rmax ? e : e - rmax - 1;
+                double* row = M + i + int64_t(r0) * n;
+                const double a0 = row[0], a1 = row[n], a2 = row[2 * int64_t(n)];
+                const double s = beta * fma(a2, v2, fma(a1, v1, a0 * v0));
+                row[0] = a0 - s * v0;
+                row[n] = a1 - s * v1;
+                row[2 * int64_t(n)] = a2 - s * v2;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                s_x[0] = A[(r0 + 1) + int64_t(r0) * n];
+                s_x[1] = A[(r0 + 2) + int64_t(r0) * n];
+                s_x[2] = (kk < ns - 3) ? A[(r0 + 3) + int64_t(r0) * n] : 0.0;
+            }
+        }
+        if (tid == 0) {
+            double v[3], beta;
+            house(s_x, 2, v, beta);
+            s_v[0] = v[0];
+            s_v[1] = v[1];
+            s_beta = beta;
+        }
+        __syncthreads();
+        {
+            const double v0 = s_v[0], v1 = s_v[1], beta = s_beta;
+            for (int j = u - 2 + tid; j < n; j += NT) {
+                double* col = A + int64_t(j) * n + (u - 1);
+                const double a0 = col[0], a1 = col[1];
+                const double s = beta * fma(v1, a1, v0 * a0);
+                col[0] = a0 - s * v0;
+                col[1] = a1 - s * v1;
+            }
+            __syncthreads();
+            for (int e = tid; e < u + 1 + n; e += NT) {
+                double* M = e <= u ? A : Z;
+                const int i = e <= u ? e : e - u - 1;
+                double* row = M + i + int64_t(u - 1) * n;
+                const double a0 = row[0], a1 = row[n];
+                const double s = beta * fma(a1, v1, a0 * v0);
+                row[0] = a0 - s * v0;
+                row[n] = a1 - s * v1;
+            }
+            __syncthreads();
+        }
+        // clean the bulge remnants below the subdiagonal of the window
+        for (int e = tid; e < ns * ns; e += NT) {
+            const int i = l + e % ns, j = l + e / ns;
+            if (i > j + 1) A[i + int64_t(j) * n] = 0.0;
+        }
+        __syncthreads();
+    }
+
+    const int fail = s_fail;
+    const int nv = min(max(nvec, 1), n);
+    if (!fail && sym) {
+        // ---- symmetric: the real Schur form is diagonal, so ordering is a
+        // permutation of the Schur vectors (stable for ties) ----
+        int* rk = reinterpret_cast<int*>(hv);
+        for (int i = tid; i < n; i += NT) {
+            const double di = A[i + int64_t(i) * n];
+            int rank = 0;
+            for (int j = 0; j < n; ++j) {
+                const double dj = A[j + int64_t(j) * n];
+                if (dj > di || (dj == di && j < i)) ++rank;
+            }
+            wr_out[rank] = di;
+            if (wi_out) wi_out[rank] = 0.0;
+            rk[i] = rank;
+        }
+        __syncthreads();
+        for (int64_t e = tid; e < nn; e += NT) {
+            const int i = int(e % n), c = int(e / n);
+            const double z = Z[e];
+            if (Vout) Vout[i + int64_t(rk[c]) * n] = z;
+            if (Qout) Qout[i + int64_t(rk[c]) * n] = z;
+        }
+    } else if (!fail) {
+        // ---- ordering of the real Schur form by decreasing real part ----
+        order_schur(A, Z, n, anorm, hv, ord);
+        __syncthreads();
+
+        // ---- eigenvalues of the ordered blocks ----
+        for (int i = tid; i < n; i += NT) {
+            const bool first = (i + 1 < n) && A[(i + 1) + int64_t(i) * n] != 0.0;
+            const bool second = (i > 0) && A[i + int64_t(i - 1) * n] != 0.0;
+            if (first || second) {
+                const int b0 = first ? i : i - 1;
+                const double a = A[b0 + int64_t(b0) * n], b = A[b0 + int64_t(b0 + 1) * n];
+                const double c = A[(b0 + 1) + int64_t(b0) * n], d = A[(b0 + 1) + int64_t(b0 + 1) * n];
+                const double pp = 0.5 * (a - d), q = pp * pp + b * c;
+                const double im = q < 0.0 ? sqrt(-q) : 0.0;
+                wr[i] = d + pp;
+                wi[i] = first ? im : -im;
+            } else {
+                wr[i] = A[i + int64_t(i) * n];
+                wi[i] = 0.0;
+            }
+        }
+        __syncthreads();
+
+        // ---- eigenvectors of the leading nv columns of T by back substitution ----
+        // Diagonal entries within 1e-10 ||T|| of the eigenvalue belong to its
+        // cluster; their components are set to zero instead of dividing by a
+        // vanishing pivot, so the vectors of a (numerically) multiple
+        // eigenvalue stay independent (its invariant subspace is spanned by
+        // Schur vectors).
+        const int nve = (nv < n && wi[nv - 1] > 0.0) ? nv + 1 : nv;
+        const double small = DBL_EPSILON * fmax(anorm, DBL_MIN);
+        const double clus = 1e-10 * anorm;
+        for (int col = tid; col < nve; col += NT) {
+            double* xr = X + int64_t(col) * n;
+            if (wi[col] == 0.0) {
+                const double lam = wr[col];
+                for (int i = 0; i < n; ++i) xr[i] = 0.0;
+                xr[col] = 1.0;
+                for (int j = col - 1; j >= 0; --j) {
+                    const bool two = (j > 0) && A[j + int64_t(j - 1) * n] != 0.0;
+                    if (!two) {
+                        double s = 0.0;
+                        for (int l2 = j + 1; l2 <= col; ++l2) s = fma(A[j + int64_t(l2) * n], xr[l2], s);
+                        double den = A[j + int64_t(j) * n] - lam;
+                        if (fabs(den) <= clus) {
+                            xr[j] = 0.0;
+                            continue;
+                        }
+                        if (fabs(den) < small) den = small;
+                        xr[j] = -s / den;
+                    } else {
+                        // 2x2 system for rows j-1, j
+                        double s1 = 0.0, s2 = 0.0;
+                        for (int l2 = j + 1; l2 <= col; ++l2) {
+                            s1 = fma(A[(j - 1) + int64_t(l2) * n], xr[l2], s1);
+                            s2 = fma(A[j + int64_t(l2) * n], xr[l2], s2);
+                        }
+                        const double a11 = A[(j - 1) + int64_t(j - 1) * n] - lam, a12 = A[(j - 1) + int64_t(j) * n];
+                        const double a21 = A[j + int64_t(j - 1) * n], a22 = A[j + int64_t(j) * n] - lam;
+                        double det = a11 * a22 - a12 * a21;
+                        if (fabs(det) < small * small) det = small * small;
+                        xr[j - 1] = (-s1 * a22 + s2 * a12) / det;
+                        xr[j] = (-s2 * a11 + s1 * a21) / det;
+                        --j;
+                    }
+                }
+            } else if (wi[col] > 0.0) {
+                // complex pair (col, col+1): vector for lambda = wr + i wi, stored
+                // as real part in column col and imaginary part in column col+1
+                double* xi = X + int64_t(col + 1) * n;
+                const cplx lam = {wr[col], wi[col]};
+                for (int i = 0; i < n; ++i) xr[i] = xi[i] = 0.0;
+                // (b12, lambda - b11) solves the first row of (B - lambda I) x = 0
+                // for the 2x2 block B and is non-zero because lambda is not real
+                const int q = col;
+                xr[q] = A[q + int64_t(q + 1) * n];
+                xi[q] = 0.0;
+                xr[q + 1] = lam.re - A[q + int64_t(q) * n];
+                xi[q + 1] = lam.im;
+                for (int j = q - 1; j >= 0; --j) {
+                    const bool two = (j > 0) && A[j + int64_t(j - 1) * n] != 0.0;
+                    if (!two) {
+                        cplx s = {0.0, 0.0};
+                        for (int l2 = j + 1; l2 <= q + 1; ++l2) {
+                            s.re += A[j + int64_t(l2) * n] * xr[l2];
+                            s.im += A[j + int64_t(l2) * n] * xi[l2];
+                        }
+                        cplx den = {A[j + int64_t(j) * n] - lam.re, -lam.im};
+                        if (fabs(den.re) + fabs(den.im) < small) den.re = small;
+                        const cplx r = cdiv({-s.re, -s.im}, den);
+                        xr[j] = r.re;
+                        xi[j] = r.im;
+                    } else {
+                        cplx s1 = {0.0, 0.0}, s2 = {0.0, 0.0};
+                        for (int l2 = j + 1; l2 <= q + 1; ++l2) {
+                            s1.re += A[(j - 1) + int64_t(l2) * n] * xr[l2];
+                            s1.im += A[(j - 1) + int64_t(l2) * n] * xi[l2];
+                            s2.re += A[j + int64_t(l2) * n] * xr[l2];
+                            s2.im += A[j + int64_t(l2) * n] * xi[l2];
+                        }
+                        const cplx a11 = {A[(j - 1) + int64_t(j - 1) * n] - lam.re, -lam.im};
+                        const cplx a12 = {A[(j - 1) + int64_t(j) * n], 0.0};
+                        const cplx a21 = {A[j + int64_t(j - 1) * n], 0.0};
+                        const cplx a22 = {A[j + int64_t(j) * n] - lam.re, -lam.im};
+                        cplx det = {cmul(a11, a22).re - cmul(a12, a21).re, cmul(a11, a22).im - cmul(a12, a21).im};
+                        if (fabs(det.re) + fabs(det.im) < small * small) det.re = small * small;
+                        const cplx n1 = {-(cmul(s1, a22).re) + cmul(s2, a12).re, -(cmul(s1, a22).im) + cmul(s2, a12).im};
+                        const cplx n2 = {-(cmul(s2, a11).re) + cmul(s1, a21).re, -(cmul(s2, a11).im) + cmul(s1, a21).im};
+                        const cplx r1 = cdiv(n1, det), r2 = cdiv(n2, det);
+                        xr[j - 1] = r1.re;
+                        xi[j - 1] = r1.im;
+                        xr[j] = r2.re;
+                        xi[j] = r2.im;
+                        --j;
+                    }
+                }
+            }
+            // wi < 0: second member of a pair, written by its partner
+        }
+        __syncthreads();
+        // V = Z X for the leading columns (X(:, c) vanishes below row c + 1),
+        // then unit columns (complex pairs jointly)
+        double* Vt = A;  // the Schur form is no longer needed
+        for (int64_t e = tid; e < int64_t(n) * nve; e += NT) {
+            const int i = int(e % n), c = int(e / n);
+            const int top = min(n - 1, c + 1);
+            double s = 0.0;
+            for (int l2 = 0; l2 <= top; ++l2) s = fma(Z[i + int64_t(l2) * n], X[l2 + int64_t(c) * n], s);
+            Vt[i + int64_t(c) * n] = s;
+        }
+        __syncthreads();
+        for (int c = tid; c < nve; c += NT) {
+            if (wi[c] < 0.0) continue;
+            const int w2 = (wi[c] > 0.0) ? 2 : 1;
+            double s = 0.0;
+            for (int t = 0; t < w2; ++t)
+                for (int i = 0; i < n; ++i) s = fma(Vt[i + int64_t(c + t) * n], Vt[i + int64_t(c + t) * n], s);
+            s = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+            for (int t = 0; t < w2; ++t)
+                for (int i = 0; i < n; ++i) Vt[i + int64_t(c + t) * n] *= s;
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += NT) {
+            wr_out[i] = wr[i];
+            if (wi_out) wi_out[i] = wi[i];
+        }
+        if (Vout)
+            for (int64_t e = tid; e < int64_t(n) * nve; e += NT) Vout[e] = Vt[e];
+        if (Qout)
+            for (int64_t e = tid; e < nn; e += NT) Qout[e] = Z[e];
+    }
+    if (tid == 0) {
+        status[0] = fail ? 1 : 0;
+        // diagnostics after the status word: QR iterations, last window end,
+        // iterations spent on it
+        status[1] = total_its;
+        status[2] = s_u;
+        status[3] = s_its;
+    }
+}
+
+// Shared-memory level for an n x n problem (see the kernel).
+int eig_smem_level(int n, size_t* bytes) {
+    const size_t nn = size_t(n) * n;
+    const size_t limit = 220 * 1024;
+    if ((3 * nn + 9 * size_t(n)) * sizeof(double) <= limit) {
+        *bytes = (3 * nn + 9 * size_t(n)) * sizeof(double);
+        return 2;
+    }
+    if ((nn + n) * sizeof(double) <= limit) {
+        *bytes = (nn + n) * sizeof(double);
+        return 1;
+    }
+    *bytes = 0;
+    return 0;
+}
+
+cudaError_t launch_eig(const double* H, int n, double* wr, double* wi, double* V, double* Q, double* work,
+                       int* status, int sym, int nvec, cudaStream_t s) {
+    if (n <= 0) return cudaErrorInvalidValue;
+    size_t bytes = 0;
+    const int level = eig_smem_level(n, &bytes);
+    if (bytes > 0) {
+        cudaError_t e = cudaFuncSetAttribute(nonsym_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+        if (e != cudaSuccess) return e;
+    }
+    nonsym_eig_kernel<<<1, kEigThreads, bytes, s>>>(H, n, wr, wi, V, Q, work, status, level, sym, nvec);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int64_t nonsym_eig_work_doubles(int n) { return 3 * int64_t(n) * n + 11 * int64_t(n); }
+int64_t sym_eig_work_doubles(int n) { return nonsym_eig_work_doubles(n); }
+
+// Symmetric eigenproblem: the same Hessenberg (here tridiagonal) reduction and
+// Francis QR; the ordered real Schur form of a symmetric matrix is diagonal,
+// so the ordered Schur vectors are orthonormal eigenvectors.
+cudaError_t launch_sym_eig(const double* H, int n, double* w, double* V, double* work, int* status,
+                           cudaStream_t s) {
+    return launch_eig(H, n, w, nullptr, V, nullptr, work, status, 1, n, s);
+}
+
+cudaError_t launch_nonsym_eig(const double* H, int n, double* wr, double* wi, double* V, double* Q,
+                              double* work, int* status, cudaStream_t s, int nvec) {
+    return launch_eig(H, n, wr, wi, V, Q, work, status, 0, nvec > 0 ? nvec : n, s);
+}
+
+}  // namespace kl

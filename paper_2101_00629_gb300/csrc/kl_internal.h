@@ -119,18 +119,20 @@ cudaError_t launch_gemm_nn(const double* A, int64_t lda, const double* B, int64_
 // Lower Cholesky of the n x n SPD G (in place) and Rinv = L^-T (upper), flags
 // columns whose pivot collapsed (rank deficiency) in bad[n] (0/1).
 cudaError_t launch_chol_rinv(double* G, int n, double* Rinv, int* bad, cudaStream_t s);
-// Symmetric eigen-decomposition of the n x n H (cyclic Jacobi), eigenvalues
-// descending in w, eigenvectors in V (n x n).
+// Symmetric eigen-decomposition of the n x n H (Hessenberg/tridiagonal
+// reduction + Francis QR), eigenvalues descending in w, orthonormal
+// eigenvectors in V (n x n). status[0]: 0 ok, 1 no convergence.
 cudaError_t launch_sym_eig(const double* H, int n, double* w, double* V, double* work,
                            int* status, cudaStream_t s);
-// Real non-symmetric eigen-decomposition (Hessenberg + Francis QR + back
-// substitution). wr/wi eigenvalues sorted by real part descending, V real
-// vectors (complex pairs as Re, Im columns), unit 2-norm. When every
-// eigenvalue is real the Schur form is reordered and Q (optional) receives
-// the Schur vectors in the same order (status 0); status 2 means complex
-// pairs were met and Q is not ordered; status 1 means no convergence.
+// Real non-symmetric eigen-decomposition (Hessenberg + Francis QR + ordering
+// of the real Schur form + back substitution). wr/wi eigenvalues by real part
+// descending; Q (optional, n x n) the Schur vectors in the same order, so its
+// leading columns span the invariant subspace of the leading eigenvalues; V
+// the unit-norm eigenvectors of the leading nvec eigenvalues (complex pairs as
+// Re, Im columns; one more column when nvec splits a pair; nvec <= 0: all).
+// status[0]: 0 ok, 1 no convergence.
 cudaError_t launch_nonsym_eig(const double* H, int n, double* wr, double* wi, double* V, double* Q,
-                              double* work, int* status, cudaStream_t s);
+                              double* work, int* status, cudaStream_t s, int nvec = 0);
 int64_t nonsym_eig_work_doubles(int n);
 int64_t sym_eig_work_doubles(int n);
 // Column 2-norms of X (K x n).

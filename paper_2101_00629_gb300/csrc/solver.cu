@@ -55,6 +55,7 @@ struct Ctx {
     int mmax;
     bool sym;
     bool schur_ok = false;      // Q holds ordered Schur vectors of the last H
+    int nvec = 0;               // eigenvectors of H needed (leading, ordered)
     unsigned long long rng_offset = 0;
     int applies = 0, vectors_applied = 0;
 };
@@ -157,7 +158,7 @@ int rayleigh_ritz(Ctx& c, const double* V, const double* AV, int nv, double* max
         if (max_imag) *max_imag = 0.0;
     } else {
         KL_TRY(ck(c, launch_nonsym_eig(c.w.H, nv, c.w.theta, c.w.thetai, c.w.S, c.w.Q, c.w.la_work,
-                                       c.w.ibuf, c.h->stream), "nonsym_eig"));
+                                       c.w.ibuf, c.h->stream, c.nvec), "nonsym_eig"));
         KL_TRY(sync_copy(c, &status, c.w.ibuf, sizeof(int)));
         c.schur_ok = status == 0;
         if (status == 2) status = 0;  // complex pairs: eigenvectors valid, Schur order not
@@ -211,6 +212,9 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
     const int mmax_full = std::max(2 * nkeep_full, nkeep_full + 2 * b);
     if (mmax_full + b > 512 && mmax_full < N) return fail(h, KL_ERR_ARG, "M + 3 block_k too large for the basis limit 512");
     const int nkeep = int(std::min<int64_t>(nkeep_full, N));
+    // Ritz vectors are used for the M wanted pairs and at most nkeep + 1
+    // restart vectors (nkeep >= M + b)
+    c.nvec = nkeep + 1;
     const int mmax = int(std::min<int64_t>(mmax_full, N));
     // a restart keeps one extra vector rather than split a complex pair, so
     // the basis may grow to mmax + b - 1 columns
@@ -423,7 +427,10 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
         info->seconds = secs;
     }
     if (status_out != KL_OK) return fail(h, status_out, "iteration limit reached before convergence");
-    if (!c.sym && max_imag > 1e-8) {
+    // an imaginary part below the residual tolerance (relative to |lambda_1|)
+    // is not resolved by the solve: a numerically multiple real eigenvalue
+    // of a non-normal projected matrix splits into such pairs
+    if (!c.sym && max_imag > std::max(1e-8, tol)) {
         h->err = "complex eigenvalues among the returned pairs";
         return KL_WARN_COMPLEX;
     }
