@@ -51,10 +51,20 @@ constexpr int kStages = 4;                // TMEM A-operand ring (kernel tiles)
 constexpr int kProducers = 256;           // two warpgroups
 constexpr int kThreads = kProducers + 64; // + MMA warp + loader warp
 constexpr int kTmemCols = 256;
-constexpr int kDCols = 64;                // columns of one accumulator buffer (N <= 64)
-constexpr int kAColBase = 2 * kDCols;     // two accumulator buffers, then the A stages
 constexpr int kAColsPerStage = 32;        // hi 16 + lo 16 columns
 constexpr int kGroup = 8;                 // chunks accumulated in FP32 before a flush
+constexpr int kFlushLag = 4;              // chunks between a group's end and its flush
+// Tensor memory of a CTA (256 columns): two accumulator buffers (32 columns
+// each for N <= 32, else 64); for N <= 32 the running (hi, lo) sums of the
+// unit (2N columns); then the 4-stage ring of kernel tiles (32 columns each).
+template <int NP>
+struct TmemLayout {
+    static constexpr bool kSum = NP <= 32;             // running sums in TMEM
+    static constexpr int kDStride = NP <= 32 ? 32 : 64;
+    static constexpr int kSBase = 2 * kDStride;
+    static constexpr int kAColBase = kSum ? kSBase + (2 * NP + 31) / 32 * 32 : 2 * kDStride;
+    static_assert(kAColBase + kStages * kAColsPerStage <= kTmemCols, "tensor memory overflow");
+};
 constexpr long long kWaitLimit = 2000000000LL;  // clock cycles (~1 s)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -145,6 +155,13 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
                  : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
@@ -167,18 +184,52 @@ __device__ __forceinline__ uint32_t cvt_bf16x2(float even_k, float odd_k) {
     return r;
 }
 
+// Packed FP32 pairs (sm_100 f32x2 arithmetic: one instruction, two values;
+// the first value in the low half).
+__device__ __forceinline__ uint64_t pk2(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void up2(uint64_t v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2sub(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2mul(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // Split (g0, g1) into packed hi and lo BF16 pairs with g ~ hi + lo.
 __device__ __forceinline__ void split_bf16(float g0, float g1, uint32_t& hi, uint32_t& lo) {
     hi = cvt_bf16x2(g0, g1);
-    const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xffff0000u);
-    lo = cvt_bf16x2(g0 - h0, g1 - h1);
+    const uint64_t h = pk2(__uint_as_float(hi << 16), __uint_as_float(hi & 0xffff0000u));
+    float l0, l1;
+    up2(f2sub(pk2(g0, g1), h), l0, l1);
+    lo = cvt_bf16x2(l0, l1);
 }
 
-// Split g into hi (mantissa truncated to the 10 bits a TF32 operand keeps)
-// and lo = g - hi (exact in FP32; the tensor core uses its leading 10 bits).
-__device__ __forceinline__ void split_tf32(float g, uint32_t& hi, uint32_t& lo) {
-    hi = __float_as_uint(g) & 0xffffe000u;
-    lo = __float_as_uint(g - __uint_as_float(hi));
+// Split (g0, g1) into hi (mantissa truncated to the 10 bits a TF32 operand
+// keeps) and lo = g - hi (exact in FP32; the tensor core uses its leading 10
+// bits).
+__device__ __forceinline__ void split_tf32(float g0, float g1, uint32_t& hi0, uint32_t& hi1, uint32_t& lo0,
+                                           uint32_t& lo1) {
+    hi0 = __float_as_uint(g0) & 0xffffe000u;
+    hi1 = __float_as_uint(g1) & 0xffffe000u;
+    float l0, l1;
+    up2(f2sub(pk2(g0, g1), pk2(__uint_as_float(hi0), __uint_as_float(hi1))), l0, l1);
+    lo0 = __float_as_uint(l0);
+    lo1 = __float_as_uint(l1);
 }
 
 // Kernel value without sigma^2 from pre-scaled coordinate differences: the
@@ -197,6 +248,41 @@ __device__ __forceinline__ float gamma_scaled(float dx, float dy, float dz) {
     return 1.0f;
 }
 
+// Two kernel values from packed pre-scaled differences (dx0, dx1), ...
+template <int KIND>
+__device__ __forceinline__ void gamma2(uint64_t dx, uint64_t dy, uint64_t dz, float& g0, float& g1) {
+    if (KIND == KL_KERNEL_EXP_SEP) {
+        float x0, x1, y0, y1, z0, z1;
+        up2(dx, x0, x1);
+        up2(dy, y0, y1);
+        up2(dz, z0, z1);
+        g0 = ex2_approx(-(fabsf(x0) + fabsf(y0) + fabsf(z0)));
+        g1 = ex2_approx(-(fabsf(x1) + fabsf(y1) + fabsf(z1)));
+        return;
+    }
+    if (KIND == KL_KERNEL_CONST) {
+        g0 = g1 = 1.0f;
+        return;
+    }
+    float r0, r1;
+    up2(f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx))), r0, r1);
+    if (KIND == KL_KERNEL_GAUSS) {
+        g0 = ex2_approx(-r0);
+        g1 = ex2_approx(-r1);
+        return;
+    }
+    r0 = sqrt_approx(r0);
+    r1 = sqrt_approx(r1);
+    if (KIND == KL_KERNEL_EXP) {
+        g0 = ex2_approx(-r0);
+        g1 = ex2_approx(-r1);
+        return;
+    }
+    // Matern-3/2: a r = r' ln 2 with r' = a log2(e) r
+    g0 = fmaf(0.69314718055994531f, r0, 1.0f) * ex2_approx(-r0);
+    g1 = fmaf(0.69314718055994531f, r1, 1.0f) * ex2_approx(-r1);
+}
+
 // Coordinate scale c of gamma_scaled: the argument a r^2 log2(e) (Gaussian) or
 // a r log2(e) (exponentials, Matern) becomes |c x - c y|^2 or |c x - c y|.
 float coord_scale(const KernelSpec& ks) {
@@ -206,11 +292,11 @@ float coord_scale(const KernelSpec& ks) {
     return float(ks.a * l2e);
 }
 
-// Depth of the shared-memory stage ring: as many stages as fit in ~100 KB
-// (two CTAs per SM), at most 16, at least the TMEM ring depth.
+// Depth of the shared-memory stage ring: the largest power of two (16 at
+// most, the TMEM ring depth at least) whose stages fit in ~100 KB (two CTAs
+// per SM). Powers of two keep the ring arithmetic to shifts and masks.
 __host__ __device__ constexpr int smem_stages(int stage_bytes) {
-    return (99 * 1024) / stage_bytes >= 16 ? 16
-         : ((99 * 1024) / stage_bytes < kStages ? kStages : (99 * 1024) / stage_bytes);
+    return (99 * 1024) / stage_bytes >= 16 ? 16 : (99 * 1024) / stage_bytes >= 8 ? 8 : kStages;
 }
 
 // Byte offset of element (n, kk) inside one hi or lo image of a chunk:
@@ -229,7 +315,7 @@ __host__ __device__ inline uint32_t img_offset(int n, int kk, int np, int esize)
 __global__ void tc_convert_kernel(const double* __restrict__ X, int64_t ldx, int64_t S, int c0, int kc,
                                   int np, int kchunk, bool tf32, float cscale, const float* __restrict__ sx,
                                   const float* __restrict__ sy, const float* __restrict__ sz,
-                                  float4* __restrict__ src4, uint8_t* __restrict__ img, int64_t nchunks) {
+                                  float* __restrict__ srcc, uint8_t* __restrict__ img, int64_t nchunks) {
     const int esize = tf32 ? 4 : 2;
     const int64_t img_bytes = int64_t(np) * kchunk * esize;  // one of hi / lo
     const int64_t total = nchunks * kchunk * np;
@@ -253,9 +339,13 @@ __global__ void tc_convert_kernel(const double* __restrict__ X, int64_t ldx, int
             *reinterpret_cast<__nv_bfloat16*>(base + off) = h;
             *reinterpret_cast<__nv_bfloat16*>(base + img_bytes + off) = l;
         }
-        if (n == 0)
-            src4[s] = (s < S) ? make_float4(cscale * sx[s], cscale * sy[s], cscale * sz[s], 0.f)
-                              : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (n == 0) {
+            // chunk-wise structure of arrays: x[kchunk], y[kchunk], z[kchunk]
+            float* c = srcc + ch * 3 * kchunk + kk;
+            c[0] = s < S ? cscale * sx[s] : 0.f;
+            c[kchunk] = s < S ? cscale * sy[s] : 0.f;
+            c[2 * kchunk] = s < S ? cscale * sz[s] : 0.f;
+        }
     }
 }
 
@@ -299,15 +389,19 @@ __device__ __forceinline__ Unit unit_of(int64_t u, int splits, int64_t nchunks, 
 template <int KIND, bool TF32, int NP>
 __global__ void __launch_bounds__(kThreads, 2)
 pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const float* __restrict__ tz,
-               int64_t T, const float4* __restrict__ src4, const uint8_t* __restrict__ img,
+               int64_t T, const float* __restrict__ srcc, const uint8_t* __restrict__ img,
                int64_t nchunks, int cps, int splits, int64_t nunits, float cscale,
-               double* __restrict__ part, int k_total, int c0, int kc, int* __restrict__ err) {
+               float2* __restrict__ part, int k_total, int c0, int kc, int* __restrict__ err) {
     constexpr int ESIZE = TF32 ? 4 : 2;
     constexpr int KC = TF32 ? 16 : 32;                  // sources per chunk (16 TMEM columns)
     constexpr int IMG = NP * KC * ESIZE;                // bytes of one of hi / lo
-    constexpr int STAGE_BYTES = 2 * IMG + KC * 16;      // hi, lo, coordinates
+    constexpr int STAGE_BYTES = 2 * IMG + KC * 12;      // hi, lo, coordinates x[KC] y[KC] z[KC]
     constexpr int SSTAGES = smem_stages(STAGE_BYTES);   // shared-memory ring (>= kStages)
     constexpr uint32_t IDESC = instr_desc(NP, TF32);
+    constexpr bool kSum = TmemLayout<NP>::kSum;
+    constexpr int kDStride = TmemLayout<NP>::kDStride;
+    constexpr int kSBase = TmemLayout<NP>::kSBase;
+    constexpr int kAColBase = TmemLayout<NP>::kAColBase;
 
     extern __shared__ __align__(1024) uint8_t smem[];
     // loaded/sempty: shared-memory ring (bulk copies ahead of use);
@@ -352,71 +446,114 @@ pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const
         const int ptid = tid & 127;
         const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
         bool ok = true;
-        int64_t jbase = 0;   // chunks of earlier units (stage ring position)
-        int64_t gbase = 0;   // accumulator groups of earlier units
+        uint32_t jbase = 0;  // chunks of earlier units (stage ring position)
+        uint32_t gbase = 0;  // accumulator groups of earlier units
         for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
             const Unit un = unit_of(u, splits, nchunks, cps);
             const int64_t t = un.tile * 128 + ptid;
             const float px = t < T ? cscale * tx[t] : 0.f;
             const float py = t < T ? cscale * ty[t] : 0.f;
             const float pz = t < T ? cscale * tz[t] : 0.f;
-            double* prow = part + (int64_t(un.split) * k_total + c0) * T + t;
+            const uint64_t ppx = pk2(px, px), ppy = pk2(py, py), ppz = pk2(pz, pz);
+            float2* prow = part + (int64_t(un.split) * k_total + c0) * T + t;
             const int ngroups = (un.nloc + kGroup - 1) / kGroup;
             int flushed = 0;
-            // warpgroup 0 adds the finished accumulator of local group g into
-            // this unit's FP64 partial sums (rows owned by this thread)
-            auto flush = [&](int g) {
-                const int64_t gg = gbase + g;
+            // Warpgroup 0 folds the finished accumulator of local group g into
+            // the unit's running sums (rows owned by this thread) as FP32
+            // (hi, lo) pairs: an error-free two-sum of hi and the group's sum,
+            // its error added into lo (about 48 significant bits at FP32
+            // instruction cost). For N <= 32 the running sums stay in tensor
+            // memory and the last group writes them to the partial-sum array;
+            // otherwise every group updates that array in global memory.
+            auto flush = [&](int g, bool last) {
+                const uint32_t gg = gbase + uint32_t(g);
                 const bool got = ok && warp_wait(&dfull_bar[gg & 1], uint32_t((gg >> 1) & 1));
                 if (!got) ok = false;
                 tc_fence_after();
-                uint32_t v[16];
-                const uint32_t dcol = uint32_t((gg & 1) * kDCols);
+                const uint32_t dcol = uint32_t((gg & 1) * kDStride);
 #pragma unroll 1
-                for (int cb = 0; cb < NP; cb += 16) {
+                for (int cb = 0; cb < NP; cb += 8) {
+                    uint32_t v[8], h[8], l[8];
                     __syncwarp();
-                    tmem_ld16(tmem + lane_base + dcol + uint32_t(cb), v);
+                    tmem_ld8(tmem + lane_base + dcol + uint32_t(cb), v);
+                    if (kSum && g > 0) {
+                        tmem_ld8(tmem + lane_base + uint32_t(kSBase + cb), h);
+                        tmem_ld8(tmem + lane_base + uint32_t(kSBase + NP + cb), l);
+                    }
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (got && t < T) {
 #pragma unroll
-                        for (int q = 0; q < 16; ++q) {
-                            const int c = cb + q;
-                            if (c < kc) {
-                                const double x = double(__uint_as_float(v[q]));
-                                prow[int64_t(c) * T] = (g == 0) ? x : prow[int64_t(c) * T] + x;
+                    for (int q = 0; q < 8; ++q) {
+                        const float x = __uint_as_float(v[q]);
+                        float hs = x, ls = 0.f;
+                        if (kSum) {
+                            if (g > 0) {
+                                const float o = __uint_as_float(h[q]);
+                                hs = __fadd_rn(o, x);
+                                const float bb = __fsub_rn(hs, o);
+                                const float er = __fadd_rn(__fsub_rn(o, __fsub_rn(hs, bb)), __fsub_rn(x, bb));
+                                ls = __fadd_rn(__uint_as_float(l[q]), er);
                             }
+                        } else if (g > 0 && got && t < T && cb + q < kc) {
+                            const float2 o = prow[int64_t(cb + q) * T];
+                            hs = __fadd_rn(o.x, x);
+                            const float bb = __fsub_rn(hs, o.x);
+                            const float er = __fadd_rn(__fsub_rn(o.x, __fsub_rn(hs, bb)), __fsub_rn(x, bb));
+                            ls = __fadd_rn(o.y, er);
                         }
+                        h[q] = __float_as_uint(hs);
+                        l[q] = __float_as_uint(ls);
+                    }
+                    if (kSum && !last) {
+                        tmem_st8(tmem + lane_base + uint32_t(kSBase + cb), h);
+                        tmem_st8(tmem + lane_base + uint32_t(kSBase + NP + cb), l);
+                    } else if (got && t < T) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            if (cb + q < kc)
+                                prow[int64_t(cb + q) * T] = make_float2(__uint_as_float(h[q]), __uint_as_float(l[q]));
                     }
                 }
+                if (kSum && !last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
                 mbar_arrive(&dfree_bar[gg & 1]);
             };
             for (int jl = wg; jl < un.nloc; jl += 2) {
                 if (wg == 0) {
-                    while (ok && flushed < jl / kGroup) flush(flushed++);
+                    // group g is folded kFlushLag chunks after it ends, when
+                    // the tensor core has long finished it (never the last
+                    // group of the unit here)
+                    while (ok && jl >= kFlushLag && flushed < (jl - kFlushLag) / kGroup) {
+                        flush(flushed, false);
+                        ++flushed;
+                    }
                     if (!ok) break;
                 }
-                const int64_t jg = jbase + jl;
+                const uint32_t jg = jbase + uint32_t(jl);
                 const int ss = int(jg % SSTAGES), s = int(jg % kStages);
                 if (!warp_wait(&loaded_bar[ss], uint32_t((jg / SSTAGES) & 1))) { ok = false; break; }
                 if (jg >= kStages && !warp_wait(&tfree_bar[s], uint32_t(((jg / kStages) - 1) & 1))) { ok = false; break; }
-                const float4* sc = reinterpret_cast<const float4*>(smem + ss * STAGE_BYTES + 2 * IMG);
+                const float* cx = reinterpret_cast<const float*>(smem + ss * STAGE_BYTES + 2 * IMG);
                 const uint32_t acol = uint32_t(kAColBase + s * kAColsPerStage);
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
+                    // 16 (BF16) or 8 (TF32) sources: four per 16-byte load of
+                    // each coordinate, differences and squares two at a time
                     uint32_t hi[8], lo[8];
-                    if (TF32) {
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const float4 y = sc[8 * half + q];
-                            split_tf32(gamma_scaled<KIND>(px - y.x, py - y.y, pz - y.z), hi[q], lo[q]);
-                        }
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const float4 y0 = sc[16 * half + 2 * q], y1 = sc[16 * half + 2 * q + 1];
-                            split_bf16(gamma_scaled<KIND>(px - y0.x, py - y0.y, pz - y0.z),
-                                       gamma_scaled<KIND>(px - y1.x, py - y1.y, pz - y1.z), hi[q], lo[q]);
+                    for (int q4 = 0; q4 < (TF32 ? 2 : 4); ++q4) {
+                        const int j0 = (KC / 2) * half + 4 * q4;
+                        const ulonglong2 xv = *reinterpret_cast<const ulonglong2*>(cx + j0);
+                        const ulonglong2 yv = *reinterpret_cast<const ulonglong2*>(cx + KC + j0);
+                        const ulonglong2 zv = *reinterpret_cast<const ulonglong2*>(cx + 2 * KC + j0);
+                        float g0, g1, g2, g3;
+                        gamma2<KIND>(f2sub(ppx, xv.x), f2sub(ppy, yv.x), f2sub(ppz, zv.x), g0, g1);
+                        gamma2<KIND>(f2sub(ppx, xv.y), f2sub(ppy, yv.y), f2sub(ppz, zv.y), g2, g3);
+                        if (TF32) {
+                            split_tf32(g0, g1, hi[4 * q4], hi[4 * q4 + 1], lo[4 * q4], lo[4 * q4 + 1]);
+                            split_tf32(g2, g3, hi[4 * q4 + 2], hi[4 * q4 + 3], lo[4 * q4 + 2], lo[4 * q4 + 3]);
+                        } else {
+                            split_bf16(g0, g1, hi[2 * q4], lo[2 * q4]);
+                            split_bf16(g2, g3, hi[2 * q4 + 1], lo[2 * q4 + 1]);
                         }
                     }
                     __syncwarp();
@@ -428,7 +565,10 @@ pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const
                 mbar_arrive(&full_bar[s]);
             }
             if (wg == 0) {
-                while (ok && flushed < ngroups) flush(flushed++);
+                while (ok && flushed < ngroups) {
+                    flush(flushed, flushed == ngroups - 1);
+                    ++flushed;
+                }
             }
             jbase += un.nloc;
             gbase += ngroups;
@@ -438,15 +578,15 @@ pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             bool ok = true;
-            int64_t jbase = 0, gbase = 0;
+            uint32_t jbase = 0, gbase = 0;
             for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
                 const Unit un = unit_of(u, splits, nchunks, cps);
                 for (int jl = 0; jl < un.nloc; ++jl) {
-                    const int64_t jg = jbase + jl;
+                    const uint32_t jg = jbase + uint32_t(jl);
                     const int s = int(jg % kStages), ss = int(jg % SSTAGES);
-                    const int64_t gg = gbase + jl / kGroup;
+                    const uint32_t gg = gbase + uint32_t(jl / kGroup);
                     const bool first = (jl % kGroup) == 0;
-                    const uint32_t d_tmem = tmem + uint32_t((gg & 1) * kDCols);
+                    const uint32_t d_tmem = tmem + uint32_t((gg & 1) * kDStride);
                     if (first && gg >= 2 && !mbar_wait(&dfree_bar[gg & 1], uint32_t(((gg >> 1) - 1) & 1))) { ok = false; break; }
                     if (!mbar_wait(&full_bar[s], uint32_t((jg / kStages) & 1))) { ok = false; break; }
                     tc_fence_after();
@@ -493,7 +633,7 @@ pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const
                     const int64_t ch = un.c0 + jl;
                     mbar_arrive_expect_tx(&loaded_bar[ss], uint32_t(STAGE_BYTES));
                     bulk_g2s(st, img + ch * int64_t(2 * IMG), uint32_t(2 * IMG), &loaded_bar[ss]);
-                    bulk_g2s(st + 2 * IMG, src4 + ch * KC, uint32_t(KC * 16), &loaded_bar[ss]);
+                    bulk_g2s(st + 2 * IMG, srcc + ch * 3 * KC, uint32_t(KC * 12), &loaded_bar[ss]);
                 }
                 jbase += un.nloc;
             }
@@ -515,11 +655,11 @@ pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const
 }
 
 template <int KIND, bool TF32, int NP>
-cudaError_t launch_np(const TcArgs& a, int c0, int kc, const float4* src4, const uint8_t* img,
-                      int64_t nchunks, int cps, int splits, double* part, int* err, cudaStream_t s) {
+cudaError_t launch_np(const TcArgs& a, int c0, int kc, const float* srcc, const uint8_t* img,
+                      int64_t nchunks, int cps, int splits, float2* part, int* err, cudaStream_t s) {
     constexpr int ESIZE = TF32 ? 4 : 2;
     constexpr int KC = TF32 ? 16 : 32;
-    constexpr int STAGE_BYTES = 2 * NP * KC * ESIZE + KC * 16;
+    constexpr int STAGE_BYTES = 2 * NP * KC * ESIZE + KC * 12;
     // at least ~100 KB so that no more than two CTAs share an SM (256 TMEM
     // columns each)
     const int smem = std::max(smem_stages(STAGE_BYTES) * STAGE_BYTES + 1024, 100 * 1024);
@@ -529,31 +669,50 @@ cudaError_t launch_np(const TcArgs& a, int c0, int kc, const float4* src4, const
     const int64_t tiles = (a.T + 127) / 128;
     const int64_t nunits = tiles * splits;
     const int64_t grid = std::min<int64_t>(nunits, 2LL * a.sm_count);
-    kern<<<unsigned(grid), kThreads, smem, s>>>(a.tx, a.ty, a.tz, a.T, src4, img, nchunks, cps, splits, nunits,
+    kern<<<unsigned(grid), kThreads, smem, s>>>(a.tx, a.ty, a.tz, a.T, srcc, img, nchunks, cps, splits, nunits,
                                                 coord_scale(a.ks), part, a.k, c0, kc, err);
     return cudaGetLastError();
 }
 
 template <int KIND, bool TF32>
-cudaError_t launch_kind_tc(const TcArgs& a, int c0, int kc, int np, const float4* src4, const uint8_t* img,
-                           int64_t nchunks, int cps, int splits, double* part, int* err, cudaStream_t s) {
+cudaError_t launch_kind_tc(const TcArgs& a, int c0, int kc, int np, const float* srcc, const uint8_t* img,
+                           int64_t nchunks, int cps, int splits, float2* part, int* err, cudaStream_t s) {
     switch (np) {
-        case 16: return launch_np<KIND, TF32, 16>(a, c0, kc, src4, img, nchunks, cps, splits, part, err, s);
-        case 32: return launch_np<KIND, TF32, 32>(a, c0, kc, src4, img, nchunks, cps, splits, part, err, s);
-        case 48: return launch_np<KIND, TF32, 48>(a, c0, kc, src4, img, nchunks, cps, splits, part, err, s);
-        default: return launch_np<KIND, TF32, 64>(a, c0, kc, src4, img, nchunks, cps, splits, part, err, s);
+        case 16: return launch_np<KIND, TF32, 16>(a, c0, kc, srcc, img, nchunks, cps, splits, part, err, s);
+        case 32: return launch_np<KIND, TF32, 32>(a, c0, kc, srcc, img, nchunks, cps, splits, part, err, s);
+        case 48: return launch_np<KIND, TF32, 48>(a, c0, kc, srcc, img, nchunks, cps, splits, part, err, s);
+        default: return launch_np<KIND, TF32, 64>(a, c0, kc, srcc, img, nchunks, cps, splits, part, err, s);
     }
 }
 
 template <bool TF32>
-cudaError_t launch_tc(const TcArgs& a, int c0, int kc, int np, const float4* src4, const uint8_t* img,
-                      int64_t nchunks, int cps, int splits, double* part, int* err, cudaStream_t s) {
+cudaError_t launch_tc(const TcArgs& a, int c0, int kc, int np, const float* srcc, const uint8_t* img,
+                      int64_t nchunks, int cps, int splits, float2* part, int* err, cudaStream_t s) {
     switch (a.ks.kind) {
-        case KL_KERNEL_GAUSS: return launch_kind_tc<KL_KERNEL_GAUSS, TF32>(a, c0, kc, np, src4, img, nchunks, cps, splits, part, err, s);
-        case KL_KERNEL_EXP_SEP: return launch_kind_tc<KL_KERNEL_EXP_SEP, TF32>(a, c0, kc, np, src4, img, nchunks, cps, splits, part, err, s);
-        case KL_KERNEL_EXP: return launch_kind_tc<KL_KERNEL_EXP, TF32>(a, c0, kc, np, src4, img, nchunks, cps, splits, part, err, s);
-        case KL_KERNEL_MATERN32: return launch_kind_tc<KL_KERNEL_MATERN32, TF32>(a, c0, kc, np, src4, img, nchunks, cps, splits, part, err, s);
-        default: return launch_kind_tc<KL_KERNEL_CONST, TF32>(a, c0, kc, np, src4, img, nchunks, cps, splits, part, err, s);
+        case KL_KERNEL_GAUSS: return launch_kind_tc<KL_KERNEL_GAUSS, TF32>(a, c0, kc, np, srcc, img, nchunks, cps, splits, part, err, s);
+        case KL_KERNEL_EXP_SEP: return launch_kind_tc<KL_KERNEL_EXP_SEP, TF32>(a, c0, kc, np, srcc, img, nchunks, cps, splits, part, err, s);
+        case KL_KERNEL_EXP: return launch_kind_tc<KL_KERNEL_EXP, TF32>(a, c0, kc, np, srcc, img, nchunks, cps, splits, part, err, s);
+        case KL_KERNEL_MATERN32: return launch_kind_tc<KL_KERNEL_MATERN32, TF32>(a, c0, kc, np, srcc, img, nchunks, cps, splits, part, err, s);
+        default: return launch_kind_tc<KL_KERNEL_CONST, TF32>(a, c0, kc, np, srcc, img, nchunks, cps, splits, part, err, s);
+    }
+}
+
+// W = sigma^2 * post * sum over source splits of the (hi, lo) partial sums,
+// in a fixed order (FP64).
+__global__ void tc_reduce_kernel(const float2* __restrict__ part, int splits, int64_t T, int k, double sigma2,
+                                 const double* __restrict__ post, double* __restrict__ Y, int64_t ldy) {
+    const int64_t total = T * k;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t c = i / T, t = i - c * T;
+        double s = 0.0;
+        for (int sp = 0; sp < splits; ++sp) {
+            const float2 v = part[(int64_t(sp) * k + c) * T + t];
+            s += double(v.x) + double(v.y);
+        }
+        s *= sigma2;
+        if (post) s *= post[t];
+        Y[c * ldy + t] = s;
     }
 }
 
@@ -585,7 +744,7 @@ TcPlan plan(int64_t T, int64_t S, int k, int sm_count, bool tf32) {
     p.splits = int((p.nchunks + p.cps - 1) / p.cps);
     const int esize = tf32 ? 4 : 2;
     p.img_doubles = (p.nchunks * 2 * p.np_max * p.kchunk * esize + 7) / 8;
-    p.src_doubles = p.nchunks * p.kchunk * 2;  // float4 = 2 doubles
+    p.src_doubles = (p.nchunks * p.kchunk * 3 + 3) / 4 * 2;  // 3 floats per source, 16-byte multiple
     p.part_doubles = int64_t(p.splits) * k * T;
     return p;
 }
@@ -604,9 +763,9 @@ cudaError_t launch_pair_tc(const TcArgs& a, cudaStream_t s, int* launched) {
     const TcPlan p = plan(a.T, a.S, a.k, a.sm_count, a.tf32);
     if (p.img_doubles + p.src_doubles + p.part_doubles + 64 > a.scratch_len) return cudaErrorInvalidValue;
     uint8_t* img = reinterpret_cast<uint8_t*>(a.scratch);
-    float4* src4 = reinterpret_cast<float4*>(a.scratch + p.img_doubles);
-    double* part = a.scratch + p.img_doubles + p.src_doubles;
-    int* err = reinterpret_cast<int*>(part + p.part_doubles);
+    float* srcc = reinterpret_cast<float*>(a.scratch + p.img_doubles);
+    float2* part = reinterpret_cast<float2*>(a.scratch + p.img_doubles + p.src_doubles);
+    int* err = reinterpret_cast<int*>(a.scratch + p.img_doubles + p.src_doubles + p.part_doubles);
     cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     for (int c0 = 0; c0 < a.k; c0 += 64) {
@@ -615,17 +774,21 @@ cudaError_t launch_pair_tc(const TcArgs& a, cudaStream_t s, int* launched) {
         const int64_t total = p.nchunks * p.kchunk * np;
         const int g = int(std::min<int64_t>((total + 255) / 256, 152 * 64));
         tc_convert_kernel<<<g, 256, 0, s>>>(a.X, a.ldx, a.S, c0, kc, np, p.kchunk, a.tf32, coord_scale(a.ks),
-                                            a.sx, a.sy, a.sz, src4, img, p.nchunks);
+                                            a.sx, a.sy, a.sz, srcc, img, p.nchunks);
         ++*launched;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        e = a.tf32 ? launch_tc<true>(a, c0, kc, np, src4, img, p.nchunks, p.cps, p.splits, part, err, s)
-                   : launch_tc<false>(a, c0, kc, np, src4, img, p.nchunks, p.cps, p.splits, part, err, s);
+        e = a.tf32 ? launch_tc<true>(a, c0, kc, np, srcc, img, p.nchunks, p.cps, p.splits, part, err, s)
+                   : launch_tc<false>(a, c0, kc, np, srcc, img, p.nchunks, p.cps, p.splits, part, err, s);
         ++*launched;
         if (e != cudaSuccess) return e;
     }
-    e = launch_pair_reduce(part, p.splits, a.T, a.k, a.ks.sigma2, a.post, a.Y, a.ldy, s);
-    ++*launched;
-    return e;
+    {
+        const int64_t total = a.T * a.k;
+        const int g = int(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 8)));
+        tc_reduce_kernel<<<g, 256, 0, s>>>(part, p.splits, a.T, a.k, a.ks.sigma2, a.post, a.Y, a.ldy);
+        ++*launched;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace kl
