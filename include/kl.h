@@ -240,6 +240,77 @@ int kl_pairwise_noalloc(int kernel, double sigma, double L, const double* tgt, i
                         const double* src, int64_t S, const double* X, int64_t ldx, double* Y,
                         int64_t ldy, int k, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Memory estimate (host only, no GPU needed)
+ * ------------------------------------------------------------------------
+ * Upper estimate of the device bytes a handle with these parameters holds
+ * while kl_eigs(M) runs (tables, point sets, operator workspaces, pairwise
+ * scratch for block_k vectors, eigensolver workspace). Used by the serving
+ * loop to admit requests by HBM budget. KL_ERR_ARG for invalid parameters. */
+int kl_estimate_bytes(const kl_params* params, int M, int64_t* bytes);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of K-L solves on one GPU
+ * ------------------------------------------------------------------------
+ * No paper passage: the paper solves one problem at a time on one CPU core
+ * (Sec. 4). A server owns max_slots worker threads. A submitted request waits
+ * in a FIFO queue until a slot is free and its kl_estimate_bytes fits in what
+ * is left of hbm_budget_bytes (the first 8 queued requests are scanned, so a
+ * large request does not block smaller ones behind it indefinitely: it keeps
+ * its place and is admitted as soon as memory frees up); it then gets its own
+ * handle, stream and device state (tables, Krylov basis) for the whole solve,
+ * and is freed when it completes. While several solves run, the tensor-core
+ * pairwise products of all of them that are ready within batch_window_us go
+ * into ONE persistent kernel launch (uneven instances: different meshes,
+ * degrees, kernels; grouped by precision and block width). The rest of each
+ * solve (sum factorisation, orthogonalisation, Rayleigh-Ritz) runs on its own
+ * stream and overlaps on the device. FP64/FP32 requests run unbatched. */
+typedef struct kl_server kl_server;
+
+typedef struct kl_serve_config {
+    int64_t hbm_budget_bytes; /* 0: 80% of the free device memory at open    */
+    int max_slots;            /* concurrent solves, 1..64 (0: 8)               */
+    int batch_window_us;      /* wait for more ready products (0: 300)        */
+} kl_serve_config;
+
+typedef struct kl_serve_result {
+    int64_t request_id;
+    int status;          /* kl_eigs status (KL_OK, KL_WARN_COMPLEX, ...)  */
+    int M;
+    int applies, restarts;
+    double max_resid;
+    double queue_ms;     /* submit -> admitted                           */
+    double solve_ms;     /* admitted -> finished (create + eigs + free)  */
+    double latency_ms;   /* submit -> finished                           */
+    int64_t est_bytes;   /* admission estimate                           */
+} kl_serve_result;
+
+typedef struct kl_serve_stats {
+    long long submitted, completed;
+    long long batches;           /* batched tensor-core launches           */
+    long long batched_products;  /* products (instances) in those launches */
+    int max_batch;               /* most instances in one launch           */
+    int max_concurrent;          /* most solves admitted at once           */
+    int64_t peak_est_bytes;      /* most admitted estimate at once         */
+    int64_t budget_bytes;
+} kl_serve_stats;
+
+/* Starts the worker threads on the current device. */
+int kl_serve_open(const kl_serve_config* cfg, kl_server** out);
+/* Queues a solve of M eigenpairs (tol as in kl_eigs). lambda_out (host, M
+ * doubles) and V_out (host, N x M, ldv >= N, or NULL) are written by the
+ * worker before the result is reported by kl_serve_poll and must stay valid
+ * until then. Thread-safe. KL_ERR_ARG for invalid parameters or a request
+ * whose estimate exceeds the whole budget. */
+int kl_serve_submit(kl_server* s, const kl_params* params, int M, double tol, int64_t request_id,
+                    double* lambda_out, double* V_out, int64_t ldv);
+/* Copies up to cap finished results (completion order) into out, *n of them;
+ * waits up to wait_ms for at least one when none is ready. */
+int kl_serve_poll(kl_server* s, kl_serve_result* out, int cap, int* n, int wait_ms);
+int kl_serve_get_stats(kl_server* s, kl_serve_stats* out);
+/* Waits for every queued and running solve, stops the workers, frees. */
+int kl_serve_close(kl_server* s);
+
 /* Last error message of the handle (h may be NULL: last kl_create error). */
 const char* kl_last_error(const kl_solver* h);
 const char* kl_status_string(int status);

@@ -17,7 +17,9 @@ __all__ = [
     "kl_default_params", "kl_create", "kl_destroy", "kl_dims", "kl_apply_A",
     "kl_apply_Zinv", "kl_apply_Aprime", "kl_eigs", "kl_profile_enable",
     "kl_profile_read", "kl_launch_count", "kl_memory", "kl_last_error",
-    "kl_status_string", "kl_measure_peaks", "kl_pairwise_noalloc", "library_path", "EXPORTED_SYMBOLS",
+    "kl_status_string", "kl_measure_peaks", "kl_pairwise_noalloc", "kl_estimate_bytes",
+    "kl_serve_config", "kl_serve_result", "kl_serve_stats", "kl_serve_open", "kl_serve_submit",
+    "kl_serve_poll", "kl_serve_get_stats", "kl_serve_close", "library_path", "EXPORTED_SYMBOLS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -37,7 +39,8 @@ EXPORTED_SYMBOLS = (
     "kl_default_params", "kl_create", "kl_destroy", "kl_dims", "kl_apply_A",
     "kl_apply_Zinv", "kl_apply_Aprime", "kl_eigs", "kl_profile_enable",
     "kl_profile_read", "kl_launch_count", "kl_memory", "kl_last_error",
-    "kl_status_string", "kl_measure_peaks", "kl_pairwise_noalloc",
+    "kl_status_string", "kl_measure_peaks", "kl_pairwise_noalloc", "kl_estimate_bytes",
+    "kl_serve_open", "kl_serve_submit", "kl_serve_poll", "kl_serve_get_stats", "kl_serve_close",
 )
 
 
@@ -88,6 +91,42 @@ class kl_kernel_stats(ctypes.Structure):
     ]
 
 
+class kl_serve_config(ctypes.Structure):
+    _fields_ = [
+        ("hbm_budget_bytes", ctypes.c_int64),
+        ("max_slots", ctypes.c_int),
+        ("batch_window_us", ctypes.c_int),
+    ]
+
+
+class kl_serve_result(ctypes.Structure):
+    _fields_ = [
+        ("request_id", ctypes.c_int64),
+        ("status", ctypes.c_int),
+        ("M", ctypes.c_int),
+        ("applies", ctypes.c_int),
+        ("restarts", ctypes.c_int),
+        ("max_resid", ctypes.c_double),
+        ("queue_ms", ctypes.c_double),
+        ("solve_ms", ctypes.c_double),
+        ("latency_ms", ctypes.c_double),
+        ("est_bytes", ctypes.c_int64),
+    ]
+
+
+class kl_serve_stats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_longlong),
+        ("completed", ctypes.c_longlong),
+        ("batches", ctypes.c_longlong),
+        ("batched_products", ctypes.c_longlong),
+        ("max_batch", ctypes.c_int),
+        ("max_concurrent", ctypes.c_int),
+        ("peak_est_bytes", ctypes.c_int64),
+        ("budget_bytes", ctypes.c_int64),
+    ]
+
+
 _lib = None
 
 
@@ -120,6 +159,12 @@ def _load():
         "kl_status_string": (ctypes.c_char_p, [c_int]),
         "kl_measure_peaks": (c_int, [ctypes.POINTER(dbl)] * 3),
         "kl_pairwise_noalloc": (c_int, [c_int, dbl, dbl, vp, i64, vp, i64, vp, i64, vp, i64, c_int, vp]),
+        "kl_estimate_bytes": (c_int, [ctypes.POINTER(kl_params), c_int, ctypes.POINTER(i64)]),
+        "kl_serve_open": (c_int, [ctypes.POINTER(kl_serve_config), ctypes.POINTER(vp)]),
+        "kl_serve_submit": (c_int, [vp, ctypes.POINTER(kl_params), c_int, dbl, i64, vp, vp, i64]),
+        "kl_serve_poll": (c_int, [vp, ctypes.POINTER(kl_serve_result), c_int, ctypes.POINTER(c_int), c_int]),
+        "kl_serve_get_stats": (c_int, [vp, ctypes.POINTER(kl_serve_stats)]),
+        "kl_serve_close": (c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -270,3 +315,48 @@ def kl_pairwise_noalloc(kernel, sigma, L, tgt, T, src, S, X, ldx, Y, ldy, k, str
     rc = _load().kl_pairwise_noalloc(int(kernel), float(sigma), float(L), _ptr(tgt), int(T), _ptr(src), int(S),
                                      _ptr(X), int(ldx), _ptr(Y), int(ldy), int(k), stream)
     return _check(None, rc)
+
+
+def kl_estimate_bytes(p, M):
+    """Device bytes a handle with params p holds while solving for M pairs
+    (host-side estimate, no GPU needed)."""
+    b = ctypes.c_int64()
+    _check(None, _load().kl_estimate_bytes(ctypes.byref(p), int(M), ctypes.byref(b)))
+    return b.value
+
+
+def kl_serve_open(hbm_budget_bytes=0, max_slots=0, batch_window_us=0):
+    cfg = kl_serve_config(int(hbm_budget_bytes), int(max_slots), int(batch_window_us))
+    s = ctypes.c_void_p()
+    _check(None, _load().kl_serve_open(ctypes.byref(cfg), ctypes.byref(s)))
+    return s
+
+
+def kl_serve_submit(s, p, M, tol, request_id, lambda_out, V_out=None, ldv=0):
+    """lambda_out / V_out: host buffers (numpy arrays or addresses) that must
+    stay alive until the result has been polled."""
+    def addr(x):
+        if x is None:
+            return None
+        if isinstance(x, int):
+            return x
+        return x.ctypes.data
+    return _check(None, _load().kl_serve_submit(s, ctypes.byref(p), int(M), float(tol), int(request_id),
+                                                addr(lambda_out), addr(V_out), int(ldv)))
+
+
+def kl_serve_poll(s, cap=64, wait_ms=0):
+    buf = (kl_serve_result * cap)()
+    n = ctypes.c_int()
+    _check(None, _load().kl_serve_poll(s, buf, int(cap), ctypes.byref(n), int(wait_ms)))
+    return [{f[0]: getattr(buf[i], f[0]) for f in kl_serve_result._fields_} for i in range(n.value)]
+
+
+def kl_serve_get_stats(s):
+    st = kl_serve_stats()
+    _check(None, _load().kl_serve_get_stats(s, ctypes.byref(st)))
+    return {f[0]: getattr(st, f[0]) for f in kl_serve_stats._fields_}
+
+
+def kl_serve_close(s):
+    return _check(None, _load().kl_serve_close(s))

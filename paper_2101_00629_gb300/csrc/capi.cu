@@ -11,9 +11,10 @@
 
 #include "handle.h"
 #include "kernels_tc.h"
+#include "serve.h"
 
 namespace {
-std::string g_create_error;
+thread_local std::string g_create_error;  // per host thread (servers create handles concurrently)
 }
 
 namespace kl {
@@ -163,14 +164,46 @@ static int pairwise(kl_solver* h, int precision, const double* U, double* W, int
         a.post = post; a.ks = ks; a.tf32 = precision == KL_MIXED_TF32;
         a.scratch = h->pair_scratch; a.scratch_len = h->pair_scratch_len;
         a.sm_count = h->sm_count;
+        a.err = h->d_err;
         ProfScope ps(h, precision == KL_MIXED_TF32 ? "pair_tc_tf32" : "pair_tc_bf16", pairs);
         int launched = 0;
-        cudaError_t e = launch_pair_tc(a, h->stream, &launched);
-        h->launches += launched;
-        if (e != cudaSuccess) return cuda_fail(h, e, "pairwise (tcgen05)");
+        if (!h->batcher) {
+            cudaError_t e = launch_pair_tc(a, h->stream, &launched);
+            h->launches += launched;
+            if (e != cudaSuccess) return cuda_fail(h, e, "pairwise (tcgen05)");
+            return KL_OK;
+        }
+        // serving: conversion here, the tcgen05 launch shared with the other
+        // running solves, the reduction back on this stream
+        BatchJob job;
+        job.tf32 = a.tf32;
+        job.err = h->d_err;
+        cudaError_t e = tc_prepare(a, h->stream, job.inst, &job.n, &job.np, &launched);
+        if (e == cudaSuccess && !h->ev_ready) e = cudaEventCreateWithFlags(&h->ev_ready, cudaEventDisableTiming);
+        if (e == cudaSuccess && !h->ev_done) e = cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming);
+        job.ready = h->ev_ready;
+        job.done = h->ev_done;
+        if (e == cudaSuccess) e = cudaEventRecord(job.ready, h->stream);
+        if (e == cudaSuccess) e = h->batcher->run(job);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, job.done, 0);
+        if (e == cudaSuccess) e = tc_finish(a, h->stream, &launched);
+        h->launches += launched + 1;
+        if (e != cudaSuccess) return cuda_fail(h, e, "pairwise (tcgen05, batched)");
         return KL_OK;
     }
     return fail(h, KL_ERR_ARG, "unknown precision");
+}
+
+int check_device_error(kl_solver* h) {
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "device error word");
+    if (v != 0) {
+        cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
+        return fail(h, KL_ERR_TIMEOUT, "a bounded wait inside a tensor-core kernel gave up");
+    }
+    return KL_OK;
 }
 
 int apply_operator(kl_solver* h, int which, int precision, const double* X, int64_t ldx, double* Y,
@@ -383,6 +416,9 @@ int kl_create(const kl_params* params, void* stream, kl_solver** out) {
     if ((e = dalloc(h, &h->d_points, npts)) != cudaSuccess) return bail(cuda_fail(h, e, "points alloc"));
     if ((e = dalloc(h, &h->d_points32, 3 * T + 3 * S)) != cudaSuccess)
         return bail(cuda_fail(h, e, "points alloc"));
+    if ((e = dalloc(h, &h->d_err, 1)) != cudaSuccess) return bail(cuda_fail(h, e, "error word alloc"));
+    if ((e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream)) != cudaSuccess)
+        return bail(cuda_fail(h, e, "error word"));
     double geo[3] = {p.geo[0], p.geo[1], p.geo[2]};
     const int* nsrc = gal ? h->Nt1 : h->Nq1;
     h->sx = h->d_points;
@@ -430,6 +466,60 @@ int kl_create(const kl_params* params, void* stream, kl_solver** out) {
     return KL_OK;
 }
 
+int kl_estimate_bytes(const kl_params* params, int M, int64_t* bytes) {
+    g_create_error.clear();
+    if (!params || !bytes) return fail(nullptr, KL_ERR_ARG, "params and bytes must not be NULL");
+    if (M < 1) return fail(nullptr, KL_ERR_ARG, "M must be >= 1");
+    std::string msg = check_params(*params);
+    if (!msg.empty()) return fail(nullptr, KL_ERR_ARG, msg);
+    kl_params p = *params;
+    if (p.block_k == 0) p.block_k = 8;
+    const bool gal = p.method == KL_GALERKIN_IBQ;
+    const bool exp_kernel = p.kernel == KL_KERNEL_EXP || p.kernel == KL_KERNEL_EXP_SEP;
+    const int icont = p.interp_continuity == -2 ? (exp_kernel ? 0 : p.degree - 1) : p.interp_continuity;
+    int64_t N = 1, Nt = 1, Nq = 1, tab = 0;
+    auto add = [&](int64_t n) { tab += (n + 3) / 4 * 4; };
+    for (int d = 0; d < 3; ++d) {
+        Dir1D q;
+        const bool present = d < p.dim;
+        const bool rational = (p.geometry == KL_GEOM_QUARTER_ANNULUS) && d == 0;
+        std::string m = setup_direction(q, present, present ? p.elems[d] : 1, p.degree, icont, rational, gal, !gal);
+        if (!m.empty()) return fail(nullptr, KL_ERR_NUMERIC, "set-up: " + m);
+        N *= q.N;
+        Nt *= q.Nt;
+        Nq *= q.nq;
+        const int64_t ns = gal ? q.Nt : q.nq;
+        for (int i = 0; i < 4; ++i) add(ns * q.N);
+        add(int64_t(q.N) * q.N);
+        add(int64_t(q.N) * q.N);
+        add(gal ? q.Nt : q.N);
+        add(ns);
+        add(ns);
+    }
+    const int64_t S = gal ? Nt : Nq, T = gal ? S : N;
+    int sm = 152;
+    int dev = 0, ndev = 0;
+    if (cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0 && cudaGetDevice(&dev) == cudaSuccess) {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) sm = prop.multiProcessorCount;
+    } else {
+        cudaGetLastError();
+    }
+    const int b = int(std::min<int64_t>(p.block_k, N));
+    const int mcap = eig_basis_cap(N, std::min<int64_t>(M, N), b);
+    // widest operator application: the final refinement of nkeep + 1 vectors
+    const int kmax = std::max(b, (M + 2 * b - 1) / b * b + 1);
+    const int64_t points = (gal ? 4 * S : 3 * T + 4 * S) + (3 * T + 3 * S + 1) / 2 + 1;
+    const int64_t ws = 3 * std::max(S, T) * int64_t(kmax);
+    const int64_t pair = std::max<int64_t>(pair_scratch_doubles(T, kmax, pair_choose_splits(T, S, sm)),
+                                           tc_scratch_doubles(T, S, kmax, sm));
+    const int64_t eig = eig_workspace_doubles(N, mcap);
+    const int64_t total = 8 * (tab + points + ws + pair + eig);
+    // allocation granularity and runtime bookkeeping
+    *bytes = total + total / 32 + (int64_t(8) << 20);
+    return KL_OK;
+}
+
 int kl_destroy(kl_solver* h) {
     if (!h) return KL_OK;
     if (h->stream || true) cudaStreamSynchronize(h->stream);
@@ -444,6 +534,9 @@ int kl_destroy(kl_solver* h) {
     for (int i = 0; i < 3; ++i) dfree(h->ws[i]);
     dfree(h->pair_scratch);
     dfree(h->eig_ws);
+    dfree(h->d_err);
+    if (h->ev_ready) cudaEventDestroy(h->ev_ready);
+    if (h->ev_done) cudaEventDestroy(h->ev_done);
     delete h;
     return KL_OK;
 }

@@ -17,6 +17,10 @@ struct kl_prof_entry {
     std::vector<double> pending_units;
 };
 
+namespace kl {
+class Batcher;
+}
+
 struct kl_solver {
     kl_params prm{};
     cudaStream_t stream = nullptr;
@@ -60,6 +64,15 @@ struct kl_solver {
     int64_t pair_scratch_len = 0;
     int pair_splits = 1;
 
+    // device word set by kernels whose bounded waits gave up (read after a
+    // synchronisation; see check_device_error)
+    int* d_err = nullptr;
+
+    // serving: tensor-core pairwise products go through this batcher (set
+    // by the server's worker; null for a stand-alone handle)
+    kl::Batcher* batcher = nullptr;
+    cudaEvent_t ev_ready = nullptr, ev_done = nullptr;
+
     // eigensolver workspaces
     int64_t eig_cap_bytes = 0;
     void* eig_ws = nullptr;
@@ -76,6 +89,12 @@ namespace kl {
 int fail(kl_solver* h, int code, const std::string& msg);
 int cuda_fail(kl_solver* h, cudaError_t e, const char* where);
 int ensure_workspace(kl_solver* h, int k);
+// Eigensolver sizing shared by kl_eigs and kl_estimate_bytes.
+int eig_basis_cap(int64_t N, int M, int b);
+int64_t eig_workspace_doubles(int64_t N, int mcap);
+// KL_ERR_TIMEOUT (and clears the word) if a kernel of this handle recorded a
+// bounded wait that gave up; synchronises the handle's stream.
+int check_device_error(kl_solver* h);
 // Operator applications on device blocks (k <= h->k_cap after ensure_workspace).
 // which: 0 = A (generalized), 1 = A' (standard form). precision: KL_* precision.
 int apply_operator(kl_solver* h, int which, int precision, const double* X, int64_t ldx,

@@ -16,6 +16,7 @@
 // of the bulge chase is a one-thread chain.
 #include <cfloat>
 #include <cmath>
+#include <mutex>
 
 #include "kl_internal.h"
 
@@ -24,6 +25,7 @@ namespace kl {
 namespace {
 
 constexpr int kEigThreads = 128;
+constexpr size_t kEigSmemLimit = 220 * 1024;  // dynamic shared memory of the largest level
 constexpr int kEigWarps = kEigThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -841,7 +843,7 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
 // Shared-memory level for an n x n problem (see the kernel).
 int eig_smem_level(int n, size_t* bytes) {
     const size_t nn = size_t(n) * n;
-    const size_t limit = 220 * 1024;
+    const size_t limit = kEigSmemLimit;
     if ((3 * nn + 9 * size_t(n)) * sizeof(double) <= limit) {
         *bytes = (3 * nn + 9 * size_t(n)) * sizeof(double);
         return 2;
@@ -859,10 +861,15 @@ cudaError_t launch_eig(const double* H, int n, double* wr, double* wi, double* V
     if (n <= 0) return cudaErrorInvalidValue;
     size_t bytes = 0;
     const int level = eig_smem_level(n, &bytes);
-    if (bytes > 0) {
-        cudaError_t e = cudaFuncSetAttribute(nonsym_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-        if (e != cudaSuccess) return e;
-    }
+    // the attribute is set once to the largest size any call uses: host
+    // threads launching concurrently must not lower it under each other
+    static std::once_flag once;
+    static cudaError_t attr_error = cudaSuccess;
+    std::call_once(once, [] {
+        attr_error = cudaFuncSetAttribute(nonsym_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          int(kEigSmemLimit));
+    });
+    if (attr_error != cudaSuccess) return attr_error;
     nonsym_eig_kernel<<<1, kEigThreads, bytes, s>>>(H, n, wr, wi, V, Q, work, status, level, sym, nvec);
     return cudaGetLastError();
 }

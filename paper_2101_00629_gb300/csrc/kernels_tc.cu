@@ -283,6 +283,24 @@ __device__ __forceinline__ void gamma2(uint64_t dx, uint64_t dy, uint64_t dz, fl
     g1 = fmaf(0.69314718055994531f, r1, 1.0f) * ex2_approx(-r1);
 }
 
+// Kernel kind chosen per work unit at run time (batched launches of several
+// problems); other values of KIND fix it at compile time.
+constexpr int kKindAny = -1;
+template <int KIND>
+__device__ __forceinline__ void gamma2_k(int kind, uint64_t dx, uint64_t dy, uint64_t dz, float& g0, float& g1) {
+    if (KIND != kKindAny) {
+        gamma2<(KIND == kKindAny ? KL_KERNEL_CONST : KIND)>(dx, dy, dz, g0, g1);
+        return;
+    }
+    switch (kind) {
+        case KL_KERNEL_GAUSS: gamma2<KL_KERNEL_GAUSS>(dx, dy, dz, g0, g1); break;
+        case KL_KERNEL_EXP_SEP: gamma2<KL_KERNEL_EXP_SEP>(dx, dy, dz, g0, g1); break;
+        case KL_KERNEL_EXP: gamma2<KL_KERNEL_EXP>(dx, dy, dz, g0, g1); break;
+        case KL_KERNEL_MATERN32: gamma2<KL_KERNEL_MATERN32>(dx, dy, dz, g0, g1); break;
+        default: gamma2<KL_KERNEL_CONST>(dx, dy, dz, g0, g1); break;
+    }
+}
+
 // Coordinate scale c of gamma_scaled: the argument a r^2 log2(e) (Gaussian) or
 // a r log2(e) (exponentials, Matern) becomes |c x - c y|^2 or |c x - c y|.
 float coord_scale(const KernelSpec& ks) {
@@ -386,12 +404,17 @@ __device__ __forceinline__ Unit unit_of(int64_t u, int splits, int64_t nchunks, 
     return r;
 }
 
+// Instance of global work unit u (units are assigned contiguously).
+__device__ __forceinline__ int inst_of(const TcBatch& b, int64_t u) {
+    int p = 0;
+    while (p + 1 < b.ninst && b.inst[p + 1].unit0 <= u) ++p;
+    return p;
+}
+
 template <int KIND, bool TF32, int NP>
 __global__ void __launch_bounds__(kThreads, 2)
-pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const float* __restrict__ tz,
-               int64_t T, const float* __restrict__ srcc, const uint8_t* __restrict__ img,
-               int64_t nchunks, int cps, int splits, int64_t nunits, float cscale,
-               float2* __restrict__ part, int k_total, int c0, int kc, int* __restrict__ err) {
+pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
+    const int64_t nunits = batch.nunits;
     constexpr int ESIZE = TF32 ? 4 : 2;
     constexpr int KC = TF32 ? 16 : 32;                  // sources per chunk (16 TMEM columns)
     constexpr int IMG = NP * KC * ESIZE;                // bytes of one of hi / lo
@@ -449,13 +472,19 @@ pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const
         uint32_t jbase = 0;  // chunks of earlier units (stage ring position)
         uint32_t gbase = 0;  // accumulator groups of earlier units
         for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
-            const Unit un = unit_of(u, splits, nchunks, cps);
+            const TcInstance& I = batch.inst[inst_of(batch, u)];
+            const Unit un = unit_of(u - I.unit0, I.splits, I.nchunks, I.cps);
+            const int64_t T = I.T;
+            const float cscale = I.cscale;
+            const int kc = I.kc;
+            const float *tx = I.tx, *ty = I.ty, *tz = I.tz;
             const int64_t t = un.tile * 128 + ptid;
             const float px = t < T ? cscale * tx[t] : 0.f;
             const float py = t < T ? cscale * ty[t] : 0.f;
             const float pz = t < T ? cscale * tz[t] : 0.f;
             const uint64_t ppx = pk2(px, px), ppy = pk2(py, py), ppz = pk2(pz, pz);
-            float2* prow = part + (int64_t(un.split) * k_total + c0) * T + t;
+            float2* prow = I.part + (int64_t(un.split) * I.k_total + I.c0) * T + t;
+            const int kind = I.kind;
             const int ngroups = (un.nloc + kGroup - 1) / kGroup;
             int flushed = 0;
             // Warpgroup 0 folds the finished accumulator of local group g into
@@ -546,8 +575,8 @@ pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const
                         const ulonglong2 yv = *reinterpret_cast<const ulonglong2*>(cx + KC + j0);
                         const ulonglong2 zv = *reinterpret_cast<const ulonglong2*>(cx + 2 * KC + j0);
                         float g0, g1, g2, g3;
-                        gamma2<KIND>(f2sub(ppx, xv.x), f2sub(ppy, yv.x), f2sub(ppz, zv.x), g0, g1);
-                        gamma2<KIND>(f2sub(ppx, xv.y), f2sub(ppy, yv.y), f2sub(ppz, zv.y), g2, g3);
+                        gamma2_k<KIND>(kind, f2sub(ppx, xv.x), f2sub(ppy, yv.x), f2sub(ppz, zv.x), g0, g1);
+                        gamma2_k<KIND>(kind, f2sub(ppx, xv.y), f2sub(ppy, yv.y), f2sub(ppz, zv.y), g2, g3);
                         if (TF32) {
                             split_tf32(g0, g1, hi[4 * q4], hi[4 * q4 + 1], lo[4 * q4], lo[4 * q4 + 1]);
                             split_tf32(g2, g3, hi[4 * q4 + 2], hi[4 * q4 + 3], lo[4 * q4 + 2], lo[4 * q4 + 3]);
@@ -580,7 +609,8 @@ pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const
             bool ok = true;
             uint32_t jbase = 0, gbase = 0;
             for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
-                const Unit un = unit_of(u, splits, nchunks, cps);
+                const TcInstance& I = batch.inst[inst_of(batch, u)];
+                const Unit un = unit_of(u - I.unit0, I.splits, I.nchunks, I.cps);
                 for (int jl = 0; jl < un.nloc; ++jl) {
                     const uint32_t jg = jbase + uint32_t(jl);
                     const int s = int(jg % kStages), ss = int(jg % SSTAGES);
@@ -622,7 +652,10 @@ pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const
             bool ok = true;
             int64_t jbase = 0, issued = 0;
             for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
-                const Unit un = unit_of(u, splits, nchunks, cps);
+                const TcInstance& I = batch.inst[inst_of(batch, u)];
+                const Unit un = unit_of(u - I.unit0, I.splits, I.nchunks, I.cps);
+                const uint8_t* img = I.img;
+                const float* srcc = I.srcc;
                 for (int jl = 0; jl < un.nloc; ++jl) {
                     const int64_t jg = jbase + jl;
                     const int ss = int(jg % SSTAGES);
@@ -655,8 +688,7 @@ pair_tc_kernel(const float* __restrict__ tx, const float* __restrict__ ty, const
 }
 
 template <int KIND, bool TF32, int NP>
-cudaError_t launch_np(const TcArgs& a, int c0, int kc, const float* srcc, const uint8_t* img,
-                      int64_t nchunks, int cps, int splits, float2* part, int* err, cudaStream_t s) {
+cudaError_t launch_batch_np(const TcBatch& b, int sm_count, int* err, cudaStream_t s) {
     constexpr int ESIZE = TF32 ? 4 : 2;
     constexpr int KC = TF32 ? 16 : 32;
     constexpr int STAGE_BYTES = 2 * NP * KC * ESIZE + KC * 12;
@@ -666,34 +698,33 @@ cudaError_t launch_np(const TcArgs& a, int c0, int kc, const float* srcc, const 
     auto kern = pair_tc_kernel<KIND, TF32, NP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const int64_t tiles = (a.T + 127) / 128;
-    const int64_t nunits = tiles * splits;
-    const int64_t grid = std::min<int64_t>(nunits, 2LL * a.sm_count);
-    kern<<<unsigned(grid), kThreads, smem, s>>>(a.tx, a.ty, a.tz, a.T, srcc, img, nchunks, cps, splits, nunits,
-                                                coord_scale(a.ks), part, a.k, c0, kc, err);
+    const int64_t grid = std::min<int64_t>(b.nunits, 2LL * sm_count);
+    kern<<<unsigned(grid), kThreads, smem, s>>>(b, err);
     return cudaGetLastError();
 }
 
 template <int KIND, bool TF32>
-cudaError_t launch_kind_tc(const TcArgs& a, int c0, int kc, int np, const float* srcc, const uint8_t* img,
-                           int64_t nchunks, int cps, int splits, float2* part, int* err, cudaStream_t s) {
+cudaError_t launch_batch_kind(const TcBatch& b, int np, int sm_count, int* err, cudaStream_t s) {
     switch (np) {
-        case 16: return launch_np<KIND, TF32, 16>(a, c0, kc, srcc, img, nchunks, cps, splits, part, err, s);
-        case 32: return launch_np<KIND, TF32, 32>(a, c0, kc, srcc, img, nchunks, cps, splits, part, err, s);
-        case 48: return launch_np<KIND, TF32, 48>(a, c0, kc, srcc, img, nchunks, cps, splits, part, err, s);
-        default: return launch_np<KIND, TF32, 64>(a, c0, kc, srcc, img, nchunks, cps, splits, part, err, s);
+        case 16: return launch_batch_np<KIND, TF32, 16>(b, sm_count, err, s);
+        case 32: return launch_batch_np<KIND, TF32, 32>(b, sm_count, err, s);
+        case 48: return launch_batch_np<KIND, TF32, 48>(b, sm_count, err, s);
+        default: return launch_batch_np<KIND, TF32, 64>(b, sm_count, err, s);
     }
 }
 
 template <bool TF32>
-cudaError_t launch_tc(const TcArgs& a, int c0, int kc, int np, const float* srcc, const uint8_t* img,
-                      int64_t nchunks, int cps, int splits, float2* part, int* err, cudaStream_t s) {
-    switch (a.ks.kind) {
-        case KL_KERNEL_GAUSS: return launch_kind_tc<KL_KERNEL_GAUSS, TF32>(a, c0, kc, np, srcc, img, nchunks, cps, splits, part, err, s);
-        case KL_KERNEL_EXP_SEP: return launch_kind_tc<KL_KERNEL_EXP_SEP, TF32>(a, c0, kc, np, srcc, img, nchunks, cps, splits, part, err, s);
-        case KL_KERNEL_EXP: return launch_kind_tc<KL_KERNEL_EXP, TF32>(a, c0, kc, np, srcc, img, nchunks, cps, splits, part, err, s);
-        case KL_KERNEL_MATERN32: return launch_kind_tc<KL_KERNEL_MATERN32, TF32>(a, c0, kc, np, srcc, img, nchunks, cps, splits, part, err, s);
-        default: return launch_kind_tc<KL_KERNEL_CONST, TF32>(a, c0, kc, np, srcc, img, nchunks, cps, splits, part, err, s);
+cudaError_t launch_batch_prec(const TcBatch& b, int np, int sm_count, int* err, cudaStream_t s) {
+    int kind = b.inst[0].kind;
+    for (int i = 1; i < b.ninst; ++i)
+        if (b.inst[i].kind != kind) kind = kKindAny;
+    switch (kind) {
+        case KL_KERNEL_GAUSS: return launch_batch_kind<KL_KERNEL_GAUSS, TF32>(b, np, sm_count, err, s);
+        case KL_KERNEL_EXP_SEP: return launch_batch_kind<KL_KERNEL_EXP_SEP, TF32>(b, np, sm_count, err, s);
+        case KL_KERNEL_EXP: return launch_batch_kind<KL_KERNEL_EXP, TF32>(b, np, sm_count, err, s);
+        case KL_KERNEL_MATERN32: return launch_batch_kind<KL_KERNEL_MATERN32, TF32>(b, np, sm_count, err, s);
+        case KL_KERNEL_CONST: return launch_batch_kind<KL_KERNEL_CONST, TF32>(b, np, sm_count, err, s);
+        default: return launch_batch_kind<kKindAny, TF32>(b, np, sm_count, err, s);
     }
 }
 
@@ -721,7 +752,8 @@ struct TcPlan {
     int64_t nchunks;
     int np_max;
     int splits, cps;
-    int64_t img_doubles, src_doubles, part_doubles;
+    int nblk;  // column blocks of at most 64 vectors (one instance each)
+    int64_t img_blk_doubles, img_doubles, src_doubles, part_doubles;
 };
 
 // Persistent schedule: 2 CTAs per SM walk the units (tile, source range)
@@ -743,7 +775,9 @@ TcPlan plan(int64_t T, int64_t S, int k, int sm_count, bool tf32) {
     p.cps = int((p.nchunks + want - 1) / want);
     p.splits = int((p.nchunks + p.cps - 1) / p.cps);
     const int esize = tf32 ? 4 : 2;
-    p.img_doubles = (p.nchunks * 2 * p.np_max * p.kchunk * esize + 7) / 8;
+    p.nblk = (k + 63) / 64;
+    p.img_blk_doubles = (p.nchunks * 2 * p.np_max * p.kchunk * esize + 7) / 8;
+    p.img_doubles = p.nblk * p.img_blk_doubles;
     p.src_doubles = (p.nchunks * p.kchunk * 3 + 3) / 4 * 2;  // 3 floats per source, 16-byte multiple
     p.part_doubles = int64_t(p.splits) * k * T;
     return p;
@@ -755,40 +789,84 @@ int64_t tc_scratch_doubles(int64_t T, int64_t S, int k, int sm_count) {
     const TcPlan pb = plan(T, S, k, sm_count, false), pt = plan(T, S, k, sm_count, true);
     const int64_t b = pb.img_doubles + pb.src_doubles + pb.part_doubles;
     const int64_t t = pt.img_doubles + pt.src_doubles + pt.part_doubles;
-    return std::max(b, t) + 64;
+    return std::max(b, t);
+}
+
+cudaError_t tc_prepare(const TcArgs& a, cudaStream_t s, TcInstance* out, int* n, int* np, int* launched) {
+    *n = 0;
+    const TcPlan p = plan(a.T, a.S, a.k, a.sm_count, a.tf32);
+    if (p.img_doubles + p.src_doubles + p.part_doubles > a.scratch_len) return cudaErrorInvalidValue;
+    if (p.nblk > 4) return cudaErrorInvalidValue;
+    float* srcc = reinterpret_cast<float*>(a.scratch + p.img_doubles);
+    float2* part = reinterpret_cast<float2*>(a.scratch + p.img_doubles + p.src_doubles);
+    const float cscale = coord_scale(a.ks);
+    // every column block uses the image layout of the widest one (the last
+    // block's missing columns are zero), so that they share one launch
+    *np = p.np_max;
+    for (int blk = 0; blk < p.nblk; ++blk) {
+        const int c0 = 64 * blk, kc = std::min(64, a.k - c0);
+        uint8_t* img = reinterpret_cast<uint8_t*>(a.scratch + blk * p.img_blk_doubles);
+        const int64_t total = p.nchunks * p.kchunk * p.np_max;
+        const int g = int(std::min<int64_t>((total + 255) / 256, 152 * 64));
+        tc_convert_kernel<<<g, 256, 0, s>>>(a.X, a.ldx, a.S, c0, kc, p.np_max, p.kchunk, a.tf32, cscale, a.sx,
+                                            a.sy, a.sz, srcc, img, p.nchunks);
+        ++*launched;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        TcInstance& I = out[blk];
+        I.tx = a.tx;
+        I.ty = a.ty;
+        I.tz = a.tz;
+        I.srcc = srcc;
+        I.img = img;
+        I.part = part;
+        I.T = a.T;
+        I.nchunks = p.nchunks;
+        I.unit0 = 0;
+        I.cps = p.cps;
+        I.splits = p.splits;
+        I.kind = a.ks.kind;
+        I.k_total = a.k;
+        I.c0 = c0;
+        I.kc = kc;
+        I.cscale = cscale;
+        ++*n;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t tc_launch_batch(TcBatch& b, bool tf32, int np, int sm_count, int* err, cudaStream_t s) {
+    if (b.ninst < 1 || b.ninst > kTcMaxBatch) return cudaErrorInvalidValue;
+    int64_t u = 0;
+    for (int i = 0; i < b.ninst; ++i) {
+        b.inst[i].unit0 = u;
+        u += (b.inst[i].T + 127) / 128 * b.inst[i].splits;
+    }
+    b.nunits = u;
+    if (u == 0) return cudaSuccess;
+    return tf32 ? launch_batch_prec<true>(b, np, sm_count, err, s) : launch_batch_prec<false>(b, np, sm_count, err, s);
+}
+
+cudaError_t tc_finish(const TcArgs& a, cudaStream_t s, int* launched) {
+    const TcPlan p = plan(a.T, a.S, a.k, a.sm_count, a.tf32);
+    const float2* part = reinterpret_cast<const float2*>(a.scratch + p.img_doubles + p.src_doubles);
+    const int64_t total = a.T * a.k;
+    const int g = int(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 8)));
+    tc_reduce_kernel<<<g, 256, 0, s>>>(part, p.splits, a.T, a.k, a.ks.sigma2, a.post, a.Y, a.ldy);
+    ++*launched;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pair_tc(const TcArgs& a, cudaStream_t s, int* launched) {
     *launched = 0;
-    const TcPlan p = plan(a.T, a.S, a.k, a.sm_count, a.tf32);
-    if (p.img_doubles + p.src_doubles + p.part_doubles + 64 > a.scratch_len) return cudaErrorInvalidValue;
-    uint8_t* img = reinterpret_cast<uint8_t*>(a.scratch);
-    float* srcc = reinterpret_cast<float*>(a.scratch + p.img_doubles);
-    float2* part = reinterpret_cast<float2*>(a.scratch + p.img_doubles + p.src_doubles);
-    int* err = reinterpret_cast<int*>(a.scratch + p.img_doubles + p.src_doubles + p.part_doubles);
-    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    TcBatch b;
+    int np = 16;
+    cudaError_t e = tc_prepare(a, s, b.inst, &b.ninst, &np, launched);
     if (e != cudaSuccess) return e;
-    for (int c0 = 0; c0 < a.k; c0 += 64) {
-        const int kc = std::min(64, a.k - c0);
-        const int np = std::max(16, (kc + 15) / 16 * 16);
-        const int64_t total = p.nchunks * p.kchunk * np;
-        const int g = int(std::min<int64_t>((total + 255) / 256, 152 * 64));
-        tc_convert_kernel<<<g, 256, 0, s>>>(a.X, a.ldx, a.S, c0, kc, np, p.kchunk, a.tf32, coord_scale(a.ks),
-                                            a.sx, a.sy, a.sz, srcc, img, p.nchunks);
-        ++*launched;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        e = a.tf32 ? launch_tc<true>(a, c0, kc, np, srcc, img, p.nchunks, p.cps, p.splits, part, err, s)
-                   : launch_tc<false>(a, c0, kc, np, srcc, img, p.nchunks, p.cps, p.splits, part, err, s);
-        ++*launched;
-        if (e != cudaSuccess) return e;
-    }
-    {
-        const int64_t total = a.T * a.k;
-        const int g = int(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 8)));
-        tc_reduce_kernel<<<g, 256, 0, s>>>(part, p.splits, a.T, a.k, a.ks.sigma2, a.post, a.Y, a.ldy);
-        ++*launched;
-    }
-    return cudaGetLastError();
+    e = tc_launch_batch(b, a.tf32, np, a.sm_count, a.err, s);
+    ++*launched;
+    if (e != cudaSuccess) return e;
+    return tc_finish(a, s, launched);
 }
 
 }  // namespace kl

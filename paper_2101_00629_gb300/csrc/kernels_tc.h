@@ -24,13 +24,45 @@ struct TcArgs {
     double* scratch;
     int64_t scratch_len;  // doubles
     int sm_count;
+    int* err;  // device word set when a bounded wait inside the kernel gives up
 };
 
+// One pairwise product inside a persistent launch: its target points, the
+// chunk-wise pre-scaled source coordinates and split images of X (written by
+// the conversion kernel), its (hi, lo) partial sums, and its range of work
+// units [unit0, unit0 + tiles * splits) in the launch.
+struct TcInstance {
+    const float *tx, *ty, *tz;
+    const float* srcc;
+    const uint8_t* img;
+    float2* part;
+    int64_t T, nchunks, unit0;
+    int cps, splits, kind, k_total, c0, kc;
+    float cscale;
+};
+// Instances of one launch (same precision and N rounded to 16); passed by
+// value as a kernel parameter.
+constexpr int kTcMaxBatch = 32;
+struct TcBatch {
+    TcInstance inst[kTcMaxBatch];
+    int ninst;
+    int64_t nunits;
+};
+
+// Phase 1 of a pairwise product: conversion kernels on stream s and the
+// instance descriptors (unit0 = 0) of its column blocks of at most 64
+// vectors (*n of them, <= 4). tf32/np of the descriptors in *tf32, *np.
+cudaError_t tc_prepare(const TcArgs& a, cudaStream_t s, TcInstance* out, int* n, int* np, int* launched);
+// Phase 2: one persistent launch over the instances of b (same tf32 and np),
+// units assigned contiguously in order; err: device word set on a timeout.
+cudaError_t tc_launch_batch(TcBatch& b, bool tf32, int np, int sm_count, int* err, cudaStream_t s);
+// Phase 3: reduction of the partial sums into Y on stream s.
+cudaError_t tc_finish(const TcArgs& a, cudaStream_t s, int* launched);
 // Scratch needed by launch_pair_tc for T targets and k vectors (doubles).
 int64_t tc_scratch_doubles(int64_t T, int64_t S, int k, int sm_count);
 // Enqueues the conversion, the tcgen05 kernel and the split reduction.
-// *launched receives the number of kernels launched. Returns
-// cudaErrorLaunchTimeout if a bounded wait inside the kernel gave up.
+// *launched receives the number of kernels launched. A bounded wait that gives
+// up inside the kernel sets *a.err (read by the caller after a synchronisation).
 cudaError_t launch_pair_tc(const TcArgs& a, cudaStream_t s, int* launched);
 
 // Reduction of split partials shared with the CUDA-core kernels.

@@ -181,6 +181,23 @@ int rayleigh_ritz(Ctx& c, const double* V, const double* AV, int nv, double* max
 }
 
 }  // namespace
+
+// Basis width limit of kl_eigs for M wanted pairs and block size b (<= N).
+int eig_basis_cap(int64_t N, int M, int b) {
+    b = int(std::min<int64_t>(b, N));
+    const int nkeep_full = (M + b + b - 1) / b * b;
+    const int mmax_full = std::max(2 * nkeep_full, nkeep_full + 2 * b);
+    const int mmax = int(std::min<int64_t>(mmax_full, N));
+    return int(std::min<int64_t>(int64_t(mmax) + b, N));
+}
+
+// Doubles of the eigensolver workspace for N dofs and basis width mcap.
+int64_t eig_workspace_doubles(int64_t N, int mcap) {
+    const int64_t tn_len = std::max(gemm_tn_scratch_doubles(mcap, mcap, N), int64_t(1));
+    const int64_t la = std::max(sym_eig_work_doubles(mcap), nonsym_eig_work_doubles(mcap));
+    return 4 * N * mcap + 5 * int64_t(mcap) * mcap + 8 * int64_t(mcap) + la + tn_len + (int64_t(mcap) + 2) / 2 + 64;
+}
+
 }  // namespace kl
 
 using namespace kl;
@@ -224,8 +241,7 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
     // ---- workspace (one allocation, reused across calls) ----
     const int64_t tn_len = std::max(gemm_tn_scratch_doubles(mcap, mcap, N), int64_t(1));
     const int64_t la = std::max(sym_eig_work_doubles(mcap), nonsym_eig_work_doubles(mcap));
-    const int64_t need = 4 * N * mcap + 5 * int64_t(mcap) * mcap + 8 * int64_t(mcap) + la + tn_len +
-                         (int64_t(mcap) + 2) / 2 + 64;
+    const int64_t need = eig_workspace_doubles(N, mcap);
     if (need * int64_t(sizeof(double)) > h->eig_cap_bytes) {
         cudaStreamSynchronize(h->stream);
         if (h->eig_ws) cudaFree(h->eig_ws);
@@ -416,6 +432,7 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
     }
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "kl_eigs sync");
+    if (int rc = check_device_error(h); rc != KL_OK) return rc;
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     if (info) {
         info->restarts = restarts;

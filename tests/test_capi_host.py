@@ -47,9 +47,11 @@ def test_struct_layout_matches_c(kl):
     #include <stddef.h>
     #include "kl.h"
     int main(void) {
-      printf("%zu %zu %zu %zu %zu %zu\n", sizeof(kl_params), offsetof(kl_params, sigma),
+      printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(kl_params), offsetof(kl_params, sigma),
              offsetof(kl_params, seed), sizeof(kl_solve_info), sizeof(kl_kernel_stats),
-             offsetof(kl_params, precision));
+             offsetof(kl_params, precision), sizeof(kl_serve_config), sizeof(kl_serve_result),
+             offsetof(kl_serve_result, max_resid), sizeof(kl_serve_stats),
+             offsetof(kl_serve_stats, peak_est_bytes));
       return 0;
     }
     """
@@ -62,7 +64,9 @@ def test_struct_layout_matches_c(kl):
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
     assert vals == [ctypes.sizeof(kl.kl_params), kl.kl_params.sigma.offset, kl.kl_params.seed.offset,
                     ctypes.sizeof(kl.kl_solve_info), ctypes.sizeof(kl.kl_kernel_stats),
-                    kl.kl_params.precision.offset]
+                    kl.kl_params.precision.offset, ctypes.sizeof(kl.kl_serve_config),
+                    ctypes.sizeof(kl.kl_serve_result), kl.kl_serve_result.max_resid.offset,
+                    ctypes.sizeof(kl.kl_serve_stats), kl.kl_serve_stats.peak_est_bytes.offset]
 
 
 def test_default_params_and_status_strings(kl):
@@ -106,3 +110,37 @@ def test_null_arguments(kl):
     assert lib.kl_apply_A(None, None, 0, None, 0, 1) == -1
     assert lib.kl_eigs(None, 1, 0.0, None, None, 0, 0, None, None) == -1
     assert lib.kl_launch_count(None) == 0
+    assert lib.kl_serve_submit(None, None, 1, 0.0, 0, None, None, 0) == -1
+    assert lib.kl_serve_close(None) == 0
+
+
+def _est(kl, **kw):
+    args = dict(geometry="cube", degree=2, elems=(8, 8, 8), kernel="gauss", sigma=1.0, L=0.5,
+                method="galerkin", precision="bf16", block_k=8)
+    M = kw.pop("M", 10)
+    args.update(kw)
+    return kl.kl_estimate_bytes(kl.params(**args), M)
+
+
+def test_estimate_bytes_on_host(kl):
+    """The admission estimate needs no GPU and grows with what the handle holds:
+    the mesh (tables, points, operator workspaces), the basis (M, block size)
+    and, for collocation, the quadrature point set."""
+    base = _est(kl)
+    assert base > 0
+    assert _est(kl, elems=(16, 8, 8)) > base
+    assert _est(kl, M=40) > base
+    assert _est(kl, block_k=32) > base
+    assert _est(kl, method="collocation") > base
+    # C0 interpolation of the exponential kernels has about p^3 more points
+    assert _est(kl, kernel="exp") > 2 * base
+    # lower bound: the Krylov basis and its image alone (2 N mcap doubles)
+    p = kl.params(geometry="cube", degree=2, elems=(16, 16, 16), kernel="exp_sep", method="galerkin",
+                  precision="bf16", block_k=8)
+    N = 18 ** 3
+    assert kl.kl_estimate_bytes(p, 20) > 2 * N * 72 * 8
+    with pytest.raises(kl.KLError):
+        kl.kl_estimate_bytes(p, 0)
+    bad = kl.params(geometry="cube", degree=0)
+    with pytest.raises(kl.KLError):
+        kl.kl_estimate_bytes(bad, 10)

@@ -1,0 +1,160 @@
+"""Serving with continuous batching (GPU): each result is the same alone and
+in the mix, the tensor-core products of concurrent solves share launches, and
+the HBM budget limits how many solves run at once."""
+import time
+
+import numpy as np
+import pytest
+
+from kl_inputs import PARITY_CASES
+
+pytestmark = pytest.mark.gpu
+
+M = 8
+# uneven instances: two geometries, degrees 2 and 3, four kernels, both methods
+MIX = [
+    ("cube_p2_e6x5x7_expsep", "galerkin"),
+    ("annulus_p2_e4x4x2_gauss", "collocation"),
+    ("cube_p3_e4x3x3_matern", "galerkin"),
+    ("annulus_p3_e4x3x2_exp", "collocation"),
+    ("cube_p2_e5x4x4_exp", "galerkin"),
+    ("cube_p2_e3x4x5_gauss", "collocation"),
+]
+MIXED_TOL = 1e-5  # eigenvalue relative error allowed for the mixed precisions
+OK = (0, 1)  # KL_OK, KL_WARN_COMPLEX
+
+
+@pytest.fixture(scope="module")
+def kl():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2101_00629_gb300 import _build
+    _build.build()
+    import paper_2101_00629_gb300 as mod
+    return mod
+
+
+def _params(kl, case, method, precision="bf16", block_k=8):
+    c = PARITY_CASES[case]
+    return kl.params(geometry=c["geometry"], degree=c["p"], elems=c["elems"], kernel=c["kernel"],
+                     sigma=c["sigma"], L=c["L"], method=method, precision=precision, block_k=block_k, seed=31)
+
+
+def _alone(kl, p):
+    import torch
+    h = kl.kl_create(p, torch.cuda.current_stream())
+    try:
+        lam = np.zeros(M)
+        rc = kl.kl_eigs(h, M, 0.0, lam, None, 0, 0)
+    finally:
+        kl.kl_destroy(h)
+    return rc, lam
+
+
+def _serve(kl, plist, budget=0, slots=8, window_us=0, stagger_s=0.0):
+    s = kl.kl_serve_open(budget, slots, window_us)
+    lams = [np.zeros(M) for _ in plist]
+    results = {}
+    try:
+        for i, p in enumerate(plist):
+            kl.kl_serve_submit(s, p, M, 0.0, i, lams[i])
+            if stagger_s:
+                time.sleep(stagger_s)
+        t_end = time.time() + 300
+        while len(results) < len(plist) and time.time() < t_end:
+            for r in kl.kl_serve_poll(s, 16, 200):
+                results[r["request_id"]] = r
+        stats = kl.kl_serve_get_stats(s)
+    finally:
+        kl.kl_serve_close(s)
+    assert len(results) == len(plist), "not every request finished"
+    return lams, results, stats
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-6 * np.abs(b[0]))))
+
+
+def test_each_result_same_alone_and_in_the_mix(kl):
+    plist = [_params(kl, c, m) for c, m in MIX]
+    alone = [_alone(kl, p) for p in plist]
+    lams, results, stats = _serve(kl, plist, stagger_s=0.002)
+    worst = 0.0
+    for i, (c, m) in enumerate(MIX):
+        assert results[i]["status"] == alone[i][0] and alone[i][0] in OK, (c, m, results[i])
+        err = _rel(lams[i], alone[i][1])
+        worst = max(worst, err)
+        print(f"{c} {m}: mix vs alone {err:.2e}, latency {results[i]['latency_ms']:.1f} ms, "
+              f"applies {results[i]['applies']}")
+        assert err <= MIXED_TOL
+    print("stats", stats, "worst", worst)
+    # the products of concurrent solves shared launches
+    assert stats["max_concurrent"] >= 2
+    assert stats["batched_products"] > stats["batches"]
+    assert stats["max_batch"] >= 2
+    assert stats["completed"] == len(plist)
+
+
+def test_later_arrivals_join_running_solves(kl):
+    """Requests submitted while others run are admitted as slots free up:
+    with two slots, six requests all finish and at most two run at once."""
+    plist = [_params(kl, c, m) for c, m in MIX]
+    lams, results, stats = _serve(kl, plist, slots=2, stagger_s=0.01)
+    assert stats["max_concurrent"] <= 2
+    for i in range(len(plist)):
+        assert results[i]["status"] in OK
+    # queueing shows up in the latency of the later requests
+    assert max(r["queue_ms"] for r in results.values()) > 0.0
+
+
+def test_hbm_budget_limits_admission(kl):
+    # four requests of one size (different start blocks); the budget holds
+    # one and a half of them, so they must run one at a time
+    plist = []
+    for seed in range(4):
+        p = _params(kl, *MIX[0])
+        p.seed = 100 + seed
+        plist.append(p)
+    est = kl.kl_estimate_bytes(plist[0], M)
+    budget = est + est // 2
+    lams, results, stats = _serve(kl, plist, budget=budget)
+    assert stats["max_concurrent"] == 1
+    assert stats["peak_est_bytes"] <= budget
+    for i in range(len(plist)):
+        assert results[i]["status"] in OK
+        assert results[i]["est_bytes"] == est
+    # a request larger than the whole budget is refused at submission
+    s = kl.kl_serve_open(est // 2, 2, 0)
+    try:
+        with pytest.raises(kl.KLError):
+            kl.kl_serve_submit(s, plist[0], M, 0.0, 99, np.zeros(M))
+    finally:
+        kl.kl_serve_close(s)
+
+
+def test_estimate_covers_device_memory(kl):
+    """The admission estimate is an upper bound of what a handle holds after
+    a full solve (tables, points, workspaces, pairwise scratch)."""
+    import torch
+    for c, m in MIX[:3]:
+        p = _params(kl, c, m)
+        est = kl.kl_estimate_bytes(p, M)
+        h = kl.kl_create(p, torch.cuda.current_stream())
+        try:
+            lam = np.zeros(M)
+            kl.kl_eigs(h, M, 0.0, lam, None, 0, 0)
+            _, dev = kl.kl_memory(h)
+        finally:
+            kl.kl_destroy(h)
+        assert dev <= est, (c, m, dev, est)
+
+
+def test_fp64_requests_run_unbatched(kl):
+    plist = [_params(kl, c, m, precision="fp64") for c, m in MIX[:2]]
+    alone = [_alone(kl, p) for p in plist]
+    lams, results, stats = _serve(kl, plist)
+    for i in range(len(plist)):
+        assert results[i]["status"] == kl.KL_OK
+        assert _rel(lams[i], alone[i][1]) <= 1e-12
+    assert stats["batches"] == 0
