@@ -49,7 +49,110 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile-step", action="store_true",
                     help="run exactly one untimed step (for ncu launch lists); prints nothing")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving (continuous batching) leg")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests of the seeded serving stream replayed by the serving leg")
+    ap.add_argument("--serve-max-elems", type=int, default=8,
+                    help="per-axis element cap of the serving stream sample")
+    ap.add_argument("--serve-slots", type=int, default=8)
     return ap.parse_args()
+
+
+def _recorded_traffic():
+    """DRAM bytes per launch of the pairwise kernel from the committed ncu
+    summary, if the kernel source is unchanged since it was taken (else None)."""
+    import hashlib
+    try:
+        rec = {}
+        for line in open(os.path.join(ROOT, "profiles", "pair_tc_kernel_traffic.txt")):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+        if hashlib.sha1(src).hexdigest() != rec["source_sha1"]:
+            return None
+        return int(rec["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def _serve_leg(a, kl, stream):
+    """Replays a bounded sample of the seeded serving stream (Poisson
+    arrivals) through kl_serve_*, then the same requests one at a time."""
+    import numpy as np
+    import torch
+    from kl_inputs import serving_requests
+
+    reqs = serving_requests(a.serve_requests, seed=2101, max_elems=a.serve_max_elems, mean_interarrival_s=0.02)
+
+    def prm(r, precision):
+        return kl.params(geometry=r["geometry"], degree=r["p"], elems=r["elems"], kernel=r["kernel"],
+                         sigma=r["sigma"], L=r["L"], method=r["method"], precision=precision, block_k=8,
+                         seed=5 + r["id"])
+
+    # untimed warm-up of the batched path (module load, first launches)
+    s = kl.kl_serve_open(0, a.serve_slots, 0)
+    warm = [np.zeros(reqs[i]["M"]) for i in range(min(2, len(reqs)))]
+    for i, buf in enumerate(warm):
+        kl.kl_serve_submit(s, prm(reqs[i], a.precision), reqs[i]["M"], 0.0, i, buf)
+    got = 0
+    while got < len(warm):
+        got += len(kl.kl_serve_poll(s, 16, 500))
+    kl.kl_serve_close(s)
+
+    s = kl.kl_serve_open(0, a.serve_slots, 0)
+    bufs = [np.zeros(r["M"]) for r in reqs]
+    results = {}
+    t0 = time.perf_counter()
+    for r, buf in zip(reqs, bufs):
+        while time.perf_counter() - t0 < r["t"]:
+            for x in kl.kl_serve_poll(s, 64, 0):
+                results[x["request_id"]] = (x, time.perf_counter() - t0)
+            time.sleep(0.0005)
+        kl.kl_serve_submit(s, prm(r, a.precision), r["M"], 0.0, r["id"], buf)
+    while len(results) < len(reqs):
+        for x in kl.kl_serve_poll(s, 64, 200):
+            results[x["request_id"]] = (x, time.perf_counter() - t0)
+    wall = max(t for _, t in results.values())
+    stats = kl.kl_serve_get_stats(s)
+    kl.kl_serve_close(s)
+    lat = [x["latency_ms"] for x, _ in results.values()]
+    pairs = sum(r["M"] for r in reqs)
+    bad = sum(1 for x, _ in results.values() if x["status"] not in (0, 1))
+
+    # the same requests one at a time (no batching, no overlap)
+    def one(r, precision):
+        h = kl.kl_create(prm(r, precision), stream)
+        lam = np.zeros(r["M"])
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        kl.kl_eigs(h, r["M"], 0.0, lam, None, 0, 0)
+        dt = time.perf_counter() - t
+        kl.kl_destroy(h)
+        return dt, lam
+
+    seq = [one(r, a.precision) for r in reqs]
+    seq_s = sum(d for d, _ in seq)
+    # agreement of the served eigenvalues with the one-at-a-time solves
+    agree = max(float(np.max(np.abs(bufs[i] - seq[i][1]) / np.maximum(np.abs(seq[i][1]), 1e-6 * abs(seq[i][1][0]))))
+                for i in range(len(reqs)))
+    nfp = min(4, len(reqs))
+    fp64 = [one(reqs[i], "fp64")[0] for i in range(nfp)]
+    return {
+        "workload": "seeded Poisson stream of K-L requests (cube/annulus, p 2-4, Gauss/exp/Matern-3/2, "
+                    "L log-uniform 0.1-2, M 10-100, Galerkin/collocation)",
+        "sample": f"first {len(reqs)} requests, per-axis elements <= {a.serve_max_elems}, mean inter-arrival 20 ms",
+        "precision": a.precision, "slots": a.serve_slots, "requests": len(reqs), "failed": bad,
+        "wall_s": wall, "eigenpairs_per_s": pairs / wall,
+        "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+        "queue_ms_p50": float(np.percentile([x["queue_ms"] for x, _ in results.values()], 50)),
+        "batches": stats["batches"], "batched_products": stats["batched_products"], "max_batch": stats["max_batch"],
+        "max_concurrent": stats["max_concurrent"],
+        "one_at_a_time_s": seq_s, "throughput_vs_one_at_a_time": seq_s / wall,
+        "max_lam_rel_diff_vs_one_at_a_time": agree,
+        "fp64_one_at_a_time_s_first": {"requests": nfp, "fp64_s": sum(fp64),
+                                       "mixed_s": sum(seq[i][0] for i in range(nfp))},
+    }
 
 
 # --------------------------------------------------------------------------
@@ -294,6 +397,11 @@ def run_gpu(a):
                            lam_rel_err=err.tolist(), max_lam_rel_err=float(err.max()))
             kl.kl_destroy(h64)
 
+    # ---- serving: continuous batching of a seeded request stream ----
+    serving = None
+    if not a.no_serve and rank == 0 and world == 1:
+        serving = _serve_leg(a, kl, stream)
+
     # ---- end to end through the C ABI with host buffers ----
     e2e_ms = []
     lam_h = np.zeros(M)
@@ -330,7 +438,7 @@ def run_gpu(a):
         peak_fp32 = fp32_fma / fp32_per_pair / 1e9
         peak = min(peak_mufu, peak_fp32)
         roof = {"bound": "alu", "kernel": pair_name, "achieved": achieved, "peak": peak, "unit": "Gpair/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": _recorded_traffic(),
                 "peak_basis": f"min(measured MUFU ex2 {ex2 / 1e12:.2f} T/s / {mufu_per_pair} per pair, measured FP32 "
                               f"{fp32_fma / 1e12:.1f} T op/s / {fp32_per_pair} per pair); FP64 FMA "
                               f"{fp64_fma / 1e12:.2f} T/s",
@@ -367,6 +475,7 @@ def run_gpu(a):
         "cpu_baseline": cpu,
         "e2e": {"value": float(np.median(e2e_ms)) / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
+        "serving": serving,
         "gpu_launches": int(launches),
         "clocks": clk,
         "region_s": region_s,

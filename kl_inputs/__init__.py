@@ -46,3 +46,27 @@ def random_block(n, k, seed):
 def problem_args(spec):
     """The geometry/discretisation fields of a workload (no M, k, methods)."""
     return {key: spec[key] for key in ("geometry", "p", "elems", "kernel", "sigma", "L")}
+
+
+def serving_requests(n=500, seed=2101, max_elems=48, mean_interarrival_s=0.05):
+    """A seeded stream of K-L requests with Poisson arrivals: geometry cube or
+    quarter annulus, degree 2..4, per-axis elements from {8, 16, 24, 32, 40, 48}
+    (n^3 for the cube, (2n, n, n/2) for the annulus) capped at max_elems,
+    kernel Gaussian / Euclidean exponential / Matern-3/2, L log-uniform in
+    [0.1, 2], M uniform in 10..100, Galerkin or collocation with equal
+    probability. Returns a list of dicts with an arrival time "t" (seconds
+    from the first arrival) and the fields of problem_args plus M, method."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = [e for e in (8, 16, 24, 32, 40, 48) if e <= max_elems] or [max_elems]
+    out, t = [], 0.0
+    for i in range(n):
+        geometry = ("cube", "annulus")[int(rng.integers(2))]
+        e = int(sizes[int(rng.integers(len(sizes)))])
+        elems = (e, e, e) if geometry == "cube" else (2 * e, e, max(1, e // 2))
+        req = dict(id=i, t=t, geometry=geometry, p=int(rng.integers(2, 5)), elems=elems,
+                   kernel=("gauss", "exp", "matern32")[int(rng.integers(3))], sigma=1.0,
+                   L=float(np.exp(rng.uniform(np.log(0.1), np.log(2.0)))), M=int(rng.integers(10, 101)),
+                   method=("galerkin", "collocation")[int(rng.integers(2))])
+        out.append(req)
+        t += float(rng.exponential(mean_interarrival_s))
+    return out
