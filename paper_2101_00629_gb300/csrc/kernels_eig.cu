@@ -29,6 +29,27 @@ constexpr size_t kEigSmemLimit = 220 * 1024;  // dynamic shared memory of the la
 constexpr int kEigWarps = kEigThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
 
+// Arithmetic of the kernel: FP64 for the final Rayleigh-Ritz problems, FP32
+// for the restarts of the outer solver (shorter dependency chains). split:
+// relative size (to ||H||) below which a stalled window's subdiagonal may be
+// dropped and diagonal entries count as one eigenvalue cluster.
+template <class R>
+struct EigNum;
+template <>
+struct EigNum<double> {
+    static constexpr double eps = DBL_EPSILON;
+    static constexpr double tiny = DBL_MIN;
+    static constexpr double split = 1e-10;
+    static constexpr double abs_defl = 1.0;  // absolute deflation at n eps ||H||
+};
+template <>
+struct EigNum<float> {
+    static constexpr float eps = FLT_EPSILON;
+    static constexpr float tiny = FLT_MIN;
+    static constexpr float split = 1e-5f;
+    static constexpr float abs_defl = 1.0f / 64;  // about eps ||H|| for the sizes used
+};
+
 struct cplx {
     double re, im;
 };
@@ -43,20 +64,22 @@ __device__ inline cplx cdiv(cplx a, cplx b) {
     return {(a.re * r + a.im) / d, (a.im * r - a.re) / d};
 }
 
-__device__ inline double blk_sum(double v, double* red) {
+template <class R>
+__device__ inline R blk_sum(R v, R* red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
-    double s = 0.0;
+    R s = R(0.0);
     for (int w = 0; w < kEigWarps; ++w) s += red[w];
     __syncthreads();
     return s;
 }
-__device__ inline double blk_max(double v, double* red) {
+template <class R>
+__device__ inline R blk_max(R v, R* red) {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
-    double s = red[0];
+    R s = red[0];
     for (int w = 1; w < kEigWarps; ++w) s = fmax(s, red[w]);
     __syncthreads();
     return s;
@@ -73,37 +96,39 @@ __device__ inline int blk_max_int(int v, int* red) {
 
 // Householder vector for x (len 2 or 3): (I - beta v v^T) x = -sign(x0)|x| e1.
 // v^T v = 2 |x| (|x| + |x0|), so beta needs one division and no second sum.
-__device__ inline void house(const double* x, int len, double* v, double& beta) {
-    double ss = x[0] * x[0];
+template <class R>
+__device__ inline void house(const R* x, int len, R* v, R& beta) {
+    R ss = x[0] * x[0];
     for (int t = 1; t < len; ++t) ss = fma(x[t], x[t], ss);
     for (int t = 0; t < len; ++t) v[t] = x[t];
-    if (ss == 0.0) {
-        beta = 0.0;
+    if (ss == R(0.0)) {
+        beta = R(0.0);
         return;
     }
-    const double nrm = sqrt(ss);
-    v[0] += (x[0] >= 0.0 ? nrm : -nrm);
-    beta = 1.0 / (nrm * (nrm + fabs(x[0])));
+    const R nrm = sqrt(ss);
+    v[0] += (x[0] >= R(0.0) ? nrm : -nrm);
+    beta = R(1.0) / (nrm * (nrm + fabs(x[0])));
 }
 
 // Deflation test for the subdiagonal entry (l, l-1).
-__device__ inline bool deflatable(const double* A, int n, int l, double anorm) {
-    double s = fabs(A[(l - 1) + int64_t(l - 1) * n]) + fabs(A[l + int64_t(l) * n]);
-    if (s == 0.0) s = anorm;
-    const double sub = fabs(A[l + int64_t(l - 1) * n]);
+template <class R>
+__device__ inline bool deflatable(const R* A, int n, int l, R anorm) {
+    R s = fabs(A[(l - 1) + int64_t(l - 1) * n]) + fabs(A[l + int64_t(l) * n]);
+    if (s == R(0.0)) s = anorm;
+    const R sub = fabs(A[l + int64_t(l - 1) * n]);
     // absolute test at roundoff of the whole matrix: next to eigenvalues that
     // are themselves at roundoff level a relative test can never be met
-    if (sub <= double(n) * DBL_EPSILON * anorm) return true;
+    if (sub <= EigNum<R>::abs_defl * R(n) * EigNum<R>::eps * anorm) return true;
     // relative test, confirmed by the more conservative Ahues-Kressner
     // criterion (off-diagonal product against the gap of the diagonal pair)
-    if (sub <= DBL_EPSILON * s) {
-        const double up = fabs(A[(l - 1) + int64_t(l) * n]);
-        const double ab = fmax(sub, up), ba = fmin(sub, up);
-        const double dd = fabs(A[(l - 1) + int64_t(l - 1) * n] - A[l + int64_t(l) * n]);
-        const double aa = fmax(fabs(A[l + int64_t(l) * n]), dd);
-        const double bb = fmin(fabs(A[l + int64_t(l) * n]), dd);
-        const double ss = aa + ab;
-        return ba * (ab / ss) <= fmax(DBL_MIN, DBL_EPSILON * (bb * (aa / ss)));
+    if (sub <= EigNum<R>::eps * s) {
+        const R up = fabs(A[(l - 1) + int64_t(l) * n]);
+        const R ab = fmax(sub, up), ba = fmin(sub, up);
+        const R dd = fabs(A[(l - 1) + int64_t(l - 1) * n] - A[l + int64_t(l) * n]);
+        const R aa = fmax(fabs(A[l + int64_t(l) * n]), dd);
+        const R bb = fmin(fabs(A[l + int64_t(l) * n]), dd);
+        const R ss = aa + ab;
+        return ba * (ab / ss) <= fmax(EigNum<R>::tiny, EigNum<R>::eps * (bb * (aa / ss)));
     }
     return false;
 }
@@ -124,22 +149,23 @@ __device__ inline int group_size(int items) {
 // equation T11 X - X T22 = T12; the columns of [X; -I] span the
 // T22-invariant subspace and Q is the orthogonal factor of their QR
 // factorisation (Householder).
-__device__ void swap_transform(const double* A, int n, int k, int n1, int n2, double anorm, double* Qm) {
+template <class R>
+__device__ void swap_transform(const R* A, int n, int k, int n1, int n2, R anorm, R* Qm) {
     const int m = n1 + n2;
     if (n1 == 1 && n2 == 1) {
-        const double a = A[k + int64_t(k) * n], d = A[(k + 1) + int64_t(k + 1) * n];
-        const double b = A[k + int64_t(k + 1) * n];
-        const double r = hypot(b, d - a);
-        const double c = r > 0.0 ? b / r : 1.0, sn = r > 0.0 ? (d - a) / r : 0.0;
+        const R a = A[k + int64_t(k) * n], d = A[(k + 1) + int64_t(k + 1) * n];
+        const R b = A[k + int64_t(k + 1) * n];
+        const R r = hypot(b, d - a);
+        const R c = r > R(0.0) ? b / r : R(1.0), sn = r > R(0.0) ? (d - a) / r : R(0.0);
         Qm[0] = c;
         Qm[1] = sn;
         Qm[2] = -sn;
         Qm[3] = c;
         return;
     }
-    double K[16], x[4], W[8];
+    R K[16], x[4], W[8];
     const int pdim = n1 * n2;
-    for (int r = 0; r < pdim * pdim; ++r) K[r] = 0.0;
+    for (int r = 0; r < pdim * pdim; ++r) K[r] = R(0.0);
     // K = I_{n2} (x) T11 - T22^T (x) I_{n1}, x = vec(X) column-major
     for (int j = 0; j < n2; ++j)
         for (int i = 0; i < n1; ++i) {
@@ -150,58 +176,58 @@ __device__ void swap_transform(const double* A, int n, int k, int n1, int n2, do
         }
     // Gaussian elimination with partial pivoting; a pivot below eps ||T|| is
     // replaced by that bound (the blocks have close eigenvalues)
-    double kn = 0.0;
+    R kn = R(0.0);
     for (int r = 0; r < pdim * pdim; ++r) kn = fmax(kn, fabs(K[r]));
-    const double tiny = DBL_EPSILON * fmax(kn, anorm);
+    const R tiny = EigNum<R>::eps * fmax(kn, anorm);
     for (int c = 0; c < pdim; ++c) {
         int pr = c;
         for (int r = c + 1; r < pdim; ++r)
             if (fabs(K[r + pdim * c]) > fabs(K[pr + pdim * c])) pr = r;
         if (pr != c) {
             for (int cc = 0; cc < pdim; ++cc) {
-                const double t = K[c + pdim * cc];
+                const R t = K[c + pdim * cc];
                 K[c + pdim * cc] = K[pr + pdim * cc];
                 K[pr + pdim * cc] = t;
             }
-            const double t = x[c];
+            const R t = x[c];
             x[c] = x[pr];
             x[pr] = t;
         }
-        if (fabs(K[c + pdim * c]) < tiny) K[c + pdim * c] = K[c + pdim * c] >= 0.0 ? tiny : -tiny;
+        if (fabs(K[c + pdim * c]) < tiny) K[c + pdim * c] = K[c + pdim * c] >= R(0.0) ? tiny : -tiny;
         for (int r = c + 1; r < pdim; ++r) {
-            const double f = K[r + pdim * c] / K[c + pdim * c];
+            const R f = K[r + pdim * c] / K[c + pdim * c];
             for (int cc = c; cc < pdim; ++cc) K[r + pdim * cc] -= f * K[c + pdim * cc];
             x[r] -= f * x[c];
         }
     }
     for (int r = pdim - 1; r >= 0; --r) {
-        double t = x[r];
+        R t = x[r];
         for (int cc = r + 1; cc < pdim; ++cc) t -= K[r + pdim * cc] * x[cc];
         x[r] = t / K[r + pdim * r];
     }
     // W = [X; -I] (m x n2), Householder QR with Q accumulated
     for (int j = 0; j < n2; ++j)
-        for (int i = 0; i < m; ++i) W[i + m * j] = (i < n1) ? x[i + n1 * j] : (i - n1 == j ? -1.0 : 0.0);
-    for (int r = 0; r < m * m; ++r) Qm[r] = (r % m == r / m) ? 1.0 : 0.0;
+        for (int i = 0; i < m; ++i) W[i + m * j] = (i < n1) ? x[i + n1 * j] : (i - n1 == j ? -R(1.0) : R(0.0));
+    for (int r = 0; r < m * m; ++r) Qm[r] = (r % m == r / m) ? R(1.0) : R(0.0);
     for (int j = 0; j < n2; ++j) {
-        double v[4];
+        R v[4];
         const int len = m - j;
-        double ss = 0.0;
+        R ss = R(0.0);
         for (int t = 0; t < len; ++t) {
             v[t] = W[(j + t) + m * j];
             ss += v[t] * v[t];
         }
-        if (ss == 0.0) continue;
-        const double x0 = v[0], nrm = sqrt(ss);
-        v[0] += (x0 >= 0.0 ? nrm : -nrm);
-        const double beta = 1.0 / (nrm * (nrm + fabs(x0)));
+        if (ss == R(0.0)) continue;
+        const R x0 = v[0], nrm = sqrt(ss);
+        v[0] += (x0 >= R(0.0) ? nrm : -nrm);
+        const R beta = R(1.0) / (nrm * (nrm + fabs(x0)));
         for (int c = j; c < n2; ++c) {
-            double sdot = 0.0;
+            R sdot = R(0.0);
             for (int t = 0; t < len; ++t) sdot += v[t] * W[(j + t) + m * c];
             for (int t = 0; t < len; ++t) W[(j + t) + m * c] -= beta * sdot * v[t];
         }
         for (int r = 0; r < m; ++r) {
-            double sdot = 0.0;
+            R sdot = R(0.0);
             for (int t = 0; t < len; ++t) sdot += Qm[r + m * (j + t)] * v[t];
             for (int t = 0; t < len; ++t) Qm[r + m * (j + t)] -= beta * sdot * v[t];
         }
@@ -217,7 +243,8 @@ __device__ void swap_transform(const double* A, int n, int k, int n1, int n2, do
 // exchange is computed by its own thread.
 // ints: 2n ints of scratch (block starts, pair positions, pair sizes/flags);
 // ord: 8n doubles (a 4 x 4 transform per pair).
-__device__ void order_schur(double* A, double* Z, int n, double anorm, double* ints_d, double* ord) {
+template <class R>
+__device__ void order_schur(R* A, R* Z, int n, R anorm, R* ints_d, R* ord) {
     constexpr int NT = kEigThreads;
     __shared__ int s_wsum[kEigWarps];
     int* bstart = reinterpret_cast<int*>(ints_d);  // n
@@ -230,7 +257,7 @@ __device__ void order_schur(double* A, double* Z, int n, double anorm, double* i
         // block starts: i = 0 or a zero subdiagonal entry (i, i-1)
         int cnt = 0;
         for (int i = tid * ipt; i < min(n, (tid + 1) * ipt); ++i)
-            cnt += (i == 0 || A[i + int64_t(i - 1) * n] == 0.0);
+            cnt += (i == 0 || A[i + int64_t(i - 1) * n] == R(0.0));
         int incl = cnt;
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(kFull, incl, o);
@@ -244,7 +271,7 @@ __device__ void order_schur(double* A, double* Z, int n, double anorm, double* i
             nb += s_wsum[w];
         }
         for (int i = tid * ipt; i < min(n, (tid + 1) * ipt); ++i)
-            if (i == 0 || A[i + int64_t(i - 1) * n] == 0.0) bstart[pos++] = i;
+            if (i == 0 || A[i + int64_t(i - 1) * n] == R(0.0)) bstart[pos++] = i;
         __syncthreads();
         const int par = round & 1;
         const int npairs = max(0, (nb - par) / 2);
@@ -254,9 +281,9 @@ __device__ void order_schur(double* A, double* Z, int n, double anorm, double* i
             const int k = bstart[b0], k2 = bstart[b0 + 1];
             const int k3 = (b0 + 2 < nb) ? bstart[b0 + 2] : n;
             const int n1 = k2 - k, n2 = k3 - k2;
-            const double key1 = n1 == 1 ? A[k + int64_t(k) * n] : 0.5 * (A[k + int64_t(k) * n] + A[(k + 1) + int64_t(k + 1) * n]);
-            const double key2 = n2 == 1 ? A[k2 + int64_t(k2) * n]
-                                        : 0.5 * (A[k2 + int64_t(k2) * n] + A[(k2 + 1) + int64_t(k2 + 1) * n]);
+            const R key1 = n1 == 1 ? A[k + int64_t(k) * n] : R(0.5) * (A[k + int64_t(k) * n] + A[(k + 1) + int64_t(k + 1) * n]);
+            const R key2 = n2 == 1 ? A[k2 + int64_t(k2) * n]
+                                        : R(0.5) * (A[k2 + int64_t(k2) * n] + A[(k2 + 1) + int64_t(k2 + 1) * n]);
             const int f = key2 > key1;
             if (f) {
                 swap_transform(A, n, k, n1, n2, anorm, ord + 16 * int64_t(p));
@@ -283,11 +310,11 @@ __device__ void order_schur(double* A, double* Z, int n, double anorm, double* i
             if (!(info & 1)) continue;
             const int k = pk[p], m = ((info >> 1) & 3) + ((info >> 3) & 3);
             if (j < k) continue;
-            const double* Qm = ord + 16 * int64_t(p);
-            double old[4];
+            const R* Qm = ord + 16 * int64_t(p);
+            R old[4];
             for (int t = 0; t < m; ++t) old[t] = A[(k + t) + int64_t(j) * n];
             for (int t = 0; t < m; ++t) {
-                double acc = 0.0;
+                R acc = R(0.0);
                 for (int u2 = 0; u2 < m; ++u2) acc = fma(Qm[u2 + m * t], old[u2], acc);
                 A[(k + t) + int64_t(j) * n] = acc;
             }
@@ -300,14 +327,14 @@ __device__ void order_schur(double* A, double* Z, int n, double anorm, double* i
             const int info = pinfo[p];
             if (!(info & 1)) continue;
             const int k = pk[p], m = ((info >> 1) & 3) + ((info >> 3) & 3);
-            double* M = i2 < n ? A : Z;
+            R* M = i2 < n ? A : Z;
             const int r = i2 < n ? i2 : i2 - n;
             if (i2 < n && r >= k + m) continue;
-            const double* Qm = ord + 16 * int64_t(p);
-            double old[4];
+            const R* Qm = ord + 16 * int64_t(p);
+            R old[4];
             for (int t = 0; t < m; ++t) old[t] = M[r + int64_t(k + t) * n];
             for (int t = 0; t < m; ++t) {
-                double acc = 0.0;
+                R acc = R(0.0);
                 for (int u2 = 0; u2 < m; ++u2) acc = fma(old[u2], Qm[u2 + m * t], acc);
                 M[r + int64_t(k + t) * n] = acc;
             }
@@ -320,7 +347,7 @@ __device__ void order_schur(double* A, double* Z, int n, double anorm, double* i
             if (!(info & 1)) continue;
             const int k = pk[p], n1 = (info >> 1) & 3, n2 = (info >> 3) & 3, m = n1 + n2;
             for (int i = k + n2; i < k + m; ++i)
-                for (int j = k; j < k + n2; ++j) A[i + int64_t(j) * n] = 0.0;
+                for (int j = k; j < k + n2; ++j) A[i + int64_t(j) * n] = R(0.0);
             if (n1 == 1 && n2 == 1) {
                 A[k + int64_t(k) * n] = ord[16 * int64_t(p) + 5];
                 A[(k + 1) + int64_t(k + 1) * n] = ord[16 * int64_t(p) + 4];
@@ -335,66 +362,70 @@ __device__ void order_schur(double* A, double* Z, int n, double anorm, double* i
 // global work array.
 // nvec: eigenvectors wanted for the leading nvec ordered eigenvalues
 // (non-symmetric mode); the symmetric mode returns all ordered Schur vectors.
+template <class R>
 __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* __restrict__ H, int n,
                                                                  double* wr_out, double* wi_out,
-                                                                 double* Vout, double* Qout, double* work,
+                                                                 double* Vout, double* Qout, double* work_d,
                                                                  int* status, int smem_level, int sym,
                                                                  int nvec) {
-    extern __shared__ double smem_a[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* smem_a = reinterpret_cast<R*>(smem_raw);
+    R* work = reinterpret_cast<R*>(work_d);
     const int64_t nn = int64_t(n) * n;
-    double* A = smem_level >= 1 ? smem_a : work;
-    double* Z = smem_level == 2 ? smem_a + nn : work + nn;
-    double* X = smem_level == 2 ? smem_a + 2 * nn : work + 2 * nn;
-    double* hv = smem_level == 2 ? smem_a + 3 * nn : (smem_level == 1 ? smem_a + nn : work + 3 * nn + 2 * n);
-    double* wr = work + 3 * nn;
-    double* wi = wr + n;
-    double* ord = smem_level == 2 ? smem_a + 3 * nn + n : work + 3 * nn + 3 * n;  // 8n
-    __shared__ double s_red[kEigWarps];
+    R* A = smem_level >= 1 ? smem_a : work;
+    R* Z = smem_level == 2 ? smem_a + nn : work + nn;
+    R* X = smem_level == 2 ? smem_a + 2 * nn : work + 2 * nn;
+    // Householder vector / integer scratch (2n), ordering scratch (8n)
+    R* hv = smem_level == 2 ? smem_a + 3 * nn : (smem_level == 1 ? smem_a + nn : work + 3 * nn + 2 * n);
+    R* wr = work + 3 * nn;
+    R* wi = wr + n;
+    R* ord = smem_level == 2 ? smem_a + 3 * nn + 2 * n : work + 3 * nn + 4 * n;
+    __shared__ R s_red[kEigWarps];
     __shared__ int s_redi[kEigWarps];
-    __shared__ double s_v[3], s_x[3];
-    __shared__ double s_beta, s_sh, s_th;
+    __shared__ R s_v[3], s_x[3];
+    __shared__ R s_beta, s_sh, s_th;
     __shared__ int s_l, s_u, s_its, s_fail, s_action;
     const int tid = threadIdx.x;
     constexpr int NT = kEigThreads;
 
-    double amax = 0.0;
+    R amax = R(0.0);
     for (int64_t e = tid; e < nn; e += NT) {
         const int i = int(e % n), j = int(e / n);
-        const double a = sym ? 0.5 * (H[e] + H[j + int64_t(i) * n]) : H[e];
+        const R a = sym ? R(0.5) * (H[e] + H[j + int64_t(i) * n]) : H[e];
         A[e] = a;
-        Z[e] = (i == j) ? 1.0 : 0.0;
+        Z[e] = (i == j) ? R(1.0) : R(0.0);
         amax = fmax(amax, fabs(a));
     }
-    const double anorm = blk_max(amax, s_red);  // also orders the stores above
+    const R anorm = blk_max(amax, s_red);  // also orders the stores above
 
     // ---- Householder reduction to Hessenberg form ----
     for (int k = 0; k + 2 < n; ++k) {
         const int len = n - k - 1;
-        double ss = 0.0;
+        R ss = R(0.0);
         for (int t = tid; t < len; t += NT) {
-            const double x = A[(k + 1 + t) + int64_t(k) * n];
+            const R x = A[(k + 1 + t) + int64_t(k) * n];
             hv[t] = x;
             ss = fma(x, x, ss);
         }
         ss = blk_sum(ss, s_red);
         if (tid == 0) {
-            double beta = 0.0;
-            if (ss > 0.0) {
-                const double x0 = hv[0], nrm = sqrt(ss);
-                hv[0] = x0 + (x0 >= 0.0 ? nrm : -nrm);
-                beta = 1.0 / (nrm * (nrm + fabs(x0)));
+            R beta = R(0.0);
+            if (ss > R(0.0)) {
+                const R x0 = hv[0], nrm = sqrt(ss);
+                hv[0] = x0 + (x0 >= R(0.0) ? nrm : -nrm);
+                beta = R(1.0) / (nrm * (nrm + fabs(x0)));
             }
             s_beta = beta;
         }
         __syncthreads();
-        const double beta = s_beta;
-        if (beta != 0.0) {
+        const R beta = s_beta;
+        if (beta != R(0.0)) {
             // left: rows k+1..n-1 of columns k..n-1
             const int ncols = n - k;
             const int g = group_size(ncols), per = NT / g;
             for (int base = 0; base < ncols; base += per) {
                 const int c = base + tid / g, p = tid % g;
-                double s = 0.0;
+                R s = R(0.0);
                 if (c < ncols)
                     for (int t = p; t < len; t += g) s = fma(hv[t], A[(k + 1 + t) + int64_t(k + c) * n], s);
                 for (int o = g / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
@@ -408,9 +439,9 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             const int g2 = group_size(items), per2 = NT / g2;
             for (int base = 0; base < items; base += per2) {
                 const int it = base + tid / g2, p = tid % g2;
-                double* M = it < n ? A : Z;
+                R* M = it < n ? A : Z;
                 const int i = it < n ? it : it - n;
-                double s = 0.0;
+                R s = R(0.0);
                 if (it < items)
                     for (int t = p; t < len; t += g2) s = fma(M[i + int64_t(k + 1 + t) * n], hv[t], s);
                 for (int o = g2 / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
@@ -420,11 +451,11 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             }
         }
         __syncthreads();
-        for (int i = k + 2 + tid; i < n; i += NT) A[i + int64_t(k) * n] = 0.0;
+        for (int i = k + 2 + tid; i < n; i += NT) A[i + int64_t(k) * n] = R(0.0);
         __syncthreads();
     }
 
-    // ---- Francis double-shift QR to real Schur form ----
+    // ---- Francis R-shift QR to real Schur form ----
     if (tid == 0) {
         s_u = n - 1;
         s_its = 0;
@@ -446,7 +477,7 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         if (tid == 0) {
             const int u = u0;
             int l = cand;
-            if (l >= 1) A[l + int64_t(l - 1) * n] = 0.0;
+            if (l >= 1) A[l + int64_t(l - 1) * n] = R(0.0);
             int action = (l == u) ? 1 : (l == u - 1) ? 2 : 3;  // 1: one root, 2: 2x2 block, 3: Francis step
             if (action == 3 && s_its >= 30 && s_its % 10 == 5) {
                 // A window that resists the shifts for 30 iterations is a
@@ -461,8 +492,8 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                 int m = l + 1;
                 for (int i = l + 2; i <= u; ++i)
                     if (fabs(A[i + int64_t(i - 1) * n]) < fabs(A[m + int64_t(m - 1) * n])) m = i;
-                if (fabs(A[m + int64_t(m - 1) * n]) <= 1e-10 * anorm) {
-                    A[m + int64_t(m - 1) * n] = 0.0;
+                if (fabs(A[m + int64_t(m - 1) * n]) <= EigNum<R>::split * anorm) {
+                    A[m + int64_t(m - 1) * n] = R(0.0);
                     action = 5;  // split: look for deflations again
                     s_its = s_its + 1;
                 }
@@ -472,23 +503,23 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                     s_fail = 1;
                     action = 4;
                 } else {
-                    double sh, th;
+                    R sh, th;
                     if (s_its > 0 && s_its % 10 == 0) {  // exceptional shift
-                        const double ex = fabs(A[u + int64_t(u - 1) * n]) + fabs(A[(u - 1) + int64_t(u - 2) * n]);
-                        const double c = A[u + int64_t(u) * n] + 0.75 * ex;
-                        sh = 2.0 * c;
-                        th = c * c + 0.4375 * ex * ex;
+                        const R ex = fabs(A[u + int64_t(u - 1) * n]) + fabs(A[(u - 1) + int64_t(u - 2) * n]);
+                        const R c = A[u + int64_t(u) * n] + R(0.75) * ex;
+                        sh = R(2.0) * c;
+                        th = c * c + R(0.4375) * ex * ex;
                     } else {
-                        const double a = A[(u - 1) + int64_t(u - 1) * n], b = A[(u - 1) + int64_t(u) * n];
-                        const double c = A[u + int64_t(u - 1) * n], d = A[u + int64_t(u) * n];
+                        const R a = A[(u - 1) + int64_t(u - 1) * n], b = A[(u - 1) + int64_t(u) * n];
+                        const R c = A[u + int64_t(u - 1) * n], d = A[u + int64_t(u) * n];
                         sh = a + d;
                         th = a * d - b * c;
                     }
                     s_its = s_its + 1;
                     // first column of (H - s1)(H - s2) restricted to the window
-                    const double h11 = A[l + int64_t(l) * n], h12 = A[l + int64_t(l + 1) * n];
-                    const double h21 = A[(l + 1) + int64_t(l) * n], h22 = A[(l + 1) + int64_t(l + 1) * n];
-                    const double h32 = A[(l + 2) + int64_t(l + 1) * n];
+                    const R h11 = A[l + int64_t(l) * n], h12 = A[l + int64_t(l + 1) * n];
+                    const R h21 = A[(l + 1) + int64_t(l) * n], h22 = A[(l + 1) + int64_t(l + 1) * n];
+                    const R h32 = A[(l + 2) + int64_t(l + 1) * n];
                     s_x[0] = h11 * h11 + h12 * h21 - sh * h11 + th;
                     s_x[1] = h21 * (h11 + h22 - sh);
                     s_x[2] = h21 * h32;
@@ -496,7 +527,7 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             }
             if (action == 1) {
                 wr[u] = A[u + int64_t(u) * n];
-                wi[u] = 0.0;
+                wi[u] = R(0.0);
             }
             s_l = l;
             s_action = action;
@@ -516,27 +547,27 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         }
         if (action == 2) {
             // 2x2 block at (u-1, u): triangularise if its eigenvalues are real
-            __shared__ double s_cs, s_sn;
+            __shared__ R s_cs, s_sn;
             __shared__ int s_rot;
             if (tid == 0) {
-                const double a = A[(u - 1) + int64_t(u - 1) * n], b = A[(u - 1) + int64_t(u) * n];
-                const double c = A[u + int64_t(u - 1) * n], d = A[u + int64_t(u) * n];
-                const double p = 0.5 * (a - d);
+                const R a = A[(u - 1) + int64_t(u - 1) * n], b = A[(u - 1) + int64_t(u) * n];
+                const R c = A[u + int64_t(u - 1) * n], d = A[u + int64_t(u) * n];
+                const R p = R(0.5) * (a - d);
                 // a symmetric matrix has real eigenvalues: rounding may leave
                 // b c slightly negative, which must not create a complex pair
-                const double q = sym ? fmax(p * p + b * c, 0.0) : p * p + b * c;
+                const R q = sym ? fmax(p * p + b * c, R(0.0)) : p * p + b * c;
                 s_rot = 0;
-                if (q >= 0.0) {
-                    const double zz = p + (p >= 0.0 ? sqrt(q) : -sqrt(q));
-                    const double r = hypot(zz, c);
-                    if (r > 0.0) {
+                if (q >= R(0.0)) {
+                    const R zz = p + (p >= R(0.0) ? sqrt(q) : -sqrt(q));
+                    const R r = hypot(zz, c);
+                    if (r > R(0.0)) {
                         s_cs = zz / r;
                         s_sn = c / r;
                         s_rot = 1;
                     }
                     wr[u - 1] = d + zz;
-                    wr[u] = (zz != 0.0) ? d - b * c / zz : d + zz;
-                    wi[u - 1] = wi[u] = 0.0;
+                    wr[u] = (zz != R(0.0)) ? d - b * c / zz : d + zz;
+                    wi[u - 1] = wi[u] = R(0.0);
                 } else {
                     wr[u - 1] = wr[u] = d + p;
                     wi[u - 1] = sqrt(-q);
@@ -545,23 +576,23 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             }
             __syncthreads();
             if (s_rot) {
-                const double cs = s_cs, sn = s_sn;
+                const R cs = s_cs, sn = s_sn;
                 for (int j = u - 1 + tid; j < n; j += NT) {
-                    const double x1 = A[(u - 1) + int64_t(j) * n], x2 = A[u + int64_t(j) * n];
+                    const R x1 = A[(u - 1) + int64_t(j) * n], x2 = A[u + int64_t(j) * n];
                     A[(u - 1) + int64_t(j) * n] = cs * x1 + sn * x2;
                     A[u + int64_t(j) * n] = -sn * x1 + cs * x2;
                 }
                 __syncthreads();
                 for (int e = tid; e < u + 1 + n; e += NT) {
-                    double* M = e <= u ? A : Z;
+                    R* M = e <= u ? A : Z;
                     const int i = e <= u ? e : e - u - 1;
-                    const double x1 = M[i + int64_t(u - 1) * n], x2 = M[i + int64_t(u) * n];
+                    const R x1 = M[i + int64_t(u - 1) * n], x2 = M[i + int64_t(u) * n];
                     M[i + int64_t(u - 1) * n] = cs * x1 + sn * x2;
                     M[i + int64_t(u) * n] = -sn * x1 + cs * x2;
                 }
                 __syncthreads();
                 if (tid == 0) {
-                    A[u + int64_t(u - 1) * n] = 0.0;
+                    A[u + int64_t(u - 1) * n] = R(0.0);
                     // diagonal entries now hold the two real eigenvalues
                     wr[u - 1] = A[(u - 1) + int64_t(u - 1) * n];
                     wr[u] = A[u + int64_t(u) * n];
@@ -574,12 +605,12 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             __syncthreads();
             continue;
         }
-        // Francis double-shift step on the window [l, u] (size ns >= 3)
+        // Francis R-shift step on the window [l, u] (size ns >= 3)
         ++total_its;
         const int ns = u - l + 1;
         for (int kk = 0; kk <= ns - 3; ++kk) {
             if (tid == 0) {
-                double v[3], beta;
+                R v[3], beta;
                 house(s_x, 3, v, beta);
                 s_v[0] = v[0];
                 s_v[1] = v[1];
@@ -587,13 +618,13 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                 s_beta = beta;
             }
             __syncthreads();
-            const double v0 = s_v[0], v1 = s_v[1], v2 = s_v[2], beta = s_beta;
+            const R v0 = s_v[0], v1 = s_v[1], v2 = s_v[2], beta = s_beta;
             const int r0 = l + kk;
             const int c0 = l + (kk > 0 ? kk - 1 : 0);
             for (int j = c0 + tid; j < n; j += NT) {
-                double* col = A + int64_t(j) * n + r0;
-                const double a0 = col[0], a1 = col[1], a2 = col[2];
-                const double s = beta * fma(v2, a2, fma(v1, a1, v0 * a0));
+                R* col = A + int64_t(j) * n + r0;
+                const R a0 = col[0], a1 = col[1], a2 = col[2];
+                const R s = beta * fma(v2, a2, fma(v1, a1, v0 * a0));
                 col[0] = a0 - s * v0;
                 col[1] = a1 - s * v1;
                 col[2] = a2 - s * v2;
@@ -601,11 +632,11 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             __syncthreads();
             const int rmax = min(l + kk + 3, u);  // last row of A touched (inclusive)
             for (int e = tid; e < rmax + 1 + n; e += NT) {
-                double* M = e <= rmax ? A : Z;
+                R* M = e <= rmax ? A : Z;
                 const int i = e <= rmax ? e : e - rmax - 1;
-                double* row = M + i + int64_t(r0) * n;
-                const double a0 = row[0], a1 = row[n], a2 = row[2 * int64_t(n)];
-                const double s = beta * fma(a2, v2, fma(a1, v1, a0 * v0));
+                R* row = M + i + int64_t(r0) * n;
+                const R a0 = row[0], a1 = row[n], a2 = row[2 * int64_t(n)];
+                const R s = beta * fma(a2, v2, fma(a1, v1, a0 * v0));
                 row[0] = a0 - s * v0;
                 row[n] = a1 - s * v1;
                 row[2 * int64_t(n)] = a2 - s * v2;
@@ -614,11 +645,11 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             if (tid == 0) {
                 s_x[0] = A[(r0 + 1) + int64_t(r0) * n];
                 s_x[1] = A[(r0 + 2) + int64_t(r0) * n];
-                s_x[2] = (kk < ns - 3) ? A[(r0 + 3) + int64_t(r0) * n] : 0.0;
+                s_x[2] = (kk < ns - 3) ? A[(r0 + 3) + int64_t(r0) * n] : R(0.0);
             }
         }
         if (tid == 0) {
-            double v[3], beta;
+            R v[3], beta;
             house(s_x, 2, v, beta);
             s_v[0] = v[0];
             s_v[1] = v[1];
@@ -626,21 +657,21 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         }
         __syncthreads();
         {
-            const double v0 = s_v[0], v1 = s_v[1], beta = s_beta;
+            const R v0 = s_v[0], v1 = s_v[1], beta = s_beta;
             for (int j = u - 2 + tid; j < n; j += NT) {
-                double* col = A + int64_t(j) * n + (u - 1);
-                const double a0 = col[0], a1 = col[1];
-                const double s = beta * fma(v1, a1, v0 * a0);
+                R* col = A + int64_t(j) * n + (u - 1);
+                const R a0 = col[0], a1 = col[1];
+                const R s = beta * fma(v1, a1, v0 * a0);
                 col[0] = a0 - s * v0;
                 col[1] = a1 - s * v1;
             }
             __syncthreads();
             for (int e = tid; e < u + 1 + n; e += NT) {
-                double* M = e <= u ? A : Z;
+                R* M = e <= u ? A : Z;
                 const int i = e <= u ? e : e - u - 1;
-                double* row = M + i + int64_t(u - 1) * n;
-                const double a0 = row[0], a1 = row[n];
-                const double s = beta * fma(a1, v1, a0 * v0);
+                R* row = M + i + int64_t(u - 1) * n;
+                const R a0 = row[0], a1 = row[n];
+                const R s = beta * fma(a1, v1, a0 * v0);
                 row[0] = a0 - s * v0;
                 row[n] = a1 - s * v1;
             }
@@ -649,7 +680,7 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         // clean the bulge remnants below the subdiagonal of the window
         for (int e = tid; e < ns * ns; e += NT) {
             const int i = l + e % ns, j = l + e / ns;
-            if (i > j + 1) A[i + int64_t(j) * n] = 0.0;
+            if (i > j + 1) A[i + int64_t(j) * n] = R(0.0);
         }
         __syncthreads();
     }
@@ -661,20 +692,20 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         // permutation of the Schur vectors (stable for ties) ----
         int* rk = reinterpret_cast<int*>(hv);
         for (int i = tid; i < n; i += NT) {
-            const double di = A[i + int64_t(i) * n];
+            const R di = A[i + int64_t(i) * n];
             int rank = 0;
             for (int j = 0; j < n; ++j) {
-                const double dj = A[j + int64_t(j) * n];
+                const R dj = A[j + int64_t(j) * n];
                 if (dj > di || (dj == di && j < i)) ++rank;
             }
             wr_out[rank] = di;
-            if (wi_out) wi_out[rank] = 0.0;
+            if (wi_out) wi_out[rank] = R(0.0);
             rk[i] = rank;
         }
         __syncthreads();
         for (int64_t e = tid; e < nn; e += NT) {
             const int i = int(e % n), c = int(e / n);
-            const double z = Z[e];
+            const R z = Z[e];
             if (Vout) Vout[i + int64_t(rk[c]) * n] = z;
             if (Qout) Qout[i + int64_t(rk[c]) * n] = z;
         }
@@ -685,19 +716,19 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
 
         // ---- eigenvalues of the ordered blocks ----
         for (int i = tid; i < n; i += NT) {
-            const bool first = (i + 1 < n) && A[(i + 1) + int64_t(i) * n] != 0.0;
-            const bool second = (i > 0) && A[i + int64_t(i - 1) * n] != 0.0;
+            const bool first = (i + 1 < n) && A[(i + 1) + int64_t(i) * n] != R(0.0);
+            const bool second = (i > 0) && A[i + int64_t(i - 1) * n] != R(0.0);
             if (first || second) {
                 const int b0 = first ? i : i - 1;
-                const double a = A[b0 + int64_t(b0) * n], b = A[b0 + int64_t(b0 + 1) * n];
-                const double c = A[(b0 + 1) + int64_t(b0) * n], d = A[(b0 + 1) + int64_t(b0 + 1) * n];
-                const double pp = 0.5 * (a - d), q = pp * pp + b * c;
-                const double im = q < 0.0 ? sqrt(-q) : 0.0;
+                const R a = A[b0 + int64_t(b0) * n], b = A[b0 + int64_t(b0 + 1) * n];
+                const R c = A[(b0 + 1) + int64_t(b0) * n], d = A[(b0 + 1) + int64_t(b0 + 1) * n];
+                const R pp = R(0.5) * (a - d), q = pp * pp + b * c;
+                const R im = q < R(0.0) ? sqrt(-q) : R(0.0);
                 wr[i] = d + pp;
                 wi[i] = first ? im : -im;
             } else {
                 wr[i] = A[i + int64_t(i) * n];
-                wi[i] = 0.0;
+                wi[i] = R(0.0);
             }
         }
         __syncthreads();
@@ -708,60 +739,60 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         // vanishing pivot, so the vectors of a (numerically) multiple
         // eigenvalue stay independent (its invariant subspace is spanned by
         // Schur vectors).
-        const int nve = (nv < n && wi[nv - 1] > 0.0) ? nv + 1 : nv;
-        const double small = DBL_EPSILON * fmax(anorm, DBL_MIN);
-        const double clus = 1e-10 * anorm;
+        const int nve = (nv < n && wi[nv - 1] > R(0.0)) ? nv + 1 : nv;
+        const R small = EigNum<R>::eps * fmax(anorm, EigNum<R>::tiny);
+        const R clus = EigNum<R>::split * anorm;
         for (int col = tid; col < nve; col += NT) {
-            double* xr = X + int64_t(col) * n;
-            if (wi[col] == 0.0) {
-                const double lam = wr[col];
-                for (int i = 0; i < n; ++i) xr[i] = 0.0;
-                xr[col] = 1.0;
+            R* xr = X + int64_t(col) * n;
+            if (wi[col] == R(0.0)) {
+                const R lam = wr[col];
+                for (int i = 0; i < n; ++i) xr[i] = R(0.0);
+                xr[col] = R(1.0);
                 for (int j = col - 1; j >= 0; --j) {
-                    const bool two = (j > 0) && A[j + int64_t(j - 1) * n] != 0.0;
+                    const bool two = (j > 0) && A[j + int64_t(j - 1) * n] != R(0.0);
                     if (!two) {
-                        double s = 0.0;
+                        R s = R(0.0);
                         for (int l2 = j + 1; l2 <= col; ++l2) s = fma(A[j + int64_t(l2) * n], xr[l2], s);
-                        double den = A[j + int64_t(j) * n] - lam;
+                        R den = A[j + int64_t(j) * n] - lam;
                         if (fabs(den) <= clus) {
-                            xr[j] = 0.0;
+                            xr[j] = R(0.0);
                             continue;
                         }
                         if (fabs(den) < small) den = small;
                         xr[j] = -s / den;
                     } else {
                         // 2x2 system for rows j-1, j
-                        double s1 = 0.0, s2 = 0.0;
+                        R s1 = R(0.0), s2 = R(0.0);
                         for (int l2 = j + 1; l2 <= col; ++l2) {
                             s1 = fma(A[(j - 1) + int64_t(l2) * n], xr[l2], s1);
                             s2 = fma(A[j + int64_t(l2) * n], xr[l2], s2);
                         }
-                        const double a11 = A[(j - 1) + int64_t(j - 1) * n] - lam, a12 = A[(j - 1) + int64_t(j) * n];
-                        const double a21 = A[j + int64_t(j - 1) * n], a22 = A[j + int64_t(j) * n] - lam;
-                        double det = a11 * a22 - a12 * a21;
+                        const R a11 = A[(j - 1) + int64_t(j - 1) * n] - lam, a12 = A[(j - 1) + int64_t(j) * n];
+                        const R a21 = A[j + int64_t(j - 1) * n], a22 = A[j + int64_t(j) * n] - lam;
+                        R det = a11 * a22 - a12 * a21;
                         if (fabs(det) < small * small) det = small * small;
                         xr[j - 1] = (-s1 * a22 + s2 * a12) / det;
                         xr[j] = (-s2 * a11 + s1 * a21) / det;
                         --j;
                     }
                 }
-            } else if (wi[col] > 0.0) {
+            } else if (wi[col] > R(0.0)) {
                 // complex pair (col, col+1): vector for lambda = wr + i wi, stored
                 // as real part in column col and imaginary part in column col+1
-                double* xi = X + int64_t(col + 1) * n;
+                R* xi = X + int64_t(col + 1) * n;
                 const cplx lam = {wr[col], wi[col]};
-                for (int i = 0; i < n; ++i) xr[i] = xi[i] = 0.0;
+                for (int i = 0; i < n; ++i) xr[i] = xi[i] = R(0.0);
                 // (b12, lambda - b11) solves the first row of (B - lambda I) x = 0
                 // for the 2x2 block B and is non-zero because lambda is not real
                 const int q = col;
                 xr[q] = A[q + int64_t(q + 1) * n];
-                xi[q] = 0.0;
+                xi[q] = R(0.0);
                 xr[q + 1] = lam.re - A[q + int64_t(q) * n];
                 xi[q + 1] = lam.im;
                 for (int j = q - 1; j >= 0; --j) {
-                    const bool two = (j > 0) && A[j + int64_t(j - 1) * n] != 0.0;
+                    const bool two = (j > 0) && A[j + int64_t(j - 1) * n] != R(0.0);
                     if (!two) {
-                        cplx s = {0.0, 0.0};
+                        cplx s = {R(0.0), R(0.0)};
                         for (int l2 = j + 1; l2 <= q + 1; ++l2) {
                             s.re += A[j + int64_t(l2) * n] * xr[l2];
                             s.im += A[j + int64_t(l2) * n] * xi[l2];
@@ -772,7 +803,7 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                         xr[j] = r.re;
                         xi[j] = r.im;
                     } else {
-                        cplx s1 = {0.0, 0.0}, s2 = {0.0, 0.0};
+                        cplx s1 = {R(0.0), R(0.0)}, s2 = {R(0.0), R(0.0)};
                         for (int l2 = j + 1; l2 <= q + 1; ++l2) {
                             s1.re += A[(j - 1) + int64_t(l2) * n] * xr[l2];
                             s1.im += A[(j - 1) + int64_t(l2) * n] * xi[l2];
@@ -780,8 +811,8 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                             s2.im += A[j + int64_t(l2) * n] * xi[l2];
                         }
                         const cplx a11 = {A[(j - 1) + int64_t(j - 1) * n] - lam.re, -lam.im};
-                        const cplx a12 = {A[(j - 1) + int64_t(j) * n], 0.0};
-                        const cplx a21 = {A[j + int64_t(j - 1) * n], 0.0};
+                        const cplx a12 = {A[(j - 1) + int64_t(j) * n], R(0.0)};
+                        const cplx a21 = {A[j + int64_t(j - 1) * n], R(0.0)};
                         const cplx a22 = {A[j + int64_t(j) * n] - lam.re, -lam.im};
                         cplx det = {cmul(a11, a22).re - cmul(a12, a21).re, cmul(a11, a22).im - cmul(a12, a21).im};
                         if (fabs(det.re) + fabs(det.im) < small * small) det.re = small * small;
@@ -801,22 +832,22 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         __syncthreads();
         // V = Z X for the leading columns (X(:, c) vanishes below row c + 1),
         // then unit columns (complex pairs jointly)
-        double* Vt = A;  // the Schur form is no longer needed
+        R* Vt = A;  // the Schur form is no longer needed
         for (int64_t e = tid; e < int64_t(n) * nve; e += NT) {
             const int i = int(e % n), c = int(e / n);
             const int top = min(n - 1, c + 1);
-            double s = 0.0;
+            R s = R(0.0);
             for (int l2 = 0; l2 <= top; ++l2) s = fma(Z[i + int64_t(l2) * n], X[l2 + int64_t(c) * n], s);
             Vt[i + int64_t(c) * n] = s;
         }
         __syncthreads();
         for (int c = tid; c < nve; c += NT) {
-            if (wi[c] < 0.0) continue;
-            const int w2 = (wi[c] > 0.0) ? 2 : 1;
-            double s = 0.0;
+            if (wi[c] < R(0.0)) continue;
+            const int w2 = (wi[c] > R(0.0)) ? 2 : 1;
+            R s = R(0.0);
             for (int t = 0; t < w2; ++t)
                 for (int i = 0; i < n; ++i) s = fma(Vt[i + int64_t(c + t) * n], Vt[i + int64_t(c + t) * n], s);
-            s = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+            s = s > R(0.0) ? R(1.0) / sqrt(s) : R(1.0);
             for (int t = 0; t < w2; ++t)
                 for (int i = 0; i < n; ++i) Vt[i + int64_t(c + t) * n] *= s;
         }
@@ -841,55 +872,61 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
 }
 
 // Shared-memory level for an n x n problem (see the kernel).
-int eig_smem_level(int n, size_t* bytes) {
+int eig_smem_level(int n, size_t esize, size_t* bytes) {
     const size_t nn = size_t(n) * n;
-    const size_t limit = kEigSmemLimit;
-    if ((3 * nn + 9 * size_t(n)) * sizeof(double) <= limit) {
-        *bytes = (3 * nn + 9 * size_t(n)) * sizeof(double);
+    if ((3 * nn + 10 * size_t(n)) * esize <= kEigSmemLimit) {
+        *bytes = (3 * nn + 10 * size_t(n)) * esize;
         return 2;
     }
-    if ((nn + n) * sizeof(double) <= limit) {
-        *bytes = (nn + n) * sizeof(double);
+    if ((nn + 2 * size_t(n)) * esize <= kEigSmemLimit) {
+        *bytes = (nn + 2 * size_t(n)) * esize;
         return 1;
     }
     *bytes = 0;
     return 0;
 }
 
-cudaError_t launch_eig(const double* H, int n, double* wr, double* wi, double* V, double* Q, double* work,
-                       int* status, int sym, int nvec, cudaStream_t s) {
-    if (n <= 0) return cudaErrorInvalidValue;
+template <class R>
+cudaError_t launch_eig_t(const double* H, int n, double* wr, double* wi, double* V, double* Q, double* work,
+                         int* status, int sym, int nvec, cudaStream_t s) {
     size_t bytes = 0;
-    const int level = eig_smem_level(n, &bytes);
+    const int level = eig_smem_level(n, sizeof(R), &bytes);
     // the attribute is set once to the largest size any call uses: host
     // threads launching concurrently must not lower it under each other
     static std::once_flag once;
     static cudaError_t attr_error = cudaSuccess;
     std::call_once(once, [] {
-        attr_error = cudaFuncSetAttribute(nonsym_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        attr_error = cudaFuncSetAttribute(nonsym_eig_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           int(kEigSmemLimit));
     });
     if (attr_error != cudaSuccess) return attr_error;
-    nonsym_eig_kernel<<<1, kEigThreads, bytes, s>>>(H, n, wr, wi, V, Q, work, status, level, sym, nvec);
+    nonsym_eig_kernel<R><<<1, kEigThreads, bytes, s>>>(H, n, wr, wi, V, Q, work, status, level, sym, nvec);
     return cudaGetLastError();
+}
+
+cudaError_t launch_eig(const double* H, int n, double* wr, double* wi, double* V, double* Q, double* work,
+                       int* status, int sym, int nvec, bool fp32, cudaStream_t s) {
+    if (n <= 0) return cudaErrorInvalidValue;
+    return fp32 ? launch_eig_t<float>(H, n, wr, wi, V, Q, work, status, sym, nvec, s)
+                : launch_eig_t<double>(H, n, wr, wi, V, Q, work, status, sym, nvec, s);
 }
 
 }  // namespace
 
-int64_t nonsym_eig_work_doubles(int n) { return 3 * int64_t(n) * n + 11 * int64_t(n); }
+int64_t nonsym_eig_work_doubles(int n) { return 3 * int64_t(n) * n + 12 * int64_t(n); }
 int64_t sym_eig_work_doubles(int n) { return nonsym_eig_work_doubles(n); }
 
 // Symmetric eigenproblem: the same Hessenberg (here tridiagonal) reduction and
 // Francis QR; the ordered real Schur form of a symmetric matrix is diagonal,
 // so the ordered Schur vectors are orthonormal eigenvectors.
 cudaError_t launch_sym_eig(const double* H, int n, double* w, double* V, double* work, int* status,
-                           cudaStream_t s) {
-    return launch_eig(H, n, w, nullptr, V, nullptr, work, status, 1, n, s);
+                           cudaStream_t s, bool fp32) {
+    return launch_eig(H, n, w, nullptr, V, nullptr, work, status, 1, n, fp32, s);
 }
 
 cudaError_t launch_nonsym_eig(const double* H, int n, double* wr, double* wi, double* V, double* Q,
-                              double* work, int* status, cudaStream_t s, int nvec) {
-    return launch_eig(H, n, wr, wi, V, Q, work, status, 0, nvec > 0 ? nvec : n, s);
+                              double* work, int* status, cudaStream_t s, int nvec, bool fp32) {
+    return launch_eig(H, n, wr, wi, V, Q, work, status, 0, nvec > 0 ? nvec : n, fp32, s);
 }
 
 }  // namespace kl

@@ -122,8 +122,10 @@ cudaError_t launch_chol_rinv(double* G, int n, double* Rinv, int* bad, cudaStrea
 // Symmetric eigen-decomposition of the n x n H (Hessenberg/tridiagonal
 // reduction + Francis QR), eigenvalues descending in w, orthonormal
 // eigenvectors in V (n x n). status[0]: 0 ok, 1 no convergence.
+// fp32: the whole decomposition in FP32 arithmetic (inputs and outputs stay
+// FP64; accuracy ~1e-7 ||H||), for the restarts of the outer solver.
 cudaError_t launch_sym_eig(const double* H, int n, double* w, double* V, double* work,
-                           int* status, cudaStream_t s);
+                           int* status, cudaStream_t s, bool fp32 = false);
 // Real non-symmetric eigen-decomposition (Hessenberg + Francis QR + ordering
 // of the real Schur form + back substitution). wr/wi eigenvalues by real part
 // descending; Q (optional, n x n) the Schur vectors in the same order, so its
@@ -132,7 +134,7 @@ cudaError_t launch_sym_eig(const double* H, int n, double* w, double* V, double*
 // Re, Im columns; one more column when nvec splits a pair; nvec <= 0: all).
 // status[0]: 0 ok, 1 no convergence.
 cudaError_t launch_nonsym_eig(const double* H, int n, double* wr, double* wi, double* V, double* Q,
-                              double* work, int* status, cudaStream_t s, int nvec = 0);
+                              double* work, int* status, cudaStream_t s, int nvec = 0, bool fp32 = false);
 int64_t nonsym_eig_work_doubles(int n);
 int64_t sym_eig_work_doubles(int n);
 // Column 2-norms of X (K x n).

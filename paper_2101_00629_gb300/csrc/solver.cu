@@ -56,6 +56,7 @@ struct Ctx {
     bool sym;
     bool schur_ok = false;      // Q holds ordered Schur vectors of the last H
     int nvec = 0;               // eigenvectors of H needed (leading, ordered)
+    bool rr_fp32 = false;       // the last Rayleigh-Ritz problem was solved in FP32
     unsigned long long rng_offset = 0;
     int applies = 0, vectors_applied = 0;
 };
@@ -149,16 +150,19 @@ int apply(Ctx& c, int precision, const double* X, double* Y, int k) {
 }
 
 // Rayleigh-Ritz on the first nv columns: theta (desc), S (nv x nv, ld nv).
-int rayleigh_ritz(Ctx& c, const double* V, const double* AV, int nv, double* max_imag) {
+// fp32: the small eigenproblem in FP32 arithmetic (restarts far from the
+// tolerance; its vectors are then re-orthonormalised in FP64 by the caller).
+int rayleigh_ritz(Ctx& c, const double* V, const double* AV, int nv, double* max_imag, bool fp32 = false) {
     KL_TRY(tn(c, V, c.N, AV, c.N, c.w.H, nv, nv, nv));
     int status = 0;
+    c.rr_fp32 = fp32;
     if (c.sym) {
-        KL_TRY(ck(c, launch_sym_eig(c.w.H, nv, c.w.theta, c.w.S, c.w.la_work, c.w.ibuf, c.h->stream), "sym_eig"));
+        KL_TRY(ck(c, launch_sym_eig(c.w.H, nv, c.w.theta, c.w.S, c.w.la_work, c.w.ibuf, c.h->stream, fp32), "sym_eig"));
         KL_TRY(sync_copy(c, &status, c.w.ibuf, sizeof(int)));
         if (max_imag) *max_imag = 0.0;
     } else {
         KL_TRY(ck(c, launch_nonsym_eig(c.w.H, nv, c.w.theta, c.w.thetai, c.w.S, c.w.Q, c.w.la_work,
-                                       c.w.ibuf, c.h->stream, c.nvec), "nonsym_eig"));
+                                       c.w.ibuf, c.h->stream, c.nvec, fp32), "nonsym_eig"));
         KL_TRY(sync_copy(c, &status, c.w.ibuf, sizeof(int)));
         c.schur_ok = status == 0;
         if (status == 2) status = 0;  // complex pairs: eigenvectors valid, Schur order not
@@ -181,6 +185,12 @@ int rayleigh_ritz(Ctx& c, const double* V, const double* AV, int nv, double* max
 }
 
 }  // namespace
+
+// Smallest relative tolerance an FP32 Rayleigh-Ritz problem resolves: its
+// Ritz values and vectors are accurate to a few 1e-6 ||H|| (measured on
+// GB300 for n = 40..170). Tighter tolerances use FP32 only while the
+// residuals are above 1e-3 (and 1e3 tol), i.e. for the early restarts.
+constexpr double kFp32RrTol = 1e-4;
 
 // Basis width limit of kl_eigs for M wanted pairs and block size b (<= N).
 int eig_basis_cap(int64_t N, int M, int b) {
@@ -290,6 +300,32 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
 
     int restarts = 0, nconv = 0;
     bool done = false, complete = false;
+    bool bad_num = false;
+    double last_resid = HUGE_VAL;  // largest wanted relative residual of the last Rayleigh-Ritz
+    // Rayleigh-Ritz on the basis, Ritz vectors Y = V S(:, :mr) in T1 and
+    // A'Y = AV S(:, :mr) in T2, residual norms; sets nconv and last_resid
+    auto rr_residuals = [&](bool fp32) -> int {
+        if (int rc = rayleigh_ritz(c, V, AV, nv, nullptr, fp32); rc != KL_OK) return rc;
+        const int mr = std::min(M, nv);
+        if (int rc = nn(c, V, N, c.w.S, nv, c.w.T1, N, nv, mr, 1.0, 0.0); rc != KL_OK) return rc;
+        if (int rc = nn(c, AV, N, c.w.S, nv, c.w.T2, N, nv, mr, 1.0, 0.0); rc != KL_OK) return rc;
+        if (int rc = ck(c, launch_resid_norms(c.w.T1, N, c.w.T2, N, c.w.theta, N, mr, c.w.norms, h->stream), "resid"); rc != KL_OK) return rc;
+        if (int rc = sync_copy(c, th.data(), c.w.theta, nv * sizeof(double)); rc != KL_OK) return rc;
+        if (!c.sym) {
+            if (int rc = sync_copy(c, thi.data(), c.w.thetai, nv * sizeof(double)); rc != KL_OK) return rc;
+        }
+        if (int rc = sync_copy(c, rn.data(), c.w.norms, mr * sizeof(double)); rc != KL_OK) return rc;
+        const double scale = std::max(std::fabs(th[0]), 1e-300);
+        nconv = 0;
+        last_resid = 0.0;
+        bad_num = false;
+        for (int i = 0; i < mr; ++i) {
+            if (!std::isfinite(rn[i]) || !std::isfinite(th[i])) bad_num = true;
+            if (rn[i] <= tol * scale) ++nconv;
+            last_resid = std::max(last_resid, rn[i] / scale);
+        }
+        return KL_OK;
+    };
     double max_imag = 0.0;
     int status_out = KL_OK;
     while (!done) {
@@ -306,23 +342,15 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
         }
         complete = nv >= N;
         // ---- Rayleigh-Ritz ----
-        if (int rc = rayleigh_ritz(c, V, AV, nv, nullptr); rc != KL_OK) return rc;
-        const int mr = std::min(M, nv);
-        // Ritz vectors Y = V S(:, :mr) in T1, A'Y = AV S(:, :mr) in T2
-        if (int rc = nn(c, V, N, c.w.S, nv, c.w.T1, N, nv, mr, 1.0, 0.0); rc != KL_OK) return rc;
-        if (int rc = nn(c, AV, N, c.w.S, nv, c.w.T2, N, nv, mr, 1.0, 0.0); rc != KL_OK) return rc;
-        if (int rc = ck(c, launch_resid_norms(c.w.T1, N, c.w.T2, N, c.w.theta, N, mr, c.w.norms, h->stream), "resid"); rc != KL_OK) return rc;
-        if (int rc = sync_copy(c, th.data(), c.w.theta, nv * sizeof(double)); rc != KL_OK) return rc;
-        if (!c.sym) {
-            if (int rc = sync_copy(c, thi.data(), c.w.thetai, nv * sizeof(double)); rc != KL_OK) return rc;
-        }
-        if (int rc = sync_copy(c, rn.data(), c.w.norms, mr * sizeof(double)); rc != KL_OK) return rc;
-        const double scale = std::max(std::fabs(th[0]), 1e-300);
-        nconv = 0;
-        bool bad_num = false;
-        for (int i = 0; i < mr; ++i) {
-            if (!std::isfinite(rn[i]) || !std::isfinite(th[i])) bad_num = true;
-            if (rn[i] <= tol * scale) ++nconv;
+        // Mixed precisions: in FP32 while the residuals are far above the
+        // tolerance (an FP32 restart perturbs the kept vectors by a few 1e-6,
+        // below the operator's own error there); a convergence claim FP32
+        // cannot resolve is re-checked in FP64. FP64 solves stay in FP64:
+        // such perturbations would undo pairs already converged to 1e-10.
+        const bool use32 = prec != KL_FP64 && (tol >= kFp32RrTol || last_resid > std::max(1e3 * tol, 1e-3));
+        if (int rc = rr_residuals(use32); rc != KL_OK) return rc;
+        if (use32 && tol < kFp32RrTol && (nconv >= M || complete || restarts >= h->prm.max_restarts)) {
+            if (int rc = rr_residuals(false); rc != KL_OK) return rc;
         }
         if (bad_num) return fail(h, KL_ERR_NUMERIC, "NaN or Inf in the Ritz values");
         if (nconv >= M || complete) break;
@@ -348,9 +376,10 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
         if (int rc = ck(c, launch_copy_block(c.w.T2, N, V, N, N, keep, h->stream), "copy"); rc != KL_OK) return rc;
         if (int rc = nn(c, AV, N, Rk, nv, c.w.T2, N, nv, keep, 1.0, 0.0); rc != KL_OK) return rc;
         if (int rc = ck(c, launch_copy_block(c.w.T2, N, AV, N, N, keep, h->stream), "copy"); rc != KL_OK) return rc;
-        if (!c.sym && !c.schur_ok) {
-            // Ritz (or real/imaginary) vectors are not orthonormal: CholQR2 on V
-            // and the same right factor on AV
+        if ((!c.sym && !c.schur_ok) || c.rr_fp32) {
+            // Ritz (or real/imaginary) vectors, or vectors of an FP32
+            // Rayleigh-Ritz, are not orthonormal to FP64: CholQR2 on V and
+            // the same right factor on AV
             for (int pass = 0; pass < 2; ++pass) {
                 if (int rc = tn(c, V, N, V, N, c.w.G, keep, keep, keep); rc != KL_OK) return rc;
                 if (int rc = ck(c, launch_chol_rinv(c.w.G, keep, c.w.Rinv, c.w.ibuf, h->stream), "chol"); rc != KL_OK) return rc;
@@ -365,6 +394,12 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
         na = keep;
     }
 
+    // the final pairs come from an FP64 Rayleigh-Ritz problem: the refinement
+    // below, or the last one of the loop
+    if (c.rr_fp32 && !(prec != KL_FP64 && h->prm.refine > 0)) {
+        if (int rc = rr_residuals(false); rc != KL_OK) return rc;
+    }
+
     // ---- final Ritz pairs (optionally refined by an FP64 Rayleigh-Ritz) ----
     int nk = std::min(nv, nkeep);
     if (nk < M) nk = std::min(nv, M);
@@ -374,7 +409,7 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
     const bool use_schur = !c.sym && c.schur_ok && prec != KL_FP64 && h->prm.refine > 0;
     if (int rc = nn(c, V, N, use_schur ? c.w.Q : c.w.S, nv, Y, N, nv, nk, 1.0, 0.0); rc != KL_OK) return rc;
     if (prec != KL_FP64 && h->prm.refine > 0) {
-        if (!c.sym && !use_schur) {
+        if ((!c.sym && !use_schur) || c.rr_fp32) {
             // orthonormal basis of the Ritz subspace
             for (int pass = 0; pass < 2; ++pass) {
                 if (int rc = tn(c, Y, N, Y, N, c.w.G, nk, nk, nk); rc != KL_OK) return rc;
