@@ -240,6 +240,30 @@ int kl_pairwise_noalloc(int kernel, double sigma, double L, const double* tgt, i
                         const double* src, int64_t S, const double* X, int64_t ldx, double* Y,
                         int64_t ldy, int k, void* stream);
 
+/* CUDA graphs of operator applications (default on): the second application
+ * with the same operator, precision, block width and buffers is captured into
+ * a graph on the handle's stream and later ones replay it (one launch instead
+ * of ~10). While profiling, the sum-factorisation parts are two graphs and the
+ * pairwise product runs eagerly between its timing events. Not used for
+ * handles run by a server. Turning it off drops the captured graphs.
+ * Synchronises the stream. */
+int kl_set_graphs(kl_solver* h, int on);
+/* Block size (vectors per operator application) the handle uses: params'
+ * block_k, or the autotuned value for block_k = 0 (see kl_autotune). */
+int kl_block_size(const kl_solver* h);
+
+/* Block-size autotuner: times complete solves (kl_eigs, M pairs, tol) for
+ * block sizes 8, 16 and 32 on `stream` (each solved twice, the second timed;
+ * sizes the basis limit or convergence rule out are skipped), returns the
+ * fastest in *best_k and the times in seconds[3] (or NULL; -1 when skipped),
+ * and appends "<problem key> <k> <seconds>" to cache_path (or NULL). A handle
+ * created with block_k = 0 takes, at each kl_eigs, the last cached block size
+ * for its parameters and M from the file named by the environment variable
+ * KL_TUNE_CACHE (8 when there is none). The tuning itself is not meant to be
+ * timed: run it once and keep the cache. */
+int kl_autotune(const kl_params* params, int M, double tol, void* stream, const char* cache_path, int* best_k,
+                double* seconds);
+
 /* ------------------------------------------------------------------------
  * Memory estimate (host only, no GPU needed)
  * ------------------------------------------------------------------------

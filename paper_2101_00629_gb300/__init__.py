@@ -19,7 +19,8 @@ __all__ = [
     "kl_profile_read", "kl_launch_count", "kl_memory", "kl_last_error",
     "kl_status_string", "kl_measure_peaks", "kl_pairwise_noalloc", "kl_estimate_bytes",
     "kl_serve_config", "kl_serve_result", "kl_serve_stats", "kl_serve_open", "kl_serve_submit",
-    "kl_serve_poll", "kl_serve_get_stats", "kl_serve_close", "library_path", "EXPORTED_SYMBOLS",
+    "kl_serve_poll", "kl_serve_get_stats", "kl_serve_close", "kl_set_graphs", "kl_block_size",
+    "kl_autotune", "library_path", "EXPORTED_SYMBOLS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -41,6 +42,7 @@ EXPORTED_SYMBOLS = (
     "kl_profile_read", "kl_launch_count", "kl_memory", "kl_last_error",
     "kl_status_string", "kl_measure_peaks", "kl_pairwise_noalloc", "kl_estimate_bytes",
     "kl_serve_open", "kl_serve_submit", "kl_serve_poll", "kl_serve_get_stats", "kl_serve_close",
+    "kl_set_graphs", "kl_block_size", "kl_autotune",
 )
 
 
@@ -165,6 +167,10 @@ def _load():
         "kl_serve_poll": (c_int, [vp, ctypes.POINTER(kl_serve_result), c_int, ctypes.POINTER(c_int), c_int]),
         "kl_serve_get_stats": (c_int, [vp, ctypes.POINTER(kl_serve_stats)]),
         "kl_serve_close": (c_int, [vp]),
+        "kl_set_graphs": (c_int, [vp, c_int]),
+        "kl_block_size": (c_int, [vp]),
+        "kl_autotune": (c_int, [ctypes.POINTER(kl_params), c_int, dbl, vp, ctypes.c_char_p, ctypes.POINTER(c_int),
+                                ctypes.POINTER(dbl)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -360,3 +366,22 @@ def kl_serve_get_stats(s):
 
 def kl_serve_close(s):
     return _check(None, _load().kl_serve_close(s))
+
+
+def kl_set_graphs(h, on=True):
+    return _check(h, _load().kl_set_graphs(h, int(bool(on))))
+
+
+def kl_block_size(h):
+    return int(_load().kl_block_size(h))
+
+
+def kl_autotune(p, M, tol=0.0, stream=None, cache_path=None):
+    """(best block size, [seconds for k = 8, 16, 32]) from timed solves."""
+    k = ctypes.c_int()
+    secs = (ctypes.c_double * 3)()
+    if stream is not None and not isinstance(stream, int):
+        stream = stream.cuda_stream
+    _check(None, _load().kl_autotune(ctypes.byref(p), int(M), float(tol), stream,
+                                     cache_path.encode() if cache_path else None, ctypes.byref(k), secs))
+    return k.value, list(secs)

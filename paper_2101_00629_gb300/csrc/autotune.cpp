@@ -1,0 +1,97 @@
+// Block-size autotuner (no paper passage: the paper's solver is unnamed and
+// unblocked, Sec. 3.3). The block size k of the outer solver changes both
+// the cost of one operator application (the pairwise kernel's N dimension)
+// and the number of applications to convergence, so the tuner times complete
+// solves for k in {8, 16, 32} and keeps the fastest. Results go to a text
+// cache, one line per problem: "<key> <k> <seconds>"; handles created with
+// block_k = 0 look their problem up in the cache named by $KL_TUNE_CACHE.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "handle.h"
+
+namespace kl {
+
+std::string tune_key(const kl_params& p, int M) {
+    std::ostringstream o;
+    o.precision(9);
+    o << "dim" << p.dim << "_geom" << p.geometry << "_" << p.geo[0] << "," << p.geo[1] << "," << p.geo[2] << "_p"
+      << p.degree << "_e" << p.elems[0] << "x" << p.elems[1] << "x" << p.elems[2] << "_kern" << p.kernel << "_s"
+      << p.sigma << "_L" << p.L << "_meth" << p.method << "_ic" << p.interp_continuity << "_prec" << p.precision
+      << "_M" << M;
+    return o.str();
+}
+
+int tune_lookup(const kl_params& p, int M) {
+    const char* path = std::getenv("KL_TUNE_CACHE");
+    if (!path || !*path) return 0;
+    std::ifstream f(path);
+    if (!f) return 0;
+    const std::string key = tune_key(p, M);
+    std::string line, k0;
+    int best = 0;
+    while (std::getline(f, line)) {
+        std::istringstream l(line);
+        int k = 0;
+        if (l >> k0 >> k && k0 == key && (k == 8 || k == 16 || k == 32)) best = k;  // last entry wins
+    }
+    return best;
+}
+
+}  // namespace kl
+
+using namespace kl;
+
+int kl_autotune(const kl_params* params, int M, double tol, void* stream, const char* cache_path, int* best_k,
+                double* seconds) {
+    if (!params || !best_k) return fail(nullptr, KL_ERR_ARG, "params and best_k must not be NULL");
+    const int cand[3] = {8, 16, 32};
+    double best_s = HUGE_VAL;
+    int best = 0;
+    for (int i = 0; i < 3; ++i) {
+        if (seconds) seconds[i] = -1.0;
+        kl_params p = *params;
+        p.block_k = cand[i];
+        kl_solver* h = nullptr;
+        int rc = kl_create(&p, stream, &h);
+        if (rc != KL_OK) {
+            if (rc == KL_ERR_ARG) continue;  // e.g. M + 3k beyond the basis limit
+            return rc;
+        }
+        std::vector<double> lam(M);
+        double t = HUGE_VAL;
+        // the first solve captures the graphs and loads the kernels
+        for (int rep = 0; rep < 2 && rc >= 0; ++rep) {
+            const auto t0 = std::chrono::steady_clock::now();
+            rc = kl_eigs(h, M, tol, lam.data(), nullptr, 0, 0, nullptr, nullptr);
+            t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        }
+        kl_destroy(h);
+        if (rc < 0) {
+            if (rc == KL_ERR_ARG || rc == KL_ERR_NOCONV) continue;
+            return rc;
+        }
+        if (seconds) seconds[i] = t;
+        if (t < best_s) {
+            best_s = t;
+            best = cand[i];
+        }
+    }
+    if (!best) return fail(nullptr, KL_ERR_NOCONV, "no block size converged");
+    *best_k = best;
+    if (cache_path && *cache_path) {
+        FILE* f = std::fopen(cache_path, "a");
+        if (!f) return fail(nullptr, KL_ERR_ARG, std::string("cannot write ") + cache_path);
+        std::fprintf(f, "%s %d %.6g\n", tune_key(*params, M).c_str(), best, best_s);
+        std::fclose(f);
+    }
+    return KL_OK;
+}

@@ -73,6 +73,7 @@ int ensure_workspace(kl_solver* h, int k) {
     if (k <= h->k_cap) return KL_OK;
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "workspace sync");
+    clear_graphs(h);
     for (int i = 0; i < 3; ++i) {
         dfree(h->ws[i]);
         h->ws[i] = nullptr;
@@ -206,27 +207,111 @@ int check_device_error(kl_solver* h) {
     return KL_OK;
 }
 
-int apply_operator(kl_solver* h, int which, int precision, const double* X, int64_t ldx, double* Y,
-                   int64_t ldy, int k) {
-    int rc;
+void clear_graphs(kl_solver* h) {
+    for (auto& kv : h->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    h->graphs.clear();
+}
+
+// 1) sum factorisation to the source points, scaled by J (Galerkin) or
+//    w det DF (collocation, Algorithm 1 steps 1-2): X -> ws[0]
+static int apply_pre(kl_solver* h, int which, const double* X, int64_t ldx, int k) {
     const bool gal = h->prm.method == KL_GALERKIN_IBQ;
     const double* const* F = (gal && which == 1) ? h->P : h->F;
+    const int* n_src = gal ? h->Nt1 : h->Nq1;
+    return kron3(h, F, h->N1, n_src, X, ldx, h->ws[0], h->S, k, h->src_scale, 1, 2);
+}
+
+// 3) back to the trial space: Galerkin J, B~^-1, M^T (and L^-1); collocation
+//    Z^-1 for A': ws[1] -> Y
+static int apply_post(kl_solver* h, int which, double* Y, int64_t ldy, int k) {
+    const bool gal = h->prm.method == KL_GALERKIN_IBQ;
     const double* const* FT = (gal && which == 1) ? h->PT : h->FT;
     const int* n_src = gal ? h->Nt1 : h->Nq1;
-    // 1) sum factorisation to the source points, scaled by J (Galerkin) or
-    //    w det DF (collocation, Algorithm 1 steps 1-2)
-    double* U = h->ws[0];
-    if ((rc = kron3(h, F, h->N1, n_src, X, ldx, U, h->S, k, h->src_scale, 1, 2)) != KL_OK) return rc;
-    // 2) pairwise product over all (target, source) pairs (Algorithm 1 step 3)
     double* W = h->ws[1];
-    if ((rc = pairwise(h, precision, U, W, k, gal ? h->src_scale : nullptr)) != KL_OK) return rc;
-    // 3) back to the trial space: Galerkin J, B~^-1, M^T (and L^-1); collocation Z^-1 for A'
     if (gal) return kron3(h, FT, n_src, h->N1, W, h->T, Y, ldy, k, nullptr, 0, 2);
     if (which == 1) return kron3(h, h->Zinv, h->N1, h->N1, W, h->T, Y, ldy, k, nullptr, 0, 2);
     cudaError_t e = launch_copy_block(W, h->T, Y, ldy, h->T, k, h->stream);
     ++h->launches;
     if (e != cudaSuccess) return cuda_fail(h, e, "copy");
     return KL_OK;
+}
+
+// 2) pairwise product over all (target, source) pairs (Algorithm 1 step 3):
+//    ws[0] -> ws[1]
+static int apply_pair(kl_solver* h, int precision, int k) {
+    const bool gal = h->prm.method == KL_GALERKIN_IBQ;
+    return pairwise(h, precision, h->ws[0], h->ws[1], k, gal ? h->src_scale : nullptr);
+}
+
+// Runs `enqueue` (kernel launches on the handle's stream only) through the
+// graph cache: the first call of a key runs eagerly, the second is captured
+// into a CUDA graph (thread-local capture) and later ones replay it.
+template <class F>
+static int with_graph(kl_solver* h, const kl_solver::GraphKey& key, F&& enqueue) {
+    kl_solver::GraphEntry& g = h->graphs[key];
+    if (g.exec) {
+        cudaError_t e = cudaGraphLaunch(g.exec, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+        h->launches += g.launches;
+        return KL_OK;
+    }
+    if (g.failed || g.uses == 0) {
+        const long long l0 = h->launches;
+        const int rc = enqueue();
+        g.launches = h->launches - l0;
+        ++g.uses;
+        return rc;
+    }
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g.failed = true;
+        return enqueue();
+    }
+    const long long l0 = h->launches;
+    const int rc = enqueue();
+    h->launches = l0;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->stream, &graph);
+    if (rc == KL_OK && e == cudaSuccess && graph) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != KL_OK || e != cudaSuccess || !g.exec) {
+        // capture not possible here: run this and later calls eagerly
+        cudaGetLastError();
+        g.exec = nullptr;
+        g.failed = true;
+        if (rc != KL_OK) return rc;
+        return enqueue();
+    }
+    e = cudaGraphLaunch(g.exec, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+    h->launches += g.launches;
+    return KL_OK;
+}
+
+// An operator application is a fixed sequence of about ten kernels for given
+// buffers and block width; with graphs on (default) the solver's repeated
+// applications replay captured graphs: the whole application in one graph,
+// or, while profiling, the sum-factorisation parts as two graphs around the
+// pairwise product, which is launched eagerly between its timing events.
+// Served handles run eagerly (the batcher works on the host in the middle
+// of the sequence).
+int apply_operator(kl_solver* h, int which, int precision, const double* X, int64_t ldx, double* Y,
+                   int64_t ldy, int k) {
+    auto whole = [&]() -> int {
+        int rc = apply_pre(h, which, X, ldx, k);
+        if (rc == KL_OK) rc = apply_pair(h, precision, k);
+        if (rc == KL_OK) rc = apply_post(h, which, Y, ldy, k);
+        return rc;
+    };
+    if (!h->use_graphs || h->batcher) return whole();
+    if (!h->profiling) return with_graph(h, {which, precision, k, X, ldx, Y, ldy, 0}, whole);
+    int rc = with_graph(h, {which, precision, k, X, ldx, nullptr, 0, 1}, [&] { return apply_pre(h, which, X, ldx, k); });
+    if (rc == KL_OK) rc = apply_pair(h, precision, k);
+    if (rc == KL_OK)
+        rc = with_graph(h, {which, precision, k, nullptr, 0, Y, ldy, 2}, [&] { return apply_post(h, which, Y, ldy, k); });
+    return rc;
 }
 
 int apply_zinv(kl_solver* h, const double* X, int64_t ldx, double* Y, int64_t ldy, int k) {
@@ -324,7 +409,10 @@ int kl_create(const kl_params* params, void* stream, kl_solver** out) {
 
     kl_solver* h = new kl_solver();
     h->prm = *params;
-    if (h->prm.block_k == 0) h->prm.block_k = 8;
+    if (h->prm.block_k == 0) {
+        h->prm.block_k = 8;
+        h->autotune = true;
+    }
     if (h->prm.refine < 0) h->prm.refine = 1;
     if (h->prm.max_restarts == 0) h->prm.max_restarts = 200;
     h->stream = static_cast<cudaStream_t>(stream);
@@ -466,6 +554,17 @@ int kl_create(const kl_params* params, void* stream, kl_solver** out) {
     return KL_OK;
 }
 
+int kl_set_graphs(kl_solver* h, int on) {
+    if (!h) return KL_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "kl_set_graphs");
+    h->use_graphs = on != 0;
+    if (!h->use_graphs) clear_graphs(h);
+    return KL_OK;
+}
+
+int kl_block_size(const kl_solver* h) { return h ? h->prm.block_k : 0; }
+
 int kl_estimate_bytes(const kl_params* params, int M, int64_t* bytes) {
     g_create_error.clear();
     if (!params || !bytes) return fail(nullptr, KL_ERR_ARG, "params and bytes must not be NULL");
@@ -535,6 +634,7 @@ int kl_destroy(kl_solver* h) {
     dfree(h->pair_scratch);
     dfree(h->eig_ws);
     dfree(h->d_err);
+    clear_graphs(h);
     if (h->ev_ready) cudaEventDestroy(h->ev_ready);
     if (h->ev_done) cudaEventDestroy(h->ev_done);
     delete h;

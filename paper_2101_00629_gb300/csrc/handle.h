@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <map>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -68,6 +69,30 @@ struct kl_solver {
     // synchronisation; see check_device_error)
     int* d_err = nullptr;
 
+    // CUDA graphs of operator applications, keyed by operator, precision,
+    // block width and the input/output buffers (see apply_operator)
+    struct GraphKey {
+        int which, precision, k;
+        const double* X;
+        int64_t ldx;
+        double* Y;
+        int64_t ldy;
+        int part;  // 0: whole application, 1: before the pairwise product, 2: after
+        bool operator<(const GraphKey& o) const {
+            return std::tie(which, precision, k, X, ldx, Y, ldy, part) <
+                   std::tie(o.which, o.precision, o.k, o.X, o.ldx, o.Y, o.ldy, o.part);
+        }
+    };
+    struct GraphEntry {
+        int uses = 0;               // eager runs so far (capture on the second)
+        long long launches = 0;     // kernels per application
+        cudaGraphExec_t exec = nullptr;
+        bool failed = false;        // capture not possible: stay eager
+    };
+    bool use_graphs = true;
+    bool autotune = false;  // created with block_k = 0: kl_eigs looks the block size up
+    std::map<GraphKey, GraphEntry> graphs;
+
     // serving: tensor-core pairwise products go through this batcher (set
     // by the server's worker; null for a stand-alone handle)
     kl::Batcher* batcher = nullptr;
@@ -89,6 +114,10 @@ namespace kl {
 int fail(kl_solver* h, int code, const std::string& msg);
 int cuda_fail(kl_solver* h, cudaError_t e, const char* where);
 int ensure_workspace(kl_solver* h, int k);
+// Block size cached by kl_autotune for these parameters and M (0: none).
+int tune_lookup(const kl_params& p, int M);
+// Drops the captured graphs (their kernels point at the old workspaces).
+void clear_graphs(kl_solver* h);
 // Eigensolver sizing shared by kl_eigs and kl_estimate_bytes.
 int eig_basis_cap(int64_t N, int M, int b);
 int64_t eig_workspace_doubles(int64_t N, int mcap);

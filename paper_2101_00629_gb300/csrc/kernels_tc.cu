@@ -39,6 +39,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "kernel_eval.cuh"
 #include "kernels_tc.h"
@@ -696,8 +697,11 @@ cudaError_t launch_batch_np(const TcBatch& b, int sm_count, int* err, cudaStream
     // columns each)
     const int smem = std::max(smem_stages(STAGE_BYTES) * STAGE_BYTES + 1024, 100 * 1024);
     auto kern = pair_tc_kernel<KIND, TF32, NP>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
+    // set once per instantiation (before any stream capture of a launch)
+    static std::once_flag once;
+    static cudaError_t attr_error = cudaSuccess;
+    std::call_once(once, [&] { attr_error = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); });
+    if (attr_error != cudaSuccess) return attr_error;
     const int64_t grid = std::min<int64_t>(b.nunits, 2LL * sm_count);
     kern<<<unsigned(grid), kThreads, smem, s>>>(b, err);
     return cudaGetLastError();

@@ -231,6 +231,12 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
     c.N = h->N;
     c.sym = h->prm.method == KL_GALERKIN_IBQ;
     const int64_t N = h->N;
+    if (h->autotune) {
+        // block size from the autotuner's cache for this problem and M
+        kl_params key = h->prm;
+        key.block_k = 0;
+        if (const int kt = tune_lookup(key, M); kt > 0) h->prm.block_k = kt;
+    }
     const int b = int(std::min<int64_t>(h->prm.block_k, N));
     // nkeep and mmax are multiples of b so that every expansion step takes the
     // images of a full block (the Krylov-Schur relation needs the whole
