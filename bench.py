@@ -49,6 +49,8 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile-step", action="store_true",
                     help="run exactly one untimed step (for ncu launch lists); prints nothing")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="workload of kl_inputs.WORKLOADS (default: the 16^3 cube, the benchmark's configuration)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving (continuous batching) leg")
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the seeded serving stream replayed by the serving leg")
@@ -297,7 +299,7 @@ def run_gpu(a):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
-    w = WORKLOADS[WORKLOAD]
+    w = WORKLOADS[a.workload]
     args = problem_args(w)
     M, k = w["M"], w["k"]
 
@@ -444,7 +446,7 @@ def run_gpu(a):
                               f"{fp64_fma / 1e12:.2f} T/s",
                 "launches": st["launches"], "ms": st["ms"], "pairs": st["units"]}
     cpu = None
-    if rank == 0 and world == 1 and not a.no_cpu:
+    if rank == 0 and world == 1 and not a.no_cpu and a.workload == WORKLOAD:
         est, cores, sample, _ = _oracle_sample()
         cpu = {"value": est, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample}
 
@@ -463,7 +465,7 @@ def run_gpu(a):
         "vs_baseline": None,
         "dtype": "f32 kernel tiles, split-bf16 tcgen05 products, f64 solver" if a.precision == "bf16" else a.precision,
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": N, "M": M, "k": k, "methods": list(METHODS),
+        "config": {"workload": a.workload, "N": N, "M": M, "k": k, "methods": list(METHODS),
                    "precision": a.precision, "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "solve_ms_p50": p50, "solve_ms_p99": p99,

@@ -9,6 +9,7 @@
 //              transpose (CholQR), flagging collapsed pivots.
 // The small eigenproblem of the Rayleigh-Ritz step is in kernels_eig.cu.
 #include <cfloat>
+#include <algorithm>
 #include <cmath>
 
 #include "kl_internal.h"
@@ -173,8 +174,13 @@ __global__ void __launch_bounds__(256) chol_rinv_kernel(double* G, int n, double
 
 }  // namespace
 
+// Enough for every product with m' <= m, n' <= n and this K: a smaller
+// product may take more splits (fewer tiles), but splits * m' * n' never
+// exceeds min(ceil(K / 256) m n, 8 * 152 * TN_T^2) (at least m n).
 int64_t gemm_tn_scratch_doubles(int m, int n, int64_t K) {
-    return int64_t(tn_splits(m, n, K)) * m * n;
+    const int64_t s = std::max<int64_t>(1, (K + 255) / 256);
+    const int64_t bound = std::min<int64_t>(s * m * n, int64_t(8) * 152 * TN_T * TN_T);
+    return std::max<int64_t>(bound, int64_t(m) * n);
 }
 
 cudaError_t launch_gemm_tn(const double* A, int64_t lda, const double* B, int64_t ldb, double* C,

@@ -111,6 +111,7 @@ cudaError_t launch_pair_simt(const PairArgs& a, bool fp32, cudaStream_t s);
 cudaError_t launch_gemm_tn(const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
                            int64_t ldc, int m, int n, int64_t K, double alpha, double beta,
                            double* scratch, int64_t scratch_doubles, cudaStream_t s);
+// Scratch (doubles) of launch_gemm_tn for every m' <= m, n' <= n at this K.
 int64_t gemm_tn_scratch_doubles(int m, int n, int64_t K);
 // C(K x n) = alpha * A(K x m) B(m x n) + beta * C.
 cudaError_t launch_gemm_nn(const double* A, int64_t lda, const double* B, int64_t ldb, double* C,

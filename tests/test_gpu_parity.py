@@ -320,6 +320,30 @@ def test_workload_cube_p2_e16_expsep_full_size(kl, method, precision):
 
 
 @pytest.mark.parametrize("method", ["galerkin", "collocation"])
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+def test_large_basis_separable_cube(kl, method, precision):
+    """M = 50 with block size 16 (basis width 176) on 13728 dofs: the basis
+    projections then split their long dimension more finely for narrower
+    blocks than for the full basis (scratch sized for every shape). Pinned by
+    the products of 1D oracle spectra (separable kernel on a box)."""
+    w = dict(geometry="cube", p=2, elems=(24, 20, 22), kernel="exp_sep", sigma=1.0, L=0.8)
+    M = 50
+    ref = _sep_reference(w, method, M)
+    h = _create(kl, w, method, precision, block_k=16)
+    try:
+        N, _, _ = kl.kl_dims(h)
+        assert N == 26 * 22 * 24
+        rc, lam, V, res, info = _run_eigs(kl, h, M, N)
+        err = _lam_err(lam, ref)
+        print(f"large basis {method} {precision}: lambda err {err:.2e} applies {info.applies} "
+              f"restarts {info.restarts} seconds {info.seconds:.3f}")
+        assert rc == 0
+        assert err < LAM_TOL[precision]
+    finally:
+        kl.kl_destroy(h)
+
+
+@pytest.mark.parametrize("method", ["galerkin", "collocation"])
 @pytest.mark.parametrize("precision", ["fp64", "bf16", "tf32"])
 def test_workload_cube_p2_e16_expsep_apply_full_size(kl, method, precision):
     """kl_apply_A at full size against kron(A_z, A_y, A_x) of 1D oracle
