@@ -60,6 +60,15 @@ def _args():
     return ap.parse_args()
 
 
+def max_over_ranks(x, dist, device):
+    """Replicas: every rank solves its own instance; the job's step time is
+    the slowest rank's (all ranks see it)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _recorded_traffic():
     """DRAM bytes per launch of the pairwise kernel from the committed ncu
     summary, if the kernel source is unchanged since it was taken (else None)."""
@@ -375,9 +384,7 @@ def run_gpu(a):
         kl.kl_profile_enable(handles[m], False)
     ms_step = float(np.mean(step_ms))
     if dist is not None:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+        ms_step = max_over_ranks(ms_step, dist, "cuda")
 
     # ---- FP64 GPU solves of the same step (the reference precision) ----
     fp64 = {}
