@@ -240,6 +240,28 @@ int kl_pairwise_noalloc(int kernel, double sigma, double L, const double* tgt, i
                         const double* src, int64_t S, const double* X, int64_t ldx, double* Y,
                         int64_t ldy, int k, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Sampling the truncated K-L expansion (Sec. 2, the expansion of the random
+ * field): realisations alpha_M(x, xi) = sum_m sqrt(lambda_m) xi_m phi_m(x)
+ * of the centred field, phi_m(x) = sum_j V(j, m) N_j(x) in the method's
+ * trial basis N_j (B_j / sqrt(det DF) for Galerkin, Sec. 3.1; the rational
+ * basis R_j for collocation, Sec. 3.2), evaluated at the tensor Gauss grid of
+ * the parametric domain
+ * (p + 1 points per element and direction, lexicographic, direction 1
+ * fastest; kl_sample_size points).
+ * ------------------------------------------------------------------------ */
+int64_t kl_sample_size(const kl_solver* h);
+/* Physical coordinates of that grid: device xyz, 3 * kl_sample_size values
+ * (all x, then y, then z). Asynchronous on the handle's stream. */
+int kl_sample_points(kl_solver* h, double* xyz);
+/* lambda: host, M values (negative values count as 0); V: device N x M
+ * (ldv >= N), eigenvectors as returned by kl_eigs; xi: device M x ns (ldxi >=
+ * M), the standard normal variables (the caller draws them); out: device
+ * kl_sample_size x ns (ldo >= kl_sample_size). The sample scratch grows on
+ * demand (the only allocation). Errors: KL_ERR_ARG, KL_ERR_CUDA. */
+int kl_sample(kl_solver* h, int M, const double* lambda, const double* V, int64_t ldv, const double* xi,
+              int64_t ldxi, int ns, double* out, int64_t ldo);
+
 /* CUDA graphs of operator applications (default on): the second application
  * with the same operator, precision, block width and buffers is captured into
  * a graph on the handle's stream and later ones replay it (one launch instead

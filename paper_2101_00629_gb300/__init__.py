@@ -20,7 +20,7 @@ __all__ = [
     "kl_status_string", "kl_measure_peaks", "kl_pairwise_noalloc", "kl_estimate_bytes",
     "kl_serve_config", "kl_serve_result", "kl_serve_stats", "kl_serve_open", "kl_serve_submit",
     "kl_serve_poll", "kl_serve_get_stats", "kl_serve_close", "kl_set_graphs", "kl_block_size",
-    "kl_autotune", "library_path", "EXPORTED_SYMBOLS",
+    "kl_autotune", "kl_sample_size", "kl_sample_points", "kl_sample", "library_path", "EXPORTED_SYMBOLS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -42,7 +42,7 @@ EXPORTED_SYMBOLS = (
     "kl_profile_read", "kl_launch_count", "kl_memory", "kl_last_error",
     "kl_status_string", "kl_measure_peaks", "kl_pairwise_noalloc", "kl_estimate_bytes",
     "kl_serve_open", "kl_serve_submit", "kl_serve_poll", "kl_serve_get_stats", "kl_serve_close",
-    "kl_set_graphs", "kl_block_size", "kl_autotune",
+    "kl_set_graphs", "kl_block_size", "kl_autotune", "kl_sample_size", "kl_sample_points", "kl_sample",
 )
 
 
@@ -171,6 +171,9 @@ def _load():
         "kl_block_size": (c_int, [vp]),
         "kl_autotune": (c_int, [ctypes.POINTER(kl_params), c_int, dbl, vp, ctypes.c_char_p, ctypes.POINTER(c_int),
                                 ctypes.POINTER(dbl)]),
+        "kl_sample_size": (i64, [vp]),
+        "kl_sample_points": (c_int, [vp, vp]),
+        "kl_sample": (c_int, [vp, c_int, vp, vp, i64, vp, i64, c_int, vp, i64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -385,3 +388,20 @@ def kl_autotune(p, M, tol=0.0, stream=None, cache_path=None):
     _check(None, _load().kl_autotune(ctypes.byref(p), int(M), float(tol), stream,
                                      cache_path.encode() if cache_path else None, ctypes.byref(k), secs))
     return k.value, list(secs)
+
+
+def kl_sample_size(h):
+    return int(_load().kl_sample_size(h))
+
+
+def kl_sample_points(h, xyz):
+    """xyz: device buffer of 3 * kl_sample_size doubles (x, then y, then z)."""
+    return _check(h, _load().kl_sample_points(h, _ptr(xyz)))
+
+
+def kl_sample(h, M, lam, V, ldv, xi, ldxi, ns, out, ldo):
+    """lam: host float64 array (M); V, xi, out: device buffers (see kl.h)."""
+    import numpy as _np
+    lam = _np.ascontiguousarray(lam, dtype=_np.float64)
+    return _check(h, _load().kl_sample(h, int(M), lam.ctypes.data, _ptr(V), int(ldv), _ptr(xi), int(ldxi),
+                                       int(ns), _ptr(out), int(ldo)))

@@ -95,9 +95,20 @@ int ensure_workspace(kl_solver* h, int k) {
 // Y <- (x)_d F_d applied mode by mode: X has dims (n_in[0], n_in[1], n_in[2]),
 // F_d is (n_out[d] x n_in[d]). The last product writes Y (ldy) with optional
 // per-point scaling `post`; intermediates use ws[wa], ws[wb].
+static int kron3_s(kl_solver* h, const double* const* Fd, const int* n_in, const int* n_out,
+                   const double* X, int64_t ldx, double* Y, int64_t ldy, int k, const double* post,
+                   double* sa, double* sb);
+
 static int kron3(kl_solver* h, const double* const* Fd, const int* n_in, const int* n_out,
                  const double* X, int64_t ldx, double* Y, int64_t ldy, int k, const double* post,
                  int wa, int wb) {
+    return kron3_s(h, Fd, n_in, n_out, X, ldx, Y, ldy, k, post, h->ws[wa], h->ws[wb]);
+}
+
+// Same with explicit scratch for the two intermediate products.
+static int kron3_s(kl_solver* h, const double* const* Fd, const int* n_in, const int* n_out,
+                   const double* X, int64_t ldx, double* Y, int64_t ldy, int k, const double* post,
+                   double* sa, double* sb) {
     int dims[3] = {n_in[0], n_in[1], n_in[2]};
     const double* cur = X;
     int64_t ldc = ldx;
@@ -113,7 +124,7 @@ static int kron3(kl_solver* h, const double* const* Fd, const int* n_in, const i
             out = Y;
             ldo = ldy;
         } else {
-            out = h->ws[d == 0 ? wa : wb];
+            out = d == 0 ? sa : sb;
             ldo = out_len;
         }
         cudaError_t e = launch_modeprod(Fd[d], n_out[d], n_in[d], cur, ldc, out, ldo, a, b, k,
@@ -482,6 +493,8 @@ int kl_create(const kl_params* params, void* stream, kl_solver** out) {
     for (int d = 0; d < 3; ++d) push(gal ? dir[d].xg : dir[d].xc);  // target params
     for (int d = 0; d < 3; ++d) push(gal ? dir[d].xg : dir[d].xq);  // source params
     for (int d = 0; d < 3; ++d) push(gal ? std::vector<double>(dir[d].Nt, 1.0) : dir[d].wq);
+    for (int d = 0; d < 3; ++d) push(dir[d].E.a);   // trial basis at the Gauss points
+    for (int d = 0; d < 3; ++d) push(dir[d].xe);    // those points
     if ((e = dalloc(h, &h->d_tables, int64_t(buf.size()))) != cudaSuccess)
         return bail(cuda_fail(h, e, "table alloc"));
     if ((e = cudaMemcpyAsync(h->d_tables, buf.data(), buf.size() * sizeof(double),
@@ -497,6 +510,11 @@ int kl_create(const kl_params* params, void* stream, kl_solver** out) {
         h->LinvT[d] = h->d_tables + off[6 * d + 5];
     }
     for (int j = 0; j < 9; ++j) h->pts1d[j] = h->d_tables + off[18 + j];
+    for (int d = 0; d < 3; ++d) {
+        h->E[d] = h->d_tables + off[27 + d];
+        h->xe[d] = h->d_tables + off[30 + d];
+        h->Ne1[d] = dir[d].ne;
+    }
 
     // ---- point sets and geometry factors on the device ----
     const int64_t T = h->T, S = h->S;
@@ -554,6 +572,79 @@ int kl_create(const kl_params* params, void* stream, kl_solver** out) {
     return KL_OK;
 }
 
+int64_t kl_sample_size(const kl_solver* h) {
+    return h ? int64_t(h->Ne1[0]) * h->Ne1[1] * h->Ne1[2] : 0;
+}
+
+int kl_sample_points(kl_solver* h, double* xyz) {
+    if (!h) return KL_ERR_ARG;
+    if (!xyz) return fail(h, KL_ERR_ARG, "xyz must not be NULL");
+    const int64_t Q = kl_sample_size(h);
+    double geo[3] = {h->prm.geo[0], h->prm.geo[1], h->prm.geo[2]};
+    cudaError_t e = launch_tensor_points(h->prm.geometry, geo, h->xe[0], h->xe[1], h->xe[2], h->Ne1[0], h->Ne1[1],
+                                         h->Ne1[2], nullptr, nullptr, nullptr, 0.0, xyz, xyz + Q, xyz + 2 * Q,
+                                         nullptr, h->stream);
+    ++h->launches;
+    if (e != cudaSuccess) return cuda_fail(h, e, "sample points");
+    return KL_OK;
+}
+
+int kl_sample(kl_solver* h, int M, const double* lambda, const double* V, int64_t ldv, const double* xi,
+              int64_t ldxi, int ns, double* out, int64_t ldo) {
+    if (!h) return KL_ERR_ARG;
+    const int64_t Q = kl_sample_size(h), N = h->N;
+    if (!lambda || !V || !xi || !out) return fail(h, KL_ERR_ARG, "lambda, V, xi and out must not be NULL");
+    if (M < 1 || M > N) return fail(h, KL_ERR_ARG, "M must be in 1..N");
+    if (ns < 1) return fail(h, KL_ERR_ARG, "ns must be >= 1");
+    if (ldv < N || ldxi < M || ldo < Q) return fail(h, KL_ERR_ARG, "leading dimensions too small");
+    // scratch: sqrt(lambda) (M), diag(sqrt lambda) xi (M x ns), C = V diag xi (N x ns),
+    // two intermediate products of the evaluation (<= Q x ns each)
+    const bool gal = h->prm.method == KL_GALERKIN_IBQ;
+    const int64_t need = (M + 3) / 4 * 4 + int64_t(M) * ns + N * ns + 2 * Q * ns + (gal ? 4 * Q : 0);
+    if (need > h->smp_cap) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "sample sync");
+        if (h->smp_ws) {
+            cudaFree(h->smp_ws);
+            h->dev_bytes -= h->smp_cap * int64_t(sizeof(double));
+            h->smp_ws = nullptr;
+            h->smp_cap = 0;
+        }
+        e = cudaMalloc(&h->smp_ws, size_t(need) * sizeof(double));
+        if (e != cudaSuccess) return cuda_fail(h, e, "sample workspace");
+        h->smp_cap = need;
+        h->dev_bytes += need * int64_t(sizeof(double));
+    }
+    std::vector<double> sq(M);
+    for (int m = 0; m < M; ++m) sq[m] = std::sqrt(std::max(lambda[m], 0.0));
+    double* d_sq = h->smp_ws;
+    double* Xs = d_sq + (M + 3) / 4 * 4;
+    double* C = Xs + int64_t(M) * ns;
+    double* sa = C + N * ns;
+    double* sb = sa + Q * ns;
+    // Galerkin trial functions are B_j(x^) / sqrt(det DF(x^)) (Sec. 3.1):
+    // per-point factor |det DF|^(-1/2) at the grid (x, y, z scratch before it)
+    double* jscale = gal ? sb + Q * ns + 3 * Q : nullptr;
+    cudaError_t e = cudaSuccess;
+    if (gal) {
+        double geo[3] = {h->prm.geo[0], h->prm.geo[1], h->prm.geo[2]};
+        double* xyz = sb + Q * ns;
+        e = launch_tensor_points(h->prm.geometry, geo, h->xe[0], h->xe[1], h->xe[2], h->Ne1[0], h->Ne1[1],
+                                 h->Ne1[2], nullptr, nullptr, nullptr, -0.5, xyz, xyz + Q, xyz + 2 * Q, jscale,
+                                 h->stream);
+        ++h->launches;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_sq, sq.data(), M * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // sq is a host temporary
+    // diag(sqrt lambda) xi: the transpose view (ns x M) scaled by columns
+    if (e == cudaSuccess) e = launch_copy_block(xi, ldxi, Xs, M, M, ns, h->stream);
+    if (e == cudaSuccess) e = launch_scale_rows(Xs, M, M, ns, d_sq, h->stream);
+    if (e == cudaSuccess) e = launch_gemm_nn(V, ldv, Xs, M, C, N, N, M, ns, 1.0, 0.0, h->stream);
+    h->launches += 3;
+    if (e != cudaSuccess) return cuda_fail(h, e, "sample");
+    return kron3_s(h, h->E, h->N1, h->Ne1, C, N, out, ldo, ns, jscale, sa, sb);
+}
+
 int kl_set_graphs(kl_solver* h, int on) {
     if (!h) return KL_ERR_ARG;
     cudaError_t e = cudaStreamSynchronize(h->stream);
@@ -594,6 +685,8 @@ int kl_estimate_bytes(const kl_params* params, int M, int64_t* bytes) {
         add(gal ? q.Nt : q.N);
         add(ns);
         add(ns);
+        add(int64_t(q.ne) * q.N);
+        add(q.ne);
     }
     const int64_t S = gal ? Nt : Nq, T = gal ? S : N;
     int sm = 152;
@@ -634,6 +727,7 @@ int kl_destroy(kl_solver* h) {
     dfree(h->pair_scratch);
     dfree(h->eig_ws);
     dfree(h->d_err);
+    dfree(h->smp_ws);
     clear_graphs(h);
     if (h->ev_ready) cudaEventDestroy(h->ev_ready);
     if (h->ev_done) cudaEventDestroy(h->ev_done);

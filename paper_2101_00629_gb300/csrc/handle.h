@@ -47,6 +47,9 @@ struct kl_solver {
     const double* Zinv[3] = {};   // Z_d^-1                                     (N_d x N_d)
     const double* LinvT[3] = {};  // Galerkin L_d^-T                            (N_d x N_d)
     const double* pts1d[9] = {};  // target params (3), source params (3), source weights (3)
+    const double* E[3] = {};      // trial basis at the Gauss points of direction d (Ne_d x N_d)
+    const double* xe[3] = {};     // those Gauss points (parameters)
+    int Ne1[3] = {1, 1, 1};       // Gauss points per direction (sampling grid)
 
     // device point sets
     double* d_points = nullptr;   // tx ty tz (T) sx sy sz (S) scale (S)
@@ -68,6 +71,10 @@ struct kl_solver {
     // device word set by kernels whose bounded waits gave up (read after a
     // synchronisation; see check_device_error)
     int* d_err = nullptr;
+
+    // kl_sample scratch (grown on demand)
+    double* smp_ws = nullptr;
+    int64_t smp_cap = 0;  // doubles
 
     // CUDA graphs of operator applications, keyed by operator, precision,
     // block width and the input/output buffers (see apply_operator)

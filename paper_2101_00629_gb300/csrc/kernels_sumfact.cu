@@ -71,6 +71,7 @@ __global__ void tensor_points_kernel(int geometry, double r_in, double r_out, do
         if (w1) w *= w1[i1] * w2[i2] * w3[i3];
         if (jac_power == 0.5) w *= sqrt(det);
         else if (jac_power == 1.0) w *= det;
+        else if (jac_power == -0.5) w /= sqrt(det);  // Galerkin trial functions B / sqrt(det DF)
         if (out_x) out_x[i] = x;
         if (out_y) out_y[i] = y;
         if (out_z) out_z[i] = z;
@@ -133,6 +134,14 @@ __global__ void scale_cols_kernel(double* X, int64_t ldx, int64_t K, int n,
         const int64_t c = t / K, i = t - c * K;
         const double f = invert ? 1.0 / s[c] : s[c];
         X[c * ldx + i] *= f;
+    }
+}
+
+// X(i, j) *= scale[i] (K x n block, column-major).
+__global__ void scale_rows_kernel(double* X, int64_t ldx, int64_t K, int n, const double* __restrict__ scale) {
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < K * n; e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t i = e % K, j = e / K;
+        X[i + j * ldx] *= scale[i];
     }
 }
 
@@ -257,6 +266,12 @@ cudaError_t launch_randn(double* X, int64_t ldx, int64_t K, int n, unsigned long
 cudaError_t launch_scale_cols(double* X, int64_t ldx, int64_t K, int n, const double* scale,
                               int invert, cudaStream_t s) {
     scale_cols_kernel<<<grid_for(K * n), kThreads, 0, s>>>(X, ldx, K, n, scale, invert);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_rows(double* X, int64_t ldx, int64_t K, int n, const double* scale, cudaStream_t s) {
+    if (K * n == 0) return cudaSuccess;
+    scale_rows_kernel<<<grid_for(K * n), kThreads, 0, s>>>(X, ldx, K, n, scale);
     return cudaGetLastError();
 }
 

@@ -51,6 +51,12 @@ struct Dir1D {
     std::vector<double> xq, wq; // Gauss points / weights (nq)
     std::vector<double> xc;     // Greville points of the trial space (N)
     Mat R;                      // rational basis at quadrature points (nq x N)
+    // Both methods: Gauss points of the elements and the trial basis there
+    // (B-splines for Galerkin, the rational basis for collocation), for the
+    // evaluation of fields sum_j v_j N_j at the tensor Gauss grid.
+    int ne = 1;                 // Gauss points of this direction (p + 1 per element)
+    std::vector<double> xe;     // their parameters (ne)
+    Mat E;                      // trial basis at them (ne x N)
     Mat Zinv_col;               // (R_j(xc_i))^-1      (N x N)
 };
 
@@ -71,7 +77,8 @@ struct KernelSpec {
 
 // Geometry factors at a tensor grid of parametric points.
 // out_x/y/z: physical coordinates; out_w: weight(i1)*weight(i2)*weight(i3) *
-// |det DF|^power (power 0.5 for J = sqrt(det DF), 1 for collocation).
+// |det DF|^power (power 0.5 for J = sqrt(det DF), 1 for collocation, -0.5 for
+// the Galerkin trial functions B / sqrt(det DF); 0: no Jacobian factor).
 cudaError_t launch_tensor_points(int geometry, const double* geo, const double* t1, const double* t2,
                                  const double* t3, int n1, int n2, int n3, const double* w1,
                                  const double* w2, const double* w3, double jac_power, double* out_x,
@@ -147,6 +154,8 @@ cudaError_t launch_randn(double* X, int64_t ldx, int64_t K, int n, unsigned long
 // Y(:, j) = X(:, j) * scale[j]  (scale on device).
 cudaError_t launch_scale_cols(double* X, int64_t ldx, int64_t K, int n, const double* scale,
                               int invert, cudaStream_t s);
+// X(i, j) *= scale[i] for the K x n block X (rows scaled).
+cudaError_t launch_scale_rows(double* X, int64_t ldx, int64_t K, int n, const double* scale, cudaStream_t s);
 // Copy a K x n block between leading dimensions.
 cudaError_t launch_copy_block(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t K,
                               int n, cudaStream_t s);

@@ -270,7 +270,9 @@ std::string setup_direction(Dir1D& d, bool present, int nel, int p, int interp_c
         d = Dir1D();
         d.N = d.Nt = d.nq = 1;
         d.xg = {0.0};
-        d.Q = d.P = d.LinvT = d.Zinv_gal = d.R = d.Zinv_col = identity(1);
+        d.Q = d.P = d.LinvT = d.Zinv_gal = d.R = d.Zinv_col = d.E = identity(1);
+        d.ne = 1;
+        d.xe = {0.0};
         d.xq = {0.0};
         d.wq = {1.0};
         d.xc = {0.0};
@@ -329,6 +331,9 @@ std::string setup_direction(Dir1D& d, bool present, int nel, int p, int interp_c
         const Mat Zc = rational_rows(Bc, w);
         if (!lu_solve(Zc, identity(d.N), d.Zinv_col)) return "1D collocation matrix singular";
     }
+    d.ne = int(xq.size());
+    d.xe = xq;
+    d.E = need_collocation ? d.R : BU;
     return "";
 }
 
