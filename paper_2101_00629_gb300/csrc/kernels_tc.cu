@@ -80,7 +80,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Bounded wait on the phase with the given parity. False on timeout.
+// Bounded wait on the phase with the given parity. False on timeout. Each
+// try_wait lets the thread sleep in hardware until the phase completes (at
+// most the 1 ms hint), so waiting warps take no issue slots from producing
+// ones (polling cost 5 % of the pairwise kernel's time).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     const uint32_t a = smem_u32(bar);
     const long long t0 = clock64();
@@ -88,10 +91,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(ok)
-            : "r"(a), "r"(parity)
+            : "r"(a), "r"(parity), "r"(1000000u)
             : "memory");
         if (ok) return true;
         if (clock64() - t0 > kWaitLimit) return false;
@@ -330,13 +333,16 @@ __host__ __device__ inline uint32_t img_offset(int n, int kk, int np, int esize)
     return uint32_t(((ks * 2 + kb) * (np / 8) + nb) * 128 + r * 16 + e * esize);
 }
 
-// X (FP64) -> split images + FP32 source coordinates, chunk by chunk.
+// X (FP64) -> split images + FP32 source coordinates, chunk by chunk. A chunk
+// is one contiguous record [hi image | lo image | x[kchunk] y[kchunk]
+// z[kchunk]] (the stage layout), so that one bulk copy loads it.
 __global__ void tc_convert_kernel(const double* __restrict__ X, int64_t ldx, int64_t S, int c0, int kc,
                                   int np, int kchunk, bool tf32, float cscale, const float* __restrict__ sx,
                                   const float* __restrict__ sy, const float* __restrict__ sz,
-                                  float* __restrict__ srcc, uint8_t* __restrict__ img, int64_t nchunks) {
+                                  uint8_t* __restrict__ img, int64_t nchunks) {
     const int esize = tf32 ? 4 : 2;
     const int64_t img_bytes = int64_t(np) * kchunk * esize;  // one of hi / lo
+    const int64_t rec_bytes = 2 * img_bytes + 12 * int64_t(kchunk);
     const int64_t total = nchunks * kchunk * np;
     for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
          t += int64_t(gridDim.x) * blockDim.x) {
@@ -345,7 +351,7 @@ __global__ void tc_convert_kernel(const double* __restrict__ X, int64_t ldx, int
         const int64_t ch = s / kchunk;
         const int kk = int(s % kchunk);
         const float v = (s < S && n < kc) ? float(X[s + int64_t(c0 + n) * ldx]) : 0.f;
-        uint8_t* base = img + ch * 2 * img_bytes;
+        uint8_t* base = img + ch * rec_bytes;
         const uint32_t off = img_offset(n, kk, np, esize);
         if (tf32) {
             const uint32_t hi = tf32_rna(v);
@@ -360,7 +366,7 @@ __global__ void tc_convert_kernel(const double* __restrict__ X, int64_t ldx, int
         }
         if (n == 0) {
             // chunk-wise structure of arrays: x[kchunk], y[kchunk], z[kchunk]
-            float* c = srcc + ch * 3 * kchunk + kk;
+            float* c = reinterpret_cast<float*>(base + 2 * img_bytes) + kk;
             c[0] = s < S ? cscale * sx[s] : 0.f;
             c[kchunk] = s < S ? cscale * sy[s] : 0.f;
             c[2 * kchunk] = s < S ? cscale * sz[s] : 0.f;
@@ -656,7 +662,6 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                 const TcInstance& I = batch.inst[inst_of(batch, u)];
                 const Unit un = unit_of(u - I.unit0, I.splits, I.nchunks, I.cps);
                 const uint8_t* img = I.img;
-                const float* srcc = I.srcc;
                 for (int jl = 0; jl < un.nloc; ++jl) {
                     const int64_t jg = jbase + jl;
                     const int ss = int(jg % SSTAGES);
@@ -666,8 +671,7 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                     uint8_t* st = smem + ss * STAGE_BYTES;
                     const int64_t ch = un.c0 + jl;
                     mbar_arrive_expect_tx(&loaded_bar[ss], uint32_t(STAGE_BYTES));
-                    bulk_g2s(st, img + ch * int64_t(2 * IMG), uint32_t(2 * IMG), &loaded_bar[ss]);
-                    bulk_g2s(st + 2 * IMG, srcc + ch * 3 * KC, uint32_t(KC * 12), &loaded_bar[ss]);
+                    bulk_g2s(st, img + ch * int64_t(STAGE_BYTES), uint32_t(STAGE_BYTES), &loaded_bar[ss]);
                 }
                 jbase += un.nloc;
             }
@@ -780,9 +784,10 @@ TcPlan plan(int64_t T, int64_t S, int k, int sm_count, bool tf32) {
     p.splits = int((p.nchunks + p.cps - 1) / p.cps);
     const int esize = tf32 ? 4 : 2;
     p.nblk = (k + 63) / 64;
-    p.img_blk_doubles = (p.nchunks * 2 * p.np_max * p.kchunk * esize + 7) / 8;
+    // one record per chunk: hi and lo images and the coordinates (16-byte multiple)
+    p.img_blk_doubles = (p.nchunks * (2 * p.np_max * p.kchunk * esize + 12 * p.kchunk) + 7) / 8;
     p.img_doubles = p.nblk * p.img_blk_doubles;
-    p.src_doubles = (p.nchunks * p.kchunk * 3 + 3) / 4 * 2;  // 3 floats per source, 16-byte multiple
+    p.src_doubles = 0;  // coordinates are part of the chunk records
     p.part_doubles = int64_t(p.splits) * k * T;
     return p;
 }
@@ -801,7 +806,6 @@ cudaError_t tc_prepare(const TcArgs& a, cudaStream_t s, TcInstance* out, int* n,
     const TcPlan p = plan(a.T, a.S, a.k, a.sm_count, a.tf32);
     if (p.img_doubles + p.src_doubles + p.part_doubles > a.scratch_len) return cudaErrorInvalidValue;
     if (p.nblk > 4) return cudaErrorInvalidValue;
-    float* srcc = reinterpret_cast<float*>(a.scratch + p.img_doubles);
     float2* part = reinterpret_cast<float2*>(a.scratch + p.img_doubles + p.src_doubles);
     const float cscale = coord_scale(a.ks);
     // every column block uses the image layout of the widest one (the last
@@ -813,7 +817,7 @@ cudaError_t tc_prepare(const TcArgs& a, cudaStream_t s, TcInstance* out, int* n,
         const int64_t total = p.nchunks * p.kchunk * p.np_max;
         const int g = int(std::min<int64_t>((total + 255) / 256, 152 * 64));
         tc_convert_kernel<<<g, 256, 0, s>>>(a.X, a.ldx, a.S, c0, kc, p.np_max, p.kchunk, a.tf32, cscale, a.sx,
-                                            a.sy, a.sz, srcc, img, p.nchunks);
+                                            a.sy, a.sz, img, p.nchunks);
         ++*launched;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -821,7 +825,7 @@ cudaError_t tc_prepare(const TcArgs& a, cudaStream_t s, TcInstance* out, int* n,
         I.tx = a.tx;
         I.ty = a.ty;
         I.tz = a.tz;
-        I.srcc = srcc;
+        I.srcc = nullptr;
         I.img = img;
         I.part = part;
         I.T = a.T;

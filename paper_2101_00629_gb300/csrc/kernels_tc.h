@@ -28,9 +28,9 @@ struct TcArgs {
 };
 
 // One pairwise product inside a persistent launch: its target points, the
-// chunk-wise pre-scaled source coordinates and split images of X (written by
-// the conversion kernel), its (hi, lo) partial sums, and its range of work
-// units [unit0, unit0 + tiles * splits) in the launch.
+// chunk records of X (split images and pre-scaled source coordinates, written
+// by the conversion kernel; srcc is unused), its (hi, lo) partial sums, and
+// its range of work units [unit0, unit0 + tiles * splits) in the launch.
 struct TcInstance {
     const float *tx, *ty, *tz;
     const float* srcc;
