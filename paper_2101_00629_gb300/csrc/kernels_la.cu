@@ -20,13 +20,21 @@ namespace {
 
 // ------------------------------- gemm_tn ----------------------------------
 constexpr int TN_T = 32;
+constexpr int TN_NARROW = 8;   // products with n <= 8 use 32 x 8 tiles
+constexpr int TN_KMIN = 64;    // shortest K chunk of one CTA
+constexpr int TN_CTAS = 4 * 152;
+
+inline int tn_tiles(int m, int n) {
+    const int tm = (m + TN_T - 1) / TN_T;
+    return n <= TN_NARROW ? tm : tm * ((n + TN_T - 1) / TN_T);
+}
 
 inline int tn_splits(int m, int n, int64_t K) {
-    // the long dimension is cut into chunks of >= 256 rows until about eight
-    // CTAs per SM exist (FP64 work is the limit: ~2 DFMA/clock/SM on GB300)
-    const int tiles = ((m + TN_T - 1) / TN_T) * ((n + TN_T - 1) / TN_T);
-    int64_t s = (K + 255) / 256;
-    int64_t cap = (8 * 152) / tiles;
+    // the long dimension is cut into chunks of >= 64 rows until about four
+    // CTAs per SM exist: every CTA is bound by the SM's FP64 rate (~1.7
+    // DFMA/clock on GB300), so the work must reach every SM
+    int64_t s = (K + TN_KMIN - 1) / TN_KMIN;
+    int64_t cap = TN_CTAS / tn_tiles(m, n);
     if (cap < 1) cap = 1;
     if (s > cap) s = cap;
     if (s < 1) s = 1;
@@ -67,6 +75,39 @@ __global__ void __launch_bounds__(256) gemm_tn_kernel(const double* __restrict__
             if (i < m) part[(int64_t(blockIdx.z) * n + j) * m + i] = acc[r];
         }
     }
+}
+
+// n <= 8: a 32 x 8 tile, one output per thread (the 32 x 32 tile would spend
+// three quarters of its FP64 work on zero columns).
+__global__ void __launch_bounds__(256) gemm_tn_narrow_kernel(const double* __restrict__ A, int64_t lda,
+                                                             const double* __restrict__ B, int64_t ldb,
+                                                             int m, int n, int64_t K, int64_t kchunk,
+                                                             double* __restrict__ part) {
+    __shared__ double As[TN_T][TN_T + 1];
+    __shared__ double Bs[TN_T][TN_NARROW + 1];
+    const int i0 = blockIdx.x * TN_T;
+    const int64_t k0 = int64_t(blockIdx.z) * kchunk;
+    const int64_t k1 = min(K, k0 + kchunk);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // row in the tile, column 0..7
+    double acc = 0.0;
+    for (int64_t kb = k0; kb < k1; kb += TN_T) {
+        for (int e = threadIdx.x; e < TN_T * TN_T; e += 256) {
+            const int kk = e & 31, c = e >> 5;
+            const int64_t kg = kb + kk;
+            As[kk][c] = (kg < k1 && i0 + c < m) ? A[kg + int64_t(i0 + c) * lda] : 0.0;
+        }
+        {
+            const int kk = threadIdx.x & 31, c = threadIdx.x >> 5;
+            const int64_t kg = kb + kk;
+            Bs[kk][c] = (kg < k1 && c < n) ? B[kg + int64_t(c) * ldb] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < TN_T; ++kk) acc = fma(As[kk][tx], Bs[kk][ty], acc);
+        __syncthreads();
+    }
+    const int i = i0 + tx;
+    if (i < m && ty < n) part[(int64_t(blockIdx.z) * n + ty) * m + i] = acc;
 }
 
 __global__ void gemm_tn_reduce(const double* __restrict__ part, int splits, int m, int n,
@@ -176,10 +217,11 @@ __global__ void __launch_bounds__(256) chol_rinv_kernel(double* G, int n, double
 
 // Enough for every product with m' <= m, n' <= n and this K: a smaller
 // product may take more splits (fewer tiles), but splits * m' * n' never
-// exceeds min(ceil(K / 256) m n, 8 * 152 * TN_T^2) (at least m n).
+// exceeds min(ceil(K / TN_KMIN) m n, TN_CTAS * TN_T^2) (at least m n; a tile
+// holds at most TN_T^2 outputs).
 int64_t gemm_tn_scratch_doubles(int m, int n, int64_t K) {
-    const int64_t s = std::max<int64_t>(1, (K + 255) / 256);
-    const int64_t bound = std::min<int64_t>(s * m * n, int64_t(8) * 152 * TN_T * TN_T);
+    const int64_t s = std::max<int64_t>(1, (K + TN_KMIN - 1) / TN_KMIN);
+    const int64_t bound = std::min<int64_t>(s * m * n, int64_t(TN_CTAS) * TN_T * TN_T);
     return std::max<int64_t>(bound, int64_t(m) * n);
 }
 
@@ -190,8 +232,13 @@ cudaError_t launch_gemm_tn(const double* A, int64_t lda, const double* B, int64_
     const int splits = tn_splits(m, n, K);
     if (int64_t(splits) * m * n > scratch_doubles) return cudaErrorInvalidValue;
     const int64_t kchunk = ((K + splits - 1) / splits + TN_T - 1) / TN_T * TN_T;
-    dim3 grid((m + TN_T - 1) / TN_T, (n + TN_T - 1) / TN_T, splits);
-    gemm_tn_kernel<<<grid, 256, 0, s>>>(A, lda, B, ldb, m, n, K, kchunk, scratch);
+    if (n <= TN_NARROW) {
+        dim3 grid((m + TN_T - 1) / TN_T, 1, splits);
+        gemm_tn_narrow_kernel<<<grid, 256, 0, s>>>(A, lda, B, ldb, m, n, K, kchunk, scratch);
+    } else {
+        dim3 grid((m + TN_T - 1) / TN_T, (n + TN_T - 1) / TN_T, splits);
+        gemm_tn_kernel<<<grid, 256, 0, s>>>(A, lda, B, ldb, m, n, K, kchunk, scratch);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int g = std::max(1, std::min(152 * 8, (m * n + 255) / 256));
