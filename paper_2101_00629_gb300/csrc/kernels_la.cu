@@ -123,40 +123,52 @@ __global__ void gemm_tn_reduce(const double* __restrict__ part, int splits, int 
 }
 
 // ------------------------------- gemm_nn ----------------------------------
-constexpr int NN_C = 8;     // columns per thread
-constexpr int NN_M = 512;   // rows of B staged per pass
+constexpr int NN_C = 8;     // columns of C per block
+constexpr int NN_R = 32;    // rows of C per block
+constexpr int NN_G = 8;     // threads sharing one row (the inner dimension split)
+constexpr int NN_MB = 128;  // rows of B staged per pass
 
+// C(K x n) = alpha A(K x m) B(m x n) + beta C: 32-row blocks so that the FP64
+// work (bound by each SM's FP64 rate) reaches every SM for K of a few thousand;
+// the 8 threads of a row take every 8th inner index and add up in shared memory.
 __global__ void __launch_bounds__(256) gemm_nn_kernel(const double* __restrict__ A, int64_t lda,
                                                       const double* __restrict__ B, int64_t ldb,
                                                       double* C, int64_t ldc, int64_t K, int m,
                                                       int n, double alpha, double beta) {
-    __shared__ double Bs[NN_M][NN_C];
-    const int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x;
+    __shared__ double Bs[NN_MB][NN_C];
+    __shared__ double red[NN_G][NN_R][NN_C + 1];
+    const int r = threadIdx.x % NN_R, g = threadIdx.x / NN_R;
+    const int64_t i = int64_t(blockIdx.x) * NN_R + r;
     const int c0 = blockIdx.y * NN_C;
     const int nc = min(NN_C, n - c0);
     double acc[NN_C];
 #pragma unroll
     for (int c = 0; c < NN_C; ++c) acc[c] = 0.0;
-    for (int m0 = 0; m0 < m; m0 += NN_M) {
-        const int mm = min(NN_M, m - m0);
+    for (int m0 = 0; m0 < m; m0 += NN_MB) {
+        const int mm = min(NN_MB, m - m0);
         __syncthreads();
-        for (int e = threadIdx.x; e < NN_M * NN_C; e += 256) {
+        for (int e = threadIdx.x; e < mm * NN_C; e += 256) {
             const int j = e / NN_C, c = e % NN_C;
-            Bs[j][c] = (j < mm && c < nc) ? B[(m0 + j) + int64_t(c0 + c) * ldb] : 0.0;
+            Bs[j][c] = c < nc ? B[(m0 + j) + int64_t(c0 + c) * ldb] : 0.0;
         }
         __syncthreads();
         if (i < K) {
-            for (int j = 0; j < mm; ++j) {
+            for (int j = g; j < mm; j += NN_G) {
                 const double a = A[i + int64_t(m0 + j) * lda];
 #pragma unroll
                 for (int c = 0; c < NN_C; ++c) acc[c] = fma(a, Bs[j][c], acc[c]);
             }
         }
     }
-    if (i < K) {
+#pragma unroll
+    for (int c = 0; c < NN_C; ++c) red[g][r][c] = acc[c];
+    __syncthreads();
+    if (g == 0 && i < K) {
         for (int c = 0; c < nc; ++c) {
+            double v = 0.0;
+            for (int q = 0; q < NN_G; ++q) v += red[q][r][c];
             double* p = C + i + int64_t(c0 + c) * ldc;
-            double v = alpha * acc[c];
+            v *= alpha;
             if (beta != 0.0) v += beta * (*p);
             *p = v;
         }
@@ -250,7 +262,7 @@ cudaError_t launch_gemm_nn(const double* A, int64_t lda, const double* B, int64_
                            int64_t ldc, int64_t K, int m, int n, double alpha, double beta,
                            cudaStream_t s) {
     if (K <= 0 || n <= 0) return cudaSuccess;
-    dim3 grid(unsigned((K + 255) / 256), unsigned((n + NN_C - 1) / NN_C));
+    dim3 grid(unsigned((K + NN_R - 1) / NN_R), unsigned((n + NN_C - 1) / NN_C));
     gemm_nn_kernel<<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, K, m, n, alpha, beta);
     return cudaGetLastError();
 }

@@ -737,19 +737,25 @@ cudaError_t launch_batch_prec(const TcBatch& b, int np, int sm_count, int* err, 
 }
 
 // W = sigma^2 * post * sum over source splits of the (hi, lo) partial sums,
-// in a fixed order (FP64).
+// in a fixed order.
 __global__ void tc_reduce_kernel(const float2* __restrict__ part, int splits, int64_t T, int k, double sigma2,
                                  const double* __restrict__ post, double* __restrict__ Y, int64_t ldy) {
     const int64_t total = T * k;
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
          i += int64_t(gridDim.x) * blockDim.x) {
         const int64_t c = i / T, t = i - c * T;
-        double s = 0.0;
+        // double-float accumulation (error-free two-sum into hi, errors and
+        // the partials' low parts into lo): FP32 instructions, ~48 bits
+        float hi = 0.f, lo = 0.f;
         for (int sp = 0; sp < splits; ++sp) {
             const float2 v = part[(int64_t(sp) * k + c) * T + t];
-            s += double(v.x) + double(v.y);
+            const float sum = __fadd_rn(hi, v.x);
+            const float bb = __fsub_rn(sum, hi);
+            const float er = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(v.x, bb));
+            hi = sum;
+            lo = __fadd_rn(lo, __fadd_rn(er, v.y));
         }
-        s *= sigma2;
+        double s = (double(hi) + double(lo)) * sigma2;
         if (post) s *= post[t];
         Y[c * ldy + t] = s;
     }
