@@ -308,6 +308,7 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
     bool done = false, complete = false;
     bool bad_num = false;
     double last_resid = HUGE_VAL;  // largest wanted relative residual of the last Rayleigh-Ritz
+    double last_min_resid = HUGE_VAL;  // smallest one
     // Rayleigh-Ritz on the basis, Ritz vectors Y = V S(:, :mr) in T1 and
     // A'Y = AV S(:, :mr) in T2, residual norms; sets nconv and last_resid
     auto rr_residuals = [&](bool fp32) -> int {
@@ -324,11 +325,13 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
         const double scale = std::max(std::fabs(th[0]), 1e-300);
         nconv = 0;
         last_resid = 0.0;
+        last_min_resid = HUGE_VAL;
         bad_num = false;
         for (int i = 0; i < mr; ++i) {
             if (!std::isfinite(rn[i]) || !std::isfinite(th[i])) bad_num = true;
             if (rn[i] <= tol * scale) ++nconv;
             last_resid = std::max(last_resid, rn[i] / scale);
+            last_min_resid = std::min(last_min_resid, rn[i] / scale);
         }
         return KL_OK;
     };
@@ -348,12 +351,13 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
         }
         complete = nv >= N;
         // ---- Rayleigh-Ritz ----
-        // Mixed precisions: in FP32 while the residuals are far above the
-        // tolerance (an FP32 restart perturbs the kept vectors by a few 1e-6,
-        // below the operator's own error there); a convergence claim FP32
-        // cannot resolve is re-checked in FP64. FP64 solves stay in FP64:
-        // such perturbations would undo pairs already converged to 1e-10.
-        const bool use32 = prec != KL_FP64 && (tol >= kFp32RrTol || last_resid > std::max(1e3 * tol, 1e-3));
+        // Mixed precisions: in FP32 while every wanted residual is far above
+        // the tolerance (an FP32 restart perturbs the kept vectors by a few
+        // 1e-6 of ||H||, which would undo pairs that have converged: with many
+        // wanted pairs the slowest one keeps the largest residual high long
+        // after the first ones converged); a convergence claim FP32 cannot
+        // resolve is re-checked in FP64. FP64 solves stay in FP64.
+        const bool use32 = prec != KL_FP64 && (tol >= kFp32RrTol || last_min_resid > std::max(1e3 * tol, 1e-3));
         if (int rc = rr_residuals(use32); rc != KL_OK) return rc;
         if (use32 && tol < kFp32RrTol && (nconv >= M || complete || restarts >= h->prm.max_restarts)) {
             if (int rc = rr_residuals(false); rc != KL_OK) return rc;
