@@ -12,18 +12,21 @@
 //     of the MMA without passing through shared memory.
 //   * The source values X (FP64 in HBM) are converted once per application
 //     into the same hi/lo split, laid out as K-major no-swizzle core matrices
-//     (8 rows x 16 bytes) chunk by chunk, and copied into a 4-stage shared
-//     memory ring by the producers; they are the B operand.
+//     (8 rows x 16 bytes) chunk by chunk together with the chunk's source
+//     coordinates; a loader warp streams the chunk records into a shared
+//     memory ring (up to 16 stages) with bulk copies. They are the B operand.
 //   * One thread of a ninth warp issues, per chunk and K step,
 //     D += A_hi B_hi + A_hi B_lo + A_lo B_hi  (tcgen05.mma, FP32 accumulator
-//     D in tensor memory, M = 128, N = k rounded up to 16), and tcgen05.commit
-//     releases the stage when the tensor core has read it.
+//     D in tensor memory, M = 128, N = k rounded up to 16; for N = 16 two
+//     MMAs with a combined [hi | lo] B operand), and tcgen05.commit releases
+//     the stage when the tensor core has read it.
 //   * The FP32 accumulator is double-buffered in tensor memory and restarted
-//     every kGroup chunks: warpgroup 0 reads the finished buffer with
-//     tcgen05.ld and adds it into FP64 partial sums of its own rows while the
-//     tensor core fills the other buffer. Long FP32 accumulations on the
-//     tensor core drift (the error grows linearly with their length); the
-//     flush bounds every FP32 sum to kGroup chunks.
+//     every kGroup chunks: both warpgroups read the finished buffer with
+//     tcgen05.ld (half of the columns each) and fold it into (hi, lo) FP32
+//     running sums of their rows by an error-free two-sum while the tensor
+//     core fills the other buffer. Long FP32 accumulations on the tensor
+//     core drift (the error grows linearly with their length); the fold
+//     bounds every FP32 sum to kGroup chunks.
 //   * The partial sums of each source split are reduced by a second kernel in
 //     a fixed order, which also applies sigma^2 and the per-target scale.
 //   * Coordinates are pre-scaled so that the kernel argument needs no
@@ -333,9 +336,18 @@ __host__ __device__ inline uint32_t img_offset(int n, int kk, int np, int esize)
     return uint32_t(((ks * 2 + kb) * (np / 8) + nb) * 128 + r * 16 + e * esize);
 }
 
+// BF16 products with N = 16 use one combined image per chunk: rows 0..15 the
+// hi part and rows 16..31 the lo part of X, so that one MMA of N = 32 forms
+// A_hi [X_hi | X_lo] and a second of N = 16 (the first 16 rows) adds A_lo X_hi
+// into the first half: four MMAs per chunk instead of six. The issuing
+// thread, not the tensor core, limits the pipeline at these shapes (an MMA
+// of N <= 128 costs the same issue time whatever N is).
+__host__ __device__ constexpr bool tc_concat(bool tf32, int np) { return !tf32 && np == 16; }
+
 // X (FP64) -> split images + FP32 source coordinates, chunk by chunk. A chunk
 // is one contiguous record [hi image | lo image | x[kchunk] y[kchunk]
-// z[kchunk]] (the stage layout), so that one bulk copy loads it.
+// z[kchunk]] (the stage layout), so that one bulk copy loads it; with the
+// combined layout the two images form one image of 2 np rows.
 __global__ void tc_convert_kernel(const double* __restrict__ X, int64_t ldx, int64_t S, int c0, int kc,
                                   int np, int kchunk, bool tf32, float cscale, const float* __restrict__ sx,
                                   const float* __restrict__ sy, const float* __restrict__ sz,
@@ -353,7 +365,12 @@ __global__ void tc_convert_kernel(const double* __restrict__ X, int64_t ldx, int
         const float v = (s < S && n < kc) ? float(X[s + int64_t(c0 + n) * ldx]) : 0.f;
         uint8_t* base = img + ch * rec_bytes;
         const uint32_t off = img_offset(n, kk, np, esize);
-        if (tf32) {
+        if (tc_concat(tf32, np)) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+            *reinterpret_cast<__nv_bfloat16*>(base + img_offset(n, kk, 2 * np, esize)) = h;
+            *reinterpret_cast<__nv_bfloat16*>(base + img_offset(np + n, kk, 2 * np, esize)) = l;
+        } else if (tf32) {
             const uint32_t hi = tf32_rna(v);
             const uint32_t lo = tf32_rna(v - __uint_as_float(hi));
             *reinterpret_cast<uint32_t*>(base + off) = hi;
@@ -428,6 +445,9 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
     constexpr int STAGE_BYTES = 2 * IMG + KC * 12;      // hi, lo, coordinates x[KC] y[KC] z[KC]
     constexpr int SSTAGES = smem_stages(STAGE_BYTES);   // shared-memory ring (>= kStages)
     constexpr uint32_t IDESC = instr_desc(NP, TF32);
+    constexpr bool kConcat = tc_concat(TF32, NP);
+    constexpr uint32_t IDESC2 = instr_desc(2 * NP, TF32);  // combined [hi | lo] operand
+    static_assert(!kConcat || 2 * NP <= TmemLayout<NP>::kDStride, "combined accumulator wider than its buffer");
     constexpr bool kSum = TmemLayout<NP>::kSum;
     constexpr int kDStride = TmemLayout<NP>::kDStride;
     constexpr int kSBase = TmemLayout<NP>::kSBase;
@@ -454,7 +474,7 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&dfull_bar[b], 1);
-            mbar_init(&dfree_bar[b], 128);
+            mbar_init(&dfree_bar[b], 256);  // both warpgroups fold half of the columns
         }
         mbar_init(&drain_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -494,13 +514,15 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
             const int kind = I.kind;
             const int ngroups = (un.nloc + kGroup - 1) / kGroup;
             int flushed = 0;
-            // Warpgroup 0 folds the finished accumulator of local group g into
-            // the unit's running sums (rows owned by this thread) as FP32
-            // (hi, lo) pairs: an error-free two-sum of hi and the group's sum,
-            // its error added into lo (about 48 significant bits at FP32
-            // instruction cost). For N <= 32 the running sums stay in tensor
-            // memory and the last group writes them to the partial-sum array;
-            // otherwise every group updates that array in global memory.
+            // Both warpgroups fold the finished accumulator of local group g
+            // (warpgroup w the columns [w NP/2, (w+1) NP/2)) into the unit's
+            // running sums of the rows owned by the thread, as FP32 (hi, lo)
+            // pairs: an error-free two-sum of hi and the group's sum, its error
+            // added into lo (about 48 significant bits at FP32 instruction
+            // cost). For N <= 32 the running sums stay in tensor memory and
+            // the last group writes them to the partial-sum array; otherwise
+            // every group updates that array in global memory. With the
+            // combined operand the group's sum is the sum of its two halves.
             auto flush = [&](int g, bool last) {
                 const uint32_t gg = gbase + uint32_t(g);
                 const bool got = ok && warp_wait(&dfull_bar[gg & 1], uint32_t((gg >> 1) & 1));
@@ -508,10 +530,18 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                 tc_fence_after();
                 const uint32_t dcol = uint32_t((gg & 1) * kDStride);
 #pragma unroll 1
-                for (int cb = 0; cb < NP; cb += 8) {
+                for (int cb = wg * (NP / 2); cb < (wg + 1) * (NP / 2); cb += 8) {
                     uint32_t v[8], h[8], l[8];
                     __syncwarp();
                     tmem_ld8(tmem + lane_base + dcol + uint32_t(cb), v);
+                    if (kConcat) {
+                        uint32_t v2[8];
+                        tmem_ld8(tmem + lane_base + dcol + uint32_t(NP + cb), v2);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            v[q] = __float_as_uint(__fadd_rn(__uint_as_float(v[q]), __uint_as_float(v2[q])));
+                    }
                     if (kSum && g > 0) {
                         tmem_ld8(tmem + lane_base + uint32_t(kSBase + cb), h);
                         tmem_ld8(tmem + lane_base + uint32_t(kSBase + NP + cb), l);
@@ -554,16 +584,14 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                 mbar_arrive(&dfree_bar[gg & 1]);
             };
             for (int jl = wg; jl < un.nloc; jl += 2) {
-                if (wg == 0) {
-                    // group g is folded kFlushLag chunks after it ends, when
-                    // the tensor core has long finished it (never the last
-                    // group of the unit here)
-                    while (ok && jl >= kFlushLag && flushed < (jl - kFlushLag) / kGroup) {
-                        flush(flushed, false);
-                        ++flushed;
-                    }
-                    if (!ok) break;
+                // group g is folded kFlushLag chunks after it ends, when the
+                // tensor core has long finished it (never the last group of
+                // the unit here)
+                while (ok && jl >= kFlushLag && flushed < (jl - kFlushLag) / kGroup) {
+                    flush(flushed, false);
+                    ++flushed;
                 }
+                if (!ok) break;
                 const uint32_t jg = jbase + uint32_t(jl);
                 const int ss = int(jg % SSTAGES), s = int(jg % kStages);
                 if (!warp_wait(&loaded_bar[ss], uint32_t((jg / SSTAGES) & 1))) { ok = false; break; }
@@ -600,11 +628,9 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                 tc_fence_before();
                 mbar_arrive(&full_bar[s]);
             }
-            if (wg == 0) {
-                while (ok && flushed < ngroups) {
-                    flush(flushed, flushed == ngroups - 1);
-                    ++flushed;
-                }
+            while (ok && flushed < ngroups) {
+                flush(flushed, flushed == ngroups - 1);
+                ++flushed;
             }
             jbase += un.nloc;
             gbase += ngroups;
@@ -631,13 +657,22 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                     const uint32_t acol = tmem + uint32_t(kAColBase + s * kAColsPerStage);
 #pragma unroll
                     for (int ks = 0; ks < 2; ++ks) {
-                        const uint32_t step = uint32_t(ks * 2 * (NP / 8) * 128);
-                        const uint64_t bh = smem_desc(st + step, (NP / 8) * 128, 128);
-                        const uint64_t bl = smem_desc(st + IMG + step, (NP / 8) * 128, 128);
                         const uint32_t ah = acol + uint32_t(ks * 8), al = acol + 16u + uint32_t(ks * 8);
-                        mma_tmemA(TF32, d_tmem, ah, bh, IDESC, (first && ks == 0) ? 0u : 1u);
-                        mma_tmemA(TF32, d_tmem, ah, bl, IDESC, 1u);
-                        mma_tmemA(TF32, d_tmem, al, bh, IDESC, 1u);
+                        if (kConcat) {
+                            // rows 0..2NP-1 of the combined image: [X_hi | X_lo];
+                            // its first NP rows: X_hi
+                            const uint32_t step = uint32_t(ks * 2 * (2 * NP / 8) * 128);
+                            const uint64_t bb = smem_desc(st + step, (2 * NP / 8) * 128, 128);
+                            mma_tmemA(TF32, d_tmem, ah, bb, IDESC2, (first && ks == 0) ? 0u : 1u);
+                            mma_tmemA(TF32, d_tmem, al, bb, IDESC, 1u);
+                        } else {
+                            const uint32_t step = uint32_t(ks * 2 * (NP / 8) * 128);
+                            const uint64_t bh = smem_desc(st + step, (NP / 8) * 128, 128);
+                            const uint64_t bl = smem_desc(st + IMG + step, (NP / 8) * 128, 128);
+                            mma_tmemA(TF32, d_tmem, ah, bh, IDESC, (first && ks == 0) ? 0u : 1u);
+                            mma_tmemA(TF32, d_tmem, ah, bl, IDESC, 1u);
+                            mma_tmemA(TF32, d_tmem, al, bh, IDESC, 1u);
+                        }
                     }
                     mma_commit(&sempty_bar[ss]);
                     mma_commit(&tfree_bar[s]);
