@@ -4,12 +4,14 @@
 // 3 of the collocation matvec (Sec. 3.2), with Gamma never stored:
 //
 //   * A CTA owns 128 target points; target t is tensor-memory lane t. Eight
-//     producer warps (two warpgroups, warp w serving lanes 32*(w%4)..) take
-//     source chunks in turn; each thread evaluates Gamma(x_t, y_j) for the
-//     chunk's sources in FP32 registers, splits every value into a high and a
-//     low part (BF16 + BF16 or TF32 + TF32) and writes both straight into
-//     tensor memory with tcgen05.st: the kernel tile becomes the A operand
-//     of the MMA without passing through shared memory.
+//     producer warps (two warpgroups, warp w serving lanes 32*(w%4)..) share
+//     every chunk of 64 (BF16) or 32 (TF32) sources, each warpgroup one half;
+//     each thread evaluates Gamma(x_t, y_j) for its sources in FP32
+//     registers, splits every value into a high and a low part (BF16 + BF16
+//     or TF32 + TF32) and writes both straight into tensor memory with
+//     tcgen05.st: the kernel tile becomes the A operand of the MMA without
+//     passing through shared memory. Two tiles alternate, so the producers
+//     fill one while the tensor core reads the other.
 //   * The source values X (FP64 in HBM) are converted once per application
 //     into the same hi/lo split, laid out as K-major no-swizzle core matrices
 //     (8 rows x 16 bytes) chunk by chunk together with the chunk's source
@@ -51,16 +53,18 @@ namespace kl {
 
 namespace {
 
-constexpr int kStages = 4;                // TMEM A-operand ring (kernel tiles)
+constexpr int kStages = 2;                // TMEM A-operand ring (kernel tiles of one chunk)
 constexpr int kProducers = 256;           // two warpgroups
 constexpr int kThreads = kProducers + 64; // + MMA warp + loader warp
 constexpr int kTmemCols = 256;
-constexpr int kAColsPerStage = 32;        // hi 16 + lo 16 columns
-constexpr int kGroup = 8;                 // chunks accumulated in FP32 before a flush
-constexpr int kFlushLag = 4;              // chunks between a group's end and its flush
+constexpr int kAColsPerStage = 64;        // hi 32 + lo 32 columns (64 BF16 / 32 TF32 sources)
+constexpr int kKSteps = 4;                // MMA K steps per chunk (K = 16 BF16 / 8 TF32 each)
+constexpr int kGroup = 4;                 // chunks accumulated in FP32 before a fold
+                                          // (256 BF16 / 128 TF32 sources)
+constexpr int kFlushLag = 2;              // chunks between a group's end and its fold
 // Tensor memory of a CTA (256 columns): two accumulator buffers (32 columns
 // each for N <= 32, else 64); for N <= 32 the running (hi, lo) sums of the
-// unit (2N columns); then the 4-stage ring of kernel tiles (32 columns each).
+// unit (2N columns); then the 2-slot ring of kernel tiles (64 columns each).
 template <int NP>
 struct TmemLayout {
     static constexpr bool kSum = NP <= 32;             // running sums in TMEM
@@ -89,6 +93,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // ones (polling cost 5 % of the pairwise kernel's time).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     const uint32_t a = smem_u32(bar);
+    uint32_t ready;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ready)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ready) return true;
     const long long t0 = clock64();
     while (true) {
         uint32_t ok;
@@ -318,10 +331,10 @@ float coord_scale(const KernelSpec& ks) {
 }
 
 // Depth of the shared-memory stage ring: the largest power of two (16 at
-// most, the TMEM ring depth at least) whose stages fit in ~100 KB (two CTAs
-// per SM). Powers of two keep the ring arithmetic to shifts and masks.
+// most, 4 at least) whose stages fit in ~100 KB (two CTAs per SM). Powers of
+// two keep the ring arithmetic to shifts and masks.
 __host__ __device__ constexpr int smem_stages(int stage_bytes) {
-    return (99 * 1024) / stage_bytes >= 16 ? 16 : (99 * 1024) / stage_bytes >= 8 ? 8 : kStages;
+    return (99 * 1024) / stage_bytes >= 16 ? 16 : (99 * 1024) / stage_bytes >= 8 ? 8 : 4;
 }
 
 // Byte offset of element (n, kk) inside one hi or lo image of a chunk:
@@ -440,7 +453,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
     const int64_t nunits = batch.nunits;
     constexpr int ESIZE = TF32 ? 4 : 2;
-    constexpr int KC = TF32 ? 16 : 32;                  // sources per chunk (16 TMEM columns)
+    constexpr int KC = TF32 ? 32 : 64;                  // sources per chunk (32 TMEM columns)
+    constexpr int SW = KC / 2;                          // sources of each warpgroup
     constexpr int IMG = NP * KC * ESIZE;                // bytes of one of hi / lo
     constexpr int STAGE_BYTES = 2 * IMG + KC * 12;      // hi, lo, coordinates x[KC] y[KC] z[KC]
     constexpr int SSTAGES = smem_stages(STAGE_BYTES);   // shared-memory ring (>= kStages)
@@ -469,7 +483,7 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
             mbar_init(&sempty_bar[s], 1);
         }
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full_bar[s], 128);
+            mbar_init(&full_bar[s], 256);  // both warpgroups write half of every tile
             mbar_init(&tfree_bar[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -491,7 +505,7 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
     const uint32_t tmem = tmem_slot;
 
     if (warp < 8) {
-        // ---------------- producers (two warpgroups, alternate chunks) ----------------
+        // ---------------- producers (two warpgroups, half of each chunk) ----------------
         const int wg = warp >> 2;
         const int ptid = tid & 127;
         const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
@@ -583,7 +597,7 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                 tc_fence_before();
                 mbar_arrive(&dfree_bar[gg & 1]);
             };
-            for (int jl = wg; jl < un.nloc; jl += 2) {
+            for (int jl = 0; jl < un.nloc; ++jl) {
                 // group g is folded kFlushLag chunks after it ends, when the
                 // tensor core has long finished it (never the last group of
                 // the unit here)
@@ -596,7 +610,7 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                 const int ss = int(jg % SSTAGES), s = int(jg % kStages);
                 if (!warp_wait(&loaded_bar[ss], uint32_t((jg / SSTAGES) & 1))) { ok = false; break; }
                 if (jg >= kStages && !warp_wait(&tfree_bar[s], uint32_t(((jg / kStages) - 1) & 1))) { ok = false; break; }
-                const float* cx = reinterpret_cast<const float*>(smem + ss * STAGE_BYTES + 2 * IMG);
+                const float* cx = reinterpret_cast<const float*>(smem + ss * STAGE_BYTES + 2 * IMG) + wg * SW;
                 const uint32_t acol = uint32_t(kAColBase + s * kAColsPerStage);
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
@@ -605,7 +619,7 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                     uint32_t hi[8], lo[8];
 #pragma unroll
                     for (int q4 = 0; q4 < (TF32 ? 2 : 4); ++q4) {
-                        const int j0 = (KC / 2) * half + 4 * q4;
+                        const int j0 = (SW / 2) * half + 4 * q4;
                         const ulonglong2 xv = *reinterpret_cast<const ulonglong2*>(cx + j0);
                         const ulonglong2 yv = *reinterpret_cast<const ulonglong2*>(cx + KC + j0);
                         const ulonglong2 zv = *reinterpret_cast<const ulonglong2*>(cx + 2 * KC + j0);
@@ -621,8 +635,8 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                         }
                     }
                     __syncwarp();
-                    tmem_st8(tmem + lane_base + acol + uint32_t(8 * half), hi);
-                    tmem_st8(tmem + lane_base + acol + 16u + uint32_t(8 * half), lo);
+                    tmem_st8(tmem + lane_base + acol + uint32_t(16 * wg + 8 * half), hi);
+                    tmem_st8(tmem + lane_base + acol + 32u + uint32_t(16 * wg + 8 * half), lo);
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
@@ -656,8 +670,8 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                     const uint32_t st = smem_u32(smem + ss * STAGE_BYTES);
                     const uint32_t acol = tmem + uint32_t(kAColBase + s * kAColsPerStage);
 #pragma unroll
-                    for (int ks = 0; ks < 2; ++ks) {
-                        const uint32_t ah = acol + uint32_t(ks * 8), al = acol + 16u + uint32_t(ks * 8);
+                    for (int ks = 0; ks < kKSteps; ++ks) {
+                        const uint32_t ah = acol + uint32_t(ks * 8), al = acol + 32u + uint32_t(ks * 8);
                         if (kConcat) {
                             // rows 0..2NP-1 of the combined image: [X_hi | X_lo];
                             // its first NP rows: X_hi
@@ -730,7 +744,7 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
 template <int KIND, bool TF32, int NP>
 cudaError_t launch_batch_np(const TcBatch& b, int sm_count, int* err, cudaStream_t s) {
     constexpr int ESIZE = TF32 ? 4 : 2;
-    constexpr int KC = TF32 ? 16 : 32;
+    constexpr int KC = TF32 ? 32 : 64;
     constexpr int STAGE_BYTES = 2 * NP * KC * ESIZE + KC * 12;
     // at least ~100 KB so that no more than two CTAs share an SM (256 TMEM
     // columns each)
@@ -808,17 +822,17 @@ struct TcPlan {
 // Persistent schedule: 2 CTAs per SM walk the units (tile, source range)
 // round-robin. Splitting every tile's sources into `splits` ranges of equal
 // length gives about 16 units per CTA (load imbalance <= 1/16) while keeping
-// ranges >= 24 chunks long and the FP64 partial sums <= 64 MiB.
+// ranges >= 768 sources long and the partial sums <= 64 MiB.
 TcPlan plan(int64_t T, int64_t S, int k, int sm_count, bool tf32) {
     TcPlan p;
-    p.kchunk = tf32 ? 16 : 32;
+    p.kchunk = tf32 ? 32 : 64;
     p.nchunks = std::max<int64_t>(1, (S + p.kchunk - 1) / p.kchunk);
     const int kmax = std::min(k, 64);
     p.np_max = std::max(16, (kmax + 15) / 16 * 16);
     const int64_t tiles = (T + 127) / 128;
     const int64_t grid = 2LL * sm_count;
     int64_t want = (16 * grid + tiles - 1) / tiles;
-    want = std::min(want, std::max<int64_t>(1, p.nchunks / 24));
+    want = std::min(want, std::max<int64_t>(1, p.nchunks * p.kchunk / 768));
     want = std::min(want, std::max<int64_t>(1, (int64_t(8) << 20) / (int64_t(k) * T)));
     want = std::max<int64_t>(1, want);
     p.cps = int((p.nchunks + want - 1) / want);
