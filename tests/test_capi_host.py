@@ -132,8 +132,9 @@ def test_estimate_bytes_on_host(kl):
     assert _est(kl, M=40) > base
     assert _est(kl, block_k=32) > base
     assert _est(kl, method="collocation") > base
-    # C0 interpolation of the exponential kernels has about p^3 more points
-    assert _est(kl, kernel="exp") > 2 * base
+    # C0 interpolation of the exponential kernels has about 5x the points
+    # (17^3 vs 10^3 here); the basis and its workspaces do not grow with them
+    assert _est(kl, kernel="exp") > 1.5 * base
     # lower bound: the Krylov basis and its image alone (2 N mcap doubles)
     p = kl.params(geometry="cube", degree=2, elems=(16, 16, 16), kernel="exp_sep", method="galerkin",
                   precision="bf16", block_k=8)
