@@ -52,6 +52,9 @@ def _args():
     ap.add_argument("--workload", default=WORKLOAD,
                     help="workload of kl_inputs.WORKLOADS (default: the 16^3 cube, the benchmark's configuration)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving (continuous batching) leg")
+    ap.add_argument("--autotune", action="store_true",
+                    help="choose each method's block size with kl_autotune (complete solves for k = 8, 16, 32, "
+                         "before the timed region) instead of the workload's k")
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the seeded serving stream replayed by the serving leg")
     ap.add_argument("--serve-max-elems", type=int, default=8,
@@ -313,6 +316,16 @@ def run_gpu(a):
     w = WORKLOADS[a.workload]
     args = problem_args(w)
     M, k = w["M"], w["k"]
+    ks = {m: k for m in METHODS}
+    tuned = {}
+    if a.autotune:
+        for m in METHODS:
+            pt = kl.params(geometry=args["geometry"], degree=args["p"], elems=args["elems"], kernel=args["kernel"],
+                           sigma=args["sigma"], L=args["L"], method=m, precision=a.precision, block_k=8,
+                           seed=2101 + 7919 * rank)
+            best, secs = kl.kl_autotune(pt, M, 0.0, stream)
+            ks[m] = best
+            tuned[m] = {"k": best, "solve_s": {str(c): (round(t, 4) if t >= 0 else None) for c, t in zip((8, 16, 32), secs)}}
 
     # one stream per solve: the two independent solves of a step run
     # concurrently (the GPU is mostly idle during one solve's one-CTA
@@ -321,7 +334,7 @@ def run_gpu(a):
 
     def make(method, precision, st=None):
         p = kl.params(geometry=args["geometry"], degree=args["p"], elems=args["elems"], kernel=args["kernel"],
-                      sigma=args["sigma"], L=args["L"], method=method, precision=precision, block_k=k,
+                      sigma=args["sigma"], L=args["L"], method=method, precision=precision, block_k=ks[method],
                       seed=2101 + 7919 * rank)
         return kl.kl_create(p, st if st is not None else stream)
 
@@ -479,7 +492,7 @@ def run_gpu(a):
         t0 = time.perf_counter()
         for m in METHODS:
             p = kl.params(geometry=args["geometry"], degree=args["p"], elems=args["elems"], kernel=args["kernel"],
-                          sigma=args["sigma"], L=args["L"], method=m, precision=a.precision, block_k=k)
+                          sigma=args["sigma"], L=args["L"], method=m, precision=a.precision, block_k=ks[m])
             h = kl.kl_create(p, stream)
             h2d_m, _ = kl.kl_memory(h)
             kl.kl_eigs(h, M, 0.0, lam_h, V_h, N, 0)
@@ -533,7 +546,8 @@ def run_gpu(a):
         "vs_baseline": None,
         "dtype": "f32 kernel tiles, split-bf16 tcgen05 products, f64 solver" if a.precision == "bf16" else a.precision,
         "data": "synthetic",
-        "config": {"workload": a.workload, "N": N, "M": M, "k": k, "methods": list(METHODS),
+        "config": {"workload": a.workload, "N": N, "M": M, "k": (dict(ks) if a.autotune else k), "methods": list(METHODS),
+                   **({"autotune": tuned} if a.autotune else {}),
                    "precision": a.precision, "l2": "flushed between steps (256 MB write)",
                    "step": "the Galerkin and the collocation solve run concurrently on two streams",
                    "parallelism": "replicas" if world > 1 else "single"},

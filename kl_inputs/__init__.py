@@ -23,6 +23,9 @@ WORKLOADS = {
     "annulus_p2_e64x32x16_exp": dict(geometry="annulus", p=2, elems=(64, 32, 16), kernel="exp",
                                       sigma=1.0, L=1.0, M=100, k=32,
                                       methods=("galerkin", "collocation")),
+    "annulus_p4_e64x32x16_exp": dict(geometry="annulus", p=4, elems=(64, 32, 16), kernel="exp",
+                                      sigma=1.0, L=1.0, M=100, k=32,
+                                      methods=("galerkin", "collocation")),
 }
 
 # Small parity cases: several 128-point tiles with ragged tails, sizes the
