@@ -914,13 +914,19 @@ cudaError_t launch_eig(const double* H, int n, double* wr, double* wi, double* V
 }  // namespace
 
 int64_t nonsym_eig_work_doubles(int n) { return 3 * int64_t(n) * n + 12 * int64_t(n); }
-int64_t sym_eig_work_doubles(int n) { return nonsym_eig_work_doubles(n); }
+int64_t sym_eig_work_doubles(int n) { return std::max(nonsym_eig_work_doubles(n), jacobi_work_doubles(n)); }
 
-// Symmetric eigenproblem: the same Hessenberg (here tridiagonal) reduction and
-// Francis QR; the ordered real Schur form of a symmetric matrix is diagonal,
-// so the ordered Schur vectors are orthonormal eigenvectors.
+// Symmetric eigenproblem. FP64: parallel Jacobi in FP32 refined in FP64 up to
+// jacobi_max_n(). FP32, and FP64 beyond that order: the same Hessenberg (here
+// tridiagonal) reduction and Francis QR as the non-symmetric one: the ordered
+// real Schur form of a symmetric matrix is diagonal, so the ordered Schur
+// vectors are orthonormal eigenvectors. (FP32 Jacobi alone accumulates the
+// rounding of thousands of rotations in its vectors: invariant subspaces of
+// clustered K-L eigenvalues came out 1e-4 off, against 1e-6 for the QR path,
+// and restarts from them slowed convergence.)
 cudaError_t launch_sym_eig(const double* H, int n, double* w, double* V, double* work, int* status,
                            cudaStream_t s, bool fp32) {
+    if (!fp32 && n <= jacobi_max_n()) return launch_sym_eig_jacobi(H, n, w, V, work, status, s, false);
     return launch_eig(H, n, w, nullptr, V, nullptr, work, status, 1, n, fp32, s);
 }
 

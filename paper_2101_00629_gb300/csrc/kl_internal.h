@@ -145,6 +145,12 @@ cudaError_t launch_nonsym_eig(const double* H, int n, double* wr, double* wi, do
                               double* work, int* status, cudaStream_t s, int nvec = 0, bool fp32 = false);
 int64_t nonsym_eig_work_doubles(int n);
 int64_t sym_eig_work_doubles(int n);
+// Symmetric eigenproblems of order n <= jacobi_max_n() by parallel Jacobi
+// (FP32, or FP32 refined in FP64); workspace of the FP64 form in doubles.
+int jacobi_max_n();
+int64_t jacobi_work_doubles(int n);
+cudaError_t launch_sym_eig_jacobi(const double* H, int n, double* w, double* V, double* work, int* status,
+                                  cudaStream_t s, bool fp32);
 // Column 2-norms of X (K x n).
 cudaError_t launch_col_norms(const double* X, int64_t ldx, int64_t K, int n, double* out,
                              cudaStream_t s);
