@@ -17,6 +17,14 @@
  *                    Z_ij = R_j(x_i) (Eq. colloc system matrices), applied by
  *                    Algorithm 1 with (p+1)^3 Gauss points per element and the
  *                    Kronecker structure of Z (Sec. 3.3, Remark).
+ *   KL_GALERKIN_STD  Sec. 3.1 (the standard method the IBQ replaces): the
+ *                    trial space of KL_GALERKIN_IBQ with both integrals of
+ *                    Eq. galerkin_system_matrices evaluated by the Gauss-Legendre
+ *                    rule of (p+1)^3 points per element,
+ *                    A = N_q^T W Gamma W N_q with N_q the trial functions at the
+ *                    points and W their weights times det DF; Gamma over all
+ *                    pairs of Gauss points (O(N_e^2 (p+1)^6) per application).
+ *                    Z as for KL_GALERKIN_IBQ. Reference solutions (Sec. 4).
  *
  * Conventions used by every entry point:
  *   - Dofs and points are ordered lexicographically with parametric
@@ -72,7 +80,7 @@ enum { KL_GEOM_CUBE = 0, KL_GEOM_QUARTER_ANNULUS = 1 };
 enum { KL_KERNEL_GAUSS = 0, KL_KERNEL_EXP_SEP = 1, KL_KERNEL_EXP = 2,
        KL_KERNEL_MATERN32 = 3, KL_KERNEL_CONST = 4 };
 
-enum { KL_GALERKIN_IBQ = 0, KL_COLLOCATION = 1 };
+enum { KL_GALERKIN_IBQ = 0, KL_COLLOCATION = 1, KL_GALERKIN_STD = 2 };
 
 /* Arithmetic of the pairwise product Gamma * X (the O(N~^2) / O(N N_e N_q)
  * step; Sec. 3.3). Everything else (sum factorisation, Z solves,
@@ -97,7 +105,8 @@ typedef struct kl_params {
     int kernel;              /* KL_KERNEL_*                                   */
     double sigma;            /* standard deviation (> 0)                      */
     double L;                /* correlation length (> 0)                      */
-    int method;              /* KL_GALERKIN_IBQ or KL_COLLOCATION             */
+    int method;              /* KL_GALERKIN_IBQ, KL_COLLOCATION or
+                                KL_GALERKIN_STD                               */
     int interp_continuity;   /* Galerkin interpolation space continuity:
                                 -2 = rule of Sec. 4 (C^0 for the exponential
                                 kernels, C^{p-1} otherwise), else 0 .. p-1    */

@@ -32,7 +32,7 @@ KL_WARN_COMPLEX = 1
 
 GEOMETRIES = {"cube": 0, "annulus": 1}
 KERNELS = {"gauss": 0, "exp_sep": 1, "exp": 2, "matern32": 3, "const": 4}
-METHODS = {"galerkin": 0, "collocation": 1}
+METHODS = {"galerkin": 0, "collocation": 1, "galerkin_std": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2, "tf32": 3}
 
 # Every entry point declared in include/kl.h.

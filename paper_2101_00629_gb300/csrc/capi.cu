@@ -227,20 +227,18 @@ void clear_graphs(kl_solver* h) {
 // 1) sum factorisation to the source points, scaled by J (Galerkin) or
 //    w det DF (collocation, Algorithm 1 steps 1-2): X -> ws[0]
 static int apply_pre(kl_solver* h, int which, const double* X, int64_t ldx, int k) {
-    const bool gal = h->prm.method == KL_GALERKIN_IBQ;
+    const bool gal = galerkin_form(h->prm.method);
     const double* const* F = (gal && which == 1) ? h->P : h->F;
-    const int* n_src = gal ? h->Nt1 : h->Nq1;
-    return kron3(h, F, h->N1, n_src, X, ldx, h->ws[0], h->S, k, h->src_scale, 1, 2);
+    return kron3(h, F, h->N1, h->Ns1, X, ldx, h->ws[0], h->S, k, h->src_scale, 1, 2);
 }
 
 // 3) back to the trial space: Galerkin J, B~^-1, M^T (and L^-1); collocation
 //    Z^-1 for A': ws[1] -> Y
 static int apply_post(kl_solver* h, int which, double* Y, int64_t ldy, int k) {
-    const bool gal = h->prm.method == KL_GALERKIN_IBQ;
+    const bool gal = galerkin_form(h->prm.method);
     const double* const* FT = (gal && which == 1) ? h->PT : h->FT;
-    const int* n_src = gal ? h->Nt1 : h->Nq1;
     double* W = h->ws[1];
-    if (gal) return kron3(h, FT, n_src, h->N1, W, h->T, Y, ldy, k, nullptr, 0, 2);
+    if (gal) return kron3(h, FT, h->Ns1, h->N1, W, h->T, Y, ldy, k, nullptr, 0, 2);
     if (which == 1) return kron3(h, h->Zinv, h->N1, h->N1, W, h->T, Y, ldy, k, nullptr, 0, 2);
     cudaError_t e = launch_copy_block(W, h->T, Y, ldy, h->T, k, h->stream);
     ++h->launches;
@@ -251,7 +249,7 @@ static int apply_post(kl_solver* h, int which, double* Y, int64_t ldy, int k) {
 // 2) pairwise product over all (target, source) pairs (Algorithm 1 step 3):
 //    ws[0] -> ws[1]
 static int apply_pair(kl_solver* h, int precision, int k) {
-    const bool gal = h->prm.method == KL_GALERKIN_IBQ;
+    const bool gal = galerkin_form(h->prm.method);
     return pairwise(h, precision, h->ws[0], h->ws[1], k, gal ? h->src_scale : nullptr);
 }
 
@@ -330,7 +328,7 @@ int apply_zinv(kl_solver* h, const double* X, int64_t ldx, double* Y, int64_t ld
 }
 
 int back_transform(kl_solver* h, const double* Yv, int64_t ldy, double* V, int64_t ldv, int k) {
-    if (h->prm.method == KL_GALERKIN_IBQ)
+    if (galerkin_form(h->prm.method))
         return kron3(h, h->LinvT, h->N1, h->N1, Yv, ldy, V, ldv, k, nullptr, 0, 1);
     cudaError_t e = launch_copy_block(Yv, ldy, V, ldv, h->N, k, h->stream);
     ++h->launches;
@@ -401,7 +399,8 @@ static std::string check_params(const kl_params& p) {
     if (p.kernel < KL_KERNEL_GAUSS || p.kernel > KL_KERNEL_CONST) return "unknown kernel";
     if (!(p.sigma > 0) || !std::isfinite(p.sigma)) return "sigma must be > 0";
     if (!(p.L > 0) || !std::isfinite(p.L)) return "L must be > 0";
-    if (p.method != KL_GALERKIN_IBQ && p.method != KL_COLLOCATION) return "unknown method";
+    if (p.method != KL_GALERKIN_IBQ && p.method != KL_COLLOCATION && p.method != KL_GALERKIN_STD)
+        return "unknown method";
     if (p.interp_continuity != -2 && (p.interp_continuity < 0 || p.interp_continuity > p.degree - 1))
         return "interp_continuity must be -2 or in 0..p-1";
     if (p.precision < KL_FP64 || p.precision > KL_MIXED_TF32) return "unknown precision";
@@ -444,7 +443,9 @@ int kl_create(const kl_params* params, void* stream, kl_solver** out) {
         return bail(fail(h, KL_ERR_UNSUPPORTED, "tcgen05 precisions need an sm_100-class GPU"));
 
     const kl_params& p = h->prm;
-    const bool gal = p.method == KL_GALERKIN_IBQ;
+    const bool ibq = p.method == KL_GALERKIN_IBQ;
+    const bool stdg = p.method == KL_GALERKIN_STD;  // Gauss points as sources and targets
+    const bool gal = ibq || stdg;
     const bool exp_kernel = p.kernel == KL_KERNEL_EXP || p.kernel == KL_KERNEL_EXP_SEP;
     const int icont = p.interp_continuity == -2 ? (exp_kernel ? 0 : p.degree - 1) : p.interp_continuity;
 
@@ -459,9 +460,10 @@ int kl_create(const kl_params* params, void* stream, kl_solver** out) {
         h->N1[d] = dir[d].N;
         h->Nt1[d] = dir[d].Nt;
         h->Nq1[d] = dir[d].nq;
+        h->Ns1[d] = ibq ? dir[d].Nt : stdg ? dir[d].ne : dir[d].nq;
     }
     h->N = prod3(h->N1);
-    h->S = gal ? prod3(h->Nt1) : prod3(h->Nq1);
+    h->S = prod3(h->Ns1);
     h->T = gal ? h->S : h->N;
 
     // ---- tables: pack every 1D array into one host buffer, upload once ----
@@ -474,11 +476,21 @@ int kl_create(const kl_params* params, void* stream, kl_solver** out) {
     };
     for (int d = 0; d < 3; ++d) {
         const Dir1D& q = dir[d];
-        if (gal) {
+        if (ibq) {
             push(q.Q.a);
             push(transpose(q.Q).a);
             push(q.P.a);
             push(transpose(q.P).a);
+            push(q.Zinv_gal.a);
+            push(q.LinvT.a);
+        } else if (stdg) {
+            // trial functions at the Gauss points (times sqrt(det DF) on the
+            // device), and with L^-T folded in for A'
+            const Mat EL = matmul(q.E, q.LinvT);
+            push(q.E.a);
+            push(transpose(q.E).a);
+            push(EL.a);
+            push(transpose(EL).a);
             push(q.Zinv_gal.a);
             push(q.LinvT.a);
         } else {
@@ -490,9 +502,9 @@ int kl_create(const kl_params* params, void* stream, kl_solver** out) {
             push(identity(q.N).a);
         }
     }
-    for (int d = 0; d < 3; ++d) push(gal ? dir[d].xg : dir[d].xc);  // target params
-    for (int d = 0; d < 3; ++d) push(gal ? dir[d].xg : dir[d].xq);  // source params
-    for (int d = 0; d < 3; ++d) push(gal ? std::vector<double>(dir[d].Nt, 1.0) : dir[d].wq);
+    for (int d = 0; d < 3; ++d) push(ibq ? dir[d].xg : stdg ? dir[d].xe : dir[d].xc);  // target params
+    for (int d = 0; d < 3; ++d) push(ibq ? dir[d].xg : stdg ? dir[d].xe : dir[d].xq);  // source params
+    for (int d = 0; d < 3; ++d) push(ibq ? std::vector<double>(dir[d].Nt, 1.0) : stdg ? dir[d].we : dir[d].wq);
     for (int d = 0; d < 3; ++d) push(dir[d].E.a);   // trial basis at the Gauss points
     for (int d = 0; d < 3; ++d) push(dir[d].xe);    // those points
     if ((e = dalloc(h, &h->d_tables, int64_t(buf.size()))) != cudaSuccess)
@@ -526,14 +538,14 @@ int kl_create(const kl_params* params, void* stream, kl_solver** out) {
     if ((e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream)) != cudaSuccess)
         return bail(cuda_fail(h, e, "error word"));
     double geo[3] = {p.geo[0], p.geo[1], p.geo[2]};
-    const int* nsrc = gal ? h->Nt1 : h->Nq1;
+    const int* nsrc = h->Ns1;
     h->sx = h->d_points;
     h->sy = h->sx + S;
     h->sz = h->sy + S;
     h->src_scale = h->sz + S;
     e = launch_tensor_points(p.geometry, geo, h->pts1d[3], h->pts1d[4], h->pts1d[5], nsrc[0], nsrc[1],
-                             nsrc[2], gal ? nullptr : h->pts1d[6], gal ? nullptr : h->pts1d[7],
-                             gal ? nullptr : h->pts1d[8], gal ? 0.5 : 1.0, h->sx, h->sy, h->sz,
+                             nsrc[2], ibq ? nullptr : h->pts1d[6], ibq ? nullptr : h->pts1d[7],
+                             ibq ? nullptr : h->pts1d[8], gal ? 0.5 : 1.0, h->sx, h->sy, h->sz,
                              h->src_scale, h->stream);
     ++h->launches;
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "source points"));
@@ -599,7 +611,7 @@ int kl_sample(kl_solver* h, int M, const double* lambda, const double* V, int64_
     if (ldv < N || ldxi < M || ldo < Q) return fail(h, KL_ERR_ARG, "leading dimensions too small");
     // scratch: sqrt(lambda) (M), diag(sqrt lambda) xi (M x ns), C = V diag xi (N x ns),
     // two intermediate products of the evaluation (<= Q x ns each)
-    const bool gal = h->prm.method == KL_GALERKIN_IBQ;
+    const bool gal = galerkin_form(h->prm.method);
     const int64_t need = (M + 3) / 4 * 4 + int64_t(M) * ns + N * ns + 2 * Q * ns + (gal ? 4 * Q : 0);
     if (need > h->smp_cap) {
         cudaError_t e = cudaStreamSynchronize(h->stream);
@@ -664,10 +676,12 @@ int kl_estimate_bytes(const kl_params* params, int M, int64_t* bytes) {
     if (!msg.empty()) return fail(nullptr, KL_ERR_ARG, msg);
     kl_params p = *params;
     if (p.block_k == 0) p.block_k = 8;
-    const bool gal = p.method == KL_GALERKIN_IBQ;
+    const bool ibq = p.method == KL_GALERKIN_IBQ;
+    const bool stdg = p.method == KL_GALERKIN_STD;
+    const bool gal = ibq || stdg;
     const bool exp_kernel = p.kernel == KL_KERNEL_EXP || p.kernel == KL_KERNEL_EXP_SEP;
     const int icont = p.interp_continuity == -2 ? (exp_kernel ? 0 : p.degree - 1) : p.interp_continuity;
-    int64_t N = 1, Nt = 1, Nq = 1, tab = 0;
+    int64_t N = 1, Ns = 1, tab = 0;
     auto add = [&](int64_t n) { tab += (n + 3) / 4 * 4; };
     for (int d = 0; d < 3; ++d) {
         Dir1D q;
@@ -675,20 +689,19 @@ int kl_estimate_bytes(const kl_params* params, int M, int64_t* bytes) {
         const bool rational = (p.geometry == KL_GEOM_QUARTER_ANNULUS) && d == 0;
         std::string m = setup_direction(q, present, present ? p.elems[d] : 1, p.degree, icont, rational, gal, !gal);
         if (!m.empty()) return fail(nullptr, KL_ERR_NUMERIC, "set-up: " + m);
+        const int64_t ns = ibq ? q.Nt : stdg ? q.ne : q.nq;
         N *= q.N;
-        Nt *= q.Nt;
-        Nq *= q.nq;
-        const int64_t ns = gal ? q.Nt : q.nq;
+        Ns *= ns;
         for (int i = 0; i < 4; ++i) add(ns * q.N);
         add(int64_t(q.N) * q.N);
         add(int64_t(q.N) * q.N);
-        add(gal ? q.Nt : q.N);
+        add(gal ? ns : q.N);
         add(ns);
         add(ns);
         add(int64_t(q.ne) * q.N);
         add(q.ne);
     }
-    const int64_t S = gal ? Nt : Nq, T = gal ? S : N;
+    const int64_t S = Ns, T = gal ? S : N;
     int sm = 152;
     int dev = 0, ndev = 0;
     if (cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0 && cudaGetDevice(&dev) == cudaSuccess) {

@@ -34,6 +34,7 @@ struct kl_solver {
     int N1[3] = {1, 1, 1};   // trial dofs per direction
     int Nt1[3] = {1, 1, 1};  // interpolation dofs per direction (Galerkin)
     int Nq1[3] = {1, 1, 1};  // quadrature points per direction (collocation)
+    int Ns1[3] = {1, 1, 1};  // source points per direction (Nt1, the Gauss points, Nq1)
     int64_t N = 0;           // trial dofs
     int64_t S = 0;           // pairwise sources (N~ or NeNq)
     int64_t T = 0;           // pairwise targets (N~ or N)

@@ -56,9 +56,14 @@ struct Dir1D {
     // evaluation of fields sum_j v_j N_j at the tensor Gauss grid.
     int ne = 1;                 // Gauss points of this direction (p + 1 per element)
     std::vector<double> xe;     // their parameters (ne)
+    std::vector<double> we;     // their Gauss weights (ne)
     Mat E;                      // trial basis at them (ne x N)
     Mat Zinv_col;               // (R_j(xc_i))^-1      (N x N)
 };
+
+// Both Galerkin forms (IBQ and standard quadrature): the trial space
+// B_i / sqrt(det DF), a symmetric operator in standard form A' = L^-1 A L^-T.
+inline bool galerkin_form(int method) { return method == KL_GALERKIN_IBQ || method == KL_GALERKIN_STD; }
 
 // Builds the direction's tables. `rational` = direction 1 of the annulus
 // (NURBS weights from the quadratic arc). `present` = false gives the 1-dof

@@ -273,6 +273,7 @@ std::string setup_direction(Dir1D& d, bool present, int nel, int p, int interp_c
         d.Q = d.P = d.LinvT = d.Zinv_gal = d.R = d.Zinv_col = d.E = identity(1);
         d.ne = 1;
         d.xe = {0.0};
+        d.we = {1.0};
         d.xq = {0.0};
         d.wq = {1.0};
         d.xc = {0.0};
@@ -333,6 +334,7 @@ std::string setup_direction(Dir1D& d, bool present, int nel, int p, int interp_c
     }
     d.ne = int(xq.size());
     d.xe = xq;
+    d.we = wq;
     d.E = need_collocation ? d.R : BU;
     return "";
 }

@@ -224,12 +224,12 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
     // is quadratic in the residual, that of the non-symmetric collocation form
     // only linear, hence the tighter FP64 default there.
     if (!(tol > 0))
-        tol = (prec == KL_FP64) ? (h->prm.method == KL_GALERKIN_IBQ ? 1e-10 : 1e-12) : 1e-6;
+        tol = (prec == KL_FP64) ? (galerkin_form(h->prm.method) ? 1e-10 : 1e-12) : 1e-6;
 
     Ctx c;
     c.h = h;
     c.N = h->N;
-    c.sym = h->prm.method == KL_GALERKIN_IBQ;
+    c.sym = galerkin_form(h->prm.method);
     const int64_t N = h->N;
     if (h->autotune) {
         // block size from the autotuner's cache for this problem and M
