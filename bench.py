@@ -60,6 +60,11 @@ def _args():
     ap.add_argument("--serve-max-elems", type=int, default=8,
                     help="per-axis element cap of the serving stream sample")
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--accuracy", action="store_true",
+                    help="accuracy-versus-time study instead of the benchmark: every method on a sequence of cube "
+                         "meshes against the standard Gauss-Legendre Galerkin solution on the finest one")
+    ap.add_argument("--accuracy-elems", default="4,8,12,16", help="per-axis element counts of the study")
+    ap.add_argument("--accuracy-kernel", default="exp_sep", choices=["gauss", "exp_sep", "exp", "matern32"])
     return ap.parse_args()
 
 
@@ -575,10 +580,65 @@ def run_gpu(a):
         dist.destroy_process_group()
 
 
+def run_accuracy(a):
+    """Accuracy versus time in the manner of Sec. 4 (Figs. 4-6): the mixed
+    precision solves of every method on h-refined unit-cube meshes (p = 2),
+    their eigensolver time, and the mean / largest relative error of their
+    first M eigenvalues against the reference, the standard Gauss-Legendre
+    Galerkin solution in FP64 on the finest mesh (as the paper's reference is
+    the standard Galerkin solution on its finest mesh)."""
+    import numpy as np
+    import torch
+    import paper_2101_00629_gb300 as kl
+
+    M, k = 20, 8
+    L = {"gauss": 0.5}.get(a.accuracy_kernel, 1.0)
+    elems = [int(x) for x in a.accuracy_elems.split(",")]
+    stream = torch.cuda.current_stream()
+
+    def solve(method, e, precision, reps=2):
+        p = kl.params(geometry="cube", degree=2, elems=(e, e, e), kernel=a.accuracy_kernel, sigma=1.0, L=L,
+                      method=method, precision=precision, block_k=k, seed=2101)
+        h = kl.kl_create(p, stream)
+        N = kl.kl_dims(h)[0]
+        lam = np.zeros(M)
+        ms = None
+        for _ in range(reps):  # the first solve captures the graphs
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc = kl.kl_eigs(h, M, 0.0, lam, None, 0, 0)
+            e1.record(stream)
+            e1.synchronize()
+            if rc not in (0, 1):
+                raise RuntimeError(f"{method} {e}^3 {precision}: status {rc}")
+            ms = e0.elapsed_time(e1)
+        kl.kl_destroy(h)
+        return N, ms, lam.copy()
+
+    N_ref, ref_ms, ref = solve("galerkin_std", max(elems), "fp64", reps=1)
+    points = []
+    for method in ("galerkin", "collocation", "galerkin_std"):
+        for e in elems:
+            N, ms, lam = solve(method, e, a.precision)
+            err = np.abs(lam - ref) / np.abs(ref)
+            points.append({"method": method, "elems": e, "N": N, "solve_ms": round(ms, 3),
+                           "mean_rel_err": float(err.mean()), "max_rel_err": float(err.max())})
+    print(json.dumps({
+        "mode": "accuracy", "kernel": a.accuracy_kernel, "L": L, "sigma": 1.0, "p": 2, "M": M, "k": k,
+        "precision": a.precision,
+        "reference": {"method": "galerkin_std", "precision": "fp64", "elems": max(elems), "N": N_ref,
+                      "solve_ms": round(ref_ms, 3)},
+        "points": points,
+    }))
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+        return
+    if a.accuracy:
+        run_accuracy(a)
         return
     run_gpu(a)
 
