@@ -33,9 +33,11 @@ def nurbs_weights(prob: Problem):
     U = prob.trial_knots()
     p = prob.p
     n = [splines.n_basis(k, p) for k in U]
-    if prob.geometry != "annulus":
+    if prob.geometry not in ("annulus", "half_annulus"):
         return np.ones(int(np.prod(n)))
-    # L2 projection of W onto the 1D space of direction 1 (exact: W is quadratic)
+    # L2 projection of W onto the 1D space of direction 1 (exact: W is
+    # quadratic, piecewise with a C^0 join at 1/2 for the half annulus, where
+    # the trial space is C^0 too)
     xq, wq = splines.element_gauss(U[0], p + 2)
     B = splines.bspline_basis(U[0], p, xq)
     Wv = prob.geom.weight_function(xq)

@@ -33,7 +33,10 @@ def matrices(prob: Problem, with_parts=False):
 
     # Greville points of the interpolation space (tensor grid, direction 1 fastest)
     Xg = splines.tensor_grid([splines.greville(k, p) for k in Ut])
-    Bt = splines.tensor_basis(Ut, p, Xg)                  # B~[a, k] = B~_k(x~_a)
+    # at a C^-1 breakpoint (the half cylinder's join) two Greville points
+    # coincide; the left one belongs to the left patch's last function
+    Lg = splines.tensor_grid([splines.greville_left(k, p).astype(float) for k in Ut]) > 0.5
+    Bt = splines.tensor_basis(Ut, p, Xg, Lg)              # B~[a, k] = B~_k(x~_a)
 
     # Gauss rule on the (shared) mesh
     Xq, Wq = prob.quadrature()

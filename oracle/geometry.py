@@ -16,6 +16,10 @@ Two domains are provided:
   (radius r_in -> r_out) and direction 3 (height 0 -> h). F and DF are
   evaluated from that NURBS definition (rational basis and quotient rule),
   point by point.
+* ``HalfAnnulus``: the half annular cylinder (the shape of the paper's Sec. 4
+  benchmark), two such quarter arcs joined C^0 at the parameter 1/2: angle
+  knots 0,0,0,1/2,1/2,1,1,1, control points (1,0), (1,1), (0,1), (-1,1),
+  (-1,0) and weights 1, sqrt(2)/2, 1, sqrt(2)/2, 1.
 """
 import numpy as np
 
@@ -41,21 +45,29 @@ class Cube:
 class QuarterAnnulus:
     name = "annulus"
     d = 3
+    quarters = 1
 
     def __init__(self, r_in=1.0, r_out=2.0, height=1.0):
         self.r_in, self.r_out, self.h = float(r_in), float(r_out), float(height)
-        self.knots = [np.array([0, 0, 0, 1, 1, 1.0]),
-                      np.array([0, 0, 1, 1.0]),
-                      np.array([0, 0, 1, 1.0])]
+        s = np.sqrt(2.0) / 2.0
+        if self.quarters == 1:
+            angle_knots = np.array([0, 0, 0, 1, 1, 1.0])
+            arc = np.array([[1.0, 0.0], [1.0, 1.0], [0.0, 1.0]])
+            warc = np.array([1.0, s, 1.0])
+        else:
+            angle_knots = np.array([0, 0, 0, 0.5, 0.5, 1, 1, 1.0])
+            arc = np.array([[1.0, 0.0], [1.0, 1.0], [0.0, 1.0], [-1.0, 1.0], [-1.0, 0.0]])
+            warc = np.array([1.0, s, 1.0, s, 1.0])
+        self.warc = warc
+        self.knots = [angle_knots, np.array([0, 0, 1, 1.0]), np.array([0, 0, 1, 1.0])]
         self.degrees = [2, 1, 1]
-        arc = np.array([[1.0, 0.0], [1.0, 1.0], [0.0, 1.0]])
-        warc = np.array([1.0, np.sqrt(2.0) / 2.0, 1.0])
+        na = len(warc)
         radii = [self.r_in, self.r_out]
         zs = [0.0, self.h]
         # control points P[i1, i2, i3] and weights w[i1, i2, i3]
-        self.P = np.zeros((3, 2, 2, 3))
-        self.w = np.zeros((3, 2, 2))
-        for i1 in range(3):
+        self.P = np.zeros((na, 2, 2, 3))
+        self.w = np.zeros((na, 2, 2))
+        for i1 in range(na):
             for i2 in range(2):
                 for i3 in range(2):
                     self.P[i1, i2, i3, 0] = radii[i2] * arc[i1, 0]
@@ -102,12 +114,18 @@ class QuarterAnnulus:
 
     def weight_function(self, t):
         """The NURBS denominator W(xh_1), a quadratic polynomial in the angle
-        parameter (the radial and axial weights are all 1)."""
+        parameter (piecewise, C^0 at 1/2, for the half annulus; the radial and
+        axial weights are all 1)."""
         b = splines.bspline_basis(self.knots[0], 2, t)
-        return b @ np.array([1.0, np.sqrt(2.0) / 2.0, 1.0])
+        return b @ self.warc
 
     def volume(self):
-        return 0.25 * np.pi * (self.r_out ** 2 - self.r_in ** 2) * self.h
+        return 0.25 * self.quarters * np.pi * (self.r_out ** 2 - self.r_in ** 2) * self.h
+
+
+class HalfAnnulus(QuarterAnnulus):
+    name = "half_annulus"
+    quarters = 2
 
 
 def make_geometry(name, d=3, geo=None):
@@ -118,4 +136,9 @@ def make_geometry(name, d=3, geo=None):
             raise ValueError("the annulus is three-dimensional")
         geo = geo or (1.0, 2.0, 1.0)
         return QuarterAnnulus(*geo)
+    if name == "half_annulus":
+        if d != 3:
+            raise ValueError("the half annulus is three-dimensional")
+        geo = geo or (1.0, 2.0, 1.0)
+        return HalfAnnulus(*geo)
     raise ValueError(f"unknown geometry {name!r}")

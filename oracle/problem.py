@@ -45,12 +45,21 @@ class Problem:
         return kernels.interp_continuity(self.kernel, self.p)
 
     # -- spaces -----------------------------------------------------------
+    def _joined(self, j):
+        # the half annulus's angle direction has a C^0 geometry join at 1/2
+        return self.geometry == "half_annulus" and j == 0
+
     def trial_knots(self):
-        return [splines.open_uniform_knots(n, self.p, self.p - 1) for n in self.elems]
+        """C^{p-1} splines; C^0 at a geometry join (the trial space follows the
+        geometry's continuity)."""
+        return [splines.joined_knots(n, self.p, self.p - 1, 0) if self._joined(j)
+                else splines.open_uniform_knots(n, self.p, self.p - 1) for j, n in enumerate(self.elems)]
 
     def interp_knots(self):
+        """Continuity of the rule of Sec. 4; C^-1 at a geometry join (Sec. 4.1)."""
         r = self.interpolation_continuity()
-        return [splines.open_uniform_knots(n, self.p, r) for n in self.elems]
+        return [splines.joined_knots(n, self.p, r, -1) if self._joined(j)
+                else splines.open_uniform_knots(n, self.p, r) for j, n in enumerate(self.elems)]
 
     def quadrature(self, nq=None):
         """Tensor Gauss rule with nq (default p+1) points per direction per element."""

@@ -24,6 +24,29 @@ def open_uniform_knots(n_elem, p, cont):
     return np.concatenate([np.zeros(p + 1), interior, np.ones(p + 1)])
 
 
+def joined_knots(n_elem, p, cont, join_cont):
+    """Open knot vector like ``open_uniform_knots`` (n_elem even) whose middle
+    breakpoint 1/2 gets multiplicity p - join_cont: a C^join_cont join of two
+    patches inside one parameter domain (Sec. 4.1: the half cylinder's
+    geometry is C^0 there, its interpolation space C^-1)."""
+    if n_elem < 2 or n_elem % 2 or p < 1 or not (-1 <= cont <= p - 1) or not (-1 <= join_cont <= cont):
+        raise ValueError("bad knot parameters")
+    interior = []
+    for e in range(1, n_elem):
+        mult = p - join_cont if 2 * e == n_elem else p - cont
+        interior += [e / n_elem] * mult
+    return np.concatenate([np.zeros(p + 1), np.array(interior), np.ones(p + 1)])
+
+
+def greville_left(knots, p):
+    """Which Greville points lie at the right end of their basis function's
+    support inside the domain (a C^-1 breakpoint): there the function is
+    evaluated as the limit from the left."""
+    t = np.asarray(knots, dtype=np.float64)
+    g = greville(t, p)
+    return np.array([g[i] == t[i + p + 1] and g[i] < t[-1] for i in range(len(g))])
+
+
 def n_basis(knots, p):
     return len(knots) - p - 1
 
@@ -38,16 +61,19 @@ def _last_nonempty_span(t):
     return max(i for i in range(len(t) - 1) if t[i] < t[i + 1])
 
 
-def bspline_basis(knots, p, x):
+def bspline_basis(knots, p, x, left=None):
     """All degree-p B-splines at the points x by the Cox–de Boor recursion.
 
     Returns an array of shape (len(x), n_basis). Degree 0 splines are the
-    indicator functions of the half-open knot spans; the right end of the
-    parameter domain belongs to the last non-empty span. Terms with a zero
-    denominator (repeated knots) are dropped (the 0/0 := 0 convention).
+    indicator functions of the half-open knot spans [t_i, t_i+1); the right
+    end of the parameter domain belongs to the last non-empty span. Points
+    flagged in ``left`` use the spans (t_i, t_i+1] instead (limits from the
+    left). Terms with a zero denominator (repeated knots) are dropped (the
+    0/0 := 0 convention).
     """
     x = np.atleast_1d(np.asarray(x, dtype=np.float64))
     t = np.asarray(knots, dtype=np.float64)
+    lf = np.zeros(x.size, dtype=bool) if left is None else np.asarray(left, dtype=bool)
     m = len(t) - 1
     last = _last_nonempty_span(t)
     B = np.zeros((x.size, m))
@@ -56,7 +82,8 @@ def bspline_basis(knots, p, x):
             inside = (x >= t[i]) & (x < t[i + 1])
             if i == last:
                 inside |= x == t[i + 1]
-            B[:, i] = inside
+            inside_l = (x > t[i]) & (x <= t[i + 1])
+            B[:, i] = np.where(lf, inside_l, inside)
     for d in range(1, p + 1):
         Bn = np.zeros((x.size, m - d))
         for i in range(m - d):
@@ -127,16 +154,17 @@ def tensor_weights(wts):
     return out
 
 
-def tensor_basis(knot_list, p, X):
+def tensor_basis(knot_list, p, X, left=None):
     """Tensor-product B-splines evaluated at the d-dimensional points X.
 
     Row a of the result holds B_k(X[a]) = prod_d B_{k_d}(X[a, d]) for every
     multi-index k (direction 1 fastest). Each point is evaluated on its own;
-    no Kronecker factorisation of the resulting matrix is used.
+    no Kronecker factorisation of the resulting matrix is used. ``left``
+    (optional, shape of X) flags coordinates evaluated as limits from the left.
     """
     X = np.atleast_2d(X)
     d = X.shape[1]
-    vals = [bspline_basis(knot_list[j], p, X[:, j]) for j in range(d)]
+    vals = [bspline_basis(knot_list[j], p, X[:, j], None if left is None else left[:, j]) for j in range(d)]
     out = vals[0]
     for j in range(1, d):
         # new index = k_prev + n_prev * k_j  (previous directions vary faster)
