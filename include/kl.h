@@ -69,7 +69,17 @@ typedef enum {
                                  parts are returned)                           */
 } kl_status;
 
-enum { KL_GEOM_CUBE = 0, KL_GEOM_QUARTER_ANNULUS = 1 };
+/* Domains (single NURBS patches, Sec. 3.1):
+ *   KL_GEOM_CUBE             the unit cube (unit square / interval for dim < 3)
+ *   KL_GEOM_QUARTER_ANNULUS  quarter annular cylinder: direction 1 the angle
+ *                            (exact quadratic NURBS arc), 2 the radius, 3 the
+ *                            height
+ *   KL_GEOM_HALF_ANNULUS     half annular cylinder (the shape of the Sec. 4
+ *                            benchmark): two quarter arcs joined C^0 at the
+ *                            angle parameter 1/2; elems[0] counts both halves
+ *                            (even). The trial space is C^0 at the join, the
+ *                            Galerkin interpolation space C^-1 (Sec. 4.1). */
+enum { KL_GEOM_CUBE = 0, KL_GEOM_QUARTER_ANNULUS = 1, KL_GEOM_HALF_ANNULUS = 2 };
 
 /* Covariance kernels Gamma(x, x'), r = |x - x'| (Euclidean):
  *   KL_KERNEL_GAUSS     sigma^2 exp(-r^2 / L^2)

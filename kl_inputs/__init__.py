@@ -37,6 +37,10 @@ PARITY_CASES = {
     "cube_p2_e5x4x4_exp": dict(geometry="cube", p=2, elems=(5, 4, 4), kernel="exp", sigma=1.0, L=0.9),
     "annulus_p2_e4x4x2_gauss": dict(geometry="annulus", p=2, elems=(4, 4, 2), kernel="gauss", sigma=1.0, L=0.5),
     "annulus_p3_e4x3x2_exp": dict(geometry="annulus", p=3, elems=(4, 3, 2), kernel="exp", sigma=1.0, L=1.0),
+    # half annular cylinder (C^0 geometry join at the angle parameter 1/2)
+    "half_annulus_p2_e4x3x2_gauss": dict(geometry="half_annulus", p=2, elems=(4, 3, 2), kernel="gauss", sigma=1.0,
+                                         L=0.6),
+    "half_annulus_p2_e6x2x2_exp": dict(geometry="half_annulus", p=2, elems=(6, 2, 2), kernel="exp", sigma=1.0, L=1.0),
 }
 
 

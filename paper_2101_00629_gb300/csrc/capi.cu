@@ -388,8 +388,11 @@ const char* kl_last_error(const kl_solver* h) {
 
 static std::string check_params(const kl_params& p) {
     if (p.dim < 1 || p.dim > 3) return "dim must be 1, 2 or 3";
-    if (p.geometry != KL_GEOM_CUBE && p.geometry != KL_GEOM_QUARTER_ANNULUS) return "unknown geometry";
-    if (p.geometry == KL_GEOM_QUARTER_ANNULUS) {
+    if (p.geometry != KL_GEOM_CUBE && p.geometry != KL_GEOM_QUARTER_ANNULUS && p.geometry != KL_GEOM_HALF_ANNULUS)
+        return "unknown geometry";
+    if (p.geometry == KL_GEOM_HALF_ANNULUS && (p.elems[0] < 2 || p.elems[0] % 2))
+        return "the half annulus needs an even number of angle elements (both halves together)";
+    if (p.geometry == KL_GEOM_QUARTER_ANNULUS || p.geometry == KL_GEOM_HALF_ANNULUS) {
         if (p.dim != 3) return "the annulus needs dim = 3";
         if (!(p.geo[0] > 0 && p.geo[1] > p.geo[0] && p.geo[2] > 0)) return "annulus needs 0 < r_in < r_out, height > 0";
     }
@@ -453,9 +456,9 @@ int kl_create(const kl_params* params, void* stream, kl_solver** out) {
     Dir1D dir[3];
     for (int d = 0; d < 3; ++d) {
         const bool present = d < p.dim;
-        const bool rational = (p.geometry == KL_GEOM_QUARTER_ANNULUS) && d == 0;
+        const int arc = d != 0 ? 0 : p.geometry == KL_GEOM_QUARTER_ANNULUS ? 1 : p.geometry == KL_GEOM_HALF_ANNULUS ? 2 : 0;
         std::string m = setup_direction(dir[d], present, present ? p.elems[d] : 1, p.degree, icont,
-                                        rational, gal, !gal);
+                                        arc, gal, !gal);
         if (!m.empty()) return bail(fail(h, KL_ERR_NUMERIC, "set-up: " + m));
         h->N1[d] = dir[d].N;
         h->Nt1[d] = dir[d].Nt;
@@ -686,8 +689,8 @@ int kl_estimate_bytes(const kl_params* params, int M, int64_t* bytes) {
     for (int d = 0; d < 3; ++d) {
         Dir1D q;
         const bool present = d < p.dim;
-        const bool rational = (p.geometry == KL_GEOM_QUARTER_ANNULUS) && d == 0;
-        std::string m = setup_direction(q, present, present ? p.elems[d] : 1, p.degree, icont, rational, gal, !gal);
+        const int arc = d != 0 ? 0 : p.geometry == KL_GEOM_QUARTER_ANNULUS ? 1 : p.geometry == KL_GEOM_HALF_ANNULUS ? 2 : 0;
+        std::string m = setup_direction(q, present, present ? p.elems[d] : 1, p.degree, icont, arc, gal, !gal);
         if (!m.empty()) return fail(nullptr, KL_ERR_NUMERIC, "set-up: " + m);
         const int64_t ns = ibq ? q.Nt : stdg ? q.ne : q.nq;
         N *= q.N;

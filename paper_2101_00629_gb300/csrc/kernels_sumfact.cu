@@ -53,9 +53,19 @@ __global__ void tensor_points_kernel(int geometry, double r_in, double r_out, do
         const int i3 = int(i / (int64_t(n1) * n2));
         const double u1 = t1[i1], u2 = t2[i2], u3 = t3[i3];
         double x, y, z, det;
-        if (geometry == KL_GEOM_QUARTER_ANNULUS) {
+        if (geometry == KL_GEOM_QUARTER_ANNULUS || geometry == KL_GEOM_HALF_ANNULUS) {
             double cx, cy, dth;
-            arc_point(u1, cx, cy, dth);
+            if (geometry == KL_GEOM_QUARTER_ANNULUS) {
+                arc_point(u1, cx, cy, dth);
+            } else {
+                // two quarter arcs, the second turned by 90 degrees (C^0 at 1/2)
+                const bool second = u1 >= 0.5;
+                double ax, ay;
+                arc_point(second ? 2.0 * u1 - 1.0 : 2.0 * u1, ax, ay, dth);
+                cx = second ? -ay : ax;
+                cy = second ? ax : ay;
+                dth *= 2.0;
+            }
             const double r = r_in + (r_out - r_in) * u2;
             x = r * cx;
             y = r * cy;

@@ -65,11 +65,13 @@ struct Dir1D {
 // B_i / sqrt(det DF), a symmetric operator in standard form A' = L^-1 A L^-T.
 inline bool galerkin_form(int method) { return method == KL_GALERKIN_IBQ || method == KL_GALERKIN_STD; }
 
-// Builds the direction's tables. `rational` = direction 1 of the annulus
-// (NURBS weights from the quadratic arc). `present` = false gives the 1-dof
-// identity direction used for dim < 3. Returns an empty string on success.
+// Builds the direction's tables. `arc`: 0 polynomial direction; 1 direction 1
+// of the quarter annulus, 2 of the half annulus (NURBS weights from the
+// quadratic arc; the half arc has a C^0 geometry join at 1/2, where the trial
+// space is C^0 and the interpolation space C^-1). `present` = false gives the
+// 1-dof identity direction used for dim < 3. Returns an empty string on success.
 std::string setup_direction(Dir1D& d, bool present, int nel, int p, int interp_cont,
-                            bool rational, bool need_galerkin, bool need_collocation);
+                            int arc, bool need_galerkin, bool need_collocation);
 
 // ---------------------------------------------------------------------------
 // Device-side launchers (defined in the .cu files). All take the stream.

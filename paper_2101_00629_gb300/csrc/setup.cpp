@@ -137,6 +137,22 @@ Knots open_knots(int nel, int p, int cont) {
     return k;
 }
 
+// The same with a join at the middle breakpoint 1/2 (nel even) of
+// multiplicity p-join_cont: two patches joined C^join_cont (Sec. 4.1: C^0
+// for the trial space at the half cylinder's geometry join, C^-1 for the
+// interpolation space).
+Knots joined_knots(int nel, int p, int cont, int join_cont) {
+    Knots k;
+    k.p = p;
+    for (int i = 0; i <= p; ++i) k.t.push_back(0.0);
+    for (int e = 1; e < nel; ++e) {
+        const int mult = 2 * e == nel ? p - join_cont : p - cont;
+        for (int m = 0; m < mult; ++m) k.t.push_back(double(e) / nel);
+    }
+    for (int i = 0; i <= p; ++i) k.t.push_back(1.0);
+    return k;
+}
+
 std::vector<double> greville(const Knots& k) {
     std::vector<double> g(k.n());
     for (int i = 0; i < k.n(); ++i) {
@@ -183,12 +199,27 @@ void basis_funs(const Knots& k, int s, double x, double* out) {
     }
 }
 
-// Dense basis matrix: rows = points, columns = basis functions.
-Mat basis_matrix(const Knots& k, const std::vector<double>& x) {
+// Greville points at the right end of their function's support inside the
+// domain (a C^-1 breakpoint, where two Greville points coincide): evaluated
+// as limits from the left.
+std::vector<char> greville_left(const Knots& k) {
+    const std::vector<double> g = greville(k);
+    std::vector<char> left(g.size(), 0);
+    for (int i = 0; i < k.n(); ++i) left[i] = (g[i] == k.t[i + k.p + 1] && g[i] < k.t.back()) ? 1 : 0;
+    return left;
+}
+
+// Dense basis matrix: rows = points, columns = basis functions. Points
+// flagged in `left` use the span that ends at them (limit from the left).
+Mat basis_matrix(const Knots& k, const std::vector<double>& x, const std::vector<char>* left = nullptr) {
     Mat B(int(x.size()), k.n());
     double v[16];
     for (size_t i = 0; i < x.size(); ++i) {
-        const int s = find_span(k, x[i]);
+        int s = find_span(k, x[i]);
+        if (left && (*left)[i] && s > k.p && k.t[s] == x[i]) {
+            --s;
+            while (s > k.p && k.t[s] == k.t[s + 1]) --s;
+        }
         basis_funs(k, s, x[i], v);
         for (int j = 0; j <= k.p; ++j) B(int(i), s - k.p + j) = v[j];
     }
@@ -252,6 +283,9 @@ double arc_weight(double u) {
     return (1.0 - u) * (1.0 - u) + 2.0 * w * u * (1.0 - u) + u * u;
 }
 
+// The half arc: two quarter arcs on [0, 1/2] and [1/2, 1] (C^0 at 1/2).
+double half_arc_weight(double u) { return u < 0.5 ? arc_weight(2.0 * u) : arc_weight(2.0 * u - 1.0); }
+
 Mat rational_rows(const Mat& B, const std::vector<double>& w) {
     Mat R = B;
     for (int i = 0; i < B.rows; ++i) {
@@ -265,7 +299,9 @@ Mat rational_rows(const Mat& B, const std::vector<double>& w) {
 }  // namespace
 
 std::string setup_direction(Dir1D& d, bool present, int nel, int p, int interp_cont,
-                            bool rational, bool need_galerkin, bool need_collocation) {
+                            int arc, bool need_galerkin, bool need_collocation) {
+    const bool rational = arc != 0;
+    const bool join = arc == 2;  // C^0 geometry join at 1/2
     if (!present) {
         d = Dir1D();
         d.N = d.Nt = d.nq = 1;
@@ -280,9 +316,10 @@ std::string setup_direction(Dir1D& d, bool present, int nel, int p, int interp_c
         return "";
     }
     if (p < 1 || p > 8) return "degree must be in 1..8";
+    if (join && (nel < 2 || nel % 2)) return "the joined direction needs an even number of elements";
     d.nel = nel;
     d.p = p;
-    const Knots U = open_knots(nel, p, p - 1);
+    const Knots U = join ? joined_knots(nel, p, p - 1, 0) : open_knots(nel, p, p - 1);
     d.N = U.n();
 
     std::vector<double> xq, wq;
@@ -291,9 +328,10 @@ std::string setup_direction(Dir1D& d, bool present, int nel, int p, int interp_c
 
     if (need_galerkin) {
         if (interp_cont < 0 || interp_cont > p - 1) return "interpolation continuity out of range";
-        const Knots Ut = open_knots(nel, p, interp_cont);
+        const Knots Ut = join ? joined_knots(nel, p, interp_cont, -1) : open_knots(nel, p, interp_cont);
         d.Nt = Ut.n();
         d.xg = greville(Ut);
+        const std::vector<char> xg_left = greville_left(Ut);
         const Mat BUt = basis_matrix(Ut, xq);
         // Z_k = int B_i B_j ; M_k = int B~_a B_i
         Mat Z(d.N, d.N), M(d.Nt, d.N);
@@ -309,7 +347,7 @@ std::string setup_direction(Dir1D& d, bool present, int nel, int p, int interp_c
         const Mat Linv = lower_inverse(L);
         d.LinvT = transpose(Linv);
         d.Zinv_gal = matmul(d.LinvT, Linv);
-        const Mat Bt = basis_matrix(Ut, d.xg);  // Bt(a, j) = B~_j(x~_a)
+        const Mat Bt = basis_matrix(Ut, d.xg, &xg_left);  // Bt(a, j) = B~_j(x~_a)
         if (!lu_solve(transpose(Bt), M, d.Q)) return "1D interpolation matrix singular";
         d.P = matmul(d.Q, d.LinvT);
     }
@@ -321,7 +359,7 @@ std::string setup_direction(Dir1D& d, bool present, int nel, int p, int interp_c
             // weights of the degree-p, nel-element space that reproduce the
             // arc's quadratic denominator: interpolate it at the Greville points
             Mat rhs(d.N, 1), sol;
-            for (int i = 0; i < d.N; ++i) rhs(i, 0) = arc_weight(d.xc[i]);
+            for (int i = 0; i < d.N; ++i) rhs(i, 0) = join ? half_arc_weight(d.xc[i]) : arc_weight(d.xc[i]);
             if (!lu_solve(Bc, rhs, sol)) return "NURBS weight interpolation failed";
             for (int i = 0; i < d.N; ++i) w[i] = sol(i, 0);
         }

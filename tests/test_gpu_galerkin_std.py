@@ -15,7 +15,8 @@ pytestmark = pytest.mark.gpu
 
 APPLY_TOL = {"fp64": 1e-12, "fp32": 2e-6, "tf32": 2e-6, "bf16": 5e-5}
 LAM_TOL = {"fp64": 1e-10, "bf16": 1e-5, "tf32": 1e-5}
-CASES = ["cube_p2_e3x4x5_gauss", "annulus_p2_e4x4x2_gauss", "cube_p3_e4x3x3_matern", "cube_p2_e5x4x4_exp"]
+CASES = ["cube_p2_e3x4x5_gauss", "annulus_p2_e4x4x2_gauss", "cube_p3_e4x3x3_matern", "cube_p2_e5x4x4_exp",
+         "half_annulus_p2_e4x3x2_gauss"]
 
 
 @pytest.fixture(scope="module")

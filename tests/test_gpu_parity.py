@@ -201,7 +201,8 @@ def _run_eigs(kl, h, M, N):
 
 @pytest.mark.parametrize("precision", ["fp64", "bf16", "tf32", "fp32"])
 @pytest.mark.parametrize("case", ["cube_p2_e6x5x7_expsep", "annulus_p2_e4x4x2_gauss", "annulus_p3_e4x3x2_exp",
-                                  "cube_p3_e4x3x3_matern"])
+                                  "cube_p3_e4x3x3_matern", "half_annulus_p2_e4x3x2_gauss",
+                                  "half_annulus_p2_e6x2x2_exp"])
 @pytest.mark.parametrize("method", ["galerkin", "collocation"])
 def test_eigs_vs_oracle(kl, case, method, precision):
     prob, A, Z, Ap = _oracle(case, method)
