@@ -65,6 +65,8 @@ def _args():
                          "meshes against the standard Gauss-Legendre Galerkin solution on the finest one")
     ap.add_argument("--accuracy-elems", default="4,8,12,16", help="per-axis element counts of the study")
     ap.add_argument("--accuracy-kernel", default="exp_sep", choices=["gauss", "exp_sep", "exp", "matern32"])
+    ap.add_argument("--accuracy-study", default="cube", choices=["cube", "paper"],
+                    help="cube: h-refined unit cubes; paper: the half-cylinder cases of Tables 1-2 (Sec. 4)")
     return ap.parse_args()
 
 
@@ -632,13 +634,88 @@ def run_accuracy(a):
     }))
 
 
+# Sec. 4 benchmark cases on the half annular cylinder: the meshes reproduce the
+# dof counts of Tables 1-2 (tests/golden/half_cylinder_dofs.txt); the
+# dimensions are not printed, these give elements of about the printed mesh
+# size h; correlation length 5 (Fig. 1 caption).
+PAPER_GEO = (27.5, 30.5, 23.0)
+PAPER_L = 5.0
+PAPER_EX1 = [(1, (32, 1, 8)), (2, (28, 2, 15)), (3, (32, 2, 18)), (4, (38, 2, 21)), (5, (42, 3, 23))]
+PAPER_EX2 = [(1, 2), (2, 3), (3, 4), (4, 5), (5, 6)]
+
+
+def run_accuracy_paper(a):
+    """Example 1 (exponential kernel, h-refinement, p = 2, split-BF16 solves)
+    and Example 2 (Gaussian kernel, k-refinement on the Case 1 mesh,
+    p = 2..6, FP64 solves): eigensolver time and error of the first 20
+    eigenvalues of both methods against a standard Gauss-Legendre Galerkin
+    reference (Example 1: twice as fine as Case 5; Example 2: p = 6)."""
+    import numpy as np
+    import torch
+    import paper_2101_00629_gb300 as kl
+
+    M, k = 20, 8
+    stream = torch.cuda.current_stream()
+
+    def solve(method, p, elems, kernel, precision, reps=2):
+        prm = kl.params(geometry="half_annulus", degree=p, elems=elems, kernel=kernel, sigma=1.0, L=PAPER_L,
+                        method=method, precision=precision, block_k=k, seed=2101)
+        prm.geo[0], prm.geo[1], prm.geo[2] = PAPER_GEO
+        h = kl.kl_create(prm, stream)
+        dims = kl.kl_dims(h)
+        lam = np.zeros(M)
+        ms = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc = kl.kl_eigs(h, M, 0.0, lam, None, 0, 0)
+            e1.record(stream)
+            e1.synchronize()
+            if rc not in (0, 1):
+                raise RuntimeError(f"{method} p={p} {elems} {precision}: status {rc}")
+            ms = e0.elapsed_time(e1)
+        kl.kl_destroy(h)
+        return dims, ms, lam.copy()
+
+    out = {"mode": "accuracy", "study": "paper", "geometry": "half_annulus", "geo": PAPER_GEO, "L": PAPER_L,
+           "sigma": 1.0, "M": M, "k": k, "examples": {}}
+    fine = tuple(2 * n for n in PAPER_EX1[-1][1])
+    rdims, rms, ref1 = solve("galerkin_std", 2, fine, "exp", a.precision, reps=1)
+    pts = []
+    for case, elems in PAPER_EX1:
+        for method in ("galerkin", "collocation"):
+            dims, ms, lam = solve(method, 2, elems, "exp", a.precision)
+            err = np.abs(lam - ref1) / np.abs(ref1)
+            pts.append({"case": case, "method": method, "elems": elems, "N": dims[0], "points": dims[1],
+                        "solve_ms": round(ms, 3), "mean_rel_err": float(err.mean()), "max_rel_err": float(err.max())})
+    out["examples"]["1"] = {"kernel": "exp", "p": 2, "precision": a.precision, "points": pts,
+                            "reference": {"method": "galerkin_std", "precision": a.precision, "elems": fine,
+                                          "N": rdims[0], "solve_ms": round(rms, 3)}}
+    mesh2 = PAPER_EX1[0][1]
+    rdims, rms, ref2 = solve("galerkin_std", 6, mesh2, "gauss", "fp64", reps=1)
+    pts = []
+    for case, p in PAPER_EX2:
+        for method in ("galerkin", "collocation"):
+            dims, ms, lam = solve(method, p, mesh2, "gauss", "fp64")
+            err = np.abs(lam - ref2) / np.abs(ref2)
+            pts.append({"case": case, "method": method, "p": p, "N": dims[0], "points": dims[1],
+                        "solve_ms": round(ms, 3), "mean_rel_err": float(err.mean()), "max_rel_err": float(err.max())})
+    out["examples"]["2"] = {"kernel": "gauss", "elems": mesh2, "precision": "fp64", "points": pts,
+                            "reference": {"method": "galerkin_std", "precision": "fp64", "p": 6, "N": rdims[0],
+                                          "solve_ms": round(rms, 3)}}
+    print(json.dumps(out))
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
         return
     if a.accuracy:
-        run_accuracy(a)
+        if a.accuracy_study == "paper":
+            run_accuracy_paper(a)
+        else:
+            run_accuracy(a)
         return
     run_gpu(a)
 
