@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from kl_inputs import PARITY_CASES
-from oracle import collocation, galerkin, sampling
+from oracle import collocation, galerkin, sampling, standard
 from oracle.problem import Problem
 
 pytestmark = pytest.mark.gpu
@@ -25,16 +25,23 @@ def kl():
 @pytest.mark.parametrize("case,method", [("cube_p2_e3x4x5_gauss", "galerkin"),
                                          ("annulus_p2_e4x4x2_gauss", "galerkin"),
                                          ("annulus_p3_e4x3x2_exp", "collocation"),
-                                         ("cube_p2_e6x5x7_expsep", "collocation")])
+                                         ("cube_p2_e6x5x7_expsep", "collocation"),
+                                         ("half_annulus_p2_e4x3x2_gauss", "galerkin"),
+                                         ("half_annulus_p2_e6x2x2_exp", "collocation"),
+                                         ("half_annulus_p2_e4x3x2_gauss", "galerkin_std")])
 def test_samples_match_oracle(kl, case, method):
     import torch
     c = PARITY_CASES[case]
     prob = Problem(c["geometry"], c["p"], c["elems"], c["kernel"], c["sigma"], c["L"])
-    mod = galerkin if method == "galerkin" else collocation
     M, ns = 9, 37
-    lam, V, _ = mod.solve(prob, M)
+    if method == "galerkin_std":
+        lam, V, _ = standard.solve(prob, M)   # the IBQ trial space, standard quadrature
+        basis = "galerkin"
+    else:
+        lam, V, _ = (galerkin if method == "galerkin" else collocation).solve(prob, M)
+        basis = method
     xi = np.random.Generator(np.random.PCG64(2101)).standard_normal((M, ns))
-    ref = sampling.samples(prob, method, lam, V, xi)             # Q x ns
+    ref = sampling.samples(prob, basis, lam, V, xi)              # Q x ns
     X, W, P = sampling.grid(prob)
     p = kl.params(geometry=c["geometry"], degree=c["p"], elems=c["elems"], kernel=c["kernel"], sigma=c["sigma"],
                   L=c["L"], method=method, precision="fp64")
