@@ -20,6 +20,13 @@ carries weights w_j = coefficients of W in the degree-p spline basis of
 direction 1; they are obtained here by L2 projection of W onto that space
 (exact, because W lies in it). The 3D weight of multi-index (j1, j2, j3) is
 w_{j1}, and R_j(x^) = w_j B_j(x^) / sum_l w_l B_l(x^).
+
+On the projective cube the denominator W(x^) = 1 + c . x^ is trilinear and
+not a product of one-parameter functions; its coefficients in the 3D trial
+space are found by interpolation at the trial Greville points with the dense
+3D collocation matrix of the B-splines (exact, because W lies in the space).
+The 3D weights are then not a tensor product and neither is Z, the case
+Sec. 3.2 factors with a full pivoted LU.
 """
 import numpy as np
 import scipy.linalg as sla
@@ -33,6 +40,10 @@ def nurbs_weights(prob: Problem):
     U = prob.trial_knots()
     p = prob.p
     n = [splines.n_basis(k, p) for k in U]
+    if prob.geometry == "projective_cube":
+        Xc = collocation_points(prob)
+        Bc = splines.tensor_basis(U, p, Xc)
+        return np.linalg.solve(Bc, prob.geom.weight_function_3d(Xc))
     if prob.geometry not in ("annulus", "half_annulus"):
         return np.ones(int(np.prod(n)))
     # L2 projection of W onto the 1D space of direction 1 (exact: W is

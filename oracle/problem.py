@@ -1,7 +1,8 @@
 """Problem description shared by the oracle's Galerkin and collocation modules.
 
-A problem is a geometry (unit cube in d = 1, 2 or 3 dimensions, or the quarter
-annular cylinder), a polynomial degree p, the number of elements per
+A problem is a geometry (unit cube in d = 1, 2 or 3 dimensions, the quarter
+or half annular cylinder, or the projective image of the cube), a polynomial
+degree p, the number of elements per
 parametric direction, a covariance kernel with sigma and correlation length L.
 The kernel may also be given as a Python callable k(x, y) on broadcastable
 point arrays, which the pins use for polynomial (degenerate) kernels.
@@ -21,7 +22,7 @@ class Problem:
     kernel: object = "gauss"
     sigma: float = 1.0
     L: float = 1.0
-    geo: tuple = (1.0, 2.0, 1.0)
+    geo: tuple = None           # geometry parameters; None: the geometry's default
     interp_cont: object = None   # None: rule of Sec. 4; int: explicit continuity
 
     def __post_init__(self):
