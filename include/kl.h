@@ -78,8 +78,18 @@ typedef enum {
  *                            benchmark): two quarter arcs joined C^0 at the
  *                            angle parameter 1/2; elems[0] counts both halves
  *                            (even). The trial space is C^0 at the join, the
- *                            Galerkin interpolation space C^-1 (Sec. 4.1). */
-enum { KL_GEOM_CUBE = 0, KL_GEOM_QUARTER_ANNULUS = 1, KL_GEOM_HALF_ANNULUS = 2 };
+ *                            Galerkin interpolation space C^-1 (Sec. 4.1).
+ *   KL_GEOM_PROJECTIVE_CUBE  the unit cube mapped by x = x^ / (1 + c . x^),
+ *                            c = geo[0..2] with 1 + sum_d min(c_d, 0) > 0: a
+ *                            hexahedron with planar faces, the trilinear NURBS
+ *                            volume with corner weights 1 + c . v. Its weight
+ *                            function 1 + c . x^ is not a product of
+ *                            one-parameter functions, so the collocation
+ *                            matrix Z = (R_j(x_i)) is not a Kronecker product
+ *                            (Sec. 3.2); it is applied as
+ *                            Z^-1 = diag(1 / w) (B-spline Z)^-1 diag(W(x_i)),
+ *                            exact for any NURBS weights w_j, W = sum w_j B_j. */
+enum { KL_GEOM_CUBE = 0, KL_GEOM_QUARTER_ANNULUS = 1, KL_GEOM_HALF_ANNULUS = 2, KL_GEOM_PROJECTIVE_CUBE = 3 };
 
 /* Covariance kernels Gamma(x, x'), r = |x - x'| (Euclidean):
  *   KL_KERNEL_GAUSS     sigma^2 exp(-r^2 / L^2)
@@ -107,7 +117,8 @@ typedef struct kl_params {
     int dim;                 /* 1, 2 or 3 parametric directions (annulus: 3)  */
     int geometry;            /* KL_GEOM_*                                     */
     double geo[3];           /* annulus: r_in, r_out, height (> 0, r_out >
-                                r_in); ignored for the cube                   */
+                                r_in); projective cube: c_1, c_2, c_3;
+                                ignored for the cube                          */
     int degree;              /* p, 1 <= p <= 8 (trial and interpolation)      */
     int elems[3];            /* elements per direction (>= 1); direction 1 of
                                 the annulus is the angle, 2 the radius, 3 the

@@ -41,6 +41,11 @@ PARITY_CASES = {
     "half_annulus_p2_e4x3x2_gauss": dict(geometry="half_annulus", p=2, elems=(4, 3, 2), kernel="gauss", sigma=1.0,
                                          L=0.6),
     "half_annulus_p2_e6x2x2_exp": dict(geometry="half_annulus", p=2, elems=(6, 2, 2), kernel="exp", sigma=1.0, L=1.0),
+    # projective cube x = x^ / (1 + c . x^): NURBS weights that are not a tensor product
+    "projective_p2_e4x3x3_gauss": dict(geometry="projective_cube", p=2, elems=(4, 3, 3), kernel="gauss", sigma=1.0,
+                                       L=0.6, geo=(0.5, 0.25, -0.2)),
+    "projective_p3_e3x3x2_exp": dict(geometry="projective_cube", p=3, elems=(3, 3, 2), kernel="exp", sigma=1.2,
+                                     L=0.8, geo=(-0.3, 0.4, 0.6)),
 }
 
 
@@ -51,8 +56,10 @@ def random_block(n, k, seed):
 
 
 def problem_args(spec):
-    """The geometry/discretisation fields of a workload (no M, k, methods)."""
-    return {key: spec[key] for key in ("geometry", "p", "elems", "kernel", "sigma", "L")}
+    """The geometry/discretisation fields of a workload (no M, k, methods);
+    "geo" (geometry parameters) only where the workload sets it."""
+    keys = ("geometry", "p", "elems", "kernel", "sigma", "L") + (("geo",) if "geo" in spec else ())
+    return {key: spec[key] for key in keys}
 
 
 def serving_requests(n=500, seed=2101, max_elems=48, mean_interarrival_s=0.05):

@@ -30,7 +30,7 @@ KL_OK, KL_ERR_ARG, KL_ERR_CUDA, KL_ERR_OOM = 0, -1, -2, -3
 KL_ERR_NOCONV, KL_ERR_NUMERIC, KL_ERR_TIMEOUT, KL_ERR_UNSUPPORTED = -4, -5, -6, -7
 KL_WARN_COMPLEX = 1
 
-GEOMETRIES = {"cube": 0, "annulus": 1, "half_annulus": 2}
+GEOMETRIES = {"cube": 0, "annulus": 1, "half_annulus": 2, "projective_cube": 3}
 KERNELS = {"gauss": 0, "exp_sep": 1, "exp": 2, "matern32": 3, "const": 4}
 METHODS = {"galerkin": 0, "collocation": 1, "galerkin_std": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2, "tf32": 3}

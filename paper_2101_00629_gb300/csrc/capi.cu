@@ -93,22 +93,23 @@ int ensure_workspace(kl_solver* h, int k) {
 }
 
 // Y <- (x)_d F_d applied mode by mode: X has dims (n_in[0], n_in[1], n_in[2]),
-// F_d is (n_out[d] x n_in[d]). The last product writes Y (ldy) with optional
-// per-point scaling `post`; intermediates use ws[wa], ws[wb].
+// F_d is (n_out[d] x n_in[d]). The first product scales the input rows by
+// `pre` and the last one writes Y (ldy) with per-point scaling `post` (either
+// may be NULL); intermediates use ws[wa], ws[wb].
 static int kron3_s(kl_solver* h, const double* const* Fd, const int* n_in, const int* n_out,
                    const double* X, int64_t ldx, double* Y, int64_t ldy, int k, const double* post,
-                   double* sa, double* sb);
+                   double* sa, double* sb, const double* pre = nullptr);
 
 static int kron3(kl_solver* h, const double* const* Fd, const int* n_in, const int* n_out,
                  const double* X, int64_t ldx, double* Y, int64_t ldy, int k, const double* post,
-                 int wa, int wb) {
-    return kron3_s(h, Fd, n_in, n_out, X, ldx, Y, ldy, k, post, h->ws[wa], h->ws[wb]);
+                 int wa, int wb, const double* pre = nullptr) {
+    return kron3_s(h, Fd, n_in, n_out, X, ldx, Y, ldy, k, post, h->ws[wa], h->ws[wb], pre);
 }
 
 // Same with explicit scratch for the two intermediate products.
 static int kron3_s(kl_solver* h, const double* const* Fd, const int* n_in, const int* n_out,
                    const double* X, int64_t ldx, double* Y, int64_t ldy, int k, const double* post,
-                   double* sa, double* sb) {
+                   double* sa, double* sb, const double* pre) {
     int dims[3] = {n_in[0], n_in[1], n_in[2]};
     const double* cur = X;
     int64_t ldc = ldx;
@@ -128,7 +129,7 @@ static int kron3_s(kl_solver* h, const double* const* Fd, const int* n_in, const
             ldo = out_len;
         }
         cudaError_t e = launch_modeprod(Fd[d], n_out[d], n_in[d], cur, ldc, out, ldo, a, b, k,
-                                        d == 2 ? post : nullptr, h->stream);
+                                        d == 2 ? post : nullptr, d == 0 ? pre : nullptr, h->stream);
         ++h->launches;
         if (e != cudaSuccess) return cuda_fail(h, e, "modeprod");
         cur = out;
@@ -225,11 +226,14 @@ void clear_graphs(kl_solver* h) {
 }
 
 // 1) sum factorisation to the source points, scaled by J (Galerkin) or
-//    w det DF (collocation, Algorithm 1 steps 1-2): X -> ws[0]
+//    w det DF (collocation, Algorithm 1 steps 1-2): X -> ws[0]. With
+//    non-tensor NURBS weights R X = (B (w X)) / W, the 1 / W folded into the
+//    point scale.
 static int apply_pre(kl_solver* h, int which, const double* X, int64_t ldx, int k) {
     const bool gal = galerkin_form(h->prm.method);
     const double* const* F = (gal && which == 1) ? h->P : h->F;
-    return kron3(h, F, h->N1, h->Ns1, X, ldx, h->ws[0], h->S, k, h->src_scale, 1, 2);
+    const double* post = h->rat_w ? h->rat_src_scale : h->src_scale;
+    return kron3(h, F, h->N1, h->Ns1, X, ldx, h->ws[0], h->S, k, post, 1, 2, h->rat_w);
 }
 
 // 3) back to the trial space: Galerkin J, B~^-1, M^T (and L^-1); collocation
@@ -239,7 +243,7 @@ static int apply_post(kl_solver* h, int which, double* Y, int64_t ldy, int k) {
     const double* const* FT = (gal && which == 1) ? h->PT : h->FT;
     double* W = h->ws[1];
     if (gal) return kron3(h, FT, h->Ns1, h->N1, W, h->T, Y, ldy, k, nullptr, 0, 2);
-    if (which == 1) return kron3(h, h->Zinv, h->N1, h->N1, W, h->T, Y, ldy, k, nullptr, 0, 2);
+    if (which == 1) return kron3(h, h->Zinv, h->N1, h->N1, W, h->T, Y, ldy, k, h->rat_invw, 0, 2, h->rat_Wc);
     cudaError_t e = launch_copy_block(W, h->T, Y, ldy, h->T, k, h->stream);
     ++h->launches;
     if (e != cudaSuccess) return cuda_fail(h, e, "copy");
@@ -323,8 +327,10 @@ int apply_operator(kl_solver* h, int which, int precision, const double* X, int6
     return rc;
 }
 
+// Z^-1 (Kronecker LU solves, Sec. 3.2); with non-tensor NURBS weights
+// Z = diag(1 / W(x_i)) B diag(w), so Z^-1 = diag(1 / w) B^-1 diag(W(x_i)).
 int apply_zinv(kl_solver* h, const double* X, int64_t ldx, double* Y, int64_t ldy, int k) {
-    return kron3(h, h->Zinv, h->N1, h->N1, X, ldx, Y, ldy, k, nullptr, 0, 1);
+    return kron3(h, h->Zinv, h->N1, h->N1, X, ldx, Y, ldy, k, h->rat_invw, 0, 1, h->rat_Wc);
 }
 
 int back_transform(kl_solver* h, const double* Yv, int64_t ldy, double* V, int64_t ldv, int k) {
@@ -336,7 +342,7 @@ int back_transform(kl_solver* h, const double* Yv, int64_t ldy, double* V, int64
 }
 
 int field_at_quadrature(kl_solver* h, const double* V, int64_t ldv, double* out, int k) {
-    return kron3(h, h->F, h->N1, h->Nq1, V, ldv, out, h->S, k, nullptr, 1, 2);
+    return kron3(h, h->F, h->N1, h->Nq1, V, ldv, out, h->S, k, h->rat_invWq, 1, 2, h->rat_w);
 }
 
 }  // namespace kl
@@ -386,10 +392,42 @@ const char* kl_last_error(const kl_solver* h) {
     return h ? h->err.c_str() : g_create_error.c_str();
 }
 
+// y = ((x)_d A_d) x on the host for square 1D factors A_d (n[d] x n[d]),
+// direction 1 fastest.
+static void kron3_host(const Mat* const* A, const int* n, const double* x, double* y) {
+    const int64_t len = int64_t(n[0]) * n[1] * n[2];
+    std::vector<double> cur(x, x + len), nxt(len);
+    for (int d = 0; d < 3; ++d) {
+        int64_t a = 1, b = 1;
+        for (int j = 0; j < d; ++j) a *= n[j];
+        for (int j = d + 1; j < 3; ++j) b *= n[j];
+        const Mat& M = *A[d];
+        for (int64_t ib = 0; ib < b; ++ib)
+            for (int i = 0; i < n[d]; ++i)
+                for (int64_t ia = 0; ia < a; ++ia) {
+                    double s = 0.0;
+                    for (int l = 0; l < n[d]; ++l) s += M(i, l) * cur[ia + a * (l + int64_t(n[d]) * ib)];
+                    nxt[ia + a * (i + int64_t(n[d]) * ib)] = s;
+                }
+        cur.swap(nxt);
+    }
+    std::copy(cur.begin(), cur.end(), y);
+}
+
 static std::string check_params(const kl_params& p) {
     if (p.dim < 1 || p.dim > 3) return "dim must be 1, 2 or 3";
-    if (p.geometry != KL_GEOM_CUBE && p.geometry != KL_GEOM_QUARTER_ANNULUS && p.geometry != KL_GEOM_HALF_ANNULUS)
+    if (p.geometry != KL_GEOM_CUBE && p.geometry != KL_GEOM_QUARTER_ANNULUS && p.geometry != KL_GEOM_HALF_ANNULUS &&
+        p.geometry != KL_GEOM_PROJECTIVE_CUBE)
         return "unknown geometry";
+    if (p.geometry == KL_GEOM_PROJECTIVE_CUBE) {
+        if (p.dim != 3) return "the projective cube needs dim = 3";
+        double dmin = 1.0;
+        for (int d = 0; d < 3; ++d) {
+            if (!std::isfinite(p.geo[d])) return "projective cube: c must be finite";
+            dmin += std::min(p.geo[d], 0.0);
+        }
+        if (!(dmin > 0.0)) return "projective cube: 1 + c . x must stay positive on the unit cube";
+    }
     if (p.geometry == KL_GEOM_HALF_ANNULUS && (p.elems[0] < 2 || p.elems[0] % 2))
         return "the half annulus needs an even number of angle elements (both halves together)";
     if (p.geometry == KL_GEOM_QUARTER_ANNULUS || p.geometry == KL_GEOM_HALF_ANNULUS) {
@@ -582,6 +620,46 @@ int kl_create(const kl_params* params, void* stream, kl_solver** out) {
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(h, e, "points fp32"));
     int rc = ensure_workspace(h, h->prm.block_k);
     if (rc != KL_OK) return bail(rc);
+    if (p.geometry == KL_GEOM_PROJECTIVE_CUBE && !gal) {
+        // NURBS weights of the collocation trial space: the coefficients of
+        // the weight function W = 1 + c . x^ in the B-spline basis, found by
+        // interpolation at the Greville points (Kronecker solves, exact:
+        // W lies in the space); W itself at the Gauss points is B w.
+        const int64_t N = h->N;
+        std::vector<double> host(3 * N);
+        double* w = host.data();
+        double* iw = w + N;
+        double* Wc = iw + N;
+        for (int i3 = 0; i3 < h->N1[2]; ++i3)
+            for (int i2 = 0; i2 < h->N1[1]; ++i2)
+                for (int i1 = 0; i1 < h->N1[0]; ++i1)
+                    Wc[i1 + int64_t(h->N1[0]) * (i2 + int64_t(h->N1[1]) * i3)] =
+                        1.0 + p.geo[0] * dir[0].xc[i1] + p.geo[1] * dir[1].xc[i2] + p.geo[2] * dir[2].xc[i3];
+        const Mat* Zi[3] = {&dir[0].Zinv_col, &dir[1].Zinv_col, &dir[2].Zinv_col};
+        kron3_host(Zi, h->N1, Wc, w);
+        for (int64_t i = 0; i < N; ++i) {
+            if (!(w[i] > 0.0)) return bail(fail(h, KL_ERR_NUMERIC, "set-up: NURBS weight not positive"));
+            iw[i] = 1.0 / w[i];
+        }
+        if ((e = dalloc(h, &h->d_rat, 3 * N + 2 * S)) != cudaSuccess) return bail(cuda_fail(h, e, "weights alloc"));
+        h->rat_w = h->d_rat;
+        h->rat_invw = h->rat_w + N;
+        h->rat_Wc = h->rat_invw + N;
+        h->rat_invWq = h->rat_Wc + N;
+        h->rat_src_scale = h->rat_invWq + S;
+        if ((e = cudaMemcpyAsync(h->d_rat, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                 h->stream)) != cudaSuccess)
+            return bail(cuda_fail(h, e, "weights upload"));
+        h->h2d_bytes += int64_t(host.size() * sizeof(double));
+        if ((rc = kron3_s(h, h->F, h->N1, h->Ns1, h->rat_w, N, h->rat_invWq, S, 1, nullptr, h->ws[1], h->ws[2])) !=
+            KL_OK)
+            return bail(rc);
+        e = launch_rational_scales(h->rat_invWq, h->src_scale, h->rat_src_scale, S, h->stream);
+        ++h->launches;
+        if (e != cudaSuccess) return bail(cuda_fail(h, e, "weight scales"));
+        // the host buffer is a temporary
+        if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "weights sync"));
+    }
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "create sync"));
     *out = h;
     return KL_OK;
@@ -657,7 +735,8 @@ int kl_sample(kl_solver* h, int M, const double* lambda, const double* V, int64_
     if (e == cudaSuccess) e = launch_gemm_nn(V, ldv, Xs, M, C, N, N, M, ns, 1.0, 0.0, h->stream);
     h->launches += 3;
     if (e != cudaSuccess) return cuda_fail(h, e, "sample");
-    return kron3_s(h, h->E, h->N1, h->Ne1, C, N, out, ldo, ns, jscale, sa, sb);
+    // collocation with non-tensor NURBS weights: (B (w C)) / W at the Gauss grid
+    return kron3_s(h, h->E, h->N1, h->Ne1, C, N, out, ldo, ns, gal ? jscale : h->rat_invWq, sa, sb, h->rat_w);
 }
 
 int kl_set_graphs(kl_solver* h, int on) {
@@ -717,7 +796,8 @@ int kl_estimate_bytes(const kl_params* params, int M, int64_t* bytes) {
     const int mcap = eig_basis_cap(N, std::min<int64_t>(M, N), b);
     // widest operator application: the final refinement of nkeep + 1 vectors
     const int kmax = std::max(b, (M + 2 * b - 1) / b * b + 1);
-    const int64_t points = (gal ? 4 * S : 3 * T + 4 * S) + (3 * T + 3 * S + 1) / 2 + 1;
+    const int64_t points = (gal ? 4 * S : 3 * T + 4 * S) + (3 * T + 3 * S + 1) / 2 + 1 +
+                           (p.geometry == KL_GEOM_PROJECTIVE_CUBE && !gal ? 3 * N + 2 * S : 0);
     const int64_t ws = 3 * std::max(S, T) * int64_t(kmax);
     const int64_t pair = std::max<int64_t>(pair_scratch_doubles(T, kmax, pair_choose_splits(T, S, sm)),
                                            tc_scratch_doubles(T, S, kmax, sm));
@@ -739,6 +819,7 @@ int kl_destroy(kl_solver* h) {
     dfree(h->d_tables);
     dfree(h->d_points);
     dfree(h->d_points32);
+    dfree(h->d_rat);
     for (int i = 0; i < 3; ++i) dfree(h->ws[i]);
     dfree(h->pair_scratch);
     dfree(h->eig_ws);

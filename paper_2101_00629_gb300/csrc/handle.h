@@ -62,6 +62,17 @@ struct kl_solver {
     double* src_scale = nullptr;  // Galerkin J (= target scale too); collocation w det DF
     double* d_geo = nullptr;      // geometry parameters on the device (unused by kernels)
 
+    // collocation with NURBS weights that are not a tensor product (projective
+    // cube): R_j = w_j B_j / W with W = sum_l w_l B_l, so R v = (B (w v)) / W
+    // and Z^-1 = diag(1/w) B^-1 diag(W(x_i)) around the B-spline Kronecker
+    // tables; NULL otherwise
+    double* d_rat = nullptr;       // one allocation for the five arrays below
+    double* rat_w = nullptr;       // w_j (N)
+    double* rat_invw = nullptr;    // 1 / w_j (N)
+    double* rat_Wc = nullptr;      // W at the collocation points (N)
+    double* rat_invWq = nullptr;   // 1 / W at the Gauss points (S)
+    double* rat_src_scale = nullptr;  // Gauss weight x det DF / W (S)
+
     // workspaces for operator applications (k_cap vectors)
     int k_cap = 0;
     double* ws[3] = {nullptr, nullptr, nullptr};

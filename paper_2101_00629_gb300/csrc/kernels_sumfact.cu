@@ -39,7 +39,8 @@ __device__ inline void arc_point(double u, double& cx, double& cy, double& dthet
     dtheta = cx * dcy - cy * dcx;
 }
 
-__global__ void tensor_points_kernel(int geometry, double r_in, double r_out, double h,
+// geo: annulus r_in, r_out, height; projective cube c_1, c_2, c_3.
+__global__ void tensor_points_kernel(int geometry, double g0, double g1, double g2,
                                      const double* __restrict__ t1, const double* __restrict__ t2,
                                      const double* __restrict__ t3, int n1, int n2, int n3,
                                      const double* __restrict__ w1, const double* __restrict__ w2,
@@ -66,11 +67,21 @@ __global__ void tensor_points_kernel(int geometry, double r_in, double r_out, do
                 cy = second ? ax : ay;
                 dth *= 2.0;
             }
+            const double r_in = g0, r_out = g1, h = g2;
             const double r = r_in + (r_out - r_in) * u2;
             x = r * cx;
             y = r * cy;
             z = h * u3;
             det = r * dth * (r_out - r_in) * h;
+        } else if (geometry == KL_GEOM_PROJECTIVE_CUBE) {
+            // x = u / D, D = 1 + c . u: DF = (I - x c^T) / D, det DF = 1 / D^4
+            const double D = 1.0 + g0 * u1 + g1 * u2 + g2 * u3;
+            const double iD = 1.0 / D;
+            x = u1 * iD;
+            y = u2 * iD;
+            z = u3 * iD;
+            const double iD2 = iD * iD;
+            det = iD2 * iD2;
         } else {
             x = u1;
             y = u2;
@@ -89,11 +100,12 @@ __global__ void tensor_points_kernel(int geometry, double r_in, double r_out, do
     }
 }
 
-// out[(ia, i, ib), c] = sum_l A[i + m l] X[(ia, l, ib), c], optional post scale.
+// out[(ia, i, ib), c] = sum_l A[i + m l] pre[(ia, l, ib)] X[(ia, l, ib), c],
+// optional pre (input rows) and post (output rows) scales.
 __global__ void modeprod_kernel(const double* __restrict__ A, int m, int n,
                                 const double* __restrict__ X, int64_t ldx, double* __restrict__ Y,
                                 int64_t ldy, int64_t a, int64_t b, int k,
-                                const double* __restrict__ post) {
+                                const double* __restrict__ post, const double* __restrict__ pre) {
     const int64_t per_col = a * m * b;
     const int64_t total = per_col * k;
     for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
@@ -106,7 +118,12 @@ __global__ void modeprod_kernel(const double* __restrict__ A, int m, int n,
         const int64_t ib = rest / m;
         const double* x = X + c * ldx + ia + a * n * ib;
         double acc = 0.0;
-        for (int l = 0; l < n; ++l) acc = fma(A[i + int64_t(m) * l], x[a * l], acc);
+        if (pre) {
+            const double* s = pre + ia + a * n * ib;
+            for (int l = 0; l < n; ++l) acc = fma(A[i + int64_t(m) * l], x[a * l] * s[a * l], acc);
+        } else {
+            for (int l = 0; l < n; ++l) acc = fma(A[i + int64_t(m) * l], x[a * l], acc);
+        }
         if (post) acc *= post[r];
         Y[c * ldy + r] = acc;
     }
@@ -152,6 +169,17 @@ __global__ void scale_rows_kernel(double* X, int64_t ldx, int64_t K, int n, cons
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < K * n; e += int64_t(gridDim.x) * blockDim.x) {
         const int64_t i = e % K, j = e / K;
         X[i + j * ldx] *= scale[i];
+    }
+}
+
+// From W at the Gauss points (in place in w_inv): w_inv = 1 / W and
+// scale_out = scale / W.
+__global__ void rational_scales_kernel(double* w_inv, const double* __restrict__ scale,
+                                       double* __restrict__ scale_out, int64_t n) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const double inv = 1.0 / w_inv[i];
+        w_inv[i] = inv;
+        scale_out[i] = scale[i] * inv;
     }
 }
 
@@ -260,10 +288,17 @@ cudaError_t launch_tensor_points(int geometry, const double* geo, const double* 
 
 cudaError_t launch_modeprod(const double* A, int m, int n, const double* X, int64_t ldx, double* Y,
                             int64_t ldy, int64_t a, int64_t b, int k, const double* post,
-                            cudaStream_t s) {
+                            const double* pre, cudaStream_t s) {
     const int64_t total = a * m * b * k;
     if (total == 0) return cudaSuccess;
-    modeprod_kernel<<<grid_for(total), kThreads, 0, s>>>(A, m, n, X, ldx, Y, ldy, a, b, k, post);
+    modeprod_kernel<<<grid_for(total), kThreads, 0, s>>>(A, m, n, X, ldx, Y, ldy, a, b, k, post, pre);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rational_scales(double* w_inv, const double* scale, double* scale_out, int64_t n,
+                                   cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    rational_scales_kernel<<<grid_for(n), kThreads, 0, s>>>(w_inv, scale, scale_out, n);
     return cudaGetLastError();
 }
 

@@ -91,10 +91,15 @@ cudaError_t launch_tensor_points(int geometry, const double* geo, const double* 
                                  const double* w2, const double* w3, double jac_power, double* out_x,
                                  double* out_y, double* out_z, double* out_w, cudaStream_t s);
 
-// Y(a, m, b, c) = sum_l A(i, l) X(a, l, b, c) (+ optional scaling by post[a + A*(i + m*b)]).
+// Y(a, m, b, c) = sum_l A(i, l) X(a, l, b, c) (+ optional scaling of the
+// output rows by post[a + A*(i + m*b)] and of the input rows by
+// pre[a + A*(l + n*b)]).
 cudaError_t launch_modeprod(const double* A, int m, int n, const double* X, int64_t ldx, double* Y,
                             int64_t ldy, int64_t a, int64_t b, int k, const double* post,
-                            cudaStream_t s);
+                            const double* pre, cudaStream_t s);
+// w_inv <- 1 / w_inv (W at the Gauss points), scale_out = scale * (1 / W).
+cudaError_t launch_rational_scales(double* w_inv, const double* scale, double* scale_out, int64_t n,
+                                   cudaStream_t s);
 
 // Pairwise products W = Gamma(targets, sources) X, FP64 or FP32 on CUDA cores.
 struct PairArgs {

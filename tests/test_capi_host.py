@@ -102,6 +102,17 @@ def test_create_rejects_bad_geometry(kl):
         kl.kl_create(p)
 
 
+@pytest.mark.parametrize("geo,elems,msg", [((-0.6, -0.5, 0.0), (2, 2, 2), "positive"),
+                                           ((float("nan"), 0.0, 0.0), (2, 2, 2), "finite"),
+                                           ((0.5, 0.25, -0.2), (2, 2), "dim = 3")])
+def test_create_rejects_bad_projective_cube(kl, geo, elems, msg):
+    p = kl.params(geometry="projective_cube", elems=elems, geo=geo)
+    with pytest.raises(kl.KLError) as ei:
+        kl.kl_create(p)
+    assert ei.value.status == -1
+    assert msg in str(ei.value)
+
+
 def test_null_arguments(kl):
     lib = kl._load()
     assert lib.kl_create(None, None, None) == -1
@@ -132,6 +143,9 @@ def test_estimate_bytes_on_host(kl):
     assert _est(kl, M=40) > base
     assert _est(kl, block_k=32) > base
     assert _est(kl, method="collocation") > base
+    # non-tensor NURBS weights add the weight arrays (3 N + 2 N_e N_q values)
+    assert _est(kl, method="collocation", geometry="projective_cube", geo=(0.5, 0.25, -0.2)) > \
+        _est(kl, method="collocation")
     # C0 interpolation of the exponential kernels has about 5x the points
     # (17^3 vs 10^3 here); the basis and its workspaces do not grow with them
     assert _est(kl, kernel="exp") > 1.5 * base

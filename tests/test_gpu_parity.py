@@ -38,7 +38,8 @@ def kl():
 
 
 def _problem(spec):
-    return Problem(spec["geometry"], spec["p"], spec["elems"], spec["kernel"], spec["sigma"], spec["L"])
+    return Problem(spec["geometry"], spec["p"], spec["elems"], spec["kernel"], spec["sigma"], spec["L"],
+                   geo=spec.get("geo"))
 
 
 @functools.lru_cache(maxsize=None)
@@ -56,6 +57,8 @@ def _oracle(case, method):
 
 def _create(kl, spec, method, precision, **kw):
     import torch
+    if "geo" in spec:
+        kw = dict(kw, geo=spec["geo"])
     p = kl.params(geometry=spec["geometry"], degree=spec["p"], elems=spec["elems"], kernel=spec["kernel"],
                   sigma=spec["sigma"], L=spec["L"], method=method, precision=precision, **kw)
     return kl.kl_create(p, torch.cuda.current_stream())
@@ -106,7 +109,7 @@ def test_apply_fp64(kl, case, method):
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "tf32"])
 @pytest.mark.parametrize("case", ["cube_p2_e6x5x7_expsep", "annulus_p2_e4x4x2_gauss", "cube_p3_e4x3x3_matern",
-                                  "cube_p2_e5x4x4_exp"])
+                                  "cube_p2_e5x4x4_exp", "projective_p2_e4x3x3_gauss"])
 @pytest.mark.parametrize("method", ["galerkin", "collocation"])
 def test_apply_mixed(kl, case, method, precision):
     prob, A, Z, Ap = _oracle(case, method)
@@ -202,7 +205,8 @@ def _run_eigs(kl, h, M, N):
 @pytest.mark.parametrize("precision", ["fp64", "bf16", "tf32", "fp32"])
 @pytest.mark.parametrize("case", ["cube_p2_e6x5x7_expsep", "annulus_p2_e4x4x2_gauss", "annulus_p3_e4x3x2_exp",
                                   "cube_p3_e4x3x3_matern", "half_annulus_p2_e4x3x2_gauss",
-                                  "half_annulus_p2_e6x2x2_exp"])
+                                  "half_annulus_p2_e6x2x2_exp", "projective_p2_e4x3x3_gauss",
+                                  "projective_p3_e3x3x2_exp"])
 @pytest.mark.parametrize("method", ["galerkin", "collocation"])
 def test_eigs_vs_oracle(kl, case, method, precision):
     prob, A, Z, Ap = _oracle(case, method)

@@ -28,11 +28,13 @@ def kl():
                                          ("cube_p2_e6x5x7_expsep", "collocation"),
                                          ("half_annulus_p2_e4x3x2_gauss", "galerkin"),
                                          ("half_annulus_p2_e6x2x2_exp", "collocation"),
-                                         ("half_annulus_p2_e4x3x2_gauss", "galerkin_std")])
+                                         ("half_annulus_p2_e4x3x2_gauss", "galerkin_std"),
+                                         ("projective_p2_e4x3x3_gauss", "collocation"),
+                                         ("projective_p3_e3x3x2_exp", "galerkin")])
 def test_samples_match_oracle(kl, case, method):
     import torch
     c = PARITY_CASES[case]
-    prob = Problem(c["geometry"], c["p"], c["elems"], c["kernel"], c["sigma"], c["L"])
+    prob = Problem(c["geometry"], c["p"], c["elems"], c["kernel"], c["sigma"], c["L"], geo=c.get("geo"))
     M, ns = 9, 37
     if method == "galerkin_std":
         lam, V, _ = standard.solve(prob, M)   # the IBQ trial space, standard quadrature
@@ -44,7 +46,7 @@ def test_samples_match_oracle(kl, case, method):
     ref = sampling.samples(prob, basis, lam, V, xi)              # Q x ns
     X, W, P = sampling.grid(prob)
     p = kl.params(geometry=c["geometry"], degree=c["p"], elems=c["elems"], kernel=c["kernel"], sigma=c["sigma"],
-                  L=c["L"], method=method, precision="fp64")
+                  L=c["L"], method=method, precision="fp64", geo=c.get("geo", (1.0, 2.0, 1.0)))
     h = kl.kl_create(p, torch.cuda.current_stream())
     try:
         N = kl.kl_dims(h)[0]
