@@ -322,13 +322,14 @@ def run_gpu(a):
     stream = torch.cuda.current_stream()
     w = WORKLOADS[a.workload]
     args = problem_args(w)
+    geo = args.get("geo", (1.0, 2.0, 1.0))  # geometry parameters (annulus radii and height by default)
     M, k = w["M"], w["k"]
     ks = {m: k for m in METHODS}
     tuned = {}
     if a.autotune:
         for m in METHODS:
             pt = kl.params(geometry=args["geometry"], degree=args["p"], elems=args["elems"], kernel=args["kernel"],
-                           sigma=args["sigma"], L=args["L"], method=m, precision=a.precision, block_k=8,
+                           sigma=args["sigma"], L=args["L"], geo=geo, method=m, precision=a.precision, block_k=8,
                            seed=2101 + 7919 * rank)
             best, secs = kl.kl_autotune(pt, M, 0.0, stream)
             ks[m] = best
@@ -341,7 +342,7 @@ def run_gpu(a):
 
     def make(method, precision, st=None):
         p = kl.params(geometry=args["geometry"], degree=args["p"], elems=args["elems"], kernel=args["kernel"],
-                      sigma=args["sigma"], L=args["L"], method=method, precision=precision, block_k=ks[method],
+                      sigma=args["sigma"], L=args["L"], geo=geo, method=method, precision=precision, block_k=ks[method],
                       seed=2101 + 7919 * rank)
         return kl.kl_create(p, st if st is not None else stream)
 
@@ -499,7 +500,7 @@ def run_gpu(a):
         t0 = time.perf_counter()
         for m in METHODS:
             p = kl.params(geometry=args["geometry"], degree=args["p"], elems=args["elems"], kernel=args["kernel"],
-                          sigma=args["sigma"], L=args["L"], method=m, precision=a.precision, block_k=ks[m])
+                          sigma=args["sigma"], L=args["L"], geo=geo, method=m, precision=a.precision, block_k=ks[m])
             h = kl.kl_create(p, stream)
             h2d_m, _ = kl.kl_memory(h)
             kl.kl_eigs(h, M, 0.0, lam_h, V_h, N, 0)

@@ -26,6 +26,11 @@ WORKLOADS = {
     "annulus_p4_e64x32x16_exp": dict(geometry="annulus", p=4, elems=(64, 32, 16), kernel="exp",
                                       sigma=1.0, L=1.0, M=100, k=32,
                                       methods=("galerkin", "collocation")),
+    # the 16^3 cube workload on the projective cube x = x^ / (1 + c . x^):
+    # collocation with NURBS weights that are not a tensor product
+    "projective_p2_e16_expsep": dict(geometry="projective_cube", p=2, elems=(16, 16, 16), kernel="exp_sep",
+                                     sigma=1.0, L=1.0, M=20, k=8, geo=(0.5, 0.25, -0.2),
+                                     methods=("galerkin", "collocation")),
 }
 
 # Small parity cases: several 128-point tiles with ragged tails, sizes the
