@@ -191,6 +191,9 @@ int rayleigh_ritz(Ctx& c, const double* V, const double* AV, int nv, double* max
 // GB300 for n = 40..170). Tighter tolerances use FP32 only while the
 // residuals are above 1e-3 (and 1e3 tol), i.e. for the early restarts.
 constexpr double kFp32RrTol = 1e-4;
+// Smallest tolerance an FP32 Rayleigh-Ritz claim of convergence is tried at
+// (its residuals bottom out near a few 1e-7 of the largest Ritz value).
+constexpr double kFp32ClaimTol = 1e-6;
 
 // Basis width limit of kl_eigs for M wanted pairs and block size b (<= N).
 int eig_basis_cap(int64_t N, int M, int b) {
@@ -357,9 +360,24 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
         // wanted pairs the slowest one keeps the largest residual high long
         // after the first ones converged); a convergence claim FP32 cannot
         // resolve is re-checked in FP64. FP64 solves stay in FP64.
+        // Symmetric problems with the final refinement: the residuals of FP32
+        // Ritz pairs are those of actual vectors of the basis (computed in
+        // FP64 from A'V), and within a cluster of nearly equal eigenvalues any
+        // vector of its invariant subspace has a small residual, so an FP32
+        // claim that all wanted pairs converged is kept (the refinement then
+        // computes the pairs in FP64); FP32 is tried first also where the
+        // restart needs FP64, and the FP64 problem is solved only when that
+        // try does not converge.
         const bool use32 = prec != KL_FP64 && (tol >= kFp32RrTol || last_min_resid > std::max(1e3 * tol, 1e-3));
-        if (int rc = rr_residuals(use32); rc != KL_OK) return rc;
-        if (use32 && tol < kFp32RrTol && (nconv >= M || complete || restarts >= h->prm.max_restarts)) {
+        const bool trust32 = c.sym && prec != KL_FP64 && h->prm.refine > 0 && tol < kFp32RrTol && tol >= kFp32ClaimTol;
+        bool claimed32 = false;
+        if (use32 || trust32) {
+            if (int rc = rr_residuals(true); rc != KL_OK) return rc;
+            claimed32 = trust32 && !bad_num && nconv >= M;
+        }
+        if (!claimed32 && !use32) {
+            if (int rc = rr_residuals(false); rc != KL_OK) return rc;
+        } else if (!claimed32 && tol < kFp32RrTol && (nconv >= M || complete || restarts >= h->prm.max_restarts)) {
             if (int rc = rr_residuals(false); rc != KL_OK) return rc;
         }
         if (bad_num) return fail(h, KL_ERR_NUMERIC, "NaN or Inf in the Ritz values");
