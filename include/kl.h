@@ -104,7 +104,11 @@ enum { KL_GALERKIN_IBQ = 0, KL_COLLOCATION = 1, KL_GALERKIN_STD = 2 };
 
 /* Arithmetic of the pairwise product Gamma * X (the O(N~^2) / O(N N_e N_q)
  * step; Sec. 3.3). Everything else (sum factorisation, Z solves,
- * orthogonalisation, Rayleigh-Ritz and the small eigenproblems) is FP64.
+ * orthogonalisation, Rayleigh-Ritz) is FP64; with the reduced precisions the
+ * small eigenproblems of the early Rayleigh-Ritz steps (and, for the
+ * symmetric Galerkin problems, the one that finds all wanted residuals below
+ * the tolerance) are solved in FP32, and the returned pairs come from the
+ * FP64 Rayleigh-Ritz refinement (`refine`).
  *   KL_FP64        FP64 kernel evaluation and products (CUDA cores).
  *   KL_FP32        FP32 kernel evaluation and FP32 products (CUDA cores).
  *   KL_MIXED_BF16  FP32 kernel tiles written to tensor memory and multiplied
