@@ -167,6 +167,11 @@ int rayleigh_ritz(Ctx& c, const double* V, const double* AV, int nv, double* max
         c.schur_ok = status == 0;
         if (status == 2) status = 0;  // complex pairs: eigenvectors valid, Schur order not
     }
+    if (status != 0 && fp32) {
+        // the FP32 problem did not converge (its shorter precision can stall
+        // on tight clusters): solve the same projected matrix in FP64
+        return rayleigh_ritz(c, V, AV, nv, max_imag, false);
+    }
     if (status != 0) {
         // diagnostics: with KL_DUMP_DIR set, keep the matrix that failed
         if (const char* dir = std::getenv("KL_DUMP_DIR")) {
