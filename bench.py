@@ -97,6 +97,54 @@ def _recorded_traffic():
         return None
 
 
+def _sampling_leg(kl, handles, streams, lam, Vd, N, M, args, fp64_fma, ns=1024, reps=5):
+    """Realisations of the truncated expansion (Sec. 2) from each method's
+    eigenpairs: kl_sample at the tensor Gauss grid, ns samples per call, timed
+    with CUDA events on the handle's stream. On GB300 the FP64 FMAs bound it,
+    not HBM: the coefficient GEMM (N M ns) and the three banded passes of the
+    sum factorisation (p + 1 trial functions per Gauss point and direction,
+    direction 1 first: Ne1 N2 N3, Ne1 Ne2 N3 and Ne1 Ne2 Ne3 outputs per
+    sample). HBM figures beside it: the inputs and the output (V: N x M,
+    xi: M x ns, the samples: Q x ns, FP64) as algorithmic bytes."""
+    import numpy as np
+    import torch
+
+    peaks, src = _peaks()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(2101)
+    out = {}
+    for m, h in handles.items():
+        Q = kl.kl_sample_size(h)
+        xi = torch.randn((ns, M), dtype=torch.float64, device="cuda", generator=gen)  # column-major M x ns
+        res = torch.empty((ns, Q), dtype=torch.float64, device="cuda")
+        st = streams[m]
+        torch.cuda.synchronize()
+        for _ in range(2):
+            kl.kl_sample(h, M, lam[m], Vd[m], N, xi, M, ns, res, Q)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            kl.kl_sample(h, M, lam[m], Vd[m], N, xi, M, ns, res, Q)
+        e1.record(st)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / reps * 1e-3
+        alg = 8 * (N * M + M * ns + Q * ns)
+        p = args["p"]
+        n1 = [e + p for e in args["elems"]]           # trial functions per direction (C^{p-1})
+        ne = [(p + 1) * e for e in args["elems"]]     # Gauss points per direction
+        fma = ns * (N * M + (p + 1) * (ne[0] * n1[1] * n1[2] + ne[0] * ne[1] * n1[2] + ne[0] * ne[1] * ne[2]))
+        out[m] = {"ns": ns, "Q": Q, "ms": t * 1e3, "samples_per_s": ns / t,
+                  "bound": "fp64", "fma_per_call": fma, "achieved_tfma": fma / t / 1e12,
+                  "peak_tfma": fp64_fma / 1e12, "frac": fma / t / fp64_fma,
+                  "bytes_per_call": alg, "achieved_gbs": alg / t / 1e9, "peak_gbs": peaks["hbm_gbs"],
+                  "peak_gbs_source": src, "frac_hbm": alg / t / 1e9 / peaks["hbm_gbs"],
+                  "finite": bool(torch.isfinite(res).all().item())}
+        del res, xi
+    return out
+
+
 def _serve_leg(a, kl, stream):
     """Replays a bounded sample of the seeded serving stream (Poisson
     arrivals) through kl_serve_*, then the same requests one at a time."""
@@ -532,6 +580,9 @@ def run_gpu(a):
                               f"{fp32_fma / 1e12:.1f} T op/s / {fp32_per_pair} per pair); FP64 FMA "
                               f"{fp64_fma / 1e12:.2f} T/s",
                 "launches": st["launches"], "ms": st["ms"], "pairs": st["units"]}
+    # ---- K-L field sampling with the computed eigenpairs (not in the step) ----
+    sampling = _sampling_leg(kl, handles, streams, lam, Vd, N, M, args, fp64_fma) if rank == 0 else None
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu and a.workload == WORKLOAD:
         est, cores, sample, _ = _oracle_sample()
@@ -571,6 +622,7 @@ def run_gpu(a):
         "e2e": {"value": float(np.median(e2e_ms)) / 1e3, "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "serving": serving,
+        "sampling": sampling,
         "gpu_launches": int(launches),
         "clocks": clk,
         "region_s": region_s,

@@ -98,18 +98,19 @@ int ensure_workspace(kl_solver* h, int k) {
 // may be NULL); intermediates use ws[wa], ws[wb].
 static int kron3_s(kl_solver* h, const double* const* Fd, const int* n_in, const int* n_out,
                    const double* X, int64_t ldx, double* Y, int64_t ldy, int k, const double* post,
-                   double* sa, double* sb, const double* pre = nullptr);
+                   double* sa, double* sb, const double* pre = nullptr, const Band* bands = nullptr);
 
+// bands: banded forms of the F_d (per direction; vals NULL: dense product)
 static int kron3(kl_solver* h, const double* const* Fd, const int* n_in, const int* n_out,
                  const double* X, int64_t ldx, double* Y, int64_t ldy, int k, const double* post,
-                 int wa, int wb, const double* pre = nullptr) {
-    return kron3_s(h, Fd, n_in, n_out, X, ldx, Y, ldy, k, post, h->ws[wa], h->ws[wb], pre);
+                 int wa, int wb, const double* pre = nullptr, const Band* bands = nullptr) {
+    return kron3_s(h, Fd, n_in, n_out, X, ldx, Y, ldy, k, post, h->ws[wa], h->ws[wb], pre, bands);
 }
 
 // Same with explicit scratch for the two intermediate products.
 static int kron3_s(kl_solver* h, const double* const* Fd, const int* n_in, const int* n_out,
                    const double* X, int64_t ldx, double* Y, int64_t ldy, int k, const double* post,
-                   double* sa, double* sb, const double* pre) {
+                   double* sa, double* sb, const double* pre, const Band* bands) {
     int dims[3] = {n_in[0], n_in[1], n_in[2]};
     const double* cur = X;
     int64_t ldc = ldx;
@@ -128,8 +129,12 @@ static int kron3_s(kl_solver* h, const double* const* Fd, const int* n_in, const
             out = d == 0 ? sa : sb;
             ldo = out_len;
         }
-        cudaError_t e = launch_modeprod(Fd[d], n_out[d], n_in[d], cur, ldc, out, ldo, a, b, k,
-                                        d == 2 ? post : nullptr, d == 0 ? pre : nullptr, h->stream);
+        cudaError_t e =
+            (bands && bands[d].vals)
+                ? launch_modeprod_band(bands[d], n_out[d], n_in[d], cur, ldc, out, ldo, a, b, k,
+                                       d == 2 ? post : nullptr, d == 0 ? pre : nullptr, h->stream)
+                : launch_modeprod(Fd[d], n_out[d], n_in[d], cur, ldc, out, ldo, a, b, k, d == 2 ? post : nullptr,
+                                  d == 0 ? pre : nullptr, h->stream);
         ++h->launches;
         if (e != cudaSuccess) return cuda_fail(h, e, "modeprod");
         cur = out;
@@ -231,18 +236,20 @@ void clear_graphs(kl_solver* h) {
 //    point scale.
 static int apply_pre(kl_solver* h, int which, const double* X, int64_t ldx, int k) {
     const bool gal = galerkin_form(h->prm.method);
-    const double* const* F = (gal && which == 1) ? h->P : h->F;
+    const bool proj = gal && which == 1;
+    const double* const* F = proj ? h->P : h->F;
     const double* post = h->rat_w ? h->rat_src_scale : h->src_scale;
-    return kron3(h, F, h->N1, h->Ns1, X, ldx, h->ws[0], h->S, k, post, 1, 2, h->rat_w);
+    return kron3(h, F, h->N1, h->Ns1, X, ldx, h->ws[0], h->S, k, post, 1, 2, h->rat_w, proj ? nullptr : h->bF);
 }
 
 // 3) back to the trial space: Galerkin J, B~^-1, M^T (and L^-1); collocation
 //    Z^-1 for A': ws[1] -> Y
 static int apply_post(kl_solver* h, int which, double* Y, int64_t ldy, int k) {
     const bool gal = galerkin_form(h->prm.method);
-    const double* const* FT = (gal && which == 1) ? h->PT : h->FT;
+    const bool proj = gal && which == 1;
+    const double* const* FT = proj ? h->PT : h->FT;
     double* W = h->ws[1];
-    if (gal) return kron3(h, FT, h->Ns1, h->N1, W, h->T, Y, ldy, k, nullptr, 0, 2);
+    if (gal) return kron3(h, FT, h->Ns1, h->N1, W, h->T, Y, ldy, k, nullptr, 0, 2, nullptr, proj ? nullptr : h->bFT);
     if (which == 1) return kron3(h, h->Zinv, h->N1, h->N1, W, h->T, Y, ldy, k, h->rat_invw, 0, 2, h->rat_Wc);
     cudaError_t e = launch_copy_block(W, h->T, Y, ldy, h->T, k, h->stream);
     ++h->launches;
@@ -342,7 +349,7 @@ int back_transform(kl_solver* h, const double* Yv, int64_t ldy, double* V, int64
 }
 
 int field_at_quadrature(kl_solver* h, const double* V, int64_t ldv, double* out, int k) {
-    return kron3(h, h->F, h->N1, h->Nq1, V, ldv, out, h->S, k, h->rat_invWq, 1, 2, h->rat_w);
+    return kron3(h, h->F, h->N1, h->Nq1, V, ldv, out, h->S, k, h->rat_invWq, 1, 2, h->rat_w, h->bF);
 }
 
 }  // namespace kl
@@ -563,6 +570,71 @@ int kl_create(const kl_params* params, void* stream, kl_solver** out) {
         h->LinvT[d] = h->d_tables + off[6 * d + 5];
     }
     for (int j = 0; j < 9; ++j) h->pts1d[j] = h->d_tables + off[18 + j];
+    {
+        // banded forms of F, F^T and E (B-spline supports: p + 1 entries per
+        // row of F and E; a trial function spans p + 1 elements of Gauss
+        // points in F^T); dense projections are left dense
+        std::vector<double> bv;
+        std::vector<int> bs;
+        struct Pending {
+            Band* dst;
+            size_t v0, s0;
+            int w;
+        };
+        std::vector<Pending> pend;
+        for (int d = 0; d < 3; ++d) {
+            const Dir1D& q = dir[d];
+            const Mat* Fm = ibq ? &q.Q : stdg ? &q.E : &q.R;
+            const Mat FTm = transpose(*Fm);
+            const Mat* tabs[3] = {Fm, &FTm, &q.E};
+            Band* dst[3] = {&h->bF[d], &h->bFT[d], &h->bE[d]};
+            for (int t = 0; t < 3; ++t) {
+                const Mat& T = *tabs[t];
+                std::vector<int> lo(T.rows, 0);
+                int w = 1;
+                for (int i = 0; i < T.rows; ++i) {
+                    int a = -1, b = -1;
+                    for (int j = 0; j < T.cols; ++j)
+                        if (T(i, j) != 0.0) {
+                            if (a < 0) a = j;
+                            b = j;
+                        }
+                    lo[i] = a < 0 ? 0 : a;
+                    if (a >= 0) w = std::max(w, b - a + 1);
+                }
+                if (2 * w > T.cols) continue;  // not worth a band
+                Pending p{dst[t], bv.size(), bs.size(), w};
+                for (int i = 0; i < T.rows; ++i) {
+                    const int s0 = std::min(lo[i], T.cols - w);
+                    bs.push_back(s0);
+                    for (int j = 0; j < w; ++j) bv.push_back(T(i, s0 + j));
+                }
+                while (bv.size() % 4) bv.push_back(0.0);
+                while (bs.size() % 4) bs.push_back(0);
+                pend.push_back(p);
+            }
+        }
+        if (!pend.empty()) {
+            if ((e = dalloc(h, &h->d_band_vals, int64_t(bv.size()))) != cudaSuccess)
+                return bail(cuda_fail(h, e, "band alloc"));
+            if ((e = cudaMalloc(&h->d_band_start, bs.size() * sizeof(int))) != cudaSuccess)
+                return bail(cuda_fail(h, e, "band alloc"));
+            h->dev_bytes += int64_t(bs.size() * sizeof(int));
+            e = cudaMemcpyAsync(h->d_band_vals, bv.data(), bv.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                h->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h->d_band_start, bs.data(), bs.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                    h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // host vectors are temporaries
+            if (e != cudaSuccess) return bail(cuda_fail(h, e, "band upload"));
+            h->h2d_bytes += int64_t(bv.size() * sizeof(double) + bs.size() * sizeof(int));
+            for (const Pending& p : pend) {
+                p.dst->vals = h->d_band_vals + p.v0;
+                p.dst->start = h->d_band_start + p.s0;
+                p.dst->w = p.w;
+            }
+        }
+    }
     for (int d = 0; d < 3; ++d) {
         h->E[d] = h->d_tables + off[27 + d];
         h->xe[d] = h->d_tables + off[30 + d];
@@ -736,7 +808,7 @@ int kl_sample(kl_solver* h, int M, const double* lambda, const double* V, int64_
     h->launches += 3;
     if (e != cudaSuccess) return cuda_fail(h, e, "sample");
     // collocation with non-tensor NURBS weights: (B (w C)) / W at the Gauss grid
-    return kron3_s(h, h->E, h->N1, h->Ne1, C, N, out, ldo, ns, gal ? jscale : h->rat_invWq, sa, sb, h->rat_w);
+    return kron3_s(h, h->E, h->N1, h->Ne1, C, N, out, ldo, ns, gal ? jscale : h->rat_invWq, sa, sb, h->rat_w, h->bE);
 }
 
 int kl_set_graphs(kl_solver* h, int on) {
@@ -820,6 +892,8 @@ int kl_destroy(kl_solver* h) {
     dfree(h->d_points);
     dfree(h->d_points32);
     dfree(h->d_rat);
+    dfree(h->d_band_vals);
+    dfree(h->d_band_start);
     for (int i = 0; i < 3; ++i) dfree(h->ws[i]);
     dfree(h->pair_scratch);
     dfree(h->eig_ws);

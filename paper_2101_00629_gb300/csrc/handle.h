@@ -49,6 +49,13 @@ struct kl_solver {
     const double* LinvT[3] = {};  // Galerkin L_d^-T                            (N_d x N_d)
     const double* pts1d[9] = {};  // target params (3), source params (3), source weights (3)
     const double* E[3] = {};      // trial basis at the Gauss points of direction d (Ne_d x N_d)
+    // banded forms of the B-spline / NURBS tables (each row has at most p + 1
+    // nonzero entries next to each other): row i holds `w` values starting at
+    // column start[i]; vals == NULL where a table is not banded (dense
+    // projections and inverses)
+    kl::Band bF[3], bFT[3], bE[3];
+    double* d_band_vals = nullptr;
+    int* d_band_start = nullptr;
     const double* xe[3] = {};     // those Gauss points (parameters)
     int Ne1[3] = {1, 1, 1};       // Gauss points per direction (sampling grid)
 

@@ -129,6 +129,37 @@ __global__ void modeprod_kernel(const double* __restrict__ A, int m, int n,
     }
 }
 
+// Banded form: out[(ia, i, ib), c] = sum_j V[i w + j] pre[(ia, s_i + j, ib)]
+// X[(ia, s_i + j, ib), c] with s_i = start[i].
+__global__ void modeprod_band_kernel(const double* __restrict__ V, const int* __restrict__ start, int w, int m,
+                                     int n, const double* __restrict__ X, int64_t ldx, double* __restrict__ Y,
+                                     int64_t ldy, int64_t a, int64_t b, int k, const double* __restrict__ post,
+                                     const double* __restrict__ pre) {
+    const int64_t per_col = a * m * b;
+    const int64_t total = per_col * k;
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+         t += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t c = t / per_col;
+        const int64_t r = t - c * per_col;  // = ia + a * (i + m * ib)
+        const int64_t ia = r % a;
+        const int64_t rest = r / a;
+        const int i = int(rest % m);
+        const int64_t ib = rest / m;
+        const int64_t off = ia + a * (int64_t(start[i]) + int64_t(n) * ib);
+        const double* x = X + c * ldx + off;
+        const double* v = V + int64_t(i) * w;
+        double acc = 0.0;
+        if (pre) {
+            const double* s = pre + off;
+            for (int j = 0; j < w; ++j) acc = fma(v[j], x[a * j] * s[a * j], acc);
+        } else {
+            for (int j = 0; j < w; ++j) acc = fma(v[j], x[a * j], acc);
+        }
+        if (post) acc *= post[r];
+        Y[c * ldy + r] = acc;
+    }
+}
+
 __device__ inline unsigned long long splitmix64(unsigned long long x) {
     x += 0x9E3779B97F4A7C15ull;
     x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -292,6 +323,16 @@ cudaError_t launch_modeprod(const double* A, int m, int n, const double* X, int6
     const int64_t total = a * m * b * k;
     if (total == 0) return cudaSuccess;
     modeprod_kernel<<<grid_for(total), kThreads, 0, s>>>(A, m, n, X, ldx, Y, ldy, a, b, k, post, pre);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_modeprod_band(const Band& A, int m, int n, const double* X, int64_t ldx, double* Y,
+                                 int64_t ldy, int64_t a, int64_t b, int k, const double* post,
+                                 const double* pre, cudaStream_t s) {
+    const int64_t total = a * m * b * k;
+    if (total == 0) return cudaSuccess;
+    modeprod_band_kernel<<<grid_for(total), kThreads, 0, s>>>(A.vals, A.start, A.w, m, n, X, ldx, Y, ldy, a, b, k,
+                                                              post, pre);
     return cudaGetLastError();
 }
 

@@ -91,6 +91,18 @@ cudaError_t launch_tensor_points(int geometry, const double* geo, const double* 
                                  const double* w2, const double* w3, double jac_power, double* out_x,
                                  double* out_y, double* out_z, double* out_w, cudaStream_t s);
 
+// A banded m x n table: row i has its nonzero entries in columns
+// start[i] .. start[i] + w - 1 (start[i] + w <= n), values vals[i * w + j].
+struct Band {
+    const double* vals = nullptr;
+    const int* start = nullptr;
+    int w = 0;
+};
+// Y(a, m, b, c) = sum_j vals(i, j) X(a, start[i] + j, b, c): the mode product
+// of launch_modeprod with a banded table (same scalings).
+cudaError_t launch_modeprod_band(const Band& A, int m, int n, const double* X, int64_t ldx, double* Y,
+                                 int64_t ldy, int64_t a, int64_t b, int k, const double* post,
+                                 const double* pre, cudaStream_t s);
 // Y(a, m, b, c) = sum_l A(i, l) X(a, l, b, c) (+ optional scaling of the
 // output rows by post[a + A*(i + m*b)] and of the input rows by
 // pre[a + A*(l + n*b)]).
