@@ -11,6 +11,7 @@
 #include <cfloat>
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "kl_internal.h"
 
@@ -225,6 +226,85 @@ __global__ void __launch_bounds__(256) chol_rinv_kernel(double* G, int n, double
     }
 }
 
+// Shared-memory form for n <= kCholSmemN: L and X = L^-1 in shared memory,
+// one division per column (its reciprocal scales the column) and X by
+// column-oriented forward substitution, whose dependent chain is one
+// multiply-subtract per column of L instead of a dot product per entry.
+constexpr int kCholSmemN = 96;
+
+size_t chol_smem_bytes(int n) { return (2 * size_t(n) * n + 3 * size_t(n)) * sizeof(double); }
+
+__global__ void __launch_bounds__(256) chol_rinv_smem_kernel(double* G, int n, double* Rinv, int* bad) {
+    extern __shared__ double sm[];
+    double* L = sm;                       // n x n, column-major
+    double* X = L + int64_t(n) * n;       // L^-1, column-major
+    double* g0 = X + int64_t(n) * n;      // original diagonal
+    double* inv = g0 + n;                 // 1 / L(j, j)
+    double* s_misc = inv + n;             // [0]: largest original diagonal entry
+    __shared__ double s_inv;
+    __shared__ int s_bad;
+    const int tid = threadIdx.x;
+    const int nn = n * n;
+    for (int e = tid; e < nn; e += blockDim.x) {
+        L[e] = G[e];
+        X[e] = (e % n == e / n) ? 1.0 : 0.0;
+    }
+    for (int j = tid; j < n; j += blockDim.x) {
+        g0[j] = G[j + int64_t(j) * n];
+        bad[j] = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double m = 0.0;
+        for (int j = 0; j < n; ++j) m = fmax(m, g0[j]);
+        s_misc[0] = m;
+    }
+    __syncthreads();
+    const double maxd = s_misc[0];
+    for (int j = 0; j < n; ++j) {
+        if (tid == 0) {
+            const double d2 = L[j + j * n];
+            const bool b = !(d2 > 1e-28 * maxd) || !(d2 > 1e-14 * g0[j]) || !isfinite(d2);
+            const double d = b ? 1.0 : sqrt(d2);
+            s_bad = b ? 1 : 0;
+            s_inv = b ? 1.0 : 1.0 / d;
+            inv[j] = s_inv;
+            L[j + j * n] = d;
+            if (b) bad[j] = 1;
+        }
+        __syncthreads();
+        const double r = s_inv;
+        const int bj = s_bad;
+        for (int i = j + 1 + tid; i < n; i += blockDim.x) L[i + j * n] = bj ? 0.0 : L[i + j * n] * r;
+        __syncthreads();
+        const int rr = n - j - 1;
+        for (int e = tid; e < rr * rr; e += blockDim.x) {
+            const int ii = j + 1 + e % rr, ll = j + 1 + e / rr;
+            if (ii >= ll) L[ii + ll * n] -= L[ii + j * n] * L[ll + j * n];
+        }
+        __syncthreads();
+    }
+    // X = L^-1 (lower): row l of X is final once scaled; it then updates the
+    // rows below it (only columns c <= l are nonzero)
+    for (int l = 0; l < n; ++l) {
+        const double r = inv[l];
+        for (int c = tid; c <= l; c += blockDim.x) X[l + c * n] *= r;
+        __syncthreads();
+        const int rows = n - l - 1, cols = l + 1;
+        for (int e = tid; e < rows * cols; e += blockDim.x) {
+            const int i = l + 1 + e % rows, c = e / rows;
+            X[i + c * n] -= L[i + l * n] * X[l + c * n];
+        }
+        __syncthreads();
+    }
+    // Rinv = L^-T (upper): Rinv(c, i) = X(i, c); L back into G
+    for (int e = tid; e < nn; e += blockDim.x) {
+        const int c = e % n, i = e / n;
+        Rinv[e] = (i >= c) ? X[i + c * n] : 0.0;
+        G[e] = L[e];
+    }
+}
+
 }  // namespace
 
 // Enough for every product with m' <= m, n' <= n and this K: a smaller
@@ -268,6 +348,17 @@ cudaError_t launch_gemm_nn(const double* A, int64_t lda, const double* B, int64_
 }
 
 cudaError_t launch_chol_rinv(double* G, int n, double* Rinv, int* bad, cudaStream_t s) {
+    if (n >= 1 && n <= kCholSmemN) {
+        static std::once_flag once;
+        static cudaError_t attr_error = cudaSuccess;
+        std::call_once(once, [] {
+            attr_error = cudaFuncSetAttribute(chol_rinv_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              int(chol_smem_bytes(kCholSmemN)));
+        });
+        if (attr_error != cudaSuccess) return attr_error;
+        chol_rinv_smem_kernel<<<1, 256, chol_smem_bytes(n), s>>>(G, n, Rinv, bad);
+        return cudaGetLastError();
+    }
     chol_rinv_kernel<<<1, 256, n * sizeof(double), s>>>(G, n, Rinv, bad);
     return cudaGetLastError();
 }
