@@ -111,15 +111,32 @@ __global__ void __launch_bounds__(256) gemm_tn_narrow_kernel(const double* __res
     if (i < m && ty < n) part[(int64_t(blockIdx.z) * n + ty) * m + i] = acc;
 }
 
-__global__ void gemm_tn_reduce(const double* __restrict__ part, int splits, int m, int n,
-                               double alpha, double beta, double* C, int64_t ldc) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * n; e += gridDim.x * blockDim.x) {
-        const int i = e % m, j = e / m;
+// C = alpha * (sum of the splits' partial products) + beta * C. A block
+// takes 32 outputs (one per lane, coalesced) and its 8 warps take every 8th
+// split, so that the dependent chain of FP64 additions is splits / 8 long
+// (GB300: a dependent FP64 add waits about 63 cycles); the 8 partial sums
+// are added in a fixed order.
+__global__ void __launch_bounds__(256) gemm_tn_reduce(const double* __restrict__ part, int splits, int m, int n,
+                                                      double alpha, double beta, double* C, int64_t ldc) {
+    __shared__ double red[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int total = m * n;
+    for (int base = blockIdx.x * 32; base < total; base += gridDim.x * 32) {
+        const int e = base + tx;
         double s = 0.0;
-        for (int sp = 0; sp < splits; ++sp) s += part[(int64_t(sp) * n + j) * m + i];
-        double v = alpha * s;
-        if (beta != 0.0) v += beta * C[i + j * ldc];
-        C[i + j * ldc] = v;
+        if (e < total)
+            for (int sp = ty; sp < splits; sp += 8) s += part[int64_t(sp) * total + e];
+        red[ty][tx] = s;
+        __syncthreads();
+        if (ty == 0 && e < total) {
+            double t = red[0][tx];
+            for (int w = 1; w < 8; ++w) t += red[w][tx];
+            const int i = e % m, j = e / m;
+            double v = alpha * t;
+            if (beta != 0.0) v += beta * C[i + j * ldc];
+            C[i + j * ldc] = v;
+        }
+        __syncthreads();
     }
 }
 
@@ -333,7 +350,7 @@ cudaError_t launch_gemm_tn(const double* A, int64_t lda, const double* B, int64_
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int g = std::max(1, std::min(152 * 8, (m * n + 255) / 256));
+    const int g = std::max(1, std::min(152 * 8, (m * n + 31) / 32));
     gemm_tn_reduce<<<g, 256, 0, s>>>(scratch, splits, m, n, alpha, beta, C, ldc);
     return cudaGetLastError();
 }
