@@ -391,6 +391,35 @@ int kl_serve_get_stats(kl_server* s, kl_serve_stats* out);
 /* Waits for every queued and running solve, stops the workers, frees. */
 int kl_serve_close(kl_server* s);
 
+/* Failure injection on the host, for tests of the error paths (no paper
+ * passage). Nothing here faults, traps or hangs the GPU:
+ *   KL_DEBUG_WAIT_LIMIT  (handle) clock cycles each pipeline wait of the
+ *                        tcgen05 pairwise kernel may take before it gives up
+ *                        (0: the default, about a second). A short limit
+ *                        makes the waits give up: the kernel records the
+ *                        timeout in the handle's error word, always lets its
+ *                        issued MMAs and copies finish (default bound), frees
+ *                        its tensor memory and returns; kl_eigs then returns
+ *                        KL_ERR_TIMEOUT.
+ *   KL_DEBUG_FAIL_ALLOC  (h may be NULL; process-wide) the value-th device
+ *                        allocation of the library from now on fails as if
+ *                        the device were out of memory (KL_ERR_OOM); 0
+ *                        cancels a pending failure.
+ *   KL_DEBUG_NAN_START   (handle) value != 0 plants a NaN in the
+ *                        eigensolver's start block (kl_eigs returns
+ *                        KL_ERR_NUMERIC).
+ * Errors: KL_ERR_ARG. */
+enum { KL_DEBUG_WAIT_LIMIT = 1, KL_DEBUG_FAIL_ALLOC = 2, KL_DEBUG_NAN_START = 3 };
+int kl_debug_set(kl_solver* h, int what, long long value);
+
+/* 1 if the library was built with KL_CHECK_BOUNDS (every kernel launch first
+ * checks, on the host, that each device range it will touch lies inside one
+ * live device allocation, and the small eigensolver checks its
+ * data-dependent indices; a failed check fails the call with KL_ERR_CUDA and
+ * a message on stderr instead of launching), 0 for the regular build. No
+ * paper passage: a debugging aid of this library. */
+int kl_bounds_checked(void);
+
 /* Last error message of the handle (h may be NULL: last kl_create error). */
 const char* kl_last_error(const kl_solver* h);
 const char* kl_status_string(int status);

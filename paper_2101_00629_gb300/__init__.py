@@ -20,7 +20,8 @@ __all__ = [
     "kl_status_string", "kl_measure_peaks", "kl_pairwise_noalloc", "kl_estimate_bytes",
     "kl_serve_config", "kl_serve_result", "kl_serve_stats", "kl_serve_open", "kl_serve_submit",
     "kl_serve_poll", "kl_serve_get_stats", "kl_serve_close", "kl_set_graphs", "kl_block_size",
-    "kl_autotune", "kl_sample_size", "kl_sample_points", "kl_sample", "library_path", "EXPORTED_SYMBOLS",
+    "kl_autotune", "kl_sample_size", "kl_sample_points", "kl_sample", "kl_bounds_checked", "kl_debug_set", "library_path",
+    "EXPORTED_SYMBOLS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -29,6 +30,7 @@ _LIB_PATH = os.path.join(_HERE, "libkl.so")
 KL_OK, KL_ERR_ARG, KL_ERR_CUDA, KL_ERR_OOM = 0, -1, -2, -3
 KL_ERR_NOCONV, KL_ERR_NUMERIC, KL_ERR_TIMEOUT, KL_ERR_UNSUPPORTED = -4, -5, -6, -7
 KL_WARN_COMPLEX = 1
+KL_DEBUG_WAIT_LIMIT, KL_DEBUG_FAIL_ALLOC, KL_DEBUG_NAN_START = 1, 2, 3
 
 GEOMETRIES = {"cube": 0, "annulus": 1, "half_annulus": 2, "projective_cube": 3}
 KERNELS = {"gauss": 0, "exp_sep": 1, "exp": 2, "matern32": 3, "const": 4}
@@ -43,6 +45,7 @@ EXPORTED_SYMBOLS = (
     "kl_status_string", "kl_measure_peaks", "kl_pairwise_noalloc", "kl_estimate_bytes",
     "kl_serve_open", "kl_serve_submit", "kl_serve_poll", "kl_serve_get_stats", "kl_serve_close",
     "kl_set_graphs", "kl_block_size", "kl_autotune", "kl_sample_size", "kl_sample_points", "kl_sample",
+    "kl_bounds_checked", "kl_debug_set",
 )
 
 
@@ -174,6 +177,8 @@ def _load():
         "kl_sample_size": (i64, [vp]),
         "kl_sample_points": (c_int, [vp, vp]),
         "kl_sample": (c_int, [vp, c_int, vp, vp, i64, vp, i64, c_int, vp, i64]),
+        "kl_bounds_checked": (c_int, []),
+        "kl_debug_set": (c_int, [vp, c_int, ctypes.c_longlong]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -388,6 +393,18 @@ def kl_autotune(p, M, tol=0.0, stream=None, cache_path=None):
     _check(None, _load().kl_autotune(ctypes.byref(p), int(M), float(tol), stream,
                                      cache_path.encode() if cache_path else None, ctypes.byref(k), secs))
     return k.value, list(secs)
+
+
+def kl_debug_set(h, what, value):
+    """Host-side failure injection for tests (see kl.h): what is
+    KL_DEBUG_WAIT_LIMIT, KL_DEBUG_FAIL_ALLOC (h may be None) or
+    KL_DEBUG_NAN_START."""
+    return _check(h, _load().kl_debug_set(h, int(what), int(value)))
+
+
+def kl_bounds_checked():
+    """True if libkl.so is the bounds-checking build (KL_CHECK_BOUNDS)."""
+    return bool(_load().kl_bounds_checked())
 
 
 def kl_sample_size(h):

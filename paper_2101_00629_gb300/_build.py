@@ -3,7 +3,13 @@
 Every translation unit under ``csrc/`` is compiled in parallel into
 ``_build/`` and linked (static CUDA runtime) into ``libkl.so`` next to this
 file. No cmake; one -gencode. Rebuilds only when a source or header is newer
-than the library.
+than the library, or when the compile flags changed.
+
+With the environment variable KL_CHECK_BOUNDS=1 the library is built with
+-DKL_CHECK_BOUNDS: every launcher checks on the host, before its launch, that
+each device range its kernel touches lies inside one live allocation
+(csrc/bounds.cpp), and the small eigensolver checks its data-dependent
+indices in the kernel. A debugging build: slower launches, same results.
 """
 import concurrent.futures as cf
 import os
@@ -20,6 +26,14 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-Wall", "-diag-suppress", "177,550"]
+
+
+STAMP = os.path.join(BUILD, "flags.txt")
+
+
+def _flags():
+    extra = ["-DKL_CHECK_BOUNDS"] if os.environ.get("KL_CHECK_BOUNDS", "0") not in ("", "0") else []
+    return FLAGS + extra
 
 
 def _nvcc():
@@ -40,8 +54,11 @@ def _deps():
 
 
 def needs_build():
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return True
+    with open(STAMP) as f:
+        if f.read() != " ".join(_flags()):
+            return True
     t = os.path.getmtime(LIB)
     return any(os.path.getmtime(f) > t for f in _deps())
 
@@ -53,12 +70,13 @@ def build(force=False, verbose=False, ptxas_info=False):
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    flags = _flags()
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-I", INCLUDE, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *flags, *extra, "-I", INCLUDE, "-c", src, "-o", obj]
         if src.endswith(".cpp"):
-            cmd = [nvcc, *FLAGS, "-I", INCLUDE, "-x", "c++", "-c", src, "-o", obj]
+            cmd = [nvcc, *flags, "-I", INCLUDE, "-x", "c++", "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {os.path.basename(src)}:\n{r.stderr}")
@@ -74,6 +92,8 @@ def build(force=False, verbose=False, ptxas_info=False):
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(" ".join(flags))
     return LIB
 
 

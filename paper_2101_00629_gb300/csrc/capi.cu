@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -18,6 +19,39 @@ thread_local std::string g_create_error;  // per host thread (servers create han
 }
 
 namespace kl {
+
+int device_sm_count() {
+    constexpr int kMax = 64;
+    static std::atomic<int> cache[kMax];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMax) {
+        cudaGetLastError();
+        return 152;
+    }
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+        cudaGetLastError();
+        return 152;
+    }
+    cache[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
+
+namespace {
+// allocations left before the injected failure (kl_debug_set with
+// KL_DEBUG_FAIL_ALLOC; 0: none pending)
+std::atomic<long long> g_fail_alloc_in{0};
+}  // namespace
+
+cudaError_t device_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    long long left = g_fail_alloc_in.load();
+    while (left > 0 && !g_fail_alloc_in.compare_exchange_weak(left, left - 1)) {
+    }
+    if (left == 1) return cudaErrorMemoryAllocation;  // this is the allocation that fails
+    return cudaMalloc(p, bytes);
+}
 
 int fail(kl_solver* h, int code, const std::string& msg) {
     if (h) h->err = msg; else g_create_error = msg;
@@ -56,7 +90,7 @@ template <class T>
 cudaError_t dalloc(kl_solver* h, T** p, int64_t count) {
     *p = nullptr;
     if (count <= 0) count = 1;
-    cudaError_t e = cudaMalloc((void**)p, size_t(count) * sizeof(T));
+    cudaError_t e = device_alloc((void**)p, size_t(count) * sizeof(T));
     if (e == cudaSuccess) h->dev_bytes += count * int64_t(sizeof(T));
     return e;
 }
@@ -183,6 +217,7 @@ static int pairwise(kl_solver* h, int precision, const double* U, double* W, int
         a.scratch = h->pair_scratch; a.scratch_len = h->pair_scratch_len;
         a.sm_count = h->sm_count;
         a.err = h->d_err;
+        a.wait_limit = h->wait_limit;
         ProfScope ps(h, precision == KL_MIXED_TF32 ? "pair_tc_tf32" : "pair_tc_bf16", pairs);
         int launched = 0;
         if (!h->batcher) {
@@ -617,7 +652,7 @@ int kl_create(const kl_params* params, void* stream, kl_solver** out) {
         if (!pend.empty()) {
             if ((e = dalloc(h, &h->d_band_vals, int64_t(bv.size()))) != cudaSuccess)
                 return bail(cuda_fail(h, e, "band alloc"));
-            if ((e = cudaMalloc(&h->d_band_start, bs.size() * sizeof(int))) != cudaSuccess)
+            if ((e = device_alloc((void**)&h->d_band_start, bs.size() * sizeof(int))) != cudaSuccess)
                 return bail(cuda_fail(h, e, "band alloc"));
             h->dev_bytes += int64_t(bs.size() * sizeof(int));
             e = cudaMemcpyAsync(h->d_band_vals, bv.data(), bv.size() * sizeof(double), cudaMemcpyHostToDevice,
@@ -775,7 +810,7 @@ int kl_sample(kl_solver* h, int M, const double* lambda, const double* V, int64_
             h->smp_ws = nullptr;
             h->smp_cap = 0;
         }
-        e = cudaMalloc(&h->smp_ws, size_t(need) * sizeof(double));
+        e = device_alloc((void**)&h->smp_ws, size_t(need) * sizeof(double));
         if (e != cudaSuccess) return cuda_fail(h, e, "sample workspace");
         h->smp_cap = need;
         h->dev_bytes += need * int64_t(sizeof(double));
@@ -857,13 +892,9 @@ int kl_estimate_bytes(const kl_params* params, int M, int64_t* bytes) {
     }
     const int64_t S = Ns, T = gal ? S : N;
     int sm = 152;
-    int dev = 0, ndev = 0;
-    if (cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0 && cudaGetDevice(&dev) == cudaSuccess) {
-        cudaDeviceProp prop;
-        if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) sm = prop.multiProcessorCount;
-    } else {
-        cudaGetLastError();
-    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0) sm = device_sm_count();
+    else cudaGetLastError();
     const int b = int(std::min<int64_t>(p.block_k, N));
     const int mcap = eig_basis_cap(N, std::min<int64_t>(M, N), b);
     // widest operator application: the final refinement of nkeep + 1 vectors
@@ -990,6 +1021,29 @@ int kl_profile_read(kl_solver* h, kl_kernel_stats* out, int cap, int* n) {
 }
 
 long long kl_launch_count(const kl_solver* h) { return h ? h->launches : 0; }
+
+int kl_debug_set(kl_solver* h, int what, long long value) {
+    switch (what) {
+        case KL_DEBUG_WAIT_LIMIT:
+            if (!h) return fail(nullptr, KL_ERR_ARG, "KL_DEBUG_WAIT_LIMIT needs a handle");
+            if (value < 0) return fail(h, KL_ERR_ARG, "wait limit must be >= 0");
+            if (cudaError_t e = cudaStreamSynchronize(h->stream); e != cudaSuccess)
+                return cuda_fail(h, e, "kl_debug_set");
+            h->wait_limit = value;
+            clear_graphs(h);  // captured launches carry the old limit
+            return KL_OK;
+        case KL_DEBUG_FAIL_ALLOC:
+            if (value < 0) return fail(h, KL_ERR_ARG, "allocation count must be >= 0");
+            g_fail_alloc_in.store(value);
+            return KL_OK;
+        case KL_DEBUG_NAN_START:
+            if (!h) return fail(nullptr, KL_ERR_ARG, "KL_DEBUG_NAN_START needs a handle");
+            h->nan_start = value != 0;
+            return KL_OK;
+        default:
+            return fail(h, KL_ERR_ARG, "unknown debug setting");
+    }
+}
 
 int kl_memory(const kl_solver* h, int64_t* h2d_bytes, int64_t* device_bytes) {
     if (!h) return KL_ERR_ARG;

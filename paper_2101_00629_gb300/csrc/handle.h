@@ -91,6 +91,12 @@ struct kl_solver {
     // synchronisation; see check_device_error)
     int* d_err = nullptr;
 
+    // failure injection (kl_debug_set): clock cycles of each pipeline wait
+    // of the tcgen05 kernel (0: the default, about a second) and a NaN
+    // planted in the eigensolver's start block
+    long long wait_limit = 0;
+    bool nan_start = false;
+
     // kl_sample scratch (grown on demand)
     double* smp_ws = nullptr;
     int64_t smp_cap = 0;  // doubles

@@ -14,6 +14,7 @@
 // on the four sub-partitions, reductions by shuffles, deflation and ordering
 // decisions evaluated by all threads at once) and only the Householder vector
 // of the bulge chase is a one-thread chain.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <mutex>
@@ -244,7 +245,7 @@ __device__ void swap_transform(const R* A, int n, int k, int n1, int n2, R anorm
 // ints: 2n ints of scratch (block starts, pair positions, pair sizes/flags);
 // ord: 8n doubles (a 4 x 4 transform per pair).
 template <class R>
-__device__ void order_schur(R* A, R* Z, int n, R anorm, R* ints_d, R* ord) {
+__device__ void order_schur(R* A, R* Z, int n, R anorm, R* ints_d, R* ord, int* oob) {
     constexpr int NT = kEigThreads;
     __shared__ int s_wsum[kEigWarps];
     int* bstart = reinterpret_cast<int*>(ints_d);  // n
@@ -284,7 +285,15 @@ __device__ void order_schur(R* A, R* Z, int n, R anorm, R* ints_d, R* ord) {
             const R key1 = n1 == 1 ? A[k + int64_t(k) * n] : R(0.5) * (A[k + int64_t(k) * n] + A[(k + 1) + int64_t(k + 1) * n]);
             const R key2 = n2 == 1 ? A[k2 + int64_t(k2) * n]
                                         : R(0.5) * (A[k2 + int64_t(k2) * n] + A[(k2 + 1) + int64_t(k2 + 1) * n]);
-            const int f = key2 > key1;
+            int f = key2 > key1;
+#ifdef KL_CHECK_BOUNDS
+            // pair and block indices stay inside the scratch (n / 2 pairs) and
+            // the blocks are 1x1 or 2x2; otherwise record it, skip the exchange
+            if (b0 + 1 >= nb || p >= n / 2 || n1 < 1 || n1 > 2 || n2 < 1 || n2 > 2 || k3 > n) {
+                atomicExch(oob, 1);
+                f = 0;
+            }
+#endif
             if (f) {
                 swap_transform(A, n, k, n1, n2, anorm, ord + 16 * int64_t(p));
                 if (n1 == 1 && n2 == 1) {
@@ -384,7 +393,7 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
     __shared__ int s_redi[kEigWarps];
     __shared__ R s_v[3], s_x[3];
     __shared__ R s_beta, s_sh, s_th;
-    __shared__ int s_l, s_u, s_its, s_fail, s_action;
+    __shared__ int s_l, s_u, s_its, s_fail, s_action, s_oob;
     const int tid = threadIdx.x;
     constexpr int NT = kEigThreads;
 
@@ -460,6 +469,7 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         s_u = n - 1;
         s_its = 0;
         s_fail = 0;
+        s_oob = 0;
     }
     __syncthreads();
     int total_its = 0;
@@ -698,6 +708,12 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                 const R dj = A[j + int64_t(j) * n];
                 if (dj > di || (dj == di && j < i)) ++rank;
             }
+#ifdef KL_CHECK_BOUNDS
+            if (rank < 0 || rank >= n) {
+                atomicExch(&s_oob, 1);
+                rank = 0;
+            }
+#endif
             wr_out[rank] = di;
             if (wi_out) wi_out[rank] = R(0.0);
             rk[i] = rank;
@@ -711,7 +727,7 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         }
     } else if (!fail) {
         // ---- ordering of the real Schur form by decreasing real part ----
-        order_schur(A, Z, n, anorm, hv, ord);
+        order_schur(A, Z, n, anorm, hv, ord, &s_oob);
         __syncthreads();
 
         // ---- eigenvalues of the ordered blocks ----
@@ -862,7 +878,8 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             for (int64_t e = tid; e < nn; e += NT) Qout[e] = Z[e];
     }
     if (tid == 0) {
-        status[0] = fail ? 1 : 0;
+        // 3: the bounds-checking build found an index out of range
+        status[0] = s_oob ? 3 : fail ? 1 : 0;
         // diagnostics after the status word: QR iterations, last window end,
         // iterations spent on it
         status[1] = total_its;
@@ -907,6 +924,16 @@ cudaError_t launch_eig_t(const double* H, int n, double* wr, double* wi, double*
 cudaError_t launch_eig(const double* H, int n, double* wr, double* wi, double* V, double* Q, double* work,
                        int* status, int sym, int nvec, bool fp32, cudaStream_t s) {
     if (n <= 0) return cudaErrorInvalidValue;
+    const int64_t nn = int64_t(n) * n;
+    KL_RANGE(H, nn, double, "eig H");
+    KL_RANGE(wr, n, double, "eig wr");
+    KL_RANGE(wi, n, double, "eig wi");
+    // eigenvectors: all n (symmetric) or the leading nvec (one more to keep
+    // a complex pair whole), n rows each
+    KL_RANGE(V, sym ? nn : int64_t(n) * std::min(n, std::max(nvec, 1) + 1), double, "eig V");
+    KL_RANGE(Q, nn, double, "eig Q");
+    KL_RANGE(work, nonsym_eig_work_doubles(n), double, "eig work");
+    KL_RANGE(status, 4, int, "eig status");
     return fp32 ? launch_eig_t<float>(H, n, wr, wi, V, Q, work, status, sym, nvec, s)
                 : launch_eig_t<double>(H, n, wr, wi, V, Q, work, status, sym, nvec, s);
 }

@@ -223,7 +223,12 @@ int64_t jacobi_work_doubles(int n) {
 cudaError_t launch_sym_eig_jacobi(const double* H, int n, double* w, double* V, double* work, int* status,
                                   cudaStream_t s, bool fp32) {
     if (n <= 0 || n > kJacMaxN) return cudaErrorInvalidValue;
+    KL_RANGE(H, int64_t(n) * n, double, "jacobi H");
+    KL_RANGE(w, n, double, "jacobi w");
+    KL_RANGE(V, int64_t(n) * n, double, "jacobi V");
+    KL_RANGE(status, 1, int, "jacobi status");
     if (fp32) return launch_jacobi<float>(H, n, 30, w, V, status, s);
+    KL_RANGE(work, jacobi_work_doubles(n), double, "jacobi work");
     const int64_t nn = int64_t(n) * n;
     double* Q0 = work;       // FP32 eigenvectors
     double* G = Q0 + nn;     // Q0^T Q0, then H Q

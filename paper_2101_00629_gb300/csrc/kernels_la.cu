@@ -23,7 +23,8 @@ namespace {
 constexpr int TN_T = 32;
 constexpr int TN_NARROW = 8;   // products with n <= 8 use 32 x 8 tiles
 constexpr int TN_KMIN = 64;    // shortest K chunk of one CTA
-constexpr int TN_CTAS = 4 * 152;
+// about four CTAs per SM
+inline int tn_ctas() { return 4 * device_sm_count(); }
 
 inline int tn_tiles(int m, int n) {
     const int tm = (m + TN_T - 1) / TN_T;
@@ -35,7 +36,7 @@ inline int tn_splits(int m, int n, int64_t K) {
     // CTAs per SM exist: every CTA is bound by the SM's FP64 rate (~1.7
     // DFMA/clock on GB300), so the work must reach every SM
     int64_t s = (K + TN_KMIN - 1) / TN_KMIN;
-    int64_t cap = TN_CTAS / tn_tiles(m, n);
+    int64_t cap = tn_ctas() / tn_tiles(m, n);
     if (cap < 1) cap = 1;
     if (s > cap) s = cap;
     if (s < 1) s = 1;
@@ -326,11 +327,11 @@ __global__ void __launch_bounds__(256) chol_rinv_smem_kernel(double* G, int n, d
 
 // Enough for every product with m' <= m, n' <= n and this K: a smaller
 // product may take more splits (fewer tiles), but splits * m' * n' never
-// exceeds min(ceil(K / TN_KMIN) m n, TN_CTAS * TN_T^2) (at least m n; a tile
+// exceeds min(ceil(K / TN_KMIN) m n, tn_ctas() * TN_T^2) (at least m n; a tile
 // holds at most TN_T^2 outputs).
 int64_t gemm_tn_scratch_doubles(int m, int n, int64_t K) {
     const int64_t s = std::max<int64_t>(1, (K + TN_KMIN - 1) / TN_KMIN);
-    const int64_t bound = std::min<int64_t>(s * m * n, int64_t(TN_CTAS) * TN_T * TN_T);
+    const int64_t bound = std::min<int64_t>(s * m * n, int64_t(tn_ctas()) * TN_T * TN_T);
     return std::max<int64_t>(bound, int64_t(m) * n);
 }
 
@@ -340,6 +341,10 @@ cudaError_t launch_gemm_tn(const double* A, int64_t lda, const double* B, int64_
     if (m <= 0 || n <= 0) return cudaSuccess;
     const int splits = tn_splits(m, n, K);
     if (int64_t(splits) * m * n > scratch_doubles) return cudaErrorInvalidValue;
+    KL_RANGE(A, block_extent(K, m, lda), double, "gemm_tn A");
+    KL_RANGE(B, block_extent(K, n, ldb), double, "gemm_tn B");
+    KL_RANGE(C, block_extent(m, n, ldc), double, "gemm_tn C");
+    KL_RANGE(scratch, int64_t(splits) * m * n, double, "gemm_tn scratch");
     const int64_t kchunk = ((K + splits - 1) / splits + TN_T - 1) / TN_T * TN_T;
     if (n <= TN_NARROW) {
         dim3 grid((m + TN_T - 1) / TN_T, 1, splits);
@@ -350,7 +355,7 @@ cudaError_t launch_gemm_tn(const double* A, int64_t lda, const double* B, int64_
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int g = std::max(1, std::min(152 * 8, (m * n + 31) / 32));
+    const int g = std::max(1, std::min(device_sm_count() * 8, (m * n + 31) / 32));
     gemm_tn_reduce<<<g, 256, 0, s>>>(scratch, splits, m, n, alpha, beta, C, ldc);
     return cudaGetLastError();
 }
@@ -359,12 +364,18 @@ cudaError_t launch_gemm_nn(const double* A, int64_t lda, const double* B, int64_
                            int64_t ldc, int64_t K, int m, int n, double alpha, double beta,
                            cudaStream_t s) {
     if (K <= 0 || n <= 0) return cudaSuccess;
+    KL_RANGE(A, block_extent(K, m, lda), double, "gemm_nn A");
+    KL_RANGE(B, block_extent(m, n, ldb), double, "gemm_nn B");
+    KL_RANGE(C, block_extent(K, n, ldc), double, "gemm_nn C");
     dim3 grid(unsigned((K + NN_R - 1) / NN_R), unsigned((n + NN_C - 1) / NN_C));
     gemm_nn_kernel<<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, K, m, n, alpha, beta);
     return cudaGetLastError();
 }
 
 cudaError_t launch_chol_rinv(double* G, int n, double* Rinv, int* bad, cudaStream_t s) {
+    KL_RANGE(G, int64_t(n) * n, double, "chol G");
+    KL_RANGE(Rinv, int64_t(n) * n, double, "chol Rinv");
+    KL_RANGE(bad, n, int, "chol flags");
     if (n >= 1 && n <= kCholSmemN) {
         static std::once_flag once;
         static cudaError_t attr_error = cudaSuccess;

@@ -131,6 +131,25 @@ __global__ void pair_reduce_kernel(const double* __restrict__ part, int splits, 
 template <int KIND>
 cudaError_t launch_kind(const PairArgs& a, bool fp32, cudaStream_t s) {
     const int64_t per_split = (a.S + a.splits - 1) / a.splits;
+    if (fp32) {
+        KL_RANGE(a.tx32, a.T, float, "pair targets x");
+        KL_RANGE(a.ty32, a.T, float, "pair targets y");
+        KL_RANGE(a.tz32, a.T, float, "pair targets z");
+        KL_RANGE(a.sx32, a.S, float, "pair sources x");
+        KL_RANGE(a.sy32, a.S, float, "pair sources y");
+        KL_RANGE(a.sz32, a.S, float, "pair sources z");
+    } else {
+        KL_RANGE(a.tx, a.T, double, "pair targets x");
+        KL_RANGE(a.ty, a.T, double, "pair targets y");
+        KL_RANGE(a.tz, a.T, double, "pair targets z");
+        KL_RANGE(a.sx, a.S, double, "pair sources x");
+        KL_RANGE(a.sy, a.S, double, "pair sources y");
+        KL_RANGE(a.sz, a.S, double, "pair sources z");
+    }
+    KL_RANGE(a.X, block_extent(a.S, a.k, a.ldx), double, "pair X");
+    KL_RANGE(a.scratch, pair_scratch_doubles(a.T, a.k, a.splits), double, "pair partial sums");
+    KL_RANGE(a.Y, block_extent(a.T, a.k, a.ldy), double, "pair Y");
+    KL_RANGE(a.post, a.T, double, "pair post");
     dim3 grid(unsigned((a.T + kTgt - 1) / kTgt), unsigned(a.splits));
     const double l2e = 1.4426950408889634074;
     for (int c0 = 0; c0 < a.k; c0 += 32) {
@@ -155,7 +174,7 @@ cudaError_t launch_kind(const PairArgs& a, bool fp32, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     const int64_t total = a.T * a.k;
-    int g = int(std::min<int64_t>((total + 255) / 256, 152 * 32));
+    int g = int(std::min<int64_t>((total + 255) / 256, int64_t(device_sm_count()) * 32));
     pair_reduce_kernel<<<g < 1 ? 1 : g, 256, 0, s>>>(a.scratch, a.splits, a.T, a.k, a.ks.sigma2, a.post, a.Y, a.ldy);
     return cudaGetLastError();
 }
@@ -177,8 +196,11 @@ int pair_choose_splits(int64_t T, int64_t S, int sm_count) {
 
 cudaError_t launch_pair_reduce(const double* part, int splits, int64_t T, int k, double sigma2,
                                const double* post, double* Y, int64_t ldy, cudaStream_t s) {
+    KL_RANGE(part, pair_scratch_doubles(T, k, splits), double, "pair_reduce partial sums");
+    KL_RANGE(Y, block_extent(T, k, ldy), double, "pair_reduce Y");
+    KL_RANGE(post, T, double, "pair_reduce post");
     const int64_t total = T * k;
-    int g = int(std::min<int64_t>((total + 255) / 256, 152 * 32));
+    int g = int(std::min<int64_t>((total + 255) / 256, int64_t(device_sm_count()) * 32));
     pair_reduce_kernel<<<g < 1 ? 1 : g, 256, 0, s>>>(part, splits, T, k, sigma2, post, Y, ldy);
     return cudaGetLastError();
 }

@@ -17,7 +17,8 @@ constexpr int kThreads = 256;
 
 inline int grid_for(int64_t n, int per_block = kThreads) {
     int64_t g = (n + per_block - 1) / per_block;
-    if (g > 148 * 64) g = 148 * 64;  // grid-stride beyond this
+    const int64_t cap = int64_t(device_sm_count()) * 64;
+    if (g > cap) g = cap;  // grid-stride beyond this
     return int(g < 1 ? 1 : g);
 }
 
@@ -311,6 +312,18 @@ cudaError_t launch_tensor_points(int geometry, const double* geo, const double* 
                                  const double* w2, const double* w3, double jac_power, double* out_x,
                                  double* out_y, double* out_z, double* out_w, cudaStream_t s) {
     const int64_t n = int64_t(n1) * n2 * n3;
+    KL_RANGE(t1, n1, double, "tensor_points t1");
+    KL_RANGE(t2, n2, double, "tensor_points t2");
+    KL_RANGE(t3, n3, double, "tensor_points t3");
+    if (w1) {
+        KL_RANGE(w1, n1, double, "tensor_points w1");
+        KL_RANGE(w2, n2, double, "tensor_points w2");
+        KL_RANGE(w3, n3, double, "tensor_points w3");
+    }
+    KL_RANGE(out_x, n, double, "tensor_points x");
+    KL_RANGE(out_y, n, double, "tensor_points y");
+    KL_RANGE(out_z, n, double, "tensor_points z");
+    KL_RANGE(out_w, n, double, "tensor_points w");
     tensor_points_kernel<<<grid_for(n), kThreads, 0, s>>>(geometry, geo[0], geo[1], geo[2], t1, t2,
                                                           t3, n1, n2, n3, w1, w2, w3, jac_power,
                                                           out_x, out_y, out_z, out_w);
@@ -322,6 +335,11 @@ cudaError_t launch_modeprod(const double* A, int m, int n, const double* X, int6
                             const double* pre, cudaStream_t s) {
     const int64_t total = a * m * b * k;
     if (total == 0) return cudaSuccess;
+    KL_RANGE(A, int64_t(m) * n, double, "modeprod table");
+    KL_RANGE(X, block_extent(a * n * b, k, ldx), double, "modeprod X");
+    KL_RANGE(Y, block_extent(a * m * b, k, ldy), double, "modeprod Y");
+    KL_RANGE(post, a * m * b, double, "modeprod post");
+    KL_RANGE(pre, a * n * b, double, "modeprod pre");
     modeprod_kernel<<<grid_for(total), kThreads, 0, s>>>(A, m, n, X, ldx, Y, ldy, a, b, k, post, pre);
     return cudaGetLastError();
 }
@@ -331,6 +349,12 @@ cudaError_t launch_modeprod_band(const Band& A, int m, int n, const double* X, i
                                  const double* pre, cudaStream_t s) {
     const int64_t total = a * m * b * k;
     if (total == 0) return cudaSuccess;
+    KL_RANGE(A.vals, int64_t(m) * A.w, double, "band table");
+    KL_RANGE(A.start, m, int, "band starts");
+    KL_RANGE(X, block_extent(a * n * b, k, ldx), double, "band modeprod X");
+    KL_RANGE(Y, block_extent(a * m * b, k, ldy), double, "band modeprod Y");
+    KL_RANGE(post, a * m * b, double, "band modeprod post");
+    KL_RANGE(pre, a * n * b, double, "band modeprod pre");
     modeprod_band_kernel<<<grid_for(total), kThreads, 0, s>>>(A.vals, A.start, A.w, m, n, X, ldx, Y, ldy, a, b, k,
                                                               post, pre);
     return cudaGetLastError();
@@ -339,24 +363,32 @@ cudaError_t launch_modeprod_band(const Band& A, int m, int n, const double* X, i
 cudaError_t launch_rational_scales(double* w_inv, const double* scale, double* scale_out, int64_t n,
                                    cudaStream_t s) {
     if (n == 0) return cudaSuccess;
+    KL_RANGE(w_inv, n, double, "rational w_inv");
+    KL_RANGE(scale, n, double, "rational scale");
+    KL_RANGE(scale_out, n, double, "rational scale_out");
     rational_scales_kernel<<<grid_for(n), kThreads, 0, s>>>(w_inv, scale, scale_out, n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_randn(double* X, int64_t ldx, int64_t K, int n, unsigned long long seed,
                          unsigned long long offset, cudaStream_t s) {
+    KL_RANGE(X, block_extent(K, n, ldx), double, "randn X");
     randn_kernel<<<grid_for(K * n), kThreads, 0, s>>>(X, ldx, K, n, seed, offset);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scale_cols(double* X, int64_t ldx, int64_t K, int n, const double* scale,
                               int invert, cudaStream_t s) {
+    KL_RANGE(X, block_extent(K, n, ldx), double, "scale_cols X");
+    KL_RANGE(scale, n, double, "scale_cols scale");
     scale_cols_kernel<<<grid_for(K * n), kThreads, 0, s>>>(X, ldx, K, n, scale, invert);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scale_rows(double* X, int64_t ldx, int64_t K, int n, const double* scale, cudaStream_t s) {
     if (K * n == 0) return cudaSuccess;
+    KL_RANGE(X, block_extent(K, n, ldx), double, "scale_rows X");
+    KL_RANGE(scale, K, double, "scale_rows scale");
     scale_rows_kernel<<<grid_for(K * n), kThreads, 0, s>>>(X, ldx, K, n, scale);
     return cudaGetLastError();
 }
@@ -364,23 +396,31 @@ cudaError_t launch_scale_rows(double* X, int64_t ldx, int64_t K, int n, const do
 cudaError_t launch_copy_block(const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t K,
                               int n, cudaStream_t s) {
     if (K * n == 0) return cudaSuccess;
+    KL_RANGE(X, block_extent(K, n, ldx), double, "copy_block X");
+    KL_RANGE(Y, block_extent(K, n, ldy), double, "copy_block Y");
     copy_block_kernel<<<grid_for(K * n), kThreads, 0, s>>>(X, ldx, Y, ldy, K, n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_col_norms(const double* X, int64_t ldx, int64_t K, int n, double* out,
                              cudaStream_t s) {
+    KL_RANGE(X, block_extent(K, n, ldx), double, "col_norms X");
+    KL_RANGE(out, n, double, "col_norms out");
     weighted_norms_kernel<<<n, kThreads, 0, s>>>(X, ldx, K, nullptr, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_weighted_norms(const double* X, int64_t ldx, int64_t K, int n, const double* w,
                                   double* out, cudaStream_t s) {
+    KL_RANGE(X, block_extent(K, n, ldx), double, "weighted_norms X");
+    KL_RANGE(w, K, double, "weighted_norms w");
+    KL_RANGE(out, n, double, "weighted_norms out");
     weighted_norms_kernel<<<n, kThreads, 0, s>>>(X, ldx, K, w, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sign_fix(double* X, int64_t ldx, int64_t K, int n, cudaStream_t s) {
+    KL_RANGE(X, block_extent(K, n, ldx), double, "sign_fix X");
     sign_fix_kernel<<<n, kThreads, 0, s>>>(X, ldx, K);
     return cudaGetLastError();
 }
@@ -388,6 +428,10 @@ cudaError_t launch_sign_fix(double* X, int64_t ldx, int64_t K, int n, cudaStream
 cudaError_t launch_resid_norms(const double* Y, int64_t ldy, const double* AY, int64_t lday,
                                const double* theta, int64_t K, int n, double* out,
                                cudaStream_t s) {
+    KL_RANGE(Y, block_extent(K, n, ldy), double, "resid_norms Y");
+    KL_RANGE(AY, block_extent(K, n, lday), double, "resid_norms AY");
+    KL_RANGE(theta, n, double, "resid_norms theta");
+    KL_RANGE(out, n, double, "resid_norms out");
     resid_norms_kernel<<<n, kThreads, 0, s>>>(Y, ldy, AY, lday, theta, K, out);
     return cudaGetLastError();
 }

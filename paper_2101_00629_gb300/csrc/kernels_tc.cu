@@ -35,15 +35,19 @@
 //     multiplication (see gamma_scaled), and the hi/lo splits cost three
 //     (BF16) or two (TF32) instructions per value.
 //
-// Every mbarrier wait is bounded by a clock limit (about a second); on
-// timeout the kernel records an error flag, drains its own MMAs (also with a
-// bounded wait), frees its tensor memory and returns.
+// Every mbarrier wait is bounded by a clock limit (about a second, or the
+// launch's wait_limit); on timeout the kernel records an error flag. Before
+// the tensor memory is freed the issuing thread always waits (bounded by the
+// default limit) for every MMA it issued, and the loader for every copy it
+// issued, so that a short limit ends the kernel early but never frees memory
+// still in use.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <mutex>
 
 #include "kernel_eval.cuh"
@@ -73,7 +77,8 @@ struct TmemLayout {
     static constexpr int kAColBase = kSum ? kSBase + (2 * NP + 31) / 32 * 32 : 2 * kDStride;
     static_assert(kAColBase + kStages * kAColsPerStage <= kTmemCols, "tensor memory overflow");
 };
-constexpr long long kWaitLimit = 2000000000LL;  // clock cycles (~1 s)
+constexpr long long kWaitLimit = 2000000000LL;  // clock cycles (~1 s): the default pipeline limit
+                                                // and always the limit of the final drains
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -91,8 +96,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // try_wait lets the thread sleep in hardware until the phase completes (at
 // most the 1 ms hint), so waiting warps take no issue slots from producing
 // ones (polling cost 5 % of the pairwise kernel's time).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
     const uint32_t a = smem_u32(bar);
+    // suspend hint (ns): 1 ms under the default limit, about half the limit
+    // under a short one, so that the limit, not the hint, ends the wait
+    const uint32_t hint = limit >= 2000000LL ? 1000000u : uint32_t(limit / 4 + 16);
     uint32_t ready;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -110,10 +118,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
             "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(ok)
-            : "r"(a), "r"(parity), "r"(1000000u)
+            : "r"(a), "r"(parity), "r"(hint)
             : "memory");
         if (ok) return true;
-        if (clock64() - t0 > kWaitLimit) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
@@ -418,8 +426,8 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
 }
 
 // Bounded wait by every lane of a warp, then a warp-uniform verdict.
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity) {
-    const bool ok = mbar_wait(bar, parity);
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, long long limit) {
+    const bool ok = mbar_wait(bar, parity, limit);
     return __all_sync(0xffffffffu, ok);
 }
 
@@ -452,6 +460,7 @@ template <int KIND, bool TF32, int NP>
 __global__ void __launch_bounds__(kThreads, 2)
 pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
     const int64_t nunits = batch.nunits;
+    const long long wlim = batch.wait_limit > 0 ? batch.wait_limit : kWaitLimit;
     constexpr int ESIZE = TF32 ? 4 : 2;
     constexpr int KC = TF32 ? 32 : 64;                  // sources per chunk (32 TMEM columns)
     constexpr int SW = KC / 2;                          // sources of each warpgroup
@@ -539,7 +548,7 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
             // combined operand the group's sum is the sum of its two halves.
             auto flush = [&](int g, bool last) {
                 const uint32_t gg = gbase + uint32_t(g);
-                const bool got = ok && warp_wait(&dfull_bar[gg & 1], uint32_t((gg >> 1) & 1));
+                const bool got = ok && warp_wait(&dfull_bar[gg & 1], uint32_t((gg >> 1) & 1), wlim);
                 if (!got) ok = false;
                 tc_fence_after();
                 const uint32_t dcol = uint32_t((gg & 1) * kDStride);
@@ -608,8 +617,8 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                 if (!ok) break;
                 const uint32_t jg = jbase + uint32_t(jl);
                 const int ss = int(jg % SSTAGES), s = int(jg % kStages);
-                if (!warp_wait(&loaded_bar[ss], uint32_t((jg / SSTAGES) & 1))) { ok = false; break; }
-                if (jg >= kStages && !warp_wait(&tfree_bar[s], uint32_t(((jg / kStages) - 1) & 1))) { ok = false; break; }
+                if (!warp_wait(&loaded_bar[ss], uint32_t((jg / SSTAGES) & 1), wlim)) { ok = false; break; }
+                if (jg >= kStages && !warp_wait(&tfree_bar[s], uint32_t(((jg / kStages) - 1) & 1), wlim)) { ok = false; break; }
                 const float* cx = reinterpret_cast<const float*>(smem + ss * STAGE_BYTES + 2 * IMG) + wg * SW;
                 const uint32_t acol = uint32_t(kAColBase + s * kAColsPerStage);
 #pragma unroll
@@ -664,8 +673,8 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                     const uint32_t gg = gbase + uint32_t(jl / kGroup);
                     const bool first = (jl % kGroup) == 0;
                     const uint32_t d_tmem = tmem + uint32_t((gg & 1) * kDStride);
-                    if (first && gg >= 2 && !mbar_wait(&dfree_bar[gg & 1], uint32_t(((gg >> 1) - 1) & 1))) { ok = false; break; }
-                    if (!mbar_wait(&full_bar[s], uint32_t((jg / kStages) & 1))) { ok = false; break; }
+                    if (first && gg >= 2 && !mbar_wait(&dfree_bar[gg & 1], uint32_t(((gg >> 1) - 1) & 1), wlim)) { ok = false; break; }
+                    if (!mbar_wait(&full_bar[s], uint32_t((jg / kStages) & 1), wlim)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t st = smem_u32(smem + ss * STAGE_BYTES);
                     const uint32_t acol = tmem + uint32_t(kAColBase + s * kAColsPerStage);
@@ -695,11 +704,12 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                 jbase += un.nloc;
                 gbase += (un.nloc + kGroup - 1) / kGroup;
             }
-            if (!ok) {
-                atomicExch(err, 1);
-                mma_commit(&drain_bar);
-                mbar_wait(&drain_bar, 0);  // bounded: MMAs already issued finish
-            }
+            if (!ok) atomicExch(err, 1);
+            // every MMA issued here completes before the tensor memory is
+            // freed, also when the producers gave up first (bounded by the
+            // default limit whatever the pipeline limit is)
+            mma_commit(&drain_bar);
+            mbar_wait(&drain_bar, 0, kWaitLimit);
         }
         __syncwarp();
     } else {
@@ -715,7 +725,7 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                     const int64_t jg = jbase + jl;
                     const int ss = int(jg % SSTAGES);
                     const int64_t use = jg / SSTAGES;
-                    if (use > 0 && !mbar_wait(&sempty_bar[ss], uint32_t((use - 1) & 1))) { ok = false; break; }
+                    if (use > 0 && !mbar_wait(&sempty_bar[ss], uint32_t((use - 1) & 1), wlim)) { ok = false; break; }
                     issued = jg + 1;
                     uint8_t* st = smem + ss * STAGE_BYTES;
                     const int64_t ch = un.c0 + jl;
@@ -729,7 +739,7 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
             // last use of each stage (already complete unless an error cut
             // the pipeline short; bounded in any case)
             for (int64_t jg = issued - 1; jg >= 0 && jg >= issued - SSTAGES; --jg)
-                mbar_wait(&loaded_bar[jg % SSTAGES], uint32_t((jg / SSTAGES) & 1));
+                mbar_wait(&loaded_bar[jg % SSTAGES], uint32_t((jg / SSTAGES) & 1), kWaitLimit);
         }
         __syncwarp();
     }
@@ -850,10 +860,16 @@ TcPlan plan(int64_t T, int64_t S, int k, int sm_count, bool tf32) {
 }  // namespace
 
 int64_t tc_scratch_doubles(int64_t T, int64_t S, int k, int sm_count) {
-    const TcPlan pb = plan(T, S, k, sm_count, false), pt = plan(T, S, k, sm_count, true);
-    const int64_t b = pb.img_doubles + pb.src_doubles + pb.part_doubles;
-    const int64_t t = pt.img_doubles + pt.src_doubles + pt.part_doubles;
-    return std::max(b, t);
+    // every block width up to k: a narrower block may take more source
+    // splits (the partial sums are capped at 8M doubles per split count, not
+    // per width), so the largest need is not always at k itself
+    int64_t need = 0;
+    for (int kk = 1; kk <= k; ++kk) {
+        const TcPlan pb = plan(T, S, kk, sm_count, false), pt = plan(T, S, kk, sm_count, true);
+        need = std::max({need, pb.img_doubles + pb.src_doubles + pb.part_doubles,
+                         pt.img_doubles + pt.src_doubles + pt.part_doubles});
+    }
+    return need;
 }
 
 cudaError_t tc_prepare(const TcArgs& a, cudaStream_t s, TcInstance* out, int* n, int* np, int* launched) {
@@ -863,6 +879,11 @@ cudaError_t tc_prepare(const TcArgs& a, cudaStream_t s, TcInstance* out, int* n,
     if (p.nblk > 4) return cudaErrorInvalidValue;
     float2* part = reinterpret_cast<float2*>(a.scratch + p.img_doubles + p.src_doubles);
     const float cscale = coord_scale(a.ks);
+    KL_RANGE(a.X, block_extent(a.S, a.k, a.ldx), double, "tc convert X");
+    KL_RANGE(a.sx, a.S, float, "tc convert sources x");
+    KL_RANGE(a.sy, a.S, float, "tc convert sources y");
+    KL_RANGE(a.sz, a.S, float, "tc convert sources z");
+    KL_RANGE(a.scratch, p.img_doubles + p.src_doubles + p.part_doubles, double, "tc scratch");
     // every column block uses the image layout of the widest one (the last
     // block's missing columns are zero), so that they share one launch
     *np = p.np_max;
@@ -870,7 +891,7 @@ cudaError_t tc_prepare(const TcArgs& a, cudaStream_t s, TcInstance* out, int* n,
         const int c0 = 64 * blk, kc = std::min(64, a.k - c0);
         uint8_t* img = reinterpret_cast<uint8_t*>(a.scratch + blk * p.img_blk_doubles);
         const int64_t total = p.nchunks * p.kchunk * p.np_max;
-        const int g = int(std::min<int64_t>((total + 255) / 256, 152 * 64));
+        const int g = int(std::min<int64_t>((total + 255) / 256, int64_t(a.sm_count) * 64));
         tc_convert_kernel<<<g, 256, 0, s>>>(a.X, a.ldx, a.S, c0, kc, p.np_max, p.kchunk, a.tf32, cscale, a.sx,
                                             a.sy, a.sz, img, p.nchunks);
         ++*launched;
@@ -907,14 +928,40 @@ cudaError_t tc_launch_batch(TcBatch& b, bool tf32, int np, int sm_count, int* er
     }
     b.nunits = u;
     if (u == 0) return cudaSuccess;
+#ifdef KL_CHECK_BOUNDS
+    {
+        const int esize = tf32 ? 4 : 2, kchunk = tf32 ? 32 : 64;
+        const int64_t stage_bytes = 2 * int64_t(np) * kchunk * esize + 12 * int64_t(kchunk);
+        for (int i = 0; i < b.ninst; ++i) {
+            const TcInstance& I = b.inst[i];
+            KL_RANGE(I.tx, I.T, float, "tc targets x");
+            KL_RANGE(I.ty, I.T, float, "tc targets y");
+            KL_RANGE(I.tz, I.T, float, "tc targets z");
+            KL_RANGE(I.img, I.nchunks * stage_bytes, uint8_t, "tc chunk records");
+            // partial sums of the instance's columns c0 .. c0 + kc - 1 of every split
+            KL_RANGE(I.part, (int64_t(I.splits - 1) * I.k_total + I.c0 + I.kc) * I.T, float2, "tc partial sums");
+            if (int64_t(I.splits - 1) * I.cps >= I.nchunks || int64_t(I.splits) * I.cps < I.nchunks ||
+                I.c0 + I.kc > I.k_total || I.kc > np) {
+                std::fprintf(stderr, "kl bounds check: tc instance %d: splits %d x %d chunks against %lld, "
+                             "columns %d + %d of %d, N %d\n", i, I.splits, I.cps, (long long)I.nchunks, I.c0, I.kc,
+                             I.k_total, np);
+                return cudaErrorInvalidValue;
+            }
+        }
+        KL_RANGE(err, 1, int, "tc error word");
+    }
+#endif
     return tf32 ? launch_batch_prec<true>(b, np, sm_count, err, s) : launch_batch_prec<false>(b, np, sm_count, err, s);
 }
 
 cudaError_t tc_finish(const TcArgs& a, cudaStream_t s, int* launched) {
     const TcPlan p = plan(a.T, a.S, a.k, a.sm_count, a.tf32);
     const float2* part = reinterpret_cast<const float2*>(a.scratch + p.img_doubles + p.src_doubles);
+    KL_RANGE(part, p.part_doubles, float2, "tc_reduce partial sums");
+    KL_RANGE(a.Y, block_extent(a.T, a.k, a.ldy), double, "tc_reduce Y");
+    KL_RANGE(a.post, a.T, double, "tc_reduce post");
     const int64_t total = a.T * a.k;
-    const int g = int(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 8)));
+    const int g = int(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, int64_t(a.sm_count) * 8)));
     tc_reduce_kernel<<<g, 256, 0, s>>>(part, p.splits, a.T, a.k, a.ks.sigma2, a.post, a.Y, a.ldy);
     ++*launched;
     return cudaGetLastError();
@@ -923,6 +970,7 @@ cudaError_t tc_finish(const TcArgs& a, cudaStream_t s, int* launched) {
 cudaError_t launch_pair_tc(const TcArgs& a, cudaStream_t s, int* launched) {
     *launched = 0;
     TcBatch b;
+    b.wait_limit = a.wait_limit;
     int np = 16;
     cudaError_t e = tc_prepare(a, s, b.inst, &b.ninst, &np, launched);
     if (e != cudaSuccess) return e;

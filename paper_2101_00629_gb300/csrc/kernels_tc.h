@@ -25,6 +25,7 @@ struct TcArgs {
     int64_t scratch_len;  // doubles
     int sm_count;
     int* err;  // device word set when a bounded wait inside the kernel gives up
+    long long wait_limit;  // clock cycles per pipeline wait (0: default, about a second)
 };
 
 // One pairwise product inside a persistent launch: its target points, the
@@ -47,6 +48,7 @@ struct TcBatch {
     TcInstance inst[kTcMaxBatch];
     int ninst;
     int64_t nunits;
+    long long wait_limit;  // clock cycles of each pipeline wait (0: about a second)
 };
 
 // Phase 1 of a pairwise product: conversion kernels on stream s and the
@@ -58,7 +60,8 @@ cudaError_t tc_prepare(const TcArgs& a, cudaStream_t s, TcInstance* out, int* n,
 cudaError_t tc_launch_batch(TcBatch& b, bool tf32, int np, int sm_count, int* err, cudaStream_t s);
 // Phase 3: reduction of the partial sums into Y on stream s.
 cudaError_t tc_finish(const TcArgs& a, cudaStream_t s, int* launched);
-// Scratch needed by launch_pair_tc for T targets and k vectors (doubles).
+// Scratch needed by launch_pair_tc for T targets and any block of at most k
+// vectors (doubles).
 int64_t tc_scratch_doubles(int64_t T, int64_t S, int k, int sm_count);
 // Enqueues the conversion, the tcgen05 kernel and the split reduction.
 // *launched receives the number of kernels launched. A bounded wait that gives

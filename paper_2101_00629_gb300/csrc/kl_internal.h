@@ -73,6 +73,40 @@ inline bool galerkin_form(int method) { return method == KL_GALERKIN_IBQ || meth
 std::string setup_direction(Dir1D& d, bool present, int nel, int p, int interp_cont,
                             int arc, bool need_galerkin, bool need_collocation);
 
+// Bounds-checking build: every launcher checks, before it launches, that each
+// device range its kernel reads or writes lies inside one live allocation
+// (bounds.cpp). KL_RANGE(p, count, type, what) checks count elements of type
+// from p (skipped for NULL p or count <= 0) and returns cudaErrorInvalidValue
+// from the launcher on failure; it compiles to nothing in the regular build.
+#ifdef KL_CHECK_BOUNDS
+cudaError_t check_range(const void* p, int64_t bytes, const char* what);
+#define KL_RANGE(p, count, type, what)                                                              \
+    do {                                                                                             \
+        if ((p) != nullptr && int64_t(count) > 0) {                                                  \
+            const cudaError_t kl_range_e = ::kl::check_range((p), int64_t(count) * int64_t(sizeof(type)), (what)); \
+            if (kl_range_e != cudaSuccess) return kl_range_e;                                        \
+        }                                                                                            \
+    } while (0)
+#else
+#define KL_RANGE(p, count, type, what) \
+    do {                               \
+    } while (0)
+#endif
+// Extent (elements) of a column-major block of `rows` x `cols` with leading
+// dimension ld: the last column's last row + 1.
+inline int64_t block_extent(int64_t rows, int64_t cols, int64_t ld) {
+    return (rows <= 0 || cols <= 0) ? 0 : (cols - 1) * ld + rows;
+}
+
+// cudaMalloc of the library's device memory, with the allocation-failure
+// injection of kl_debug_set (KL_DEBUG_FAIL_ALLOC) in front of it.
+cudaError_t device_alloc(void** p, size_t bytes);
+
+// Streaming multiprocessors of the current device, cached per device; 152
+// (GB300) when no device is visible (host-only estimates). Grid sizes and the
+// split heuristics of the launchers scale with it.
+int device_sm_count();
+
 // ---------------------------------------------------------------------------
 // Device-side launchers (defined in the .cu files). All take the stream.
 // ---------------------------------------------------------------------------

@@ -70,7 +70,9 @@ extern "C" int kl_pairwise_noalloc(int kernel, double sigma, double L, const dou
     if (!tgt || !src || !X || !Y) return fail(nullptr, KL_ERR_ARG, "pointers must not be NULL");
     if (T < 1 || S < 1 || k < 1 || k > 256) return fail(nullptr, KL_ERR_ARG, "need T, S >= 1 and 1 <= k <= 256");
     if (ldx < S || ldy < T) return fail(nullptr, KL_ERR_ARG, "leading dimensions too small");
-    if (int64_t(k) * T > kNoallocScratch)
+    // T is compared against the quotient so that k * T is never formed for
+    // a T that would overflow it
+    if (T > kNoallocScratch / k)
         return fail(nullptr, KL_ERR_ARG, "k * T exceeds the static scratch of 2^21 doubles (16 MiB)");
     double* scratch = nullptr;
     int sms = 0;

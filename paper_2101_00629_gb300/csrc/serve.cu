@@ -139,6 +139,7 @@ void Batcher::loop() {
             }
             TcBatch b;
             b.ninst = 0;
+            b.wait_limit = 0;
             ErrTargets et;
             et.n = 0;
             cudaError_t err = cudaSuccess;
@@ -148,6 +149,10 @@ void Batcher::loop() {
                 et.dst[et.n++] = jb->err;
             }
             if (err == cudaSuccess) err = tc_launch_batch(b, grp[0]->tf32, grp[0]->np, sm_count_, d_err_, stream_);
+#ifdef KL_CHECK_BOUNDS
+            for (int q = 0; q < et.n && err == cudaSuccess; ++q)
+                err = check_range(et.dst[q], sizeof(int), "batch error target");
+#endif
             if (err == cudaSuccess) {
                 forward_error_kernel<<<1, 32, 0, stream_>>>(d_err_, et);
                 err = cudaGetLastError();

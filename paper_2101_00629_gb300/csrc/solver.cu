@@ -116,6 +116,11 @@ int orthonormalize(Ctx& c, const double* V, int nv, double* W, int bw) {
         KL_TRY(sync_copy(c, norms.data(), c.w.norms, 2 * bw * sizeof(double)));
         bool any = false;
         for (int j = 0; j < bw; ++j) {
+            // a NaN or Inf in a new block (the operator produced it, or the
+            // start block carried it) is an error, not a collapsed column to
+            // replace: replacing it would hide the fault
+            if (!std::isfinite(norms[j]))
+                return fail(c.h, KL_ERR_NUMERIC, "NaN or Inf in a block of the Krylov basis");
             const double before = norms[j], after = norms[bw + j];
             bad[j] = !(after > 1e-10 * before) || !(after > 1e-290) || !std::isfinite(after);
             any |= bad[j] != 0;
@@ -167,7 +172,7 @@ int rayleigh_ritz(Ctx& c, const double* V, const double* AV, int nv, double* max
         c.schur_ok = status == 0;
         if (status == 2) status = 0;  // complex pairs: eigenvectors valid, Schur order not
     }
-    if (status != 0 && fp32) {
+    if (status != 0 && status != 3 && fp32) {
         // the FP32 problem did not converge (its shorter precision can stall
         // on tight clusters): solve the same projected matrix in FP64
         return rayleigh_ritz(c, V, AV, nv, max_imag, false);
@@ -184,6 +189,7 @@ int rayleigh_ritz(Ctx& c, const double* V, const double* AV, int nv, double* max
                 }
             }
         }
+        if (status == 3) return fail(c.h, KL_ERR_CUDA, "small eigensolver: index out of range (bounds check)");
         return fail(c.h, KL_ERR_NUMERIC, "small eigensolver did not converge");
     }
     return KL_OK;
@@ -220,9 +226,29 @@ int64_t eig_workspace_doubles(int64_t N, int mcap) {
 
 using namespace kl;
 
+namespace {
+int eigs_impl(kl_solver* h, int M, double tol, double* lambda, double* Vout, int64_t ldv, int v_on_device,
+              double* resid, kl_solve_info* info);
+}  // namespace
+
+// A bounded wait that gave up inside a tensor-core kernel leaves its products
+// incomplete; the solve may then fail later for that reason (breakdown, NaN,
+// no convergence). The recorded timeout is the cause reported.
 extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* Vout, int64_t ldv,
                        int v_on_device, double* resid, kl_solve_info* info) {
     if (!h) return KL_ERR_ARG;
+    const int rc = eigs_impl(h, M, tol, lambda, Vout, ldv, v_on_device, resid, info);
+    if (rc != KL_OK && rc != KL_WARN_COMPLEX && rc != KL_ERR_CUDA && rc != KL_ERR_TIMEOUT && rc != KL_ERR_ARG) {
+        const std::string why = h->err;
+        if (check_device_error(h) == KL_ERR_TIMEOUT) return KL_ERR_TIMEOUT;
+        h->err = why;
+    }
+    return rc;
+}
+
+namespace {
+int eigs_impl(kl_solver* h, int M, double tol, double* lambda, double* Vout, int64_t ldv, int v_on_device,
+              double* resid, kl_solve_info* info) {
     const auto t_start = std::chrono::steady_clock::now();
     if (!lambda) return fail(h, KL_ERR_ARG, "lambda must not be NULL");
     if (M < 1 || M > 512 || M > h->N) return fail(h, KL_ERR_ARG, "M must be in 1..min(N, 512)");
@@ -270,7 +296,7 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
         cudaStreamSynchronize(h->stream);
         if (h->eig_ws) cudaFree(h->eig_ws);
         h->eig_ws = nullptr;
-        cudaError_t e = cudaMalloc(&h->eig_ws, size_t(need) * sizeof(double));
+        cudaError_t e = device_alloc(&h->eig_ws, size_t(need) * sizeof(double));
         if (e != cudaSuccess) {
             h->eig_cap_bytes = 0;
             return cuda_fail(h, e, "eigensolver workspace");
@@ -310,6 +336,13 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
     int nv = b, na = 0;
     if (int rc = ck(c, launch_randn(V, N, N, b, h->prm.seed, 0, h->stream), "randn"); rc != KL_OK) return rc;
     c.rng_offset = uint64_t(N) * b;
+    if (h->nan_start) {
+        // failure injection (kl_debug_set): one NaN in the start block
+        const double nan = std::nan("");
+        cudaError_t e = cudaMemcpyAsync(V, &nan, sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "NaN injection");
+    }
     if (int rc = orthonormalize(c, V, 0, V, b); rc != KL_OK) return rc;
 
     int restarts = 0, nconv = 0;
@@ -483,10 +516,13 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
     // ---- eigenvectors: back-transform, normalise, sign ----
     if (Vout) {
         double* Vd = AV;  // N x M scratch
+        // the back-transform's mode products keep two N x M intermediates in
+        // the operator workspaces: size them for M vectors (an FP64 solve has
+        // only applied blocks of b < M vectors so far)
+        if (int rc = ensure_workspace(h, M); rc != KL_OK) return rc;
         if (int rc = back_transform(h, Y, N, Vd, N, M); rc != KL_OK) return rc;
         if (!c.sym) {
             // unit L2 norm of the field sum_j v_j R_j under the Gauss rule
-            if (int rc = ensure_workspace(h, M); rc != KL_OK) return rc;
             if (int rc = field_at_quadrature(h, Vd, N, h->ws[0], M); rc != KL_OK) return rc;
             if (int rc = ck(c, launch_weighted_norms(h->ws[0], h->S, h->S, M, h->src_scale, c.w.norms, h->stream), "wnorm"); rc != KL_OK) return rc;
             if (int rc = ck(c, launch_scale_cols(Vd, N, N, M, c.w.norms, 1, h->stream), "scale"); rc != KL_OK) return rc;
@@ -521,3 +557,4 @@ extern "C" int kl_eigs(kl_solver* h, int M, double tol, double* lambda, double* 
     }
     return KL_OK;
 }
+}  // namespace

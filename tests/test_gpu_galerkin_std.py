@@ -1,12 +1,16 @@
 """GPU parity of the standard Gauss-Legendre Galerkin method (KL_GALERKIN_STD,
 Sec. 3.1: the trial space B_i / sqrt(det DF) with both integrals by the
 Gauss-Legendre rule of (p+1)^3 points per element) against the dense FP64
-oracle of the same rule. Tolerances as for the IBQ-Galerkin parity tests."""
+oracle of the same rule. Tolerances as for the IBQ-Galerkin parity tests,
+entry by entry: A = N^T W Gamma W N has no sign changes in its factors (the
+trial functions B / sqrt(det DF), the weights and the kernel are
+non-negative), so |A| |X| bounds each entry's rounding error."""
 import functools
 
 import numpy as np
 import pytest
 
+from _entrywise import assert_entrywise, bound, dense_abs
 from kl_inputs import PARITY_CASES, random_block
 from oracle import standard
 from oracle.problem import Problem
@@ -36,7 +40,7 @@ def _oracle(case):
     prob = Problem(s["geometry"], s["p"], s["elems"], s["kernel"], s["sigma"], s["L"])
     A, Z = standard.matrices(prob, prob.p + 1)
     Ap, _ = standard.standard_form(prob)
-    return prob, A, Z, Ap
+    return prob, A, Z, Ap, dense_abs(A, Z)
 
 
 def _create(kl, case, precision, **kw):
@@ -60,20 +64,24 @@ def _nw(Y, ref):
     return np.linalg.norm(Y - ref) / np.linalg.norm(ref)
 
 
+def _check(Y, ref, absop, X, tol, label):
+    r = assert_entrywise(Y, ref, bound(absop, X), tol, label)
+    print(f"{label}: worst entry {r:.2e} of the bound, normwise {_nw(Y, ref):.2e}")
+
+
 @pytest.mark.parametrize("case", CASES)
 def test_std_apply_fp64(kl, case):
-    prob, A, Z, Ap = _oracle(case)
+    prob, A, Z, Ap, sc = _oracle(case)
     h = _create(kl, case, "fp64")
     try:
         N, S, T = kl.kl_dims(h)
         assert (N, S) == standard.dims(prob)
         assert T == S  # the Gauss points are sources and targets
         X = random_block(N, 5, seed=21)
-        err = _nw(_apply(kl, kl.kl_apply_A, h, X), (A @ X.T).T)
-        print(f"{case} std apply_A fp64 {err:.2e}")
-        assert err < APPLY_TOL["fp64"]
-        assert _nw(_apply(kl, kl.kl_apply_Zinv, h, X), np.linalg.solve(Z, X.T).T) < 1e-12
-        assert _nw(_apply(kl, kl.kl_apply_Aprime, h, X), (Ap @ X.T).T) < 1e-12
+        _check(_apply(kl, kl.kl_apply_A, h, X), (A @ X.T).T, sc["A"], X, APPLY_TOL["fp64"], f"{case} std A")
+        _check(_apply(kl, kl.kl_apply_Zinv, h, X), np.linalg.solve(Z, X.T).T, sc["Zinv"], X, 1e-12,
+               f"{case} std Zinv")
+        _check(_apply(kl, kl.kl_apply_Aprime, h, X), (Ap @ X.T).T, sc["Aprime"], X, 1e-12, f"{case} std A'")
     finally:
         kl.kl_destroy(h)
 
@@ -81,14 +89,13 @@ def test_std_apply_fp64(kl, case):
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "tf32"])
 @pytest.mark.parametrize("case", CASES)
 def test_std_apply_mixed(kl, case, precision):
-    prob, A, Z, Ap = _oracle(case)
+    prob, A, Z, Ap, sc = _oracle(case)
     h = _create(kl, case, precision)
     try:
         N = kl.kl_dims(h)[0]
         X = random_block(N, 8, seed=22)
-        err = _nw(_apply(kl, kl.kl_apply_A, h, X), (A @ X.T).T)
-        print(f"{case} std apply_A {precision} {err:.2e}")
-        assert err < APPLY_TOL[precision]
+        _check(_apply(kl, kl.kl_apply_A, h, X), (A @ X.T).T, sc["A"], X, APPLY_TOL[precision],
+               f"{case} std A {precision}")
     finally:
         kl.kl_destroy(h)
 
@@ -97,7 +104,7 @@ def test_std_apply_mixed(kl, case, precision):
 @pytest.mark.parametrize("case", CASES)
 def test_std_eigenpairs(kl, case, precision):
     import torch
-    prob, A, Z, Ap = _oracle(case)
+    prob, A, Z, Ap, _ = _oracle(case)
     M = 8
     lam_ref, V_ref, _ = standard.solve(prob, M)
     h = _create(kl, case, precision)

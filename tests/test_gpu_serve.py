@@ -20,7 +20,6 @@ MIX = [
     ("cube_p2_e5x4x4_exp", "galerkin"),
     ("cube_p2_e3x4x5_gauss", "collocation"),
 ]
-MIXED_TOL = 1e-5  # eigenvalue relative error allowed for the mixed precisions
 OK = (0, 1)  # KL_OK, KL_WARN_COMPLEX
 
 
@@ -87,7 +86,10 @@ def test_each_result_same_alone_and_in_the_mix(kl):
         worst = max(worst, err)
         print(f"{c} {m}: mix vs alone {err:.2e}, latency {results[i]['latency_ms']:.1f} ms, "
               f"applies {results[i]['applies']}")
-        assert err <= MIXED_TOL
+        # every work unit of a batched launch runs its sources in the same
+        # order as alone and the splits are reduced in a fixed order: the
+        # results are bitwise identical
+        assert np.array_equal(lams[i], alone[i][1]), (c, m, lams[i] - alone[i][1])
     print("stats", stats, "worst", worst)
     # the products of concurrent solves shared launches
     assert stats["max_concurrent"] >= 2
