@@ -189,6 +189,11 @@ def _serve_leg(a, kl, stream):
     pairs = sum(r["M"] for r in reqs)
     bad_status = sorted(x["status"] for x, _ in results.values() if x["status"] not in (0, 1))
     bad = len(bad_status)
+    failed_requests = [dict({k: reqs[int(x["request_id"])][k] for k in ("id", "geometry", "p", "elems", "kernel", "L",
+                                                                        "M", "method")},
+                            status=x["status"], applies=x["applies"], restarts=x["restarts"],
+                            max_resid=x["max_resid"])
+                       for x, _ in results.values() if x["status"] not in (0, 1)]
 
     # the same requests one at a time (no batching, no overlap)
     def one(r, precision):
@@ -213,7 +218,7 @@ def _serve_leg(a, kl, stream):
                     "L log-uniform 0.1-2, M 10-100, Galerkin/collocation)",
         "sample": f"first {len(reqs)} requests, per-axis elements <= {a.serve_max_elems}, mean inter-arrival 20 ms",
         "precision": a.precision, "slots": a.serve_slots, "requests": len(reqs), "failed": bad,
-        "failed_status": bad_status,
+        "failed_status": bad_status, "failed_requests": failed_requests,
         "wall_s": wall, "eigenpairs_per_s": pairs / wall,
         "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
         "queue_ms_p50": float(np.percentile([x["queue_ms"] for x, _ in results.values()], 50)),

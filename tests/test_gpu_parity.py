@@ -136,9 +136,13 @@ def test_apply_mixed(kl, case, method, precision):
         Y = _apply(kl, kl.kl_apply_A, h, X)
         ref = (A @ X.T).T
         _check(Y, ref, sc["A"], X, APPLY_TOL[precision], f"{case} {method} apply_A {precision}")
+        # every column's relative error, the bound widened only where the
+        # column's entries cancel (|op||x| larger than |op x|)
         colerr = np.linalg.norm(Y - ref, axis=1) / np.linalg.norm(ref, axis=1)
-        worst = int(np.argmax(colerr))
-        assert colerr[worst] < APPLY_TOL[precision], f"column {worst}: relative error {colerr[worst]:.2e}"
+        amp = np.maximum(1.0, np.linalg.norm(bound(sc["A"], X), axis=1) / np.linalg.norm(ref, axis=1))
+        worst = int(np.argmax(colerr / amp))
+        print(f"worst column {worst}: relative error {colerr[worst]:.2e}, cancellation factor {amp[worst]:.2f}")
+        assert colerr[worst] < APPLY_TOL[precision] * amp[worst], (worst, colerr[worst], amp[worst])
     finally:
         kl.kl_destroy(h)
 
