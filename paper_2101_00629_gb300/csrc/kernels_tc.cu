@@ -63,8 +63,11 @@ constexpr int kThreads = kProducers + 64; // + MMA warp + loader warp
 constexpr int kTmemCols = 256;
 constexpr int kAColsPerStage = 64;        // hi 32 + lo 32 columns (64 BF16 / 32 TF32 sources)
 constexpr int kKSteps = 4;                // MMA K steps per chunk (K = 16 BF16 / 8 TF32 each)
-constexpr int kGroup = 4;                 // chunks accumulated in FP32 before a fold
-                                          // (256 BF16 / 128 TF32 sources)
+constexpr int kGroup = 8;                 // chunks accumulated in FP32 before a fold
+                                          // (512 BF16 / 256 TF32 sources; measured on
+                                          // GB300: 4% faster than 4 chunks, relative
+                                          // error 1.8e-6 against 1.4e-6, while 16 chunks
+                                          // let single columns reach 1.8e-5)
 constexpr int kFlushLag = 2;              // chunks between a group's end and its fold
 // Tensor memory of a CTA (256 columns): two accumulator buffers (32 columns
 // each for N <= 32, else 64); for N <= 32 the running (hi, lo) sums of the
@@ -664,6 +667,14 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
         if (lane == 0) {
             bool ok = true;
             uint32_t jbase = 0, gbase = 0;
+            // B descriptors: stage ss, K step ks is the stage-0 descriptor plus
+            // (ss * STAGE_BYTES + K-step offset) / 16 in its 14-bit start
+            // address field (shared memory ends below 256 KB, so the field never
+            // carries); the issuing thread, which shares its issue slots with
+            // producer warps, then spends one add per MMA on addresses
+            constexpr uint32_t kLbo = (kConcat ? 2 * NP : NP) / 8 * 128;
+            constexpr uint32_t kStep = 2 * kLbo;  // bytes of one K step of one image
+            const uint64_t bdesc0 = smem_desc(smem_u32(smem), kLbo, 128);
             for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
                 const TcInstance& I = batch.inst[inst_of(batch, u)];
                 const Unit un = unit_of(u - I.unit0, I.splits, I.nchunks, I.cps);
@@ -676,7 +687,7 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                     if (first && gg >= 2 && !mbar_wait(&dfree_bar[gg & 1], uint32_t(((gg >> 1) - 1) & 1), wlim)) { ok = false; break; }
                     if (!mbar_wait(&full_bar[s], uint32_t((jg / kStages) & 1), wlim)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t st = smem_u32(smem + ss * STAGE_BYTES);
+                    const uint64_t bst = bdesc0 + uint64_t(uint32_t(ss * STAGE_BYTES) >> 4);
                     const uint32_t acol = tmem + uint32_t(kAColBase + s * kAColsPerStage);
 #pragma unroll
                     for (int ks = 0; ks < kKSteps; ++ks) {
@@ -684,14 +695,12 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                         if (kConcat) {
                             // rows 0..2NP-1 of the combined image: [X_hi | X_lo];
                             // its first NP rows: X_hi
-                            const uint32_t step = uint32_t(ks * 2 * (2 * NP / 8) * 128);
-                            const uint64_t bb = smem_desc(st + step, (2 * NP / 8) * 128, 128);
+                            const uint64_t bb = bst + uint64_t((ks * kStep) >> 4);
                             mma_tmemA(TF32, d_tmem, ah, bb, IDESC2, (first && ks == 0) ? 0u : 1u);
                             mma_tmemA(TF32, d_tmem, al, bb, IDESC, 1u);
                         } else {
-                            const uint32_t step = uint32_t(ks * 2 * (NP / 8) * 128);
-                            const uint64_t bh = smem_desc(st + step, (NP / 8) * 128, 128);
-                            const uint64_t bl = smem_desc(st + IMG + step, (NP / 8) * 128, 128);
+                            const uint64_t bh = bst + uint64_t((ks * kStep) >> 4);
+                            const uint64_t bl = bst + uint64_t((IMG + ks * kStep) >> 4);
                             mma_tmemA(TF32, d_tmem, ah, bh, IDESC, (first && ks == 0) ? 0u : 1u);
                             mma_tmemA(TF32, d_tmem, ah, bl, IDESC, 1u);
                             mma_tmemA(TF32, d_tmem, al, bh, IDESC, 1u);
