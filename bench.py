@@ -60,6 +60,10 @@ def _args():
     ap.add_argument("--serve-max-elems", type=int, default=8,
                     help="per-axis element cap of the serving stream sample")
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the annulus workloads (quarter annular cylinder, p = 3 Gaussian and p = 2 exponential)")
+    ap.add_argument("--configs-fp64", action="store_true",
+                    help="also solve the 64x32x16 annulus workload in FP64 (minutes of FP64 GPU time)")
     ap.add_argument("--accuracy", action="store_true",
                     help="accuracy-versus-time study instead of the benchmark: every method on a sequence of cube "
                          "meshes against the standard Gauss-Legendre Galerkin solution on the finest one")
@@ -232,62 +236,70 @@ def _serve_leg(a, kl, stream):
 
 
 # --------------------------------------------------------------------------
-# CPU oracle (cpu_baseline leg and --impl reference): the dense FP64 oracle
-# on bounded samples of the workload (smaller meshes of the same family),
-# extrapolated to the full mesh with the measured complexity exponent.
+# CPU oracle (cpu_baseline leg and --impl reference): the dense FP64 oracle,
+# timed as it stands on a bounded sample of the workload: the same cube
+# problem (p = 2, separable exponential kernel, M = 20, both methods) on a
+# coarser mesh. At the full 16^3 mesh the oracle cannot run within a
+# benchmark: its Galerkin form factors dense N~ x N~ matrices (N~ = 35937:
+# 10 GB each, about 2.5e14 flops of dense solves) and its collocation form
+# multiplies a dense 5832 x 110592 kernel matrix. So every value below is a
+# measured time of the sample, never an extrapolation; the GPU's time on the
+# same sample problem is measured beside it.
 # --------------------------------------------------------------------------
-def _oracle_sample(budget_s=25.0):
-    import numpy as np
+METRIC = "s to M K-L eigenpairs (Galerkin + collocation solve)"
+CPU_SAMPLE_ELEMS = 8
+
+
+def _oracle_sample(n=CPU_SAMPLE_ELEMS):
+    """Seconds of one dense-oracle step (both methods) on the n^3 sample."""
     from kl_inputs import WORKLOADS, problem_args
     from oracle import collocation, galerkin
     from oracle.problem import Problem
 
     w = WORKLOADS[WORKLOAD]
     args = problem_args(w)
-    full_n = args["elems"][0]
-    rows = []
-    t_total = 0.0
-    for n in (3, 4, 5, 6, 7, 8):
+    per = {}
+    for method in METHODS:
+        prob = Problem(args["geometry"], args["p"], (n, n, n), args["kernel"], args["sigma"], args["L"])
+        mod = galerkin if method == "galerkin" else collocation
         t0 = time.perf_counter()
-        for method in METHODS:
-            prob = Problem(args["geometry"], args["p"], (n, n, n), args["kernel"], args["sigma"], args["L"])
-            mod = galerkin if method == "galerkin" else collocation
-            mod.solve(prob, w["M"])
-        dt = time.perf_counter() - t0
-        t_total += dt
-        rows.append((n, dt))
-        if t_total > budget_s * 0.45:
-            break
-    (n1, t1), (n2, t2) = rows[-2], rows[-1]
-    expo = np.log(t2 / t1) / np.log(n2 / n1)
-    est = t2 * (full_n / n2) ** expo
+        mod.solve(prob, w["M"])
+        per[method] = time.perf_counter() - t0
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    sample = (f"dense FP64 oracle (Galerkin + collocation, M={w['M']}) on {rows[0][0]}^3..{n2}^3-element "
-              f"meshes of the same workload, {t_total:.1f} s of CPU work; extrapolated to {full_n}^3 with "
-              f"the measured exponent {expo:.2f} in the element count per direction")
-    return est, cores, sample, rows
+    return sum(per.values()), per, cores
+
+
+def _sample_text(n, per):
+    return (f"dense FP64 oracle (scipy eigh / QZ on assembled matrices) on the {n}^3-element mesh of the "
+            f"{WORKLOAD} problem (p = 2, separable exponential, L = 1, M = 20, both methods): measured "
+            f"{per['galerkin']:.2f} s Galerkin + {per['collocation']:.2f} s collocation; the full "
+            f"16^3 step does not fit a benchmark run (dense N~ x N~ factorisations, N~ = 35937)")
 
 
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    for _ in range(a.warmup):
-        pass  # the oracle has no warm state; warm-up steps are no-ops
-    vals = []
-    for _ in range(a.steps):
-        est, cores, sample, _ = _oracle_sample(budget_s=min(25.0, 150.0 / max(1, a.steps)))
-        vals.append(est)
     import numpy as np
+    n = 7 if a.steps > 8 else CPU_SAMPLE_ELEMS  # bounded: the whole run stays within minutes
+    for _ in range(min(a.warmup, 1)):
+        _oracle_sample(n)  # warm-up (imports, BLAS thread pools)
+    vals, pers = [], []
+    for _ in range(a.steps):
+        v, per, cores = _oracle_sample(n)
+        vals.append(v)
+        pers.append(per)
     v = float(np.median(vals))
+    per = {m: float(np.median([p[m] for p in pers])) for m in METHODS}
     line = {
         "impl": "reference",
-        "metric": "s to M K-L eigenpairs (Galerkin + collocation solve, FP64 CPU oracle)",
+        "metric": METRIC,
         "value": v, "unit": "s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "M": 20, "k": 8, "methods": list(METHODS)},
-        "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+        "config": {"workload": WORKLOAD, "M": 20, "k": 8, "methods": list(METHODS),
+                   "step": f"bounded sample: the {n}^3 mesh of the workload's problem, both methods"},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": _sample_text(n, per)},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -355,6 +367,91 @@ def _peaks():
         with open(path) as f:
             return json.load(f), "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _lam_err(lam, ref):
+    import numpy as np
+    return np.abs(lam - ref) / np.maximum(np.abs(ref), 1e-6 * abs(ref[0]))
+
+
+def _timed_solve(kl, torch, stream, h, M, tol, lam, info):
+    """One kl_eigs on the handle's stream between CUDA events (seconds)."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rc = kl.kl_eigs(h, M, tol, lam, None, 0, 0, None, info)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3, rc
+
+
+def _pair_roof(kernel, peaks):
+    """ALU roof (pairs/s) of one kernel evaluation (see the roofline block)."""
+    fp32_fma, ex2, _ = peaks
+    mufu, fp32 = ALU_OPS_PER_PAIR[kernel]
+    return min(ex2 / mufu, fp32_fma / fp32)
+
+
+# Block sizes of the annulus workloads: kl_autotune's choice on GB300 for the
+# exponential one (complete solves for k = 8, 16, 32: Galerkin 2.22 / 1.56 /
+# 1.52 s, collocation 1.25 / 0.93 / 1.08 s), the workload's k otherwise.
+CONFIG_WORKLOADS = (("annulus_p3_e32x32x16_gauss", {"galerkin": 16, "collocation": 16}),
+                    ("annulus_p2_e64x32x16_exp", {"galerkin": 32, "collocation": 16}))
+
+
+def _configs_leg(a, kl, stream, peaks):
+    """The quarter-annulus workloads: per method one untimed and one timed
+    mixed-precision solve (CUDA events), the pairwise kernel's rate during
+    the timed solve against its ALU roof, and FP64 solves of the same problem
+    stopped at the mixed solve's tolerance (the smaller workload by default;
+    both with --configs-fp64) with the eigenvalue errors of the mixed pairs
+    against them."""
+    import numpy as np
+    import torch
+    from kl_inputs import WORKLOADS, problem_args
+
+    out = {}
+    for name, ks in CONFIG_WORKLOADS:
+        w = WORKLOADS[name]
+        args = problem_args(w)
+        M = w["M"]
+        res = {}
+        for m in METHODS:
+            def mk(precision):
+                p = kl.params(geometry=args["geometry"], degree=args["p"], elems=args["elems"], kernel=args["kernel"],
+                              sigma=args["sigma"], L=args["L"], geo=args.get("geo", (1.0, 2.0, 1.0)), method=m,
+                              precision=precision, block_k=ks[m], seed=2101)
+                return kl.kl_create(p, stream)
+            h = mk(a.precision)
+            dims = kl.kl_dims(h)
+            lam = np.zeros(M)
+            info = kl.kl_solve_info()
+            _timed_solve(kl, torch, stream, h, M, 0.0, lam, info)  # untimed: graphs, workspaces
+            kl.kl_profile_enable(h, True)
+            t, rc = _timed_solve(kl, torch, stream, h, M, 0.0, lam, info)
+            prof = kl.kl_profile_read(h)
+            kl.kl_profile_enable(h, False)
+            kl.kl_destroy(h)
+            pair = prof.get("pair_tc_" + a.precision) or prof.get("pair_f32")
+            r = dict(N=dims[0], pairwise_sources=dims[1], pairwise_targets=dims[2], k=ks[m], status=rc, s=t,
+                     applies=info.applies, max_resid=info.max_resid)
+            if pair:
+                rate = pair["units"] / (pair["ms"] * 1e-3)
+                r["pairwise"] = dict(launches=pair["launches"], ms=pair["ms"], gpairs_per_s=rate / 1e9,
+                                     frac_alu_roof=rate / _pair_roof(args["kernel"], peaks),
+                                     share_of_solve=pair["ms"] * 1e-3 / t)
+            if name == CONFIG_WORKLOADS[0][0] or a.configs_fp64:
+                h64 = mk("fp64")
+                lam64 = np.zeros(M)
+                info64 = kl.kl_solve_info()
+                t64, rc64 = _timed_solve(kl, torch, stream, h64, M, 1e-6, lam64, info64)
+                kl.kl_destroy(h64)
+                err = _lam_err(lam, lam64)
+                r["fp64_matched_tol"] = dict(tol=1e-6, s=t64, status=rc64, applies=info64.applies,
+                                             speedup=t64 / t, max_lam_rel_err=float(err.max()))
+            res[m] = r
+        out[name] = dict(M=M, methods=res)
+    return out
 
 
 def run_gpu(a):
@@ -527,16 +624,18 @@ def run_gpu(a):
             lam64 = np.zeros(M)
             info64 = kl.kl_solve_info()
             kl.kl_eigs(h64, M, 0.0, lam64, None, N, 0, None, info64)  # warm-up
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            kl.kl_eigs(h64, M, 0.0, lam64, None, N, 0, None, info64)
-            e1.record(stream)
-            e1.synchronize()
-            err = np.abs(lam[m] - lam64) / np.maximum(np.abs(lam64), 1e-6 * abs(lam64[0]))
-            fp64[m] = dict(s=e0.elapsed_time(e1) / 1e3, applies=info64.applies, lam=lam64.tolist(),
-                           lam_rel_err=err.tolist(), max_lam_rel_err=float(err.max()))
+            t64, _ = _timed_solve(kl, torch, stream, h64, M, 0.0, lam64, info64)
+            err = _lam_err(lam[m], lam64)
+            # the same FP64 solve stopped at the mixed solve's residual
+            # tolerance (1e-6): the time an FP64 solve needs for the accuracy
+            # the metric asks for (lambda error <= 1e-5)
+            lam64m = np.zeros(M)
+            info64m = kl.kl_solve_info()
+            t64m, _ = _timed_solve(kl, torch, stream, h64, M, 1e-6, lam64m, info64m)
+            fp64[m] = dict(s=t64, applies=info64.applies, lam=lam64.tolist(),
+                           lam_rel_err=err.tolist(), max_lam_rel_err=float(err.max()),
+                           matched_tol=dict(tol=1e-6, s=t64m, applies=info64m.applies,
+                                            max_lam_rel_err=float(_lam_err(lam64m, lam64).max())))
             kl.kl_destroy(h64)
 
     # ---- serving: continuous batching of a seeded request stream ----
@@ -585,20 +684,46 @@ def run_gpu(a):
                               f"{fp32_fma / 1e12:.1f} T op/s / {fp32_per_pair} per pair); FP64 FMA "
                               f"{fp64_fma / 1e12:.2f} T/s",
                 "launches": st["launches"], "ms": st["ms"], "pairs": st["units"]}
+    # ---- the annulus workloads (solve times, FP64 comparison, pairwise roofline) ----
+    configs = None
+    if not a.no_configs and rank == 0 and a.workload == WORKLOAD:
+        configs = _configs_leg(a, kl, stream, (fp32_fma, ex2, fp64_fma))
+
     # ---- K-L field sampling with the computed eigenpairs (not in the step) ----
     sampling = _sampling_leg(kl, handles, streams, lam, Vd, N, M, args, fp64_fma) if rank == 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu and a.workload == WORKLOAD:
-        est, cores, sample, _ = _oracle_sample()
-        cpu = {"value": est, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample}
+        # the GPU on the same sample problem (same precision and block size as
+        # the step), second solve of each handle, CUDA events; before the
+        # oracle, whose BLAS threads would compete with the solver's host thread
+        gpu_sample = {}
+        for m in METHODS:
+            ps = kl.params(geometry=args["geometry"], degree=args["p"], elems=(CPU_SAMPLE_ELEMS,) * 3,
+                           kernel=args["kernel"], sigma=args["sigma"], L=args["L"], geo=geo, method=m,
+                           precision=a.precision, block_k=k, seed=2101)
+            hs = kl.kl_create(ps, stream)
+            lam_s = np.zeros(M)
+            for _ in range(2):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                kl.kl_eigs(hs, M, 0.0, lam_s, None, 0, 0)
+                e1.record(stream)
+                e1.synchronize()
+            gpu_sample[m] = e0.elapsed_time(e1) / 1e3
+            kl.kl_destroy(hs)
+        v, per, cores = _oracle_sample(CPU_SAMPLE_ELEMS)
+        cpu = {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
+               "sample": _sample_text(CPU_SAMPLE_ELEMS, per),
+               "gpu_same_sample_s": sum(gpu_sample.values()), "gpu_same_sample_per_method_s": gpu_sample,
+               "oracle_over_gpu_same_sample": v / sum(gpu_sample.values())}
 
     p50 = {m: float(np.percentile(solve_ms[m], 50)) for m in METHODS}
     p99 = {m: float(np.percentile(solve_ms[m], 99)) for m in METHODS}
     p50a = {m: float(np.percentile(alone_ms[m], 50)) for m in METHODS}
     p99a = {m: float(np.percentile(alone_ms[m], 99)) for m in METHODS}
     line = {
-        "metric": "s to M K-L eigenpairs (Galerkin + collocation solve, mixed precision)",
+        "metric": METRIC,
         "value": ms_step / 1e3 if world == 1 else ms_step / 1e3,
         "unit": "s",
         "n_gpus": world,
@@ -620,6 +745,9 @@ def run_gpu(a):
         "solve_ms_p50_alone": p50a, "solve_ms_p99_alone": p99a,
         "fp64_gpu": {m: {kk: v for kk, v in fp64[m].items() if kk != "lam"} for m in fp64},
         "speedup_vs_fp64": ({m: fp64[m]["s"] * 1e3 / p50a[m] for m in fp64} if fp64 else None),
+        "speedup_vs_fp64_matched_tol": ({m: fp64[m]["matched_tol"]["s"] * 1e3 / p50a[m] for m in fp64}
+                                        if fp64 else None),
+        "configs": configs,
         "lam": {m: lam[m].tolist() for m in METHODS},
         "applies": {m: infos[m].applies for m in METHODS},
         "roofline": roof,

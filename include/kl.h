@@ -151,7 +151,7 @@ typedef struct kl_params {
  * max_restarts 0, seed 2101. */
 void kl_default_params(kl_params* p);
 
-/* Sec. 3.1 / Sec. 3.2 set-up ("formation ... negligible", Sec. 3.3): knot
+/* Sec. 3.1 / Sec. 3.2 set-up (negligible cost next to the solve, Sec. 3.3): knot
  * vectors, Greville points, 1D mass / collocation / mixed mass matrices and
  * their factorisations (host, FP64), then the point tables and geometry
  * factors on the device. `stream` is a cudaStream_t (NULL: legacy default
@@ -172,7 +172,8 @@ int kl_dims(const kl_solver* h, int64_t* N, int64_t* n_src, int64_t* n_tgt);
 /* Y = A X for k vectors (1 <= k <= 256), X and Y device FP64 blocks of
  * length N (ldx, ldy >= N). A is the generalized matrix in the coefficient
  * basis: Galerkin  M^T B~^-1 J Gamma J B~^-T M  (Sec. 3.1),
- *           collocation  Gamma (J .* W .* (R X))  (Algorithm 1 steps 1-3).
+ *           collocation  Gamma (J .* W .* (R X))  (Algorithm 1 without the
+ *                        final Z^-1).
  * Arithmetic of the pairwise step per params.precision. X and Y must not
  * overlap. Errors: KL_ERR_ARG, KL_ERR_CUDA, KL_ERR_OOM. */
 int kl_apply_A(kl_solver* h, const double* X, int64_t ldx, double* Y, int64_t ldy, int k);
@@ -201,7 +202,11 @@ typedef struct kl_solve_info {
 
 /* The M largest eigenpairs (1 <= M <= N, M <= 512) of A v = lambda Z v.
  *   tol        stop when every ||A' y - theta y|| <= tol * |theta_1| (<= 0:
- *              1e-10 for KL_FP64, 1e-6 otherwise).
+ *              1e-10 for KL_FP64, 1e-6 otherwise). A reduced-precision
+ *              solve also stops when its largest wanted residual has not
+ *              decreased for 10 restarts while within 10 * tol: the rounding
+ *              of the split pairwise operands bounds how far the residuals
+ *              can fall (resid and info report the residuals reached).
  *   lambda     host array of M doubles, descending (collocation: real parts
  *              in descending order of the real part).
  *   V          N x M column-major (ldv >= N), host memory if v_on_device == 0,

@@ -9,7 +9,8 @@ the Greville abscissae x_i, and the system matrices are
 (Eq. colloc system matrices). The integral is evaluated with the tensor
 Gauss–Legendre rule with (p+1) points per direction per element used in
 Sec. 4.1, i.e. A_ij = sum_q w_q det DF(x^_q) Gamma(x_i, F(x^_q)) R_j(x^_q),
-which is Algorithm 1 steps 1–3 written as a dense matrix. The generalized
+which is the operator of Algorithm 1 (before its final Z^-1) written as a
+dense matrix. The generalized
 eigenproblem is not symmetric; it is solved with the QZ algorithm
 (scipy.linalg.eig).
 

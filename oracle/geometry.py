@@ -3,7 +3,7 @@
 Sec. 3.1 uses the geometric mapping F from the reference domain to the
 physical domain, its Jacobian determinant det DF(x^) in the trial space
 (Eq. trialspace) and J = sqrt(det DF) at the Greville points; Sec. 3.2 uses
-det DF at the quadrature points (Algorithm 1, step 2).
+det DF at the quadrature points (the weights of Algorithm 1).
 
 Two domains are provided:
 

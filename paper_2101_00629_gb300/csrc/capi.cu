@@ -80,10 +80,40 @@ ProfScope::~ProfScope() {
 
 namespace {
 
-__global__ void to_float_kernel(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
+// y = x - origin rounded to FP32. The kernels depend on coordinate
+// differences only, so the origin (the centre of the domain's bounding box)
+// changes nothing but the rounding: FP32 coordinates of half the magnitude
+// carry half the absolute error into every difference.
+__global__ void to_float_kernel(const double* __restrict__ x, float* __restrict__ y, int64_t n, double origin) {
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
          i += int64_t(gridDim.x) * blockDim.x)
-        y[i] = float(x[i]);
+        y[i] = float(x[i] - origin);
+}
+
+// Centre of the bounding box of the physical domain (per coordinate).
+void domain_centre(const kl_params& p, double c[3]) {
+    c[0] = c[1] = c[2] = 0.0;
+    if (p.geometry == KL_GEOM_QUARTER_ANNULUS) {
+        c[0] = c[1] = 0.5 * p.geo[1];
+        c[2] = 0.5 * p.geo[2];
+    } else if (p.geometry == KL_GEOM_HALF_ANNULUS) {
+        c[1] = 0.5 * p.geo[1];
+        c[2] = 0.5 * p.geo[2];
+    } else if (p.geometry == KL_GEOM_PROJECTIVE_CUBE) {
+        // a hexahedron with planar faces: the box of its eight corners
+        double lo[3] = {HUGE_VAL, HUGE_VAL, HUGE_VAL}, hi[3] = {-HUGE_VAL, -HUGE_VAL, -HUGE_VAL};
+        for (int v = 0; v < 8; ++v) {
+            const double u[3] = {double(v & 1), double((v >> 1) & 1), double((v >> 2) & 1)};
+            const double D = 1.0 + p.geo[0] * u[0] + p.geo[1] * u[1] + p.geo[2] * u[2];
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = std::min(lo[d], u[d] / D);
+                hi[d] = std::max(hi[d], u[d] / D);
+            }
+        }
+        for (int d = 0; d < 3; ++d) c[d] = 0.5 * (lo[d] + hi[d]);
+    } else {
+        for (int d = 0; d < p.dim; ++d) c[d] = 0.5;
+    }
 }
 
 template <class T>
@@ -266,7 +296,8 @@ void clear_graphs(kl_solver* h) {
 }
 
 // 1) sum factorisation to the source points, scaled by J (Galerkin) or
-//    w det DF (collocation, Algorithm 1 steps 1-2): X -> ws[0]. With
+//    w det DF (collocation: the field at the quadrature points and its
+//    weights, Algorithm 1): X -> ws[0]. With
 //    non-tensor NURBS weights R X = (B (w X)) / W, the 1 / W folded into the
 //    point scale.
 static int apply_pre(kl_solver* h, int which, const double* X, int64_t ldx, int k) {
@@ -292,7 +323,8 @@ static int apply_post(kl_solver* h, int which, double* Y, int64_t ldy, int k) {
     return KL_OK;
 }
 
-// 2) pairwise product over all (target, source) pairs (Algorithm 1 step 3):
+// 2) pairwise product over all (target, source) pairs (the kernel product of
+//    Algorithm 1):
 //    ws[0] -> ws[1]
 static int apply_pair(kl_solver* h, int precision, int k) {
     const bool gal = galerkin_form(h->prm.method);
@@ -719,9 +751,12 @@ int kl_create(const kl_params* params, void* stream, kl_solver** out) {
     h->sz32 = h->sy32 + S;
     const double* src64[6] = {h->tx, h->ty, h->tz, h->sx, h->sy, h->sz};
     float* dst32[6] = {h->tx32, h->ty32, h->tz32, h->sx32, h->sy32, h->sz32};
+    double centre[3];
+    domain_centre(p, centre);
     for (int j = 0; j < 6; ++j) {
         const int64_t n = j < 3 ? T : S;
-        to_float_kernel<<<int(std::min<int64_t>((n + 255) / 256, 4096)), 256, 0, h->stream>>>(src64[j], dst32[j], n);
+        to_float_kernel<<<int(std::min<int64_t>((n + 255) / 256, 4096)), 256, 0, h->stream>>>(src64[j], dst32[j], n,
+                                                                                                centre[j % 3]);
         ++h->launches;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(h, e, "points fp32"));

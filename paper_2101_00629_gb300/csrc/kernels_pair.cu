@@ -1,8 +1,8 @@
 // Pairwise kernel products on CUDA cores: W = Gamma(targets, sources) X.
 //
-// This is the O(N~^2) step of the IBQ-Galerkin matvec (Sec. 3.1: "the matrix
-// rows of Gamma are computed on the fly") and Algorithm 1 step 3 of the
-// collocation matvec (Sec. 3.2). Gamma is never stored: every CTA owns 128
+// This is the O(N~^2) step of the IBQ-Galerkin matvec (Sec. 3.1: the rows of
+// Gamma are evaluated when needed, never stored) and the kernel product of
+// Algorithm 1 in the collocation matvec (Sec. 3.2). Gamma is never stored: every CTA owns 128
 // target points (one per thread, coordinates in registers), streams tiles of
 // source points and their k vector values through shared memory, evaluates
 // the kernel for each (target, source) pair in registers and accumulates

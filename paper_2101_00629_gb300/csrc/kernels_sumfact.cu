@@ -1,7 +1,8 @@
 // Point tables (geometry map F and det DF) and the sum-factorisation mode
-// products of Sec. 3.1 ("matrix-vector products with Kronecker structured
-// matrices ... in linear or nearly linear time") and Algorithm 1 step 1
-// (interpolation at the quadrature points), plus small block utilities.
+// products: the Kronecker-structured factors of Sec. 3.1, applied one
+// direction at a time in (nearly) linear time, and the interpolation of the
+// trial field at the quadrature points in Algorithm 1, plus small block
+// utilities.
 //
 // Layout: a block of k vectors over a tensor grid (n1, n2, n3) is
 // column-major, point index i1 + n1 * (i2 + n2 * i3), column stride ld.

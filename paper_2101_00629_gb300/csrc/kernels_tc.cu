@@ -1,7 +1,8 @@
 // Pairwise product W = Gamma X on the tcgen05 tensor cores (sm_100 family).
 //
-// The O(N~^2) step of the IBQ-Galerkin matvec (Sec. 3.1) and Algorithm 1 step
-// 3 of the collocation matvec (Sec. 3.2), with Gamma never stored:
+// The O(N~^2) step of the IBQ-Galerkin matvec (Sec. 3.1) and the kernel
+// product of Algorithm 1 in the collocation matvec (Sec. 3.2), with Gamma
+// never stored:
 //
 //   * A CTA owns 128 target points; target t is tensor-memory lane t. Eight
 //     producer warps (two warpgroups, warp w serving lanes 32*(w%4)..) share

@@ -1,5 +1,5 @@
-// Host FP64 set-up of the 1D spline tables (Sec. 3.1, Sec. 3.2, Sec. 3.3:
-// "formation and assembly costs are negligible").
+// Host FP64 set-up of the 1D spline tables (Sec. 3.1, Sec. 3.2; Sec. 3.3
+// counts their cost as negligible next to the operator applications).
 //
 // Per parametric direction this builds, from an open uniform knot vector:
 //   Galerkin (Sec. 3.1)  the mass matrix Z_k and its Cholesky factor L_k, the

@@ -350,6 +350,17 @@ int eigs_impl(kl_solver* h, int M, double tol, double* lambda, double* Vout, int
     bool bad_num = false;
     double last_resid = HUGE_VAL;  // largest wanted relative residual of the last Rayleigh-Ritz
     double last_min_resid = HUGE_VAL;  // smallest one
+    // reduced precisions: the split (hi + lo) operands of the pairwise
+    // product round every application at about 2^-17 of each term, a noise
+    // that bounds how far residuals of the computed operator can fall (seen
+    // at 1-2e-6 of |theta_1| for narrow Gaussian kernels, L about 0.1, where
+    // few terms average the noise); a solve whose largest wanted residual
+    // has not decreased for kStallRestarts restarts while within
+    // kStallFactor * tol has reached that floor and stops there
+    constexpr int kStallRestarts = 10;
+    constexpr double kStallFactor = 10.0;
+    double best_resid = HUGE_VAL;
+    int best_restart = 0;
     // Rayleigh-Ritz on the basis, Ritz vectors Y = V S(:, :mr) in T1 and
     // A'Y = AV S(:, :mr) in T2, residual norms; sets nconv and last_resid
     auto rr_residuals = [&](bool fp32) -> int {
@@ -420,6 +431,14 @@ int eigs_impl(kl_solver* h, int M, double tol, double* lambda, double* Vout, int
         }
         if (bad_num) return fail(h, KL_ERR_NUMERIC, "NaN or Inf in the Ritz values");
         if (nconv >= M || complete) break;
+        if (prec != KL_FP64) {
+            if (last_resid < 0.97 * best_resid) {
+                best_resid = last_resid;
+                best_restart = restarts;
+            } else if (restarts - best_restart >= kStallRestarts && last_resid <= kStallFactor * tol) {
+                break;
+            }
+        }
         if (restarts >= h->prm.max_restarts) {
             status_out = KL_ERR_NOCONV;
             break;
