@@ -587,15 +587,21 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             __syncthreads();
             if (s_rot) {
                 const R cs = s_cs, sn = s_sn;
-                for (int j = u - 1 + tid; j < n; j += NT) {
+                // symmetric input: the matrix is tridiagonal (plus the
+                // bulge while it is chased), so rows and columns outside a
+                // band of half-width 3 around the diagonal hold only
+                // rounding remnants and are never read: the updates skip them
+                const int jend = sym ? min(n, u + 2) : n;
+                for (int j = u - 1 + tid; j < jend; j += NT) {
                     const R x1 = A[(u - 1) + int64_t(j) * n], x2 = A[u + int64_t(j) * n];
                     A[(u - 1) + int64_t(j) * n] = cs * x1 + sn * x2;
                     A[u + int64_t(j) * n] = -sn * x1 + cs * x2;
                 }
                 __syncthreads();
-                for (int e = tid; e < u + 1 + n; e += NT) {
-                    R* M = e <= u ? A : Z;
-                    const int i = e <= u ? e : e - u - 1;
+                const int i0 = sym ? max(0, u - 2) : 0;
+                for (int e = tid; e < u + 1 - i0 + n; e += NT) {
+                    R* M = e <= u - i0 ? A : Z;
+                    const int i = e <= u - i0 ? e + i0 : e - (u + 1 - i0);
                     const R x1 = M[i + int64_t(u - 1) * n], x2 = M[i + int64_t(u) * n];
                     M[i + int64_t(u - 1) * n] = cs * x1 + sn * x2;
                     M[i + int64_t(u) * n] = -sn * x1 + cs * x2;
@@ -631,7 +637,8 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             const R v0 = s_v[0], v1 = s_v[1], v2 = s_v[2], beta = s_beta;
             const int r0 = l + kk;
             const int c0 = l + (kk > 0 ? kk - 1 : 0);
-            for (int j = c0 + tid; j < n; j += NT) {
+            const int jend = sym ? min(n, r0 + 5) : n;
+            for (int j = c0 + tid; j < jend; j += NT) {
                 R* col = A + int64_t(j) * n + r0;
                 const R a0 = col[0], a1 = col[1], a2 = col[2];
                 const R s = beta * fma(v2, a2, fma(v1, a1, v0 * a0));
@@ -641,9 +648,10 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             }
             __syncthreads();
             const int rmax = min(l + kk + 3, u);  // last row of A touched (inclusive)
-            for (int e = tid; e < rmax + 1 + n; e += NT) {
-                R* M = e <= rmax ? A : Z;
-                const int i = e <= rmax ? e : e - rmax - 1;
+            const int i0 = sym ? max(0, r0 - 2) : 0;  // first row of A touched
+            for (int e = tid; e < rmax + 1 - i0 + n; e += NT) {
+                R* M = e <= rmax - i0 ? A : Z;
+                const int i = e <= rmax - i0 ? e + i0 : e - (rmax + 1 - i0);
                 R* row = M + i + int64_t(r0) * n;
                 const R a0 = row[0], a1 = row[n], a2 = row[2 * int64_t(n)];
                 const R s = beta * fma(a2, v2, fma(a1, v1, a0 * v0));
@@ -668,7 +676,8 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         __syncthreads();
         {
             const R v0 = s_v[0], v1 = s_v[1], beta = s_beta;
-            for (int j = u - 2 + tid; j < n; j += NT) {
+            const int jend = sym ? min(n, u + 2) : n;
+            for (int j = u - 2 + tid; j < jend; j += NT) {
                 R* col = A + int64_t(j) * n + (u - 1);
                 const R a0 = col[0], a1 = col[1];
                 const R s = beta * fma(v1, a1, v0 * a0);
@@ -676,9 +685,10 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                 col[1] = a1 - s * v1;
             }
             __syncthreads();
-            for (int e = tid; e < u + 1 + n; e += NT) {
-                R* M = e <= u ? A : Z;
-                const int i = e <= u ? e : e - u - 1;
+            const int i0 = sym ? max(0, u - 4) : 0;
+            for (int e = tid; e < u + 1 - i0 + n; e += NT) {
+                R* M = e <= u - i0 ? A : Z;
+                const int i = e <= u - i0 ? e + i0 : e - (u + 1 - i0);
                 R* row = M + i + int64_t(u - 1) * n;
                 const R a0 = row[0], a1 = row[n];
                 const R s = beta * fma(a1, v1, a0 * v0);
@@ -687,10 +697,18 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             }
             __syncthreads();
         }
-        // clean the bulge remnants below the subdiagonal of the window
-        for (int e = tid; e < ns * ns; e += NT) {
-            const int i = l + e % ns, j = l + e / ns;
-            if (i > j + 1) A[i + int64_t(j) * n] = R(0.0);
+        // clean the bulge remnants below the subdiagonal of the window (for
+        // symmetric input they lie on the second and third subdiagonal)
+        if (sym) {
+            for (int e = tid; e < 2 * ns; e += NT) {
+                const int j = l + e / 2, i = j + 2 + e % 2;
+                if (i <= u) A[i + int64_t(j) * n] = R(0.0);
+            }
+        } else {
+            for (int e = tid; e < ns * ns; e += NT) {
+                const int i = l + e % ns, j = l + e / ns;
+                if (i > j + 1) A[i + int64_t(j) * n] = R(0.0);
+            }
         }
         __syncthreads();
     }
