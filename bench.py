@@ -55,7 +55,7 @@ def _args():
     ap.add_argument("--autotune", action="store_true",
                     help="choose each method's block size with kl_autotune (complete solves for k = 8, 16, 32, "
                          "before the timed region) instead of the workload's k")
-    ap.add_argument("--serve-requests", type=int, default=24,
+    ap.add_argument("--serve-requests", type=int, default=64,
                     help="requests of the seeded serving stream replayed by the serving leg")
     ap.add_argument("--serve-max-elems", type=int, default=8,
                     help="per-axis element cap of the serving stream sample")

@@ -267,7 +267,10 @@ static int pairwise(kl_solver* h, int precision, const double* U, double* W, int
         job.ready = h->ev_ready;
         job.done = h->ev_done;
         if (e == cudaSuccess) e = cudaEventRecord(job.ready, h->stream);
-        if (e == cudaSuccess) e = h->batcher->run(job);
+        if (e == cudaSuccess) {
+            h->announced = false;  // run() takes the announcement over
+            e = h->batcher->run(job);
+        }
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, job.done, 0);
         if (e == cudaSuccess) e = tc_finish(a, h->stream, &launched);
         h->launches += launched + 1;
@@ -392,7 +395,20 @@ int apply_operator(kl_solver* h, int which, int precision, const double* X, int6
         if (rc == KL_OK) rc = apply_post(h, which, Y, ldy, k);
         return rc;
     };
-    if (!h->use_graphs || h->batcher) return whole();
+    if (h->batcher) {
+        // served handle: the batcher waits for this product from now on
+        if (precision == KL_MIXED_BF16 || precision == KL_MIXED_TF32) {
+            h->batcher->announce();
+            h->announced = true;
+        }
+        const int rc = whole();
+        if (h->announced) {  // failed before its product reached the batcher
+            h->batcher->withdraw();
+            h->announced = false;
+        }
+        return rc;
+    }
+    if (!h->use_graphs) return whole();
     if (!h->profiling) return with_graph(h, {which, precision, k, X, ldx, Y, ldy, 0}, whole);
     int rc = with_graph(h, {which, precision, k, X, ldx, nullptr, 0, 1}, [&] { return apply_pre(h, which, X, ldx, k); });
     if (rc == KL_OK) rc = apply_pair(h, precision, k);

@@ -128,6 +128,7 @@ struct kl_solver {
     // serving: tensor-core pairwise products go through this batcher (set
     // by the server's worker; null for a stand-alone handle)
     kl::Batcher* batcher = nullptr;
+    bool announced = false;  // a product announced to the batcher, not yet submitted
     cudaEvent_t ev_ready = nullptr, ev_done = nullptr;
 
     // eigensolver workspaces

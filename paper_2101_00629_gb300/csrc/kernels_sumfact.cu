@@ -6,6 +6,7 @@
 //
 // Layout: a block of k vectors over a tensor grid (n1, n2, n3) is
 // column-major, point index i1 + n1 * (i2 + n2 * i3), column stride ld.
+#include <algorithm>
 #include <cmath>
 
 #include "kl_internal.h"
@@ -15,6 +16,16 @@ namespace kl {
 namespace {
 
 constexpr int kThreads = 256;
+
+// Grid of a mode product: the k columns along y, the rows of a column along x
+// (both grid-stride beyond their caps: 65535 columns, and the row blocks of
+// grid_for's cap shared among the columns).
+inline dim3 grid_cols(int64_t per_col, int k) {
+    int64_t gx = (per_col + kThreads - 1) / kThreads;
+    const int64_t cap = std::max<int64_t>(1, int64_t(device_sm_count()) * 64 / std::max(1, k));
+    if (gx > cap) gx = cap;
+    return dim3(unsigned(gx < 1 ? 1 : gx), unsigned(std::min(k, 65535)));
+}
 
 inline int grid_for(int64_t n, int per_block = kThreads) {
     int64_t g = (n + per_block - 1) / per_block;
@@ -103,62 +114,79 @@ __global__ void tensor_points_kernel(int geometry, double g0, double g1, double 
 }
 
 // out[(ia, i, ib), c] = sum_l A[i + m l] pre[(ia, l, ib)] X[(ia, l, ib), c],
-// optional pre (input rows) and post (output rows) scales.
+// optional pre (input rows) and post (output rows) scales. Column c is
+// blockIdx.y; the row r = ia + a (i + m ib) of that column is decomposed with
+// index type I (32-bit whenever a m b fits: a 64-bit division costs several
+// times the 18 FMAs of a typical output).
+template <class I>
 __global__ void modeprod_kernel(const double* __restrict__ A, int m, int n,
                                 const double* __restrict__ X, int64_t ldx, double* __restrict__ Y,
-                                int64_t ldy, int64_t a, int64_t b, int k,
-                                const double* __restrict__ post, const double* __restrict__ pre) {
-    const int64_t per_col = a * m * b;
-    const int64_t total = per_col * k;
-    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
-         t += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t c = t / per_col;
-        const int64_t r = t - c * per_col;  // = ia + a * (i + m * ib)
-        const int64_t ia = r % a;
-        const int64_t rest = r / a;
-        const int i = int(rest % m);
-        const int64_t ib = rest / m;
-        const double* x = X + c * ldx + ia + a * n * ib;
-        double acc = 0.0;
+                                int64_t ldy, I a, I b, int k, const double* __restrict__ post,
+                                const double* __restrict__ pre) {
+    const I per_col = a * I(m) * b;
+    for (int64_t c = blockIdx.y; c < k; c += gridDim.y) {
+    for (I r = I(blockIdx.x) * blockDim.x + threadIdx.x; r < per_col; r += I(gridDim.x) * blockDim.x) {
+        const I rest = r / a;
+        const I ia = r - rest * a;
+        const I ib = rest / I(m);
+        const int i = int(rest - ib * I(m));
+        const int64_t base = int64_t(ia) + int64_t(a) * n * int64_t(ib);
+        const double* x = X + c * ldx + base;
+        // four partial sums: the n-term FP64 FMA chain of one output would
+        // otherwise wait on the FMA latency (~63 cycles on GB300) n times
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        int l = 0;
+        const int64_t as = int64_t(a);
         if (pre) {
-            const double* s = pre + ia + a * n * ib;
-            for (int l = 0; l < n; ++l) acc = fma(A[i + int64_t(m) * l], x[a * l] * s[a * l], acc);
+            const double* s = pre + base;
+            for (; l + 4 <= n; l += 4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    acc[q] = fma(A[i + int64_t(m) * (l + q)], x[as * (l + q)] * s[as * (l + q)], acc[q]);
+            }
+            for (; l < n; ++l) acc[0] = fma(A[i + int64_t(m) * l], x[as * l] * s[as * l], acc[0]);
         } else {
-            for (int l = 0; l < n; ++l) acc = fma(A[i + int64_t(m) * l], x[a * l], acc);
+            for (; l + 4 <= n; l += 4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[q] = fma(A[i + int64_t(m) * (l + q)], x[as * (l + q)], acc[q]);
+            }
+            for (; l < n; ++l) acc[0] = fma(A[i + int64_t(m) * l], x[as * l], acc[0]);
         }
-        if (post) acc *= post[r];
-        Y[c * ldy + r] = acc;
+        double sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+        if (post) sum *= post[r];
+        Y[c * ldy + int64_t(r)] = sum;
+    }
     }
 }
 
 // Banded form: out[(ia, i, ib), c] = sum_j V[i w + j] pre[(ia, s_i + j, ib)]
-// X[(ia, s_i + j, ib), c] with s_i = start[i].
+// X[(ia, s_i + j, ib), c] with s_i = start[i]; the same thread mapping.
+template <class I>
 __global__ void modeprod_band_kernel(const double* __restrict__ V, const int* __restrict__ start, int w, int m,
                                      int n, const double* __restrict__ X, int64_t ldx, double* __restrict__ Y,
-                                     int64_t ldy, int64_t a, int64_t b, int k, const double* __restrict__ post,
+                                     int64_t ldy, I a, I b, int k, const double* __restrict__ post,
                                      const double* __restrict__ pre) {
-    const int64_t per_col = a * m * b;
-    const int64_t total = per_col * k;
-    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
-         t += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t c = t / per_col;
-        const int64_t r = t - c * per_col;  // = ia + a * (i + m * ib)
-        const int64_t ia = r % a;
-        const int64_t rest = r / a;
-        const int i = int(rest % m);
-        const int64_t ib = rest / m;
-        const int64_t off = ia + a * (int64_t(start[i]) + int64_t(n) * ib);
+    const I per_col = a * I(m) * b;
+    for (int64_t c = blockIdx.y; c < k; c += gridDim.y) {
+    for (I r = I(blockIdx.x) * blockDim.x + threadIdx.x; r < per_col; r += I(gridDim.x) * blockDim.x) {
+        const I rest = r / a;
+        const I ia = r - rest * a;
+        const I ib = rest / I(m);
+        const int i = int(rest - ib * I(m));
+        const int64_t off = int64_t(ia) + int64_t(a) * (int64_t(start[i]) + int64_t(n) * int64_t(ib));
         const double* x = X + c * ldx + off;
         const double* v = V + int64_t(i) * w;
+        const int64_t as = int64_t(a);
         double acc = 0.0;
         if (pre) {
             const double* s = pre + off;
-            for (int j = 0; j < w; ++j) acc = fma(v[j], x[a * j] * s[a * j], acc);
+            for (int j = 0; j < w; ++j) acc = fma(v[j], x[as * j] * s[as * j], acc);
         } else {
-            for (int j = 0; j < w; ++j) acc = fma(v[j], x[a * j], acc);
+            for (int j = 0; j < w; ++j) acc = fma(v[j], x[as * j], acc);
         }
         if (post) acc *= post[r];
-        Y[c * ldy + r] = acc;
+        Y[c * ldy + int64_t(r)] = acc;
+    }
     }
 }
 
@@ -341,7 +369,13 @@ cudaError_t launch_modeprod(const double* A, int m, int n, const double* X, int6
     KL_RANGE(Y, block_extent(a * m * b, k, ldy), double, "modeprod Y");
     KL_RANGE(post, a * m * b, double, "modeprod post");
     KL_RANGE(pre, a * n * b, double, "modeprod pre");
-    modeprod_kernel<<<grid_for(total), kThreads, 0, s>>>(A, m, n, X, ldx, Y, ldy, a, b, k, post, pre);
+    const int64_t per_col = a * m * b;
+    if (per_col < (int64_t(1) << 31))
+        modeprod_kernel<uint32_t><<<grid_cols(per_col, k), kThreads, 0, s>>>(A, m, n, X, ldx, Y, ldy, uint32_t(a),
+                                                                             uint32_t(b), k, post, pre);
+    else
+        modeprod_kernel<uint64_t><<<grid_cols(per_col, k), kThreads, 0, s>>>(A, m, n, X, ldx, Y, ldy, uint64_t(a),
+                                                                             uint64_t(b), k, post, pre);
     return cudaGetLastError();
 }
 
@@ -356,8 +390,13 @@ cudaError_t launch_modeprod_band(const Band& A, int m, int n, const double* X, i
     KL_RANGE(Y, block_extent(a * m * b, k, ldy), double, "band modeprod Y");
     KL_RANGE(post, a * m * b, double, "band modeprod post");
     KL_RANGE(pre, a * n * b, double, "band modeprod pre");
-    modeprod_band_kernel<<<grid_for(total), kThreads, 0, s>>>(A.vals, A.start, A.w, m, n, X, ldx, Y, ldy, a, b, k,
-                                                              post, pre);
+    const int64_t per_col = a * m * b;
+    if (per_col < (int64_t(1) << 31))
+        modeprod_band_kernel<uint32_t><<<grid_cols(per_col, k), kThreads, 0, s>>>(
+            A.vals, A.start, A.w, m, n, X, ldx, Y, ldy, uint32_t(a), uint32_t(b), k, post, pre);
+    else
+        modeprod_band_kernel<uint64_t><<<grid_cols(per_col, k), kThreads, 0, s>>>(
+            A.vals, A.start, A.w, m, n, X, ldx, Y, ldy, uint64_t(a), uint64_t(b), k, post, pre);
     return cudaGetLastError();
 }
 

@@ -88,8 +88,22 @@ void Batcher::set_expected(int n) {
     cv_work_.notify_all();
 }
 
+void Batcher::announce() {
+    std::lock_guard<std::mutex> lk(mu_);
+    ++announced_;
+}
+
+void Batcher::withdraw() {
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        if (announced_ > 0) --announced_;
+    }
+    cv_work_.notify_all();
+}
+
 cudaError_t Batcher::run(BatchJob& job) {
     std::unique_lock<std::mutex> lk(mu_);
+    if (announced_ > 0) --announced_;
     if (init_error_ != cudaSuccess) return init_error_;
     job.launched = false;
     job.error = cudaSuccess;
@@ -115,10 +129,13 @@ void Batcher::loop() {
                 if (stop_) break;
                 continue;
             }
-            // gather: wait for the products of the other running solves, at
-            // most window_us after the first one arrived
+            // gather: wait for the products the running solves have announced
+            // (they are in their sum factorisation and submit within
+            // microseconds), at most window_us after the first one arrived;
+            // solves busy with their orthogonalisation or Rayleigh-Ritz step
+            // are not waited for
             const auto until = Clock::now() + std::chrono::microseconds(window_us_);
-            while (!stop_ && int(pending_.size()) < expected_) {
+            while (!stop_ && announced_ > 0 && int(pending_.size()) < expected_) {
                 if (cv_work_.wait_until(lk, until) == std::cv_status::timeout) break;
             }
             take.swap(pending_);

@@ -40,9 +40,17 @@ class Batcher {
     // Blocks until the launch containing the job is enqueued on the
     // batcher's stream; the caller's stream must then wait on job.done.
     cudaError_t run(BatchJob& job);
-    // Number of solves that may submit (the batcher waits for that many
-    // products, at most window_us).
+    // Number of solves that may submit (an upper bound on the products a
+    // batch waits for).
     void set_expected(int n);
+    // A solve starts an operator application: its product will follow after
+    // the application's first sum-factorisation pass. The batcher waits (at
+    // most window_us) only for products announced this way and not yet
+    // submitted, not for solves busy elsewhere (orthogonalisation, the
+    // Rayleigh-Ritz eigenproblem).
+    void announce();
+    // An announced product will not come (the application failed first).
+    void withdraw();
     BatcherStats stats();
 
    private:
@@ -55,6 +63,7 @@ class Batcher {
     std::condition_variable cv_work_, cv_done_;
     std::vector<BatchJob*> pending_;
     int expected_ = 1;
+    int announced_ = 0;  // announced products not yet submitted
     bool stop_ = false;
     BatcherStats stats_;
     std::thread thread_;
