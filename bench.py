@@ -83,9 +83,10 @@ def max_over_ranks(x, dist, device):
     return float(t.item())
 
 
-def _recorded_traffic():
-    """DRAM bytes per launch of the pairwise kernel from the committed ncu
-    summary, if the kernel source is unchanged since it was taken (else None)."""
+def _recorded_traffic(kernel_class):
+    """DRAM bytes per launch of the pairwise kernel class from the committed
+    ncu summary, if it covers that class and the kernel source is unchanged
+    since it was taken (else None)."""
     import hashlib
     try:
         rec = {}
@@ -93,6 +94,8 @@ def _recorded_traffic():
             if ":" in line:
                 k, v = line.split(":", 1)
                 rec[k.strip()] = v.strip()
+        if rec.get("kernel_class") != kernel_class:
+            return None
         src = open(os.path.join(ROOT, rec["source"]), "rb").read()
         if hashlib.sha1(src).hexdigest() != rec["source_sha1"]:
             return None
@@ -432,12 +435,17 @@ def _configs_leg(a, kl, stream, peaks):
             prof = kl.kl_profile_read(h)
             kl.kl_profile_enable(h, False)
             kl.kl_destroy(h)
-            pair = prof.get("pair_tc_" + a.precision) or prof.get("pair_f32")
+            # the symmetric Galerkin class counts each symmetric pair once (its
+            # kernel evaluates each once); the dense classes every pair
+            pair_key = next((key for key in ("pair_tc_%s_sym" % a.precision, "pair_tc_" + a.precision, "pair_f32")
+                             if key in prof), None)
+            pair = prof.get(pair_key) if pair_key else None
             r = dict(N=dims[0], pairwise_sources=dims[1], pairwise_targets=dims[2], k=ks[m], status=rc, s=t,
                      applies=info.applies, max_resid=info.max_resid)
             if pair:
                 rate = pair["units"] / (pair["ms"] * 1e-3)
-                r["pairwise"] = dict(launches=pair["launches"], ms=pair["ms"], gpairs_per_s=rate / 1e9,
+                r["pairwise"] = dict(kernel_class=pair_key, launches=pair["launches"], ms=pair["ms"],
+                                     gpairs_per_s=rate / 1e9,
                                      frac_alu_roof=rate / _pair_roof(args["kernel"], peaks),
                                      share_of_solve=pair["ms"] * 1e-3 / t)
             if name == CONFIG_WORKLOADS[0][0] or a.configs_fp64:
@@ -614,8 +622,9 @@ def run_gpu(a):
             for key in acc:
                 acc[key] += st[key]
             # Galerkin: Gamma over one point set is symmetric, N~(N~+1)/2
-            # distinct pairs per vector block; collocation: every pair
-            sym = (S_m + 1) / (2.0 * S_m) if (m == "galerkin" and S_m == T_m) else 1.0
+            # distinct pairs per vector block (what the symmetric class
+            # counts already); collocation: every pair
+            sym = (S_m + 1) / (2.0 * S_m) if (m == "galerkin" and S_m == T_m and not name.endswith("_sym")) else 1.0
             method_units[name] = method_units.get(name, 0.0) + st["units"] * sym
         kl.kl_profile_enable(handles[m], False)
     ms_step = float(np.mean(step_ms))
@@ -686,10 +695,11 @@ def run_gpu(a):
         peak = min(peak_mufu, peak_fp32)
         achieved_m = method_units[pair_name] / (st["ms"] * 1e-3) / 1e9
         roof = {"bound": "alu", "kernel": pair_name, "achieved": achieved, "peak": peak, "unit": "Gpair/s",
-                "frac": achieved / peak, "traffic": _recorded_traffic(),
+                "frac": achieved / peak, "traffic": _recorded_traffic(pair_name),
                 "achieved_method_count": achieved_m, "frac_method_count": achieved_m / peak,
-                "method_count": "Galerkin pairs counted once per symmetric pair, N~(N~+1)/2 (the kernel evaluates "
-                                "all N~^2); collocation N N_eN_q",
+                "method_count": "Galerkin pairs counted once per symmetric pair, N~(N~+1)/2 (the symmetric class "
+                                "pair_tc_bf16_sym evaluates each once: its achieved is that count; the dense classes "
+                                "evaluate all N~^2); collocation N N_eN_q",
                 "peak_basis": f"min(measured MUFU ex2 {ex2 / 1e12:.2f} T/s / {mufu_per_pair} per pair, measured FP32 "
                               f"{fp32_fma / 1e12:.1f} T op/s / {fp32_per_pair} per pair); FP64 FMA "
                               f"{fp64_fma / 1e12:.2f} T/s",

@@ -413,8 +413,12 @@ int kl_serve_close(kl_server* s);
  *   KL_DEBUG_NAN_START   (handle) value != 0 plants a NaN in the
  *                        eigensolver's start block (kl_eigs returns
  *                        KL_ERR_NUMERIC).
+ *   KL_DEBUG_PAIR_DENSE  (handle) value != 0 makes the split-BF16 Galerkin
+ *                        pairwise product evaluate every pair (the dense
+ *                        form, as for collocation) instead of each symmetric
+ *                        pair once; for comparisons of the two forms.
  * Errors: KL_ERR_ARG. */
-enum { KL_DEBUG_WAIT_LIMIT = 1, KL_DEBUG_FAIL_ALLOC = 2, KL_DEBUG_NAN_START = 3 };
+enum { KL_DEBUG_WAIT_LIMIT = 1, KL_DEBUG_FAIL_ALLOC = 2, KL_DEBUG_NAN_START = 3, KL_DEBUG_PAIR_DENSE = 4 };
 int kl_debug_set(kl_solver* h, int what, long long value);
 
 /* 1 if the library was built with KL_CHECK_BOUNDS (every kernel launch first

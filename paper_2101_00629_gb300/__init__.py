@@ -30,7 +30,7 @@ _LIB_PATH = os.path.join(_HERE, "libkl.so")
 KL_OK, KL_ERR_ARG, KL_ERR_CUDA, KL_ERR_OOM = 0, -1, -2, -3
 KL_ERR_NOCONV, KL_ERR_NUMERIC, KL_ERR_TIMEOUT, KL_ERR_UNSUPPORTED = -4, -5, -6, -7
 KL_WARN_COMPLEX = 1
-KL_DEBUG_WAIT_LIMIT, KL_DEBUG_FAIL_ALLOC, KL_DEBUG_NAN_START = 1, 2, 3
+KL_DEBUG_WAIT_LIMIT, KL_DEBUG_FAIL_ALLOC, KL_DEBUG_NAN_START, KL_DEBUG_PAIR_DENSE = 1, 2, 3, 4
 
 GEOMETRIES = {"cube": 0, "annulus": 1, "half_annulus": 2, "projective_cube": 3}
 KERNELS = {"gauss": 0, "exp_sep": 1, "exp": 2, "matern32": 3, "const": 4}
@@ -396,9 +396,9 @@ def kl_autotune(p, M, tol=0.0, stream=None, cache_path=None):
 
 
 def kl_debug_set(h, what, value):
-    """Host-side failure injection for tests (see kl.h): what is
-    KL_DEBUG_WAIT_LIMIT, KL_DEBUG_FAIL_ALLOC (h may be None) or
-    KL_DEBUG_NAN_START."""
+    """Host-side failure injection and comparison switches for tests (see
+    kl.h): what is KL_DEBUG_WAIT_LIMIT, KL_DEBUG_FAIL_ALLOC (h may be None),
+    KL_DEBUG_NAN_START or KL_DEBUG_PAIR_DENSE."""
     return _check(h, _load().kl_debug_set(h, int(what), int(value)))
 
 

@@ -156,6 +156,40 @@ int ensure_workspace(kl_solver* h, int k) {
     return KL_OK;
 }
 
+// Symmetric split-BF16 Galerkin product: plan and scratch for blocks of k
+// vectors (k rounded up to 8, at most 16), created on the first application
+// that uses it (stand-alone handles only: served handles share batched
+// launches of the dense form). Before any graph capture of the application.
+static bool sym_applies(const kl_solver* h, int precision, int k) {
+    return galerkin_form(h->prm.method) && precision == KL_MIXED_BF16 && !h->batcher && !h->pair_dense &&
+           h->cc_major == 10 && h->T == h->S && tc_sym_eligible(h->T, k, false);
+}
+
+static int ensure_sym(kl_solver* h, int k) {
+    if (h->sym_plan && k <= h->sym_plan->kcap) return KL_OK;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "workspace sync");
+    clear_graphs(h);
+    dfree(h->sym_scratch);
+    h->dev_bytes -= h->sym_scratch_len * int64_t(sizeof(double));
+    h->sym_scratch = nullptr;
+    h->sym_scratch_len = 0;
+    delete h->sym_plan;
+    h->sym_plan = nullptr;
+    TcSymPlan* p = new TcSymPlan(tc_sym_plan(h->T, std::min(16, (k + 7) / 8 * 8), h->sm_count));
+    if ((e = dalloc(h, &h->sym_scratch, p->total)) != cudaSuccess) {
+        delete p;
+        return cuda_fail(h, e, "symmetric pair scratch alloc");
+    }
+    if ((e = tc_sym_upload(*p, h->sym_scratch, h->stream)) != cudaSuccess) {
+        delete p;
+        return cuda_fail(h, e, "symmetric pair unit table");
+    }
+    h->sym_scratch_len = p->total;
+    h->sym_plan = p;
+    return KL_OK;
+}
+
 // Y <- (x)_d F_d applied mode by mode: X has dims (n_in[0], n_in[1], n_in[2]),
 // F_d is (n_out[d] x n_in[d]). The first product scales the input rows by
 // `pre` and the last one writes Y (ldy) with per-point scaling `post` (either
@@ -248,8 +282,19 @@ static int pairwise(kl_solver* h, int precision, const double* U, double* W, int
         a.sm_count = h->sm_count;
         a.err = h->d_err;
         a.wait_limit = h->wait_limit;
-        ProfScope ps(h, precision == KL_MIXED_TF32 ? "pair_tc_tf32" : "pair_tc_bf16", pairs);
         int launched = 0;
+        if (sym_applies(h, precision, k) && h->sym_plan && k <= h->sym_plan->kcap) {
+            // each symmetric pair once (units of the method's work: N~(N~+1)/2)
+            a.sym = h->sym_plan;
+            a.scratch = h->sym_scratch;
+            a.scratch_len = h->sym_scratch_len;
+            ProfScope ps(h, "pair_tc_bf16_sym", 0.5 * double(h->T) * double(h->T + 1));
+            cudaError_t e = launch_pair_tc_sym(a, h->stream, &launched);
+            h->launches += launched;
+            if (e != cudaSuccess) return cuda_fail(h, e, "pairwise (tcgen05, symmetric)");
+            return KL_OK;
+        }
+        ProfScope ps(h, precision == KL_MIXED_TF32 ? "pair_tc_tf32" : "pair_tc_bf16", pairs);
         if (!h->batcher) {
             cudaError_t e = launch_pair_tc(a, h->stream, &launched);
             h->launches += launched;
@@ -389,6 +434,9 @@ static int with_graph(kl_solver* h, const kl_solver::GraphKey& key, F&& enqueue)
 // of the sequence).
 int apply_operator(kl_solver* h, int which, int precision, const double* X, int64_t ldx, double* Y,
                    int64_t ldy, int k) {
+    if (sym_applies(h, precision, k)) {
+        if (int rc = ensure_sym(h, k); rc != KL_OK) return rc;
+    }
     auto whole = [&]() -> int {
         int rc = apply_pre(h, which, X, ldx, k);
         if (rc == KL_OK) rc = apply_pair(h, precision, k);
@@ -978,6 +1026,8 @@ int kl_destroy(kl_solver* h) {
     dfree(h->d_band_start);
     for (int i = 0; i < 3; ++i) dfree(h->ws[i]);
     dfree(h->pair_scratch);
+    dfree(h->sym_scratch);
+    delete h->sym_plan;
     dfree(h->eig_ws);
     dfree(h->d_err);
     dfree(h->smp_ws);
@@ -1090,6 +1140,13 @@ int kl_debug_set(kl_solver* h, int what, long long value) {
         case KL_DEBUG_NAN_START:
             if (!h) return fail(nullptr, KL_ERR_ARG, "KL_DEBUG_NAN_START needs a handle");
             h->nan_start = value != 0;
+            return KL_OK;
+        case KL_DEBUG_PAIR_DENSE:
+            if (!h) return fail(nullptr, KL_ERR_ARG, "KL_DEBUG_PAIR_DENSE needs a handle");
+            if (cudaError_t e = cudaStreamSynchronize(h->stream); e != cudaSuccess)
+                return cuda_fail(h, e, "kl_debug_set");
+            h->pair_dense = value != 0;
+            clear_graphs(h);  // captured launches use the other form
             return KL_OK;
         default:
             return fail(h, KL_ERR_ARG, "unknown debug setting");

@@ -20,6 +20,7 @@ struct kl_prof_entry {
 
 namespace kl {
 class Batcher;
+struct TcSymPlan;
 }
 
 struct kl_solver {
@@ -86,6 +87,12 @@ struct kl_solver {
     double* pair_scratch = nullptr;
     int64_t pair_scratch_len = 0;
     int pair_splits = 1;
+    // symmetric split-BF16 Galerkin product (stand-alone handles): its plan
+    // for blocks of up to sym_plan->kcap vectors and its scratch
+    kl::TcSymPlan* sym_plan = nullptr;
+    double* sym_scratch = nullptr;
+    int64_t sym_scratch_len = 0;
+    bool pair_dense = false;  // kl_debug_set(KL_DEBUG_PAIR_DENSE): every pair evaluated
 
     // device word set by kernels whose bounded waits gave up (read after a
     // synchronisation; see check_device_error)

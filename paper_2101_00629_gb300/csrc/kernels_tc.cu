@@ -50,6 +50,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <mutex>
+#include <type_traits>
 
 #include "kernel_eval.cuh"
 #include "kernels_tc.h"
@@ -166,6 +167,32 @@ __device__ __forceinline__ void mma_tmemA(bool tf32, uint32_t d_tmem, uint32_t a
             "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
             : "memory");
     }
+}
+
+// Instruction descriptor of the transposed product of the symmetric mode:
+// dense, D = F32, A = B = BF16, A MN-major (transposed, bit 15), B K-major,
+// N >> 3 at bit 17, M = 64 (M >> 4 at bit 24).
+__host__ __device__ constexpr uint32_t instr_desc_t64(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (uint32_t(n >> 3) << 17) | (uint32_t(64 >> 4) << 24);
+}
+
+// D (tensor memory) += A B with both operands in shared memory (BF16).
+__device__ __forceinline__ void mma_smemA(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void st_global_v4(float* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.global.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+__device__ __forceinline__ void st_shared_v4(void* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(smem_u32(p)), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -460,9 +487,53 @@ __device__ __forceinline__ int inst_of(const TcBatch& b, int64_t u) {
     return p;
 }
 
-template <int KIND, bool TF32, int NP>
+// Symmetric mode: unit u of the launch (global unit sym_unit_begin + u) ->
+// tile (binary search of the per-tile first units) and chunk range.
+__device__ __forceinline__ Unit sym_unit_of(const TcInstance& I, int64_t u) {
+    const int64_t g = I.sym_unit_begin + u;
+    int lo = I.sym_tile0, hi = I.sym_tile1 - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (int64_t(I.sym_tab[mid].x) <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    Unit r;
+    r.tile = lo;
+    r.split = int(g - I.sym_tab[lo].x);
+    const int cps = I.sym_tab[lo].y;
+    r.c0 = 2 * int64_t(lo) + int64_t(r.split) * cps;
+    const int64_t left = I.nchunks - r.c0;
+    r.nloc = int(left < cps ? left : int64_t(cps));
+    return r;
+}
+
+// Index of the transposed partial sum of tile I and chunk c >= 2I + 2 among
+// all of them (tile by tile, chunk by chunk): tiles I' < I contribute
+// nchunks - 2 - 2 I' each.
+__host__ __device__ __forceinline__ int64_t sym_p2_index(int64_t I, int64_t c, int64_t nchunks) {
+    return I * (nchunks - 2) - I * (I - 1) + (c - 2 * I - 2);
+}
+
+// Symmetric mode layout (split BF16, N = 16): shared memory holds the ring of
+// kernel tiles of the transposed product (hi and lo image of 128 targets x
+// 64 sources each, 16 KB), then the split images of X on the unit's own tile
+// (two chunks, double-buffered across units), then the chunk-record ring.
+constexpr int kSymGBytes = 32768;               // one kernel tile: hi + lo image
+constexpr int kSymXBytes = 8192;                // X of one 128-point tile (two 4 KB images)
+constexpr int kSymRecBase = 2 * kSymGBytes + 2 * kSymXBytes;
+constexpr int kSymRecStages = 4;
+constexpr int kSymDJ = 224;                     // TMEM columns of the transposed product's two
+                                                // accumulators (16 columns each)
+// Kernel tile image of the transposed product (MN-major: sources contiguous):
+// 8 x 8 core matrices of 128 bytes, element (target t, source j) at
+// (j / 8) * 2048 + (t / 8) * 128 + (t % 8) * 16 + (j % 8) * 2.
+constexpr uint32_t kSymSrcGroupStride = 2048;   // along M (sources) of the transposed product
+constexpr uint32_t kSymTgtGroupStride = 128;    // along K (targets)
+
+template <int KIND, bool TF32, int NP, bool SYM>
 __global__ void __launch_bounds__(kThreads, 2)
 pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
+    static_assert(!SYM || (!TF32 && NP == 16), "symmetric mode: split BF16, N = 16");
     const int64_t nunits = batch.nunits;
     const long long wlim = batch.wait_limit > 0 ? batch.wait_limit : kWaitLimit;
     constexpr int ESIZE = TF32 ? 4 : 2;
@@ -470,21 +541,29 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
     constexpr int SW = KC / 2;                          // sources of each warpgroup
     constexpr int IMG = NP * KC * ESIZE;                // bytes of one of hi / lo
     constexpr int STAGE_BYTES = 2 * IMG + KC * 12;      // hi, lo, coordinates x[KC] y[KC] z[KC]
-    constexpr int SSTAGES = smem_stages(STAGE_BYTES);   // shared-memory ring (>= kStages)
+    constexpr int SSTAGES = SYM ? kSymRecStages : smem_stages(STAGE_BYTES);  // shared-memory ring (>= kStages)
+    constexpr int REC_BASE = SYM ? kSymRecBase : 0;
     constexpr uint32_t IDESC = instr_desc(NP, TF32);
     constexpr bool kConcat = tc_concat(TF32, NP);
     constexpr uint32_t IDESC2 = instr_desc(2 * NP, TF32);  // combined [hi | lo] operand
+    // transposed product: M = 64 sources, A (kernel tile) MN-major
+    constexpr uint32_t IDESC_T = instr_desc_t64(NP);
     static_assert(!kConcat || 2 * NP <= TmemLayout<NP>::kDStride, "combined accumulator wider than its buffer");
     constexpr bool kSum = TmemLayout<NP>::kSum;
     constexpr int kDStride = TmemLayout<NP>::kDStride;
     constexpr int kSBase = TmemLayout<NP>::kSBase;
     constexpr int kAColBase = TmemLayout<NP>::kAColBase;
+    static_assert(!SYM || (kAColBase + kStages * kAColsPerStage <= kSymDJ && kSymDJ + 2 * NP <= kTmemCols),
+                  "symmetric mode: tensor memory overflow");
 
     extern __shared__ __align__(1024) uint8_t smem[];
     // loaded/sempty: shared-memory ring (bulk copies ahead of use);
-    // full/tfree: TMEM ring of kernel tiles; dfull/dfree: accumulators
+    // full/tfree: TMEM ring of kernel tiles; dfull/dfree: accumulators;
+    // symmetric mode: gfree (shared-memory kernel tiles read), d2full/d2free
+    // (transposed accumulator), xload/xfree (X of the unit's tile)
     __shared__ uint64_t loaded_bar[SSTAGES], sempty_bar[SSTAGES], full_bar[kStages], tfree_bar[kStages];
     __shared__ uint64_t dfull_bar[2], dfree_bar[2], drain_bar;
+    __shared__ uint64_t gfree_bar[2], d2full_bar[2], d2free_bar[2], xload_bar[2], xfree_bar[2];
     __shared__ uint32_t tmem_slot;
 
     const int tid = threadIdx.x;
@@ -502,6 +581,13 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
         for (int b = 0; b < 2; ++b) {
             mbar_init(&dfull_bar[b], 1);
             mbar_init(&dfree_bar[b], 256);  // both warpgroups fold half of the columns
+            mbar_init(&gfree_bar[b], 1);
+            mbar_init(&xload_bar[b], 1);
+            mbar_init(&xfree_bar[b], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&d2full_bar[b], 1);
+            mbar_init(&d2free_bar[b], 256);
         }
         mbar_init(&drain_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -525,9 +611,11 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
         bool ok = true;
         uint32_t jbase = 0;  // chunks of earlier units (stage ring position)
         uint32_t gbase = 0;  // accumulator groups of earlier units
+        uint32_t og = 0;     // symmetric mode: transposed products so far
+        uint32_t drained = 0;  // symmetric mode: transposed products drained so far
         for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
-            const TcInstance& I = batch.inst[inst_of(batch, u)];
-            const Unit un = unit_of(u - I.unit0, I.splits, I.nchunks, I.cps);
+            const TcInstance& I = batch.inst[SYM ? 0 : inst_of(batch, u)];
+            const Unit un = SYM ? sym_unit_of(I, u) : unit_of(u - I.unit0, I.splits, I.nchunks, I.cps);
             const int64_t T = I.T;
             const float cscale = I.cscale;
             const int kc = I.kc;
@@ -537,7 +625,11 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
             const float py = t < T ? cscale * ty[t] : 0.f;
             const float pz = t < T ? cscale * tz[t] : 0.f;
             const uint64_t ppx = pk2(px, px), ppy = pk2(py, py), ppz = pk2(pz, pz);
-            float2* prow = I.part + (int64_t(un.split) * I.k_total + I.c0) * T + t;
+            // partial sums of this unit: by source split (dense) or by unit
+            // of the band (symmetric, 128 rows per unit and column)
+            float2* prow = SYM ? I.part + (u * I.k_total + I.c0) * 128 + ptid
+                               : I.part + (int64_t(un.split) * I.k_total + I.c0) * T + t;
+            const int64_t pstride = SYM ? 128 : T;
             const int kind = I.kind;
             const int ngroups = (un.nloc + kGroup - 1) / kGroup;
             int flushed = 0;
@@ -587,7 +679,7 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                                 ls = __fadd_rn(__uint_as_float(l[q]), er);
                             }
                         } else if (g > 0 && got && t < T && cb + q < kc) {
-                            const float2 o = prow[int64_t(cb + q) * T];
+                            const float2 o = prow[int64_t(cb + q) * pstride];
                             hs = __fadd_rn(o.x, x);
                             const float bb = __fsub_rn(hs, o.x);
                             const float er = __fadd_rn(__fsub_rn(o.x, __fsub_rn(hs, bb)), __fsub_rn(x, bb));
@@ -603,14 +695,50 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
 #pragma unroll
                         for (int q = 0; q < 8; ++q)
                             if (cb + q < kc)
-                                prow[int64_t(cb + q) * T] = make_float2(__uint_as_float(h[q]), __uint_as_float(l[q]));
+                                prow[int64_t(cb + q) * pstride] =
+                                    make_float2(__uint_as_float(h[q]), __uint_as_float(l[q]));
                     }
                 }
                 if (kSum && !last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
                 mbar_arrive(&dfree_bar[gg & 1]);
             };
-            for (int jl = 0; jl < un.nloc; ++jl) {
+            // Symmetric mode: both warpgroups read the finished transposed
+            // accumulator of product m (buffer m & 1; M = 64 rows: row 16 q + l
+            // in lane l < 16 of the lane quarter q; warpgroup w the columns
+            // [8 w, 8 w + 8)) and store it as the FP32 partial sum of the 64
+            // sources of its chunk (p2: its index within the band).
+            auto drain = [&](int64_t p2, uint32_t m) {
+                const bool got = ok && warp_wait(&d2full_bar[m & 1], (m >> 1) & 1u, wlim);
+                if (!got) ok = false;
+                tc_fence_after();
+                const int cb = wg * (NP / 2);
+                uint32_t v[8];
+                __syncwarp();
+                tmem_ld8(tmem + lane_base + uint32_t(kSymDJ + NP * int(m & 1) + cb), v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                // rows of kstride (k rounded up to 8) floats: two 16-byte
+                // stores per row and warpgroup
+                const int kstride = (I.k_total + 7) & ~7;
+                if (got && lane < 16 && cb < kstride) {
+                    const int row = (warp & 3) * 16 + lane;
+                    float* dst = I.part2 + (p2 * 64 + row) * kstride + cb;
+                    st_global_v4(dst, v[0], v[1], v[2], v[3]);
+                    st_global_v4(dst + 4, v[4], v[5], v[6], v[7]);
+                }
+                tc_fence_before();
+                mbar_arrive(&d2free_bar[m & 1]);
+            };
+            // transposed partial sum of the unit's first chunk with one
+            // (2 tile + 2), relative to the band's first
+            const int64_t p2_unit = SYM ? sym_p2_index(un.tile, 2 * un.tile + 2, I.nchunks) - I.sym_p2_off0 : 0;
+            const int first_offd = SYM ? int(2 * un.tile + 2 - un.c0) : un.nloc;  // local index
+            // One chunk: wait for its record and a free kernel-tile stage,
+            // evaluate, split, store into tensor memory (and, for a transposed
+            // product, into the shared-memory tile), arrive. OFFD is fixed per
+            // loop so that neither path tests it per source.
+            auto chunk_step = [&](int jl, auto offd_tag) -> bool {
+                constexpr bool OFFD = decltype(offd_tag)::value;
                 // group g is folded kFlushLag chunks after it ends, when the
                 // tensor core has long finished it (never the last group of
                 // the unit here)
@@ -618,13 +746,18 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                     flush(flushed, false);
                     ++flushed;
                 }
-                if (!ok) break;
+                if (!ok) return false;
                 const uint32_t jg = jbase + uint32_t(jl);
                 const int ss = int(jg % SSTAGES), s = int(jg % kStages);
-                if (!warp_wait(&loaded_bar[ss], uint32_t((jg / SSTAGES) & 1), wlim)) { ok = false; break; }
-                if (jg >= kStages && !warp_wait(&tfree_bar[s], uint32_t(((jg / kStages) - 1) & 1), wlim)) { ok = false; break; }
-                const float* cx = reinterpret_cast<const float*>(smem + ss * STAGE_BYTES + 2 * IMG) + wg * SW;
+                if (!warp_wait(&loaded_bar[ss], uint32_t((jg / SSTAGES) & 1), wlim)) return false;
+                if (jg >= kStages && !warp_wait(&tfree_bar[s], uint32_t(((jg / kStages) - 1) & 1), wlim)) return false;
+                if (OFFD && og >= 2 && !warp_wait(&gfree_bar[og & 1], ((og >> 1) - 1) & 1u, wlim)) return false;
+                const float* cx = reinterpret_cast<const float*>(smem + REC_BASE + ss * STAGE_BYTES + 2 * IMG) + wg * SW;
                 const uint32_t acol = uint32_t(kAColBase + s * kAColsPerStage);
+                // this thread's 16-byte rows of the shared-memory kernel tile
+                // (target ptid; sources wg SW + 16 half + 0..15)
+                uint8_t* grow = smem + (og & 1) * kSymGBytes + (wg * SW / 8) * kSymSrcGroupStride +
+                                (ptid / 8) * kSymTgtGroupStride + (ptid % 8) * 16;
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
                     // 16 (BF16) or 8 (TF32) sources: four per 16-byte load of
@@ -650,10 +783,44 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                     __syncwarp();
                     tmem_st8(tmem + lane_base + acol + uint32_t(16 * wg + 8 * half), hi);
                     tmem_st8(tmem + lane_base + acol + 32u + uint32_t(16 * wg + 8 * half), lo);
+                    if (OFFD) {
+                        uint8_t* gr = grow + half * 2 * kSymSrcGroupStride;
+                        st_shared_v4(gr, hi[0], hi[1], hi[2], hi[3]);
+                        st_shared_v4(gr + kSymSrcGroupStride, hi[4], hi[5], hi[6], hi[7]);
+                        st_shared_v4(gr + kSymGBytes / 2, lo[0], lo[1], lo[2], lo[3]);
+                        st_shared_v4(gr + kSymGBytes / 2 + kSymSrcGroupStride, lo[4], lo[5], lo[6], lo[7]);
+                    }
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                // generic-proxy stores to shared memory become visible to the
+                // tensor core (async proxy) before the arrival
+                if (OFFD) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 tc_fence_before();
                 mbar_arrive(&full_bar[s]);
+                if (OFFD) {
+                    // transposed products are drained two behind: product
+                    // og - 2 has long finished, and its buffer is the one the
+                    // next product needs
+                    if (og >= drained + 2) {
+                        drain(p2_unit + (jl - 2 - first_offd), drained);
+                        ++drained;
+                    }
+                    ++og;
+                }
+                return true;
+            };
+            const int ndiag = first_offd < 0 ? 0 : (first_offd > un.nloc ? un.nloc : first_offd);
+            int jl = 0;
+            for (; jl < ndiag && ok; ++jl)
+                if (!chunk_step(jl, std::false_type{})) ok = false;
+            if constexpr (SYM) {
+                for (; jl < un.nloc && ok; ++jl)
+                    if (!chunk_step(jl, std::true_type{})) ok = false;
+                // the unit's last (up to two) transposed products
+                while (ok && drained < og) {
+                    drain(p2_unit + (un.nloc - int(og - drained) - first_offd), drained);
+                    ++drained;
+                }
             }
             while (ok && flushed < ngroups) {
                 flush(flushed, flushed == ngroups - 1);
@@ -667,7 +834,7 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             bool ok = true;
-            uint32_t jbase = 0, gbase = 0;
+            uint32_t jbase = 0, gbase = 0, og = 0, xu = 0;
             // B descriptors: stage ss, K step ks is the stage-0 descriptor plus
             // (ss * STAGE_BYTES + K-step offset) / 16 in its 14-bit start
             // address field (shared memory ends below 256 KB, so the field never
@@ -675,10 +842,20 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
             // producer warps, then spends one add per MMA on addresses
             constexpr uint32_t kLbo = (kConcat ? 2 * NP : NP) / 8 * 128;
             constexpr uint32_t kStep = 2 * kLbo;  // bytes of one K step of one image
-            const uint64_t bdesc0 = smem_desc(smem_u32(smem), kLbo, 128);
+            const uint64_t bdesc0 = smem_desc(smem_u32(smem + REC_BASE), kLbo, 128);
+            // symmetric mode: kernel tiles of the transposed product (MN-major:
+            // leading byte offset along K = targets, stride byte offset along
+            // M = sources) and the split images of X on the unit's tile (the
+            // chunk-record layout, K = the tile's 128 points in 8 steps)
+            const uint64_t gdesc0 = smem_desc(smem_u32(smem), kSymTgtGroupStride, kSymSrcGroupStride);
+            const uint64_t xdesc0 = smem_desc(smem_u32(smem + 2 * kSymGBytes), kLbo, 128);
             for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
-                const TcInstance& I = batch.inst[inst_of(batch, u)];
-                const Unit un = unit_of(u - I.unit0, I.splits, I.nchunks, I.cps);
+                const TcInstance& I = batch.inst[SYM ? 0 : inst_of(batch, u)];
+                const Unit un = SYM ? sym_unit_of(I, u) : unit_of(u - I.unit0, I.splits, I.nchunks, I.cps);
+                const int64_t first_offd = 2 * un.tile + 2;  // first chunk with a transposed product
+                const bool unit_offd = SYM && un.c0 + un.nloc > first_offd;
+                const uint32_t xb = xu & 1u;
+                bool xwaited = false;
                 for (int jl = 0; jl < un.nloc; ++jl) {
                     const uint32_t jg = jbase + uint32_t(jl);
                     const int s = int(jg % kStages), ss = int(jg % SSTAGES);
@@ -710,6 +887,41 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                     mma_commit(&sempty_bar[ss]);
                     mma_commit(&tfree_bar[s]);
                     if ((jl % kGroup) == kGroup - 1 || jl == un.nloc - 1) mma_commit(&dfull_bar[gg & 1]);
+                    if (SYM && un.c0 + jl >= first_offd) {
+                        // transposed product m into accumulator m & 1:
+                        // D_c = Gamma^T X_hi (hi and lo tiles) + Gamma_hi^T X_lo
+                        // of the unit's tile, M = 64 sources, K = 128 targets
+                        const uint32_t m = og++;
+                        if (m >= 2 && !mbar_wait(&d2free_bar[m & 1], ((m >> 1) - 1) & 1u, wlim)) { ok = false; break; }
+                        if (!xwaited) {
+                            if (!mbar_wait(&xload_bar[xb], (xu >> 1) & 1u, wlim)) { ok = false; break; }
+                            xwaited = true;
+                        }
+                        tc_fence_after();
+                        const uint64_t gd = gdesc0 + uint64_t(uint32_t((m & 1) * kSymGBytes) >> 4);
+                        const uint64_t xd = xdesc0 + uint64_t(uint32_t(xb * kSymXBytes) >> 4);
+                        const uint32_t dj = tmem + uint32_t(kSymDJ + NP * int(m & 1));
+#pragma unroll
+                        for (int ks = 0; ks < 8; ++ks) {
+                            // K step ks: targets 16 ks .. 16 ks + 15 (two core
+                            // matrices along K), X rows of the same targets:
+                            // rows 0..NP-1 X_hi, rows NP..2NP-1 X_lo
+                            const uint64_t ah = gd + uint64_t((ks * 2 * kSymTgtGroupStride) >> 4);
+                            const uint64_t al = ah + uint64_t((kSymGBytes / 2) >> 4);
+                            const uint64_t bh = xd + uint64_t((ks * kStep) >> 4);
+                            const uint64_t bl = bh + uint64_t((NP / 8 * 128) >> 4);
+                            mma_smemA(dj, ah, bh, IDESC_T, ks == 0 ? 0u : 1u);
+                            mma_smemA(dj, ah, bl, IDESC_T, 1u);
+                            mma_smemA(dj, al, bh, IDESC_T, 1u);
+                        }
+                        mma_commit(&gfree_bar[m & 1]);
+                        mma_commit(&d2full_bar[m & 1]);
+                    }
+                }
+                if (!ok) break;
+                if (unit_offd) {
+                    mma_commit(&xfree_bar[xb]);
+                    ++xu;
                 }
                 jbase += un.nloc;
                 gbase += (un.nloc + kGroup - 1) / kGroup;
@@ -727,17 +939,30 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
         if (lane == 0) {
             bool ok = true;
             int64_t jbase = 0, issued = 0;
+            uint32_t xu = 0;
             for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
-                const TcInstance& I = batch.inst[inst_of(batch, u)];
-                const Unit un = unit_of(u - I.unit0, I.splits, I.nchunks, I.cps);
+                const TcInstance& I = batch.inst[SYM ? 0 : inst_of(batch, u)];
+                const Unit un = SYM ? sym_unit_of(I, u) : unit_of(u - I.unit0, I.splits, I.nchunks, I.cps);
                 const uint8_t* img = I.img;
+                if (SYM && un.c0 + un.nloc > 2 * un.tile + 2) {
+                    // split images of X on the unit's own tile (its two chunk
+                    // records' image parts) for the transposed products
+                    const uint32_t xb = xu & 1u;
+                    if (xu >= 2 && !mbar_wait(&xfree_bar[xb], ((xu >> 1) - 1) & 1u, wlim)) { ok = false; break; }
+                    uint8_t* dst = smem + 2 * kSymGBytes + xb * kSymXBytes;
+                    mbar_arrive_expect_tx(&xload_bar[xb], uint32_t(kSymXBytes));
+                    bulk_g2s(dst, img + 2 * un.tile * int64_t(STAGE_BYTES), uint32_t(2 * IMG), &xload_bar[xb]);
+                    bulk_g2s(dst + 2 * IMG, img + (2 * un.tile + 1) * int64_t(STAGE_BYTES), uint32_t(2 * IMG),
+                             &xload_bar[xb]);
+                    ++xu;
+                }
                 for (int jl = 0; jl < un.nloc; ++jl) {
                     const int64_t jg = jbase + jl;
                     const int ss = int(jg % SSTAGES);
                     const int64_t use = jg / SSTAGES;
                     if (use > 0 && !mbar_wait(&sempty_bar[ss], uint32_t((use - 1) & 1), wlim)) { ok = false; break; }
                     issued = jg + 1;
-                    uint8_t* st = smem + ss * STAGE_BYTES;
+                    uint8_t* st = smem + REC_BASE + ss * STAGE_BYTES;
                     const int64_t ch = un.c0 + jl;
                     mbar_arrive_expect_tx(&loaded_bar[ss], uint32_t(STAGE_BYTES));
                     bulk_g2s(st, img + ch * int64_t(STAGE_BYTES), uint32_t(STAGE_BYTES), &loaded_bar[ss]);
@@ -750,6 +975,8 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
             // the pipeline short; bounded in any case)
             for (int64_t jg = issued - 1; jg >= 0 && jg >= issued - SSTAGES; --jg)
                 mbar_wait(&loaded_bar[jg % SSTAGES], uint32_t((jg / SSTAGES) & 1), kWaitLimit);
+            for (int64_t x = int64_t(xu) - 1; SYM && x >= 0 && x >= int64_t(xu) - 2; --x)
+                mbar_wait(&xload_bar[x & 1], uint32_t((x >> 1) & 1), kWaitLimit);
         }
         __syncwarp();
     }
@@ -761,15 +988,16 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
     }
 }
 
-template <int KIND, bool TF32, int NP>
+template <int KIND, bool TF32, int NP, bool SYM>
 cudaError_t launch_batch_np(const TcBatch& b, int sm_count, int* err, cudaStream_t s) {
     constexpr int ESIZE = TF32 ? 4 : 2;
     constexpr int KC = TF32 ? 32 : 64;
     constexpr int STAGE_BYTES = 2 * NP * KC * ESIZE + KC * 12;
+    constexpr int ring = SYM ? kSymRecBase + kSymRecStages * STAGE_BYTES : smem_stages(STAGE_BYTES) * STAGE_BYTES;
     // at least ~100 KB so that no more than two CTAs share an SM (256 TMEM
     // columns each)
-    const int smem = std::max(smem_stages(STAGE_BYTES) * STAGE_BYTES + 1024, 100 * 1024);
-    auto kern = pair_tc_kernel<KIND, TF32, NP>;
+    const int smem = std::max(ring + 1024, 100 * 1024);
+    auto kern = pair_tc_kernel<KIND, TF32, NP, SYM>;
     // set once per instantiation (before any stream capture of a launch)
     static std::once_flag once;
     static cudaError_t attr_error = cudaSuccess;
@@ -781,27 +1009,30 @@ cudaError_t launch_batch_np(const TcBatch& b, int sm_count, int* err, cudaStream
 }
 
 template <int KIND, bool TF32>
-cudaError_t launch_batch_kind(const TcBatch& b, int np, int sm_count, int* err, cudaStream_t s) {
+cudaError_t launch_batch_kind(const TcBatch& b, int np, bool sym, int sm_count, int* err, cudaStream_t s) {
+    if constexpr (!TF32) {
+        if (sym) return launch_batch_np<KIND, false, 16, true>(b, sm_count, err, s);
+    }
     switch (np) {
-        case 16: return launch_batch_np<KIND, TF32, 16>(b, sm_count, err, s);
-        case 32: return launch_batch_np<KIND, TF32, 32>(b, sm_count, err, s);
-        case 48: return launch_batch_np<KIND, TF32, 48>(b, sm_count, err, s);
-        default: return launch_batch_np<KIND, TF32, 64>(b, sm_count, err, s);
+        case 16: return launch_batch_np<KIND, TF32, 16, false>(b, sm_count, err, s);
+        case 32: return launch_batch_np<KIND, TF32, 32, false>(b, sm_count, err, s);
+        case 48: return launch_batch_np<KIND, TF32, 48, false>(b, sm_count, err, s);
+        default: return launch_batch_np<KIND, TF32, 64, false>(b, sm_count, err, s);
     }
 }
 
 template <bool TF32>
-cudaError_t launch_batch_prec(const TcBatch& b, int np, int sm_count, int* err, cudaStream_t s) {
+cudaError_t launch_batch_prec(const TcBatch& b, int np, bool sym, int sm_count, int* err, cudaStream_t s) {
     int kind = b.inst[0].kind;
     for (int i = 1; i < b.ninst; ++i)
         if (b.inst[i].kind != kind) kind = kKindAny;
     switch (kind) {
-        case KL_KERNEL_GAUSS: return launch_batch_kind<KL_KERNEL_GAUSS, TF32>(b, np, sm_count, err, s);
-        case KL_KERNEL_EXP_SEP: return launch_batch_kind<KL_KERNEL_EXP_SEP, TF32>(b, np, sm_count, err, s);
-        case KL_KERNEL_EXP: return launch_batch_kind<KL_KERNEL_EXP, TF32>(b, np, sm_count, err, s);
-        case KL_KERNEL_MATERN32: return launch_batch_kind<KL_KERNEL_MATERN32, TF32>(b, np, sm_count, err, s);
-        case KL_KERNEL_CONST: return launch_batch_kind<KL_KERNEL_CONST, TF32>(b, np, sm_count, err, s);
-        default: return launch_batch_kind<kKindAny, TF32>(b, np, sm_count, err, s);
+        case KL_KERNEL_GAUSS: return launch_batch_kind<KL_KERNEL_GAUSS, TF32>(b, np, sym, sm_count, err, s);
+        case KL_KERNEL_EXP_SEP: return launch_batch_kind<KL_KERNEL_EXP_SEP, TF32>(b, np, sym, sm_count, err, s);
+        case KL_KERNEL_EXP: return launch_batch_kind<KL_KERNEL_EXP, TF32>(b, np, sym, sm_count, err, s);
+        case KL_KERNEL_MATERN32: return launch_batch_kind<KL_KERNEL_MATERN32, TF32>(b, np, sym, sm_count, err, s);
+        case KL_KERNEL_CONST: return launch_batch_kind<KL_KERNEL_CONST, TF32>(b, np, sym, sm_count, err, s);
+        default: return launch_batch_kind<kKindAny, TF32>(b, np, sym, sm_count, err, s);
     }
 }
 
@@ -827,6 +1058,107 @@ __global__ void tc_reduce_kernel(const float2* __restrict__ part, int splits, in
         double s = (double(hi) + double(lo)) * sigma2;
         if (post) s *= post[t];
         Y[c * ldy + t] = s;
+    }
+}
+
+// Adds v (FP32, or an FP32 (hi, lo) pair) into the double-float (hi, lo):
+// error-free two-sum into hi, the error and v's low part into lo.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float v, float vlo) {
+    const float sum = __fadd_rn(hi, v);
+    const float bb = __fsub_rn(sum, hi);
+    const float er = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(v, bb));
+    hi = sum;
+    lo = __fadd_rn(lo, __fadd_rn(er, vlo));
+}
+
+// Symmetric mode, one band of tiles [tile0, tile1). A block serves the
+// 32 / kstride consecutive points t >= tile0 * 128 held by one transposed-sum
+// row segment (lane: point, then column; kstride = k rounded up to 8) with 8
+// threads each (threadIdx.y): thread y sums, as a double-float, the y-th
+// eighth of the direct partial sums of the point's tile (when the tile is in
+// the band) and the y-th eighth of the transposed partial sums of the band's
+// tiles I below the point's tile (I ascending). The eight sums are then added
+// in the order y = 0..7 after the running sum of the earlier bands (acc; none
+// for the first band): a fixed order, with eight loads in flight per thread.
+// Points of the band's tiles are then complete, W = sigma^2 post (hi + lo);
+// later points keep the running sum in acc.
+constexpr int kSymRedSplit = 8;
+__global__ void __launch_bounds__(32 * kSymRedSplit)
+tc_sym_reduce_kernel(const float2* __restrict__ part1, const float* __restrict__ part2,
+                     const int2* __restrict__ tab, int64_t nchunks, int64_t T, int k, int tile0, int tile1,
+                     int64_t unit_begin, int64_t p2_off0, int first, float2* __restrict__ acc, double sigma2,
+                     const double* __restrict__ post, double* __restrict__ Y, int64_t ldy) {
+    __shared__ float2 sh[kSymRedSplit][32];
+    const int kstride = (k + 7) & ~7;
+    const int tpb = 32 / kstride;  // points per block
+    const int64_t t0 = int64_t(tile0) * 128;
+    const int64_t rows = T - t0;
+    const int64_t nblocks = (rows + tpb - 1) / tpb;
+    const int y = threadIdx.y;
+    const int c = threadIdx.x % kstride;
+    for (int64_t b = blockIdx.x; b < nblocks; b += gridDim.x) {
+        const int64_t t = t0 + b * tpb + threadIdx.x / kstride;
+        const bool valid = t < T && c < k;
+        float hi = 0.f, lo = 0.f;
+        if (valid) {
+            const int J = int(t / 128);
+            const int64_t ch = t / 64;
+            const int row = int(t % 64);
+            if (J < tile1) {
+                const int64_t u0 = tab[J].x, n1 = tab[J + 1].x - u0;
+                const int64_t ua = u0 + n1 * y / kSymRedSplit, ub = u0 + n1 * (y + 1) / kSymRedSplit;
+                for (int64_t u = ua; u < ub; ++u) {
+                    const float2 v = part1[((u - unit_begin) * k + c) * 128 + (t % 128)];
+                    df_add(hi, lo, v.x, v.y);
+                }
+            }
+            const int iend = J < tile1 ? J : tile1;
+            const int n2 = iend - tile0;
+            const int ia = tile0 + int(int64_t(n2) * y / kSymRedSplit);
+            const int ib = tile0 + int(int64_t(n2) * (y + 1) / kSymRedSplit);
+            // transposed sums of (I, ch) for I = ia, ia + 1, ...: their indices
+            // grow by nchunks - 4 - 2 I from one I to the next
+            const int64_t step = int64_t(64) * kstride;
+            const float* p2 = part2 + int64_t(row) * kstride + c + (sym_p2_index(ia, ch, nchunks) - p2_off0) * step;
+            int64_t d = (nchunks - 4 - 2 * int64_t(ia)) * step;
+            const int64_t dd = 2 * step;
+            int I = ia;
+            for (; I + 8 <= ib; I += 8) {
+                float v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    v[q] = *p2;
+                    p2 += d;
+                    d -= dd;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) df_add(hi, lo, v[q], 0.f);
+            }
+            for (; I < ib; ++I) {
+                df_add(hi, lo, *p2, 0.f);
+                p2 += d;
+                d -= dd;
+            }
+        }
+        sh[y][threadIdx.x] = make_float2(hi, lo);
+        __syncthreads();
+        if (y == 0 && valid) {
+            float h = 0.f, l = 0.f;
+            if (!first) {
+                const float2 a = acc[c * T + t];
+                h = a.x;
+                l = a.y;
+            }
+            for (int q = 0; q < kSymRedSplit; ++q) df_add(h, l, sh[q][threadIdx.x].x, sh[q][threadIdx.x].y);
+            if (int(t / 128) < tile1) {
+                double v = (double(h) + double(l)) * sigma2;
+                if (post) v *= post[t];
+                Y[c * ldy + t] = v;
+            } else {
+                acc[c * T + t] = make_float2(h, l);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -961,7 +1293,8 @@ cudaError_t tc_launch_batch(TcBatch& b, bool tf32, int np, int sm_count, int* er
         KL_RANGE(err, 1, int, "tc error word");
     }
 #endif
-    return tf32 ? launch_batch_prec<true>(b, np, sm_count, err, s) : launch_batch_prec<false>(b, np, sm_count, err, s);
+    return tf32 ? launch_batch_prec<true>(b, np, false, sm_count, err, s)
+                : launch_batch_prec<false>(b, np, false, sm_count, err, s);
 }
 
 cudaError_t tc_finish(const TcArgs& a, cudaStream_t s, int* launched) {
@@ -975,6 +1308,162 @@ cudaError_t tc_finish(const TcArgs& a, cudaStream_t s, int* launched) {
     tc_reduce_kernel<<<g, 256, 0, s>>>(part, p.splits, a.T, a.k, a.ks.sigma2, a.post, a.Y, a.ldy);
     ++*launched;
     return cudaGetLastError();
+}
+
+// Transposed partial sums of one band: at most this many floats (512 MB);
+// more tiles make more bands.
+constexpr int64_t kSymP2Cap = int64_t(128) << 20;
+
+bool tc_sym_eligible(int64_t T, int k, bool tf32) { return !tf32 && k >= 1 && k <= 16 && T >= 1; }
+
+TcSymPlan tc_sym_plan(int64_t T, int kcap, int sm_count) {
+    TcSymPlan p;
+    p.T = T;
+    p.kcap = kcap;
+    p.sm_count = sm_count;
+    p.nchunks = (T + 63) / 64;
+    p.nt = int((T + 127) / 128);
+    // bands: consecutive tiles while their transposed partial sums fit the cap
+    p.band.push_back(0);
+    int64_t inband = 0;
+    for (int I = 0; I < p.nt; ++I) {
+        const int64_t w = int64_t(64) * kcap * std::max<int64_t>(0, p.nchunks - 2 - 2 * int64_t(I));
+        if (inband > 0 && inband + w > kSymP2Cap) {
+            p.band.push_back(I);
+            inband = 0;
+        }
+        inband += w;
+    }
+    p.band.push_back(p.nt);
+    // units: per band, chunk ranges of cps chunks with cps from the band's
+    // chunk work (about 16 units per CTA of the persistent grid, at least 4
+    // chunks each)
+    p.tab.assign(size_t(p.nt) + 1, make_int2(0, 0));
+    const int64_t grid = 2LL * sm_count;
+    int64_t unit = 0;
+    for (size_t b = 0; b + 1 < p.band.size(); ++b) {
+        int64_t work = 0, p2 = 0;
+        for (int I = p.band[b]; I < p.band[b + 1]; ++I) {
+            work += p.nchunks - 2 * int64_t(I);
+            p2 += std::max<int64_t>(0, p.nchunks - 2 - 2 * int64_t(I));
+        }
+        const int cps = int(std::max<int64_t>(4, (work + 16 * grid - 1) / (16 * grid)));
+        const int64_t u0 = unit;
+        for (int I = p.band[b]; I < p.band[b + 1]; ++I) {
+            p.tab[I] = make_int2(int(unit), cps);
+            unit += (p.nchunks - 2 * int64_t(I) + cps - 1) / cps;
+        }
+        p.max_band_units = std::max(p.max_band_units, unit - u0);
+        p.max_band_p2 = std::max(p.max_band_p2, p2 * 64 * kcap);
+    }
+    p.tab[p.nt] = make_int2(int(unit), 0);
+    // scratch: chunk records | unit table | direct partials (float2 per unit,
+    // column and row) | transposed partials (float) | running sums (float2,
+    // with more than one band)
+    const int stage_bytes = 2 * 16 * 64 * 2 + 64 * 12;
+    p.off_img = 0;
+    p.off_tab = (p.nchunks * stage_bytes + 15) / 16 * 2;
+    p.off_part1 = p.off_tab + (int64_t(p.nt) + 2) / 2 * 2;
+    p.off_part2 = p.off_part1 + p.max_band_units * kcap * 128;
+    p.off_acc = p.off_part2 + (p.max_band_p2 + 1) / 2;
+    p.total = p.off_acc + (p.band.size() > 2 ? T * kcap : 0);
+    return p;
+}
+
+cudaError_t tc_sym_upload(const TcSymPlan& p, double* scratch, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(scratch + p.off_tab, p.tab.data(), p.tab.size() * sizeof(int2),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+}
+
+cudaError_t launch_pair_tc_sym(const TcArgs& a, cudaStream_t s, int* launched) {
+    *launched = 0;
+    const TcSymPlan& p = *a.sym;
+    if (a.tf32 || a.k < 1 || a.k > p.kcap || a.T != p.T || a.S != p.T || a.scratch_len < p.total)
+        return cudaErrorInvalidValue;
+    const float cscale = coord_scale(a.ks);
+    uint8_t* img = reinterpret_cast<uint8_t*>(a.scratch + p.off_img);
+    const int2* tab = reinterpret_cast<const int2*>(a.scratch + p.off_tab);
+    float2* part1 = reinterpret_cast<float2*>(a.scratch + p.off_part1);
+    float* part2 = reinterpret_cast<float*>(a.scratch + p.off_part2);
+    float2* acc = reinterpret_cast<float2*>(a.scratch + p.off_acc);
+    KL_RANGE(a.X, block_extent(a.S, a.k, a.ldx), double, "tc sym convert X");
+    KL_RANGE(a.sx, a.S, float, "tc sym sources x");
+    KL_RANGE(a.sy, a.S, float, "tc sym sources y");
+    KL_RANGE(a.sz, a.S, float, "tc sym sources z");
+    KL_RANGE(a.scratch, p.total, double, "tc sym scratch");
+    KL_RANGE(a.Y, block_extent(a.T, a.k, a.ldy), double, "tc sym Y");
+    KL_RANGE(a.post, a.T, double, "tc sym post");
+    {
+        const int64_t total = p.nchunks * 64 * 16;
+        const int g = int(std::min<int64_t>((total + 255) / 256, int64_t(a.sm_count) * 64));
+        tc_convert_kernel<<<g, 256, 0, s>>>(a.X, a.ldx, a.S, 0, a.k, 16, 64, false, cscale, a.sx, a.sy, a.sz, img,
+                                            p.nchunks);
+        ++*launched;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const int nbands = int(p.band.size()) - 1;
+    for (int b = 0; b < nbands; ++b) {
+        const int tile0 = p.band[b], tile1 = p.band[b + 1];
+        TcBatch batch;
+        batch.ninst = 1;
+        batch.wait_limit = a.wait_limit;
+        TcInstance& I = batch.inst[0];
+        I.tx = a.tx;
+        I.ty = a.ty;
+        I.tz = a.tz;
+        I.srcc = nullptr;
+        I.img = img;
+        I.part = part1;
+        I.T = a.T;
+        I.nchunks = p.nchunks;
+        I.unit0 = 0;
+        I.cps = 0;
+        I.splits = 0;
+        I.kind = a.ks.kind;
+        I.k_total = a.k;
+        I.c0 = 0;
+        I.kc = a.k;
+        I.cscale = cscale;
+        I.sym_tab = tab;
+        I.part2 = part2;
+        I.sym_unit_begin = p.tab[tile0].x;
+        I.sym_p2_off0 = sym_p2_index(tile0, 2 * int64_t(tile0) + 2, p.nchunks);
+        I.sym_tile0 = tile0;
+        I.sym_tile1 = tile1;
+        batch.nunits = int64_t(p.tab[tile1].x) - p.tab[tile0].x;
+#ifdef KL_CHECK_BOUNDS
+        {
+            // direct partials of the band's units, transposed partials of its
+            // tiles (those index the band's own ranges of the scratch)
+            int64_t p2 = 0;
+            for (int t = tile0; t < tile1; ++t) p2 += std::max<int64_t>(0, p.nchunks - 2 - 2 * int64_t(t));
+            if (batch.nunits > p.max_band_units || p2 * 64 * ((a.k + 7) / 8 * 8) > p.max_band_p2) {
+                std::fprintf(stderr, "kl bounds check: tc sym band %d: %lld units (max %lld), %lld transposed sums\n",
+                             b, (long long)batch.nunits, (long long)p.max_band_units,
+                             (long long)(p2 * 64 * ((a.k + 7) / 8 * 8)));
+                return cudaErrorInvalidValue;
+            }
+            KL_RANGE(a.tx, a.T, float, "tc sym targets x");
+            KL_RANGE(a.err, 1, int, "tc error word");
+        }
+#endif
+        cudaError_t e = launch_batch_prec<false>(batch, 16, true, a.sm_count, a.err, s);
+        ++*launched;
+        if (e != cudaSuccess) return e;
+        const int64_t rows = a.T - int64_t(tile0) * 128;
+        const int64_t nblk = (rows + 32 / ((a.k + 7) / 8 * 8) - 1) / (32 / ((a.k + 7) / 8 * 8));
+        const int g = int(std::max<int64_t>(1, std::min<int64_t>(nblk, int64_t(a.sm_count) * 16)));
+        tc_sym_reduce_kernel<<<g, dim3(32, kSymRedSplit), 0, s>>>(part1, part2, tab, p.nchunks, a.T, a.k, tile0, tile1,
+                                               I.sym_unit_begin, I.sym_p2_off0, b == 0, acc, a.ks.sigma2, a.post,
+                                               a.Y, a.ldy);
+        ++*launched;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_pair_tc(const TcArgs& a, cudaStream_t s, int* launched) {

@@ -4,10 +4,13 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "kl_internal.h"
 
 namespace kl {
+
+struct TcSymPlan;
 
 struct TcArgs {
     const float *tx, *ty, *tz;  // targets (T), FP32
@@ -26,6 +29,10 @@ struct TcArgs {
     int sm_count;
     int* err;  // device word set when a bounded wait inside the kernel gives up
     long long wait_limit;  // clock cycles per pipeline wait (0: default, about a second)
+    // symmetric mode (Galerkin: targets = sources, same coordinates): the plan
+    // of launch_pair_tc_sym, whose scratch is `scratch`; null for the dense
+    // product
+    const TcSymPlan* sym;
 };
 
 // One pairwise product inside a persistent launch: its target points, the
@@ -40,6 +47,14 @@ struct TcInstance {
     int64_t T, nchunks, unit0;
     int cps, splits, kind, k_total, c0, kc;
     float cscale;
+    // symmetric mode only: per tile {first unit, chunks per unit} (one entry
+    // more than tiles, global unit numbering), the launch's first unit and
+    // tile range [sym_tile0, sym_tile1), the transposed partial sums and the
+    // index of the band's first one
+    const int2* sym_tab;
+    float* part2;
+    int64_t sym_unit_begin, sym_p2_off0;
+    int sym_tile0, sym_tile1;
 };
 // Instances of one launch (same precision and N rounded to 16); passed by
 // value as a kernel parameter.
@@ -67,6 +82,33 @@ int64_t tc_scratch_doubles(int64_t T, int64_t S, int k, int sm_count);
 // *launched receives the number of kernels launched. A bounded wait that gives
 // up inside the kernel sets *a.err (read by the caller after a synchronisation).
 cudaError_t launch_pair_tc(const TcArgs& a, cudaStream_t s, int* launched);
+
+// Symmetric pairwise product (Galerkin form: Gamma over one point set is
+// symmetric, Sec. 3.1). Tiles of 128 points, chunks of 64: tile I takes the
+// source chunks from its own first chunk 2I onwards; each kernel tile of a
+// chunk c >= 2I + 2 is evaluated once and applied twice, W_I += Gamma_Ic X_c
+// and W_c += Gamma_Ic^T X_I. Split BF16 and at most 16 vectors per product.
+// The work units of a tile (chunk ranges of cps chunks each) are numbered
+// tile after tile; tiles are grouped into bands whose transposed partial
+// sums fit a fixed cap, one launch and one reduction per band.
+struct TcSymPlan {
+    int64_t T = 0, nchunks = 0;
+    int nt = 0, kcap = 0, sm_count = 0;
+    std::vector<int2> tab;      // per tile {first unit, cps}; tab[nt] = {units, 0}
+    std::vector<int> band;      // band boundaries in tiles (bands + 1 entries)
+    int64_t max_band_units = 0;
+    int64_t max_band_p2 = 0;    // transposed partial sums of the largest band (floats, kcap columns)
+    // scratch layout (doubles from the start of the scratch)
+    int64_t off_img = 0, off_tab = 0, off_part1 = 0, off_part2 = 0, off_acc = 0, total = 0;
+};
+// Whether the symmetric product applies to T points and blocks of k vectors.
+bool tc_sym_eligible(int64_t T, int k, bool tf32);
+// Plan for blocks of at most kcap vectors (kcap <= 16).
+TcSymPlan tc_sym_plan(int64_t T, int kcap, int sm_count);
+// Copies the unit table into the scratch (synchronous; before any capture).
+cudaError_t tc_sym_upload(const TcSymPlan& p, double* scratch, cudaStream_t s);
+// Conversion, one tcgen05 launch and one ordered reduction per band.
+cudaError_t launch_pair_tc_sym(const TcArgs& a, cudaStream_t s, int* launched);
 
 // Reduction of split partials shared with the CUDA-core kernels.
 cudaError_t launch_pair_reduce(const double* part, int splits, int64_t T, int k, double sigma2,

@@ -44,6 +44,10 @@ def _alone(kl, p):
     import torch
     h = kl.kl_create(p, torch.cuda.current_stream())
     try:
+        # served solves share batched launches of the dense pairwise form; a
+        # stand-alone Galerkin handle would take the symmetric form (each
+        # pair once, another summation order): compare like with like
+        kl.kl_debug_set(h, kl.KL_DEBUG_PAIR_DENSE, 1)
         lam = np.zeros(M)
         rc = kl.kl_eigs(h, M, 0.0, lam, None, 0, 0)
     finally:
