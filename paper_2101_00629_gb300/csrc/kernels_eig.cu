@@ -113,21 +113,21 @@ __device__ inline void house(const R* x, int len, R* v, R& beta) {
 
 // Deflation test for the subdiagonal entry (l, l-1).
 template <class R>
-__device__ inline bool deflatable(const R* A, int n, int l, R anorm) {
-    R s = fabs(A[(l - 1) + int64_t(l - 1) * n]) + fabs(A[l + int64_t(l) * n]);
+__device__ inline bool deflatable(const R* A, int n, int ld, int l, R anorm) {
+    R s = fabs(A[(l - 1) + int64_t(l - 1) * ld]) + fabs(A[l + int64_t(l) * ld]);
     if (s == R(0.0)) s = anorm;
-    const R sub = fabs(A[l + int64_t(l - 1) * n]);
+    const R sub = fabs(A[l + int64_t(l - 1) * ld]);
     // absolute test at roundoff of the whole matrix: next to eigenvalues that
     // are themselves at roundoff level a relative test can never be met
     if (sub <= EigNum<R>::abs_defl * R(n) * EigNum<R>::eps * anorm) return true;
     // relative test, confirmed by the more conservative Ahues-Kressner
     // criterion (off-diagonal product against the gap of the diagonal pair)
     if (sub <= EigNum<R>::eps * s) {
-        const R up = fabs(A[(l - 1) + int64_t(l) * n]);
+        const R up = fabs(A[(l - 1) + int64_t(l) * ld]);
         const R ab = fmax(sub, up), ba = fmin(sub, up);
-        const R dd = fabs(A[(l - 1) + int64_t(l - 1) * n] - A[l + int64_t(l) * n]);
-        const R aa = fmax(fabs(A[l + int64_t(l) * n]), dd);
-        const R bb = fmin(fabs(A[l + int64_t(l) * n]), dd);
+        const R dd = fabs(A[(l - 1) + int64_t(l - 1) * ld] - A[l + int64_t(l) * ld]);
+        const R aa = fmax(fabs(A[l + int64_t(l) * ld]), dd);
+        const R bb = fmin(fabs(A[l + int64_t(l) * ld]), dd);
         const R ss = aa + ab;
         return ba * (ab / ss) <= fmax(EigNum<R>::tiny, EigNum<R>::eps * (bb * (aa / ss)));
     }
@@ -151,11 +151,11 @@ __device__ inline int group_size(int items) {
 // T22-invariant subspace and Q is the orthogonal factor of their QR
 // factorisation (Householder).
 template <class R>
-__device__ void swap_transform(const R* A, int n, int k, int n1, int n2, R anorm, R* Qm) {
+__device__ void swap_transform(const R* A, int ld, int k, int n1, int n2, R anorm, R* Qm) {
     const int m = n1 + n2;
     if (n1 == 1 && n2 == 1) {
-        const R a = A[k + int64_t(k) * n], d = A[(k + 1) + int64_t(k + 1) * n];
-        const R b = A[k + int64_t(k + 1) * n];
+        const R a = A[k + int64_t(k) * ld], d = A[(k + 1) + int64_t(k + 1) * ld];
+        const R b = A[k + int64_t(k + 1) * ld];
         const R r = hypot(b, d - a);
         const R c = r > R(0.0) ? b / r : R(1.0), sn = r > R(0.0) ? (d - a) / r : R(0.0);
         Qm[0] = c;
@@ -171,9 +171,9 @@ __device__ void swap_transform(const R* A, int n, int k, int n1, int n2, R anorm
     for (int j = 0; j < n2; ++j)
         for (int i = 0; i < n1; ++i) {
             const int row = i + n1 * j;
-            for (int i2 = 0; i2 < n1; ++i2) K[row + pdim * (i2 + n1 * j)] += A[(k + i) + int64_t(k + i2) * n];
-            for (int j2 = 0; j2 < n2; ++j2) K[row + pdim * (i + n1 * j2)] -= A[(k + n1 + j2) + int64_t(k + n1 + j) * n];
-            x[row] = A[(k + i) + int64_t(k + n1 + j) * n];
+            for (int i2 = 0; i2 < n1; ++i2) K[row + pdim * (i2 + n1 * j)] += A[(k + i) + int64_t(k + i2) * ld];
+            for (int j2 = 0; j2 < n2; ++j2) K[row + pdim * (i + n1 * j2)] -= A[(k + n1 + j2) + int64_t(k + n1 + j) * ld];
+            x[row] = A[(k + i) + int64_t(k + n1 + j) * ld];
         }
     // Gaussian elimination with partial pivoting; a pivot below eps ||T|| is
     // replaced by that bound (the blocks have close eigenvalues)
@@ -245,7 +245,7 @@ __device__ void swap_transform(const R* A, int n, int k, int n1, int n2, R anorm
 // ints: 2n ints of scratch (block starts, pair positions, pair sizes/flags);
 // ord: 8n doubles (a 4 x 4 transform per pair).
 template <class R>
-__device__ void order_schur(R* A, R* Z, int n, R anorm, R* ints_d, R* ord, int* oob) {
+__device__ void order_schur(R* A, R* Z, int n, int ld, R anorm, R* ints_d, R* ord, int* oob) {
     constexpr int NT = kEigThreads;
     __shared__ int s_wsum[kEigWarps];
     int* bstart = reinterpret_cast<int*>(ints_d);  // n
@@ -258,7 +258,7 @@ __device__ void order_schur(R* A, R* Z, int n, R anorm, R* ints_d, R* ord, int* 
         // block starts: i = 0 or a zero subdiagonal entry (i, i-1)
         int cnt = 0;
         for (int i = tid * ipt; i < min(n, (tid + 1) * ipt); ++i)
-            cnt += (i == 0 || A[i + int64_t(i - 1) * n] == R(0.0));
+            cnt += (i == 0 || A[i + int64_t(i - 1) * ld] == R(0.0));
         int incl = cnt;
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(kFull, incl, o);
@@ -272,7 +272,7 @@ __device__ void order_schur(R* A, R* Z, int n, R anorm, R* ints_d, R* ord, int* 
             nb += s_wsum[w];
         }
         for (int i = tid * ipt; i < min(n, (tid + 1) * ipt); ++i)
-            if (i == 0 || A[i + int64_t(i - 1) * n] == R(0.0)) bstart[pos++] = i;
+            if (i == 0 || A[i + int64_t(i - 1) * ld] == R(0.0)) bstart[pos++] = i;
         __syncthreads();
         const int par = round & 1;
         const int npairs = max(0, (nb - par) / 2);
@@ -282,9 +282,9 @@ __device__ void order_schur(R* A, R* Z, int n, R anorm, R* ints_d, R* ord, int* 
             const int k = bstart[b0], k2 = bstart[b0 + 1];
             const int k3 = (b0 + 2 < nb) ? bstart[b0 + 2] : n;
             const int n1 = k2 - k, n2 = k3 - k2;
-            const R key1 = n1 == 1 ? A[k + int64_t(k) * n] : R(0.5) * (A[k + int64_t(k) * n] + A[(k + 1) + int64_t(k + 1) * n]);
-            const R key2 = n2 == 1 ? A[k2 + int64_t(k2) * n]
-                                        : R(0.5) * (A[k2 + int64_t(k2) * n] + A[(k2 + 1) + int64_t(k2 + 1) * n]);
+            const R key1 = n1 == 1 ? A[k + int64_t(k) * ld] : R(0.5) * (A[k + int64_t(k) * ld] + A[(k + 1) + int64_t(k + 1) * ld]);
+            const R key2 = n2 == 1 ? A[k2 + int64_t(k2) * ld]
+                                        : R(0.5) * (A[k2 + int64_t(k2) * ld] + A[(k2 + 1) + int64_t(k2 + 1) * ld]);
             int f = key2 > key1;
 #ifdef KL_CHECK_BOUNDS
             // pair and block indices stay inside the scratch (n / 2 pairs) and
@@ -295,11 +295,11 @@ __device__ void order_schur(R* A, R* Z, int n, R anorm, R* ints_d, R* ord, int* 
             }
 #endif
             if (f) {
-                swap_transform(A, n, k, n1, n2, anorm, ord + 16 * int64_t(p));
+                swap_transform(A, ld, k, n1, n2, anorm, ord + 16 * int64_t(p));
                 if (n1 == 1 && n2 == 1) {
                     // exact exchange of the diagonal pair
-                    ord[16 * int64_t(p) + 4] = A[k + int64_t(k) * n];
-                    ord[16 * int64_t(p) + 5] = A[k2 + int64_t(k2) * n];
+                    ord[16 * int64_t(p) + 4] = A[k + int64_t(k) * ld];
+                    ord[16 * int64_t(p) + 5] = A[k2 + int64_t(k2) * ld];
                 }
             }
             pk[p] = k;
@@ -321,11 +321,11 @@ __device__ void order_schur(R* A, R* Z, int n, R anorm, R* ints_d, R* ord, int* 
             if (j < k) continue;
             const R* Qm = ord + 16 * int64_t(p);
             R old[4];
-            for (int t = 0; t < m; ++t) old[t] = A[(k + t) + int64_t(j) * n];
+            for (int t = 0; t < m; ++t) old[t] = A[(k + t) + int64_t(j) * ld];
             for (int t = 0; t < m; ++t) {
                 R acc = R(0.0);
                 for (int u2 = 0; u2 < m; ++u2) acc = fma(Qm[u2 + m * t], old[u2], acc);
-                A[(k + t) + int64_t(j) * n] = acc;
+                A[(k + t) + int64_t(j) * ld] = acc;
             }
         }
         __syncthreads();
@@ -341,11 +341,11 @@ __device__ void order_schur(R* A, R* Z, int n, R anorm, R* ints_d, R* ord, int* 
             if (i2 < n && r >= k + m) continue;
             const R* Qm = ord + 16 * int64_t(p);
             R old[4];
-            for (int t = 0; t < m; ++t) old[t] = M[r + int64_t(k + t) * n];
+            for (int t = 0; t < m; ++t) old[t] = M[r + int64_t(k + t) * ld];
             for (int t = 0; t < m; ++t) {
                 R acc = R(0.0);
                 for (int u2 = 0; u2 < m; ++u2) acc = fma(old[u2], Qm[u2 + m * t], acc);
-                M[r + int64_t(k + t) * n] = acc;
+                M[r + int64_t(k + t) * ld] = acc;
             }
         }
         __syncthreads();
@@ -356,10 +356,10 @@ __device__ void order_schur(R* A, R* Z, int n, R anorm, R* ints_d, R* ord, int* 
             if (!(info & 1)) continue;
             const int k = pk[p], n1 = (info >> 1) & 3, n2 = (info >> 3) & 3, m = n1 + n2;
             for (int i = k + n2; i < k + m; ++i)
-                for (int j = k; j < k + n2; ++j) A[i + int64_t(j) * n] = R(0.0);
+                for (int j = k; j < k + n2; ++j) A[i + int64_t(j) * ld] = R(0.0);
             if (n1 == 1 && n2 == 1) {
-                A[k + int64_t(k) * n] = ord[16 * int64_t(p) + 5];
-                A[(k + 1) + int64_t(k + 1) * n] = ord[16 * int64_t(p) + 4];
+                A[k + int64_t(k) * ld] = ord[16 * int64_t(p) + 5];
+                A[(k + 1) + int64_t(k + 1) * ld] = ord[16 * int64_t(p) + 4];
             }
         }
         __syncthreads();
@@ -381,17 +381,22 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
     R* smem_a = reinterpret_cast<R*>(smem_raw);
     R* work = reinterpret_cast<R*>(work_d);
     const int64_t nn = int64_t(n) * n;
+    // A, Z and X are stored with leading dimension n + 1: a row of a matrix
+    // (consecutive columns, one per thread) then spreads over the shared-
+    // memory banks instead of hitting one bank n apart
+    const int ld = n + 1;
+    const int64_t nl = int64_t(ld) * n;
     R* A = smem_level >= 1 ? smem_a : work;
-    R* Z = smem_level == 2 ? smem_a + nn : work + nn;
-    R* X = smem_level == 2 ? smem_a + 2 * nn : work + 2 * nn;
+    R* Z = smem_level == 2 ? smem_a + nl : work + nl;
+    R* X = smem_level == 2 ? smem_a + 2 * nl : work + 2 * nl;
     // Householder vector / integer scratch (2n), ordering scratch (8n)
-    R* hv = smem_level == 2 ? smem_a + 3 * nn : (smem_level == 1 ? smem_a + nn : work + 3 * nn + 2 * n);
-    R* wr = work + 3 * nn;
+    R* hv = smem_level == 2 ? smem_a + 3 * nl : (smem_level == 1 ? smem_a + nl : work + 3 * nl + 2 * n);
+    R* wr = work + 3 * nl;
     R* wi = wr + n;
-    R* ord = smem_level == 2 ? smem_a + 3 * nn + 2 * n : work + 3 * nn + 4 * n;
+    R* ord = smem_level == 2 ? smem_a + 3 * nl + 2 * n : work + 3 * nl + 4 * n;
     __shared__ R s_red[kEigWarps];
     __shared__ int s_redi[kEigWarps];
-    __shared__ R s_v[3], s_x[3];
+    __shared__ R s_x[3], s_vb[2][3], s_bb[2];
     __shared__ R s_beta, s_sh, s_th;
     __shared__ int s_l, s_u, s_its, s_fail, s_action, s_oob;
     const int tid = threadIdx.x;
@@ -401,8 +406,8 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
     for (int64_t e = tid; e < nn; e += NT) {
         const int i = int(e % n), j = int(e / n);
         const R a = sym ? R(0.5) * (H[e] + H[j + int64_t(i) * n]) : H[e];
-        A[e] = a;
-        Z[e] = (i == j) ? R(1.0) : R(0.0);
+        A[i + int64_t(j) * ld] = a;
+        Z[i + int64_t(j) * ld] = (i == j) ? R(1.0) : R(0.0);
         amax = fmax(amax, fabs(a));
     }
     const R anorm = blk_max(amax, s_red);  // also orders the stores above
@@ -412,7 +417,7 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         const int len = n - k - 1;
         R ss = R(0.0);
         for (int t = tid; t < len; t += NT) {
-            const R x = A[(k + 1 + t) + int64_t(k) * n];
+            const R x = A[(k + 1 + t) + int64_t(k) * ld];
             hv[t] = x;
             ss = fma(x, x, ss);
         }
@@ -436,11 +441,11 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                 const int c = base + tid / g, p = tid % g;
                 R s = R(0.0);
                 if (c < ncols)
-                    for (int t = p; t < len; t += g) s = fma(hv[t], A[(k + 1 + t) + int64_t(k + c) * n], s);
+                    for (int t = p; t < len; t += g) s = fma(hv[t], A[(k + 1 + t) + int64_t(k + c) * ld], s);
                 for (int o = g / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
                 s *= beta;
                 if (c < ncols)
-                    for (int t = p; t < len; t += g) A[(k + 1 + t) + int64_t(k + c) * n] -= s * hv[t];
+                    for (int t = p; t < len; t += g) A[(k + 1 + t) + int64_t(k + c) * ld] -= s * hv[t];
             }
             __syncthreads();
             // right: all rows of A and of Z, columns k+1..n-1
@@ -452,15 +457,15 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                 const int i = it < n ? it : it - n;
                 R s = R(0.0);
                 if (it < items)
-                    for (int t = p; t < len; t += g2) s = fma(M[i + int64_t(k + 1 + t) * n], hv[t], s);
+                    for (int t = p; t < len; t += g2) s = fma(M[i + int64_t(k + 1 + t) * ld], hv[t], s);
                 for (int o = g2 / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
                 s *= beta;
                 if (it < items)
-                    for (int t = p; t < len; t += g2) M[i + int64_t(k + 1 + t) * n] -= s * hv[t];
+                    for (int t = p; t < len; t += g2) M[i + int64_t(k + 1 + t) * ld] -= s * hv[t];
             }
         }
         __syncthreads();
-        for (int i = k + 2 + tid; i < n; i += NT) A[i + int64_t(k) * n] = R(0.0);
+        for (int i = k + 2 + tid; i < n; i += NT) A[i + int64_t(k) * ld] = R(0.0);
         __syncthreads();
     }
 
@@ -479,7 +484,7 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         // largest l <= u with a negligible subdiagonal (l, l-1); 0 if none
         int cand = 0;
         for (int l = u0 - tid; l >= 1; l -= NT)
-            if (deflatable(A, n, l, anorm)) {
+            if (deflatable(A, n, ld, l, anorm)) {
                 cand = l;
                 break;
             }
@@ -487,7 +492,7 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         if (tid == 0) {
             const int u = u0;
             int l = cand;
-            if (l >= 1) A[l + int64_t(l - 1) * n] = R(0.0);
+            if (l >= 1) A[l + int64_t(l - 1) * ld] = R(0.0);
             int action = (l == u) ? 1 : (l == u - 1) ? 2 : 3;  // 1: one root, 2: 2x2 block, 3: Francis step
             if (action == 3 && s_its >= 30 && s_its % 10 == 5) {
                 // A window that resists the shifts for 30 iterations is a
@@ -501,9 +506,9 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                 // 1e-10 * ||H||).
                 int m = l + 1;
                 for (int i = l + 2; i <= u; ++i)
-                    if (fabs(A[i + int64_t(i - 1) * n]) < fabs(A[m + int64_t(m - 1) * n])) m = i;
-                if (fabs(A[m + int64_t(m - 1) * n]) <= EigNum<R>::split * anorm) {
-                    A[m + int64_t(m - 1) * n] = R(0.0);
+                    if (fabs(A[i + int64_t(i - 1) * ld]) < fabs(A[m + int64_t(m - 1) * ld])) m = i;
+                if (fabs(A[m + int64_t(m - 1) * ld]) <= EigNum<R>::split * anorm) {
+                    A[m + int64_t(m - 1) * ld] = R(0.0);
                     action = 5;  // split: look for deflations again
                     s_its = s_its + 1;
                 }
@@ -515,28 +520,28 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                 } else {
                     R sh, th;
                     if (s_its > 0 && s_its % 10 == 0) {  // exceptional shift
-                        const R ex = fabs(A[u + int64_t(u - 1) * n]) + fabs(A[(u - 1) + int64_t(u - 2) * n]);
-                        const R c = A[u + int64_t(u) * n] + R(0.75) * ex;
+                        const R ex = fabs(A[u + int64_t(u - 1) * ld]) + fabs(A[(u - 1) + int64_t(u - 2) * ld]);
+                        const R c = A[u + int64_t(u) * ld] + R(0.75) * ex;
                         sh = R(2.0) * c;
                         th = c * c + R(0.4375) * ex * ex;
                     } else {
-                        const R a = A[(u - 1) + int64_t(u - 1) * n], b = A[(u - 1) + int64_t(u) * n];
-                        const R c = A[u + int64_t(u - 1) * n], d = A[u + int64_t(u) * n];
+                        const R a = A[(u - 1) + int64_t(u - 1) * ld], b = A[(u - 1) + int64_t(u) * ld];
+                        const R c = A[u + int64_t(u - 1) * ld], d = A[u + int64_t(u) * ld];
                         sh = a + d;
                         th = a * d - b * c;
                     }
                     s_its = s_its + 1;
                     // first column of (H - s1)(H - s2) restricted to the window
-                    const R h11 = A[l + int64_t(l) * n], h12 = A[l + int64_t(l + 1) * n];
-                    const R h21 = A[(l + 1) + int64_t(l) * n], h22 = A[(l + 1) + int64_t(l + 1) * n];
-                    const R h32 = A[(l + 2) + int64_t(l + 1) * n];
+                    const R h11 = A[l + int64_t(l) * ld], h12 = A[l + int64_t(l + 1) * ld];
+                    const R h21 = A[(l + 1) + int64_t(l) * ld], h22 = A[(l + 1) + int64_t(l + 1) * ld];
+                    const R h32 = A[(l + 2) + int64_t(l + 1) * ld];
                     s_x[0] = h11 * h11 + h12 * h21 - sh * h11 + th;
                     s_x[1] = h21 * (h11 + h22 - sh);
                     s_x[2] = h21 * h32;
                 }
             }
             if (action == 1) {
-                wr[u] = A[u + int64_t(u) * n];
+                wr[u] = A[u + int64_t(u) * ld];
                 wi[u] = R(0.0);
             }
             s_l = l;
@@ -560,8 +565,8 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             __shared__ R s_cs, s_sn;
             __shared__ int s_rot;
             if (tid == 0) {
-                const R a = A[(u - 1) + int64_t(u - 1) * n], b = A[(u - 1) + int64_t(u) * n];
-                const R c = A[u + int64_t(u - 1) * n], d = A[u + int64_t(u) * n];
+                const R a = A[(u - 1) + int64_t(u - 1) * ld], b = A[(u - 1) + int64_t(u) * ld];
+                const R c = A[u + int64_t(u - 1) * ld], d = A[u + int64_t(u) * ld];
                 const R p = R(0.5) * (a - d);
                 // a symmetric matrix has real eigenvalues: rounding may leave
                 // b c slightly negative, which must not create a complex pair
@@ -593,25 +598,25 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                 // rounding remnants and are never read: the updates skip them
                 const int jend = sym ? min(n, u + 2) : n;
                 for (int j = u - 1 + tid; j < jend; j += NT) {
-                    const R x1 = A[(u - 1) + int64_t(j) * n], x2 = A[u + int64_t(j) * n];
-                    A[(u - 1) + int64_t(j) * n] = cs * x1 + sn * x2;
-                    A[u + int64_t(j) * n] = -sn * x1 + cs * x2;
+                    const R x1 = A[(u - 1) + int64_t(j) * ld], x2 = A[u + int64_t(j) * ld];
+                    A[(u - 1) + int64_t(j) * ld] = cs * x1 + sn * x2;
+                    A[u + int64_t(j) * ld] = -sn * x1 + cs * x2;
                 }
                 __syncthreads();
                 const int i0 = sym ? max(0, u - 2) : 0;
                 for (int e = tid; e < u + 1 - i0 + n; e += NT) {
                     R* M = e <= u - i0 ? A : Z;
                     const int i = e <= u - i0 ? e + i0 : e - (u + 1 - i0);
-                    const R x1 = M[i + int64_t(u - 1) * n], x2 = M[i + int64_t(u) * n];
-                    M[i + int64_t(u - 1) * n] = cs * x1 + sn * x2;
-                    M[i + int64_t(u) * n] = -sn * x1 + cs * x2;
+                    const R x1 = M[i + int64_t(u - 1) * ld], x2 = M[i + int64_t(u) * ld];
+                    M[i + int64_t(u - 1) * ld] = cs * x1 + sn * x2;
+                    M[i + int64_t(u) * ld] = -sn * x1 + cs * x2;
                 }
                 __syncthreads();
                 if (tid == 0) {
-                    A[u + int64_t(u - 1) * n] = R(0.0);
+                    A[u + int64_t(u - 1) * ld] = R(0.0);
                     // diagonal entries now hold the two real eigenvalues
-                    wr[u - 1] = A[(u - 1) + int64_t(u - 1) * n];
-                    wr[u] = A[u + int64_t(u) * n];
+                    wr[u - 1] = A[(u - 1) + int64_t(u - 1) * ld];
+                    wr[u] = A[u + int64_t(u) * ld];
                 }
             }
             if (tid == 0) {
@@ -621,25 +626,33 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             __syncthreads();
             continue;
         }
-        // Francis R-shift step on the window [l, u] (size ns >= 3)
+        // Francis R-shift step on the window [l, u] (size ns >= 3). The
+        // reflector of bulge step kk + 1 is formed from column r0 of rows
+        // r0 + 1 .. r0 + 3 once step kk's right application has updated them:
+        // warp 0 applies step kk to exactly those rows (lanes 1..3) and hands
+        // the new entries to lane 0, which forms the next reflector while the
+        // other warps apply step kk to the remaining rows of A and to Z. Two
+        // block barriers per bulge step instead of three, and the reflector's
+        // chain of dependent FP64 operations runs beside the applications.
+        // Reflectors alternate between two shared slots (the next one is
+        // written while the current one is still being read).
         ++total_its;
         const int ns = u - l + 1;
+        if (tid == 0) {
+            R v[3], beta;
+            house(s_x, 3, v, beta);
+            for (int t = 0; t < 3; ++t) s_vb[0][t] = v[t];
+            s_bb[0] = beta;
+        }
+        __syncthreads();
         for (int kk = 0; kk <= ns - 3; ++kk) {
-            if (tid == 0) {
-                R v[3], beta;
-                house(s_x, 3, v, beta);
-                s_v[0] = v[0];
-                s_v[1] = v[1];
-                s_v[2] = v[2];
-                s_beta = beta;
-            }
-            __syncthreads();
-            const R v0 = s_v[0], v1 = s_v[1], v2 = s_v[2], beta = s_beta;
+            const int b = kk & 1;
+            const R v0 = s_vb[b][0], v1 = s_vb[b][1], v2 = s_vb[b][2], beta = s_bb[b];
             const int r0 = l + kk;
             const int c0 = l + (kk > 0 ? kk - 1 : 0);
             const int jend = sym ? min(n, r0 + 5) : n;
             for (int j = c0 + tid; j < jend; j += NT) {
-                R* col = A + int64_t(j) * n + r0;
+                R* col = A + int64_t(j) * ld + r0;
                 const R a0 = col[0], a1 = col[1], a2 = col[2];
                 const R s = beta * fma(v2, a2, fma(v1, a1, v0 * a0));
                 col[0] = a0 - s * v0;
@@ -647,38 +660,57 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                 col[2] = a2 - s * v2;
             }
             __syncthreads();
-            const int rmax = min(l + kk + 3, u);  // last row of A touched (inclusive)
+            // rows of A touched: i0 .. rmax = min(r0 + 3, u); rows r0 + 1 ..
+            // rmax (nq of them, 2 or 3) go to warp 0, rows i0 .. r0 and all
+            // of Z to the other warps
+            const int rmax = min(r0 + 3, u);
+            const int nq = rmax - r0;
             const int i0 = sym ? max(0, r0 - 2) : 0;  // first row of A touched
-            for (int e = tid; e < rmax + 1 - i0 + n; e += NT) {
-                R* M = e <= rmax - i0 ? A : Z;
-                const int i = e <= rmax - i0 ? e + i0 : e - (rmax + 1 - i0);
-                R* row = M + i + int64_t(r0) * n;
-                const R a0 = row[0], a1 = row[n], a2 = row[2 * int64_t(n)];
-                const R s = beta * fma(a2, v2, fma(a1, v1, a0 * v0));
-                row[0] = a0 - s * v0;
-                row[n] = a1 - s * v1;
-                row[2 * int64_t(n)] = a2 - s * v2;
+            if (tid < 32) {
+                R xnew = R(0.0);
+                if (tid >= 1 && tid <= nq) {
+                    R* row = A + (r0 + tid) + int64_t(r0) * ld;
+                    const R a0 = row[0], a1 = row[ld], a2 = row[2 * int64_t(ld)];
+                    const R s = beta * fma(a2, v2, fma(a1, v1, a0 * v0));
+                    xnew = a0 - s * v0;
+                    row[0] = xnew;
+                    row[ld] = a1 - s * v1;
+                    row[2 * int64_t(ld)] = a2 - s * v2;
+                }
+                R xx[3];
+                xx[0] = __shfl_sync(kFull, xnew, 1);
+                xx[1] = __shfl_sync(kFull, xnew, 2);
+                xx[2] = __shfl_sync(kFull, xnew, 3);
+                if (tid == 0) {
+                    // the 2-element reflector of the window's end after the
+                    // last 3-element one
+                    R v[3], bt;
+                    house(xx, kk < ns - 3 ? 3 : 2, v, bt);
+                    for (int t = 0; t < 3; ++t) s_vb[b ^ 1][t] = v[t];
+                    s_bb[b ^ 1] = bt;
+                }
+            } else {
+                const int na = r0 + 1 - i0;
+                for (int e = tid - 32; e < na + n; e += NT - 32) {
+                    R* M = e < na ? A : Z;
+                    const int i = e < na ? e + i0 : e - na;
+                    R* row = M + i + int64_t(r0) * ld;
+                    const R a0 = row[0], a1 = row[ld], a2 = row[2 * int64_t(ld)];
+                    const R s = beta * fma(a2, v2, fma(a1, v1, a0 * v0));
+                    row[0] = a0 - s * v0;
+                    row[ld] = a1 - s * v1;
+                    row[2 * int64_t(ld)] = a2 - s * v2;
+                }
             }
             __syncthreads();
-            if (tid == 0) {
-                s_x[0] = A[(r0 + 1) + int64_t(r0) * n];
-                s_x[1] = A[(r0 + 2) + int64_t(r0) * n];
-                s_x[2] = (kk < ns - 3) ? A[(r0 + 3) + int64_t(r0) * n] : R(0.0);
-            }
         }
-        if (tid == 0) {
-            R v[3], beta;
-            house(s_x, 2, v, beta);
-            s_v[0] = v[0];
-            s_v[1] = v[1];
-            s_beta = beta;
-        }
-        __syncthreads();
         {
-            const R v0 = s_v[0], v1 = s_v[1], beta = s_beta;
+            // the last reflector (2 elements, rows u - 1 and u)
+            const int b = (ns - 2) & 1;
+            const R v0 = s_vb[b][0], v1 = s_vb[b][1], beta = s_bb[b];
             const int jend = sym ? min(n, u + 2) : n;
             for (int j = u - 2 + tid; j < jend; j += NT) {
-                R* col = A + int64_t(j) * n + (u - 1);
+                R* col = A + int64_t(j) * ld + (u - 1);
                 const R a0 = col[0], a1 = col[1];
                 const R s = beta * fma(v1, a1, v0 * a0);
                 col[0] = a0 - s * v0;
@@ -689,11 +721,11 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             for (int e = tid; e < u + 1 - i0 + n; e += NT) {
                 R* M = e <= u - i0 ? A : Z;
                 const int i = e <= u - i0 ? e + i0 : e - (u + 1 - i0);
-                R* row = M + i + int64_t(u - 1) * n;
-                const R a0 = row[0], a1 = row[n];
+                R* row = M + i + int64_t(u - 1) * ld;
+                const R a0 = row[0], a1 = row[ld];
                 const R s = beta * fma(a1, v1, a0 * v0);
                 row[0] = a0 - s * v0;
-                row[n] = a1 - s * v1;
+                row[ld] = a1 - s * v1;
             }
             __syncthreads();
         }
@@ -702,12 +734,12 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         if (sym) {
             for (int e = tid; e < 2 * ns; e += NT) {
                 const int j = l + e / 2, i = j + 2 + e % 2;
-                if (i <= u) A[i + int64_t(j) * n] = R(0.0);
+                if (i <= u) A[i + int64_t(j) * ld] = R(0.0);
             }
         } else {
             for (int e = tid; e < ns * ns; e += NT) {
                 const int i = l + e % ns, j = l + e / ns;
-                if (i > j + 1) A[i + int64_t(j) * n] = R(0.0);
+                if (i > j + 1) A[i + int64_t(j) * ld] = R(0.0);
             }
         }
         __syncthreads();
@@ -720,10 +752,10 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         // permutation of the Schur vectors (stable for ties) ----
         int* rk = reinterpret_cast<int*>(hv);
         for (int i = tid; i < n; i += NT) {
-            const R di = A[i + int64_t(i) * n];
+            const R di = A[i + int64_t(i) * ld];
             int rank = 0;
             for (int j = 0; j < n; ++j) {
-                const R dj = A[j + int64_t(j) * n];
+                const R dj = A[j + int64_t(j) * ld];
                 if (dj > di || (dj == di && j < i)) ++rank;
             }
 #ifdef KL_CHECK_BOUNDS
@@ -739,29 +771,29 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         __syncthreads();
         for (int64_t e = tid; e < nn; e += NT) {
             const int i = int(e % n), c = int(e / n);
-            const R z = Z[e];
+            const R z = Z[i + int64_t(c) * ld];
             if (Vout) Vout[i + int64_t(rk[c]) * n] = z;
             if (Qout) Qout[i + int64_t(rk[c]) * n] = z;
         }
     } else if (!fail) {
         // ---- ordering of the real Schur form by decreasing real part ----
-        order_schur(A, Z, n, anorm, hv, ord, &s_oob);
+        order_schur(A, Z, n, ld, anorm, hv, ord, &s_oob);
         __syncthreads();
 
         // ---- eigenvalues of the ordered blocks ----
         for (int i = tid; i < n; i += NT) {
-            const bool first = (i + 1 < n) && A[(i + 1) + int64_t(i) * n] != R(0.0);
-            const bool second = (i > 0) && A[i + int64_t(i - 1) * n] != R(0.0);
+            const bool first = (i + 1 < n) && A[(i + 1) + int64_t(i) * ld] != R(0.0);
+            const bool second = (i > 0) && A[i + int64_t(i - 1) * ld] != R(0.0);
             if (first || second) {
                 const int b0 = first ? i : i - 1;
-                const R a = A[b0 + int64_t(b0) * n], b = A[b0 + int64_t(b0 + 1) * n];
-                const R c = A[(b0 + 1) + int64_t(b0) * n], d = A[(b0 + 1) + int64_t(b0 + 1) * n];
+                const R a = A[b0 + int64_t(b0) * ld], b = A[b0 + int64_t(b0 + 1) * ld];
+                const R c = A[(b0 + 1) + int64_t(b0) * ld], d = A[(b0 + 1) + int64_t(b0 + 1) * ld];
                 const R pp = R(0.5) * (a - d), q = pp * pp + b * c;
                 const R im = q < R(0.0) ? sqrt(-q) : R(0.0);
                 wr[i] = d + pp;
                 wi[i] = first ? im : -im;
             } else {
-                wr[i] = A[i + int64_t(i) * n];
+                wr[i] = A[i + int64_t(i) * ld];
                 wi[i] = R(0.0);
             }
         }
@@ -777,17 +809,17 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         const R small = EigNum<R>::eps * fmax(anorm, EigNum<R>::tiny);
         const R clus = EigNum<R>::split * anorm;
         for (int col = tid; col < nve; col += NT) {
-            R* xr = X + int64_t(col) * n;
+            R* xr = X + int64_t(col) * ld;
             if (wi[col] == R(0.0)) {
                 const R lam = wr[col];
                 for (int i = 0; i < n; ++i) xr[i] = R(0.0);
                 xr[col] = R(1.0);
                 for (int j = col - 1; j >= 0; --j) {
-                    const bool two = (j > 0) && A[j + int64_t(j - 1) * n] != R(0.0);
+                    const bool two = (j > 0) && A[j + int64_t(j - 1) * ld] != R(0.0);
                     if (!two) {
                         R s = R(0.0);
-                        for (int l2 = j + 1; l2 <= col; ++l2) s = fma(A[j + int64_t(l2) * n], xr[l2], s);
-                        R den = A[j + int64_t(j) * n] - lam;
+                        for (int l2 = j + 1; l2 <= col; ++l2) s = fma(A[j + int64_t(l2) * ld], xr[l2], s);
+                        R den = A[j + int64_t(j) * ld] - lam;
                         if (fabs(den) <= clus) {
                             xr[j] = R(0.0);
                             continue;
@@ -798,11 +830,11 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                         // 2x2 system for rows j-1, j
                         R s1 = R(0.0), s2 = R(0.0);
                         for (int l2 = j + 1; l2 <= col; ++l2) {
-                            s1 = fma(A[(j - 1) + int64_t(l2) * n], xr[l2], s1);
-                            s2 = fma(A[j + int64_t(l2) * n], xr[l2], s2);
+                            s1 = fma(A[(j - 1) + int64_t(l2) * ld], xr[l2], s1);
+                            s2 = fma(A[j + int64_t(l2) * ld], xr[l2], s2);
                         }
-                        const R a11 = A[(j - 1) + int64_t(j - 1) * n] - lam, a12 = A[(j - 1) + int64_t(j) * n];
-                        const R a21 = A[j + int64_t(j - 1) * n], a22 = A[j + int64_t(j) * n] - lam;
+                        const R a11 = A[(j - 1) + int64_t(j - 1) * ld] - lam, a12 = A[(j - 1) + int64_t(j) * ld];
+                        const R a21 = A[j + int64_t(j - 1) * ld], a22 = A[j + int64_t(j) * ld] - lam;
                         R det = a11 * a22 - a12 * a21;
                         if (fabs(det) < small * small) det = small * small;
                         xr[j - 1] = (-s1 * a22 + s2 * a12) / det;
@@ -813,25 +845,25 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             } else if (wi[col] > R(0.0)) {
                 // complex pair (col, col+1): vector for lambda = wr + i wi, stored
                 // as real part in column col and imaginary part in column col+1
-                R* xi = X + int64_t(col + 1) * n;
+                R* xi = X + int64_t(col + 1) * ld;
                 const cplx lam = {wr[col], wi[col]};
                 for (int i = 0; i < n; ++i) xr[i] = xi[i] = R(0.0);
                 // (b12, lambda - b11) solves the first row of (B - lambda I) x = 0
                 // for the 2x2 block B and is non-zero because lambda is not real
                 const int q = col;
-                xr[q] = A[q + int64_t(q + 1) * n];
+                xr[q] = A[q + int64_t(q + 1) * ld];
                 xi[q] = R(0.0);
-                xr[q + 1] = lam.re - A[q + int64_t(q) * n];
+                xr[q + 1] = lam.re - A[q + int64_t(q) * ld];
                 xi[q + 1] = lam.im;
                 for (int j = q - 1; j >= 0; --j) {
-                    const bool two = (j > 0) && A[j + int64_t(j - 1) * n] != R(0.0);
+                    const bool two = (j > 0) && A[j + int64_t(j - 1) * ld] != R(0.0);
                     if (!two) {
                         cplx s = {R(0.0), R(0.0)};
                         for (int l2 = j + 1; l2 <= q + 1; ++l2) {
-                            s.re += A[j + int64_t(l2) * n] * xr[l2];
-                            s.im += A[j + int64_t(l2) * n] * xi[l2];
+                            s.re += A[j + int64_t(l2) * ld] * xr[l2];
+                            s.im += A[j + int64_t(l2) * ld] * xi[l2];
                         }
-                        cplx den = {A[j + int64_t(j) * n] - lam.re, -lam.im};
+                        cplx den = {A[j + int64_t(j) * ld] - lam.re, -lam.im};
                         if (fabs(den.re) + fabs(den.im) < small) den.re = small;
                         const cplx r = cdiv({-s.re, -s.im}, den);
                         xr[j] = r.re;
@@ -839,15 +871,15 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                     } else {
                         cplx s1 = {R(0.0), R(0.0)}, s2 = {R(0.0), R(0.0)};
                         for (int l2 = j + 1; l2 <= q + 1; ++l2) {
-                            s1.re += A[(j - 1) + int64_t(l2) * n] * xr[l2];
-                            s1.im += A[(j - 1) + int64_t(l2) * n] * xi[l2];
-                            s2.re += A[j + int64_t(l2) * n] * xr[l2];
-                            s2.im += A[j + int64_t(l2) * n] * xi[l2];
+                            s1.re += A[(j - 1) + int64_t(l2) * ld] * xr[l2];
+                            s1.im += A[(j - 1) + int64_t(l2) * ld] * xi[l2];
+                            s2.re += A[j + int64_t(l2) * ld] * xr[l2];
+                            s2.im += A[j + int64_t(l2) * ld] * xi[l2];
                         }
-                        const cplx a11 = {A[(j - 1) + int64_t(j - 1) * n] - lam.re, -lam.im};
-                        const cplx a12 = {A[(j - 1) + int64_t(j) * n], R(0.0)};
-                        const cplx a21 = {A[j + int64_t(j - 1) * n], R(0.0)};
-                        const cplx a22 = {A[j + int64_t(j) * n] - lam.re, -lam.im};
+                        const cplx a11 = {A[(j - 1) + int64_t(j - 1) * ld] - lam.re, -lam.im};
+                        const cplx a12 = {A[(j - 1) + int64_t(j) * ld], R(0.0)};
+                        const cplx a21 = {A[j + int64_t(j - 1) * ld], R(0.0)};
+                        const cplx a22 = {A[j + int64_t(j) * ld] - lam.re, -lam.im};
                         cplx det = {cmul(a11, a22).re - cmul(a12, a21).re, cmul(a11, a22).im - cmul(a12, a21).im};
                         if (fabs(det.re) + fabs(det.im) < small * small) det.re = small * small;
                         const cplx n1 = {-(cmul(s1, a22).re) + cmul(s2, a12).re, -(cmul(s1, a22).im) + cmul(s2, a12).im};
@@ -871,7 +903,7 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             const int i = int(e % n), c = int(e / n);
             const int top = min(n - 1, c + 1);
             R s = R(0.0);
-            for (int l2 = 0; l2 <= top; ++l2) s = fma(Z[i + int64_t(l2) * n], X[l2 + int64_t(c) * n], s);
+            for (int l2 = 0; l2 <= top; ++l2) s = fma(Z[i + int64_t(l2) * ld], X[l2 + int64_t(c) * ld], s);
             Vt[i + int64_t(c) * n] = s;
         }
         __syncthreads();
@@ -893,7 +925,7 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         if (Vout)
             for (int64_t e = tid; e < int64_t(n) * nve; e += NT) Vout[e] = Vt[e];
         if (Qout)
-            for (int64_t e = tid; e < nn; e += NT) Qout[e] = Z[e];
+            for (int64_t e = tid; e < nn; e += NT) Qout[e] = Z[int(e % n) + int64_t(e / n) * ld];
     }
     if (tid == 0) {
         // 3: the bounds-checking build found an index out of range
@@ -908,7 +940,7 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
 
 // Shared-memory level for an n x n problem (see the kernel).
 int eig_smem_level(int n, size_t esize, size_t* bytes) {
-    const size_t nn = size_t(n) * n;
+    const size_t nn = size_t(n + 1) * n;  // matrices with leading dimension n + 1
     if ((3 * nn + 10 * size_t(n)) * esize <= kEigSmemLimit) {
         *bytes = (3 * nn + 10 * size_t(n)) * esize;
         return 2;
@@ -958,7 +990,7 @@ cudaError_t launch_eig(const double* H, int n, double* wr, double* wi, double* V
 
 }  // namespace
 
-int64_t nonsym_eig_work_doubles(int n) { return 3 * int64_t(n) * n + 12 * int64_t(n); }
+int64_t nonsym_eig_work_doubles(int n) { return 3 * int64_t(n + 1) * n + 12 * int64_t(n); }
 int64_t sym_eig_work_doubles(int n) { return std::max(nonsym_eig_work_doubles(n), jacobi_work_doubles(n)); }
 
 // Symmetric eigenproblem. FP64: parallel Jacobi in FP32 refined in FP64 up to
