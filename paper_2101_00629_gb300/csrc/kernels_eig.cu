@@ -23,15 +23,116 @@
 
 namespace kl {
 
+// Double-float arithmetic for the small eigenproblems: a value is hi + lo, two
+// FP32 numbers with |lo| at most about half an ulp of hi (about 46-48
+// significant bits, the FP32 exponent range). Error-free transformations
+// (Knuth's two-sum, the FMA two-product) on the FP32 pipe: on GB300 a
+// dependent FP64 operation waits about 63 cycles and the FP64 unit issues one
+// warp instruction per 64 cycles per sub-partition, while a double-float
+// operation is a handful of 4-cycle FP32 steps on a pipe 64 times as wide.
+// The bulge chase of a Francis step is one long chain of dependent operations,
+// so the whole decomposition gets several times faster at ~1e-14 relative
+// accuracy. Used for the Rayleigh-Ritz problems of the reduced-precision solves
+// (whose residuals are resolved to ~1e-6); FP64 solves keep FP64. Operations
+// use the _rn intrinsics so that the compiler neither contracts nor
+// reassociates them.
+namespace dfa {
+struct dfl {
+    float hi, lo;
+    dfl() = default;
+    __device__ dfl(float h, float l) : hi(h), lo(l) {}
+    __device__ dfl(double x) {
+        hi = __double2float_rn(x);
+        lo = __double2float_rn(x - double(hi));
+    }
+    __device__ dfl(int x) : hi(float(x)), lo(0.f) {}
+};
+__device__ inline dfl fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return dfl(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ inline dfl operator+(dfl a, dfl b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    return fast_two_sum(s, e);
+}
+__device__ inline dfl operator-(dfl a) { return dfl(-a.hi, -a.lo); }
+__device__ inline dfl operator-(dfl a, dfl b) { return a + (-b); }
+__device__ inline dfl operator*(dfl a, dfl b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ inline dfl operator/(dfl a, dfl b) {
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const dfl r = a - b * dfl(q1, 0.f);
+    return fast_two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
+__device__ inline dfl& operator+=(dfl& a, dfl b) { return a = a + b; }
+__device__ inline dfl& operator-=(dfl& a, dfl b) { return a = a - b; }
+__device__ inline dfl& operator*=(dfl& a, dfl b) { return a = a * b; }
+__device__ inline bool operator<(dfl a, dfl b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ inline bool operator>(dfl a, dfl b) { return b < a; }
+__device__ inline bool operator<=(dfl a, dfl b) { return !(b < a); }
+__device__ inline bool operator>=(dfl a, dfl b) { return !(a < b); }
+__device__ inline bool operator==(dfl a, dfl b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ inline bool operator!=(dfl a, dfl b) { return !(a == b); }
+__device__ inline dfl fabs(dfl a) { return a.hi < 0.f ? -a : a; }
+__device__ inline dfl fmax(dfl a, dfl b) { return a < b ? b : a; }
+__device__ inline dfl fmin(dfl a, dfl b) { return b < a ? b : a; }
+__device__ inline dfl fma(dfl a, dfl b, dfl c) { return a * b + c; }
+__device__ inline dfl sqrt(dfl a) {
+    if (!(a.hi > 0.f)) return dfl(0.f, 0.f);
+    const float s = __fsqrt_rn(a.hi);
+    const float p = __fmul_rn(s, s);
+    const dfl r = a - dfl(p, __fmaf_rn(s, s, -p));  // a - s^2, s^2 exactly
+    return fast_two_sum(s, __fdiv_rn(r.hi, __fmul_rn(2.f, s)));
+}
+// sqrt(a^2 + b^2) with a and b first scaled by a power of two (exact), so
+// that tiny entries neither underflow nor lose their low part
+__device__ inline dfl hypot(dfl a, dfl b) {
+    const float m = fmaxf(fabsf(a.hi), fabsf(b.hi));
+    if (!(m > 0.f)) return dfl(0.f, 0.f);
+    int e;
+    frexpf(m, &e);
+    const float sc = ldexpf(1.f, -e), inv = ldexpf(1.f, e);
+    const dfl as(a.hi * sc, a.lo * sc), bs(b.hi * sc, b.lo * sc);
+    const dfl r = sqrt(as * as + bs * bs);
+    return dfl(r.hi * inv, r.lo * inv);
+}
+__device__ inline double to_d(dfl a) { return double(a.hi) + double(a.lo); }
+}  // namespace dfa
+using dfa::dfl;
+
 namespace {
+
+__device__ inline double to_d(double a) { return a; }
+__device__ inline double to_d(float a) { return double(a); }
+template <class R>
+__device__ inline R shfl_xor(R v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+template <>
+__device__ inline dfl shfl_xor<dfl>(dfl v, int o) {
+    return dfl(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+}
+template <class R>
+__device__ inline R shfl_idx(R v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+template <>
+__device__ inline dfl shfl_idx<dfl>(dfl v, int src) {
+    return dfl(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
+}
 
 constexpr int kEigThreads = 128;
 constexpr size_t kEigSmemLimit = 220 * 1024;  // dynamic shared memory of the largest level
 constexpr int kEigWarps = kEigThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
 
-// Arithmetic of the kernel: FP64 for the final Rayleigh-Ritz problems, FP32
-// for the restarts of the outer solver (shorter dependency chains). split:
+// Arithmetic of the kernel: FP64 for the Rayleigh-Ritz problems of FP64
+// solves, double-float for the final ones of reduced-precision solves, FP32
+// for their restarts (shorter dependency chains). split:
 // relative size (to ||H||) below which a stalled window's subdiagonal may be
 // dropped and diagonal entries count as one eigenvalue cluster.
 template <class R>
@@ -42,6 +143,17 @@ struct EigNum<double> {
     static constexpr double tiny = DBL_MIN;
     static constexpr double split = 1e-10;
     static constexpr double abs_defl = 1.0;  // absolute deflation at n eps ||H||
+    static constexpr double hess_min = 0.0;  // smallest column norm^2 the reduction reflects
+};
+template <>
+struct EigNum<dfl> {
+    static constexpr double eps = 1e-14;  // a few units of the double-float's last place
+    static constexpr double tiny = 1e-30;  // FP32 range, with room for the low part
+    static constexpr double split = 1e-10;
+    static constexpr double abs_defl = 1.0;
+    // below this a column's entries (< 1e-15) are dropped, not reflected:
+    // beta ~ 1 / |x|^2 would leave the FP32 exponent range
+    static constexpr double hess_min = 1e-30;
 };
 template <>
 struct EigNum<float> {
@@ -49,6 +161,7 @@ struct EigNum<float> {
     static constexpr float tiny = FLT_MIN;
     static constexpr float split = 1e-5f;
     static constexpr float abs_defl = 1.0f / 64;  // about eps ||H|| for the sizes used
+    static constexpr float hess_min = 0.f;
 };
 
 struct cplx {
@@ -67,7 +180,7 @@ __device__ inline cplx cdiv(cplx a, cplx b) {
 
 template <class R>
 __device__ inline R blk_sum(R v, R* red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     R s = R(0.0);
@@ -77,7 +190,7 @@ __device__ inline R blk_sum(R v, R* red) {
 }
 template <class R>
 __device__ inline R blk_max(R v, R* red) {
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, shfl_xor(v, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     R s = red[0];
@@ -109,6 +222,37 @@ __device__ inline void house(const R* x, int len, R* v, R& beta) {
     const R nrm = sqrt(ss);
     v[0] += (x[0] >= R(0.0) ? nrm : -nrm);
     beta = R(1.0) / (nrm * (nrm + fabs(x[0])));
+}
+// Double-float: FP32's exponent range cannot hold |x|^2 or beta ~ |x|^-2 for the
+// tiny entries a converging bulge carries (|x| ~ 1e-20 gives beta ~ 1e40), so x
+// is first scaled by a power of two (exact) to |x_i| < 1, and the vector is
+// normalised to v0 = 1 with beta = 2 / (v^T v) of that vector (bounded, and
+// orthogonal to rounding whatever the rounding of |x|).
+template <>
+__device__ inline void house<dfl>(const dfl* x, int len, dfl* v, dfl& beta) {
+    float m = 0.f;
+    for (int t = 0; t < len; ++t) m = fmaxf(m, fabsf(x[t].hi));
+    for (int t = 0; t < len; ++t) v[t] = x[t];
+    if (!(m > 0.f)) {
+        beta = dfl(0.f, 0.f);
+        return;
+    }
+    int e;
+    frexpf(m, &e);
+    const float sc = ldexpf(1.f, -e);
+    dfl xs[3];
+    for (int t = 0; t < len; ++t) xs[t] = dfl(x[t].hi * sc, x[t].lo * sc);
+    dfl ss = xs[0] * xs[0];
+    for (int t = 1; t < len; ++t) ss = fma(xs[t], xs[t], ss);
+    const dfl nrm = sqrt(ss);
+    const dfl alpha = xs[0] + (xs[0].hi >= 0.f ? nrm : -nrm);
+    dfl vtv = dfl(1.f, 0.f);
+    v[0] = dfl(1.f, 0.f);
+    for (int t = 1; t < len; ++t) {
+        v[t] = xs[t] / alpha;
+        vtv = fma(v[t], v[t], vtv);
+    }
+    beta = dfl(2.f, 0.f) / vtv;
 }
 
 // Deflation test for the subdiagonal entry (l, l-1).
@@ -236,29 +380,31 @@ __device__ void swap_transform(const R* A, int ld, int k, int n1, int n2, R anor
 }
 
 // Orders the diagonal blocks (1x1 real eigenvalues, 2x2 complex pairs) of the
-// quasi-triangular A by decreasing real part, updating the Schur vectors Z:
-// odd-even transposition sort over the blocks. In a round, blocks 2p + par
-// and 2p + par + 1 are exchanged where the second has the larger real part;
-// the exchanges act on disjoint row/column ranges and commute, so a round is
-// applied as one two-sided update (all rows, then all columns and Z). Each
-// exchange is computed by its own thread.
-// ints: 2n ints of scratch (block starts, pair positions, pair sizes/flags);
-// ord: 8n doubles (a 4 x 4 transform per pair).
+// quasi-triangular A so that the blocks holding the nwant eigenvalues of
+// largest real part come first, by decreasing real part, updating the Schur
+// vectors Z: odd-even transposition over the blocks, exchanging blocks 2p + par
+// and 2p + par + 1 where the second is wanted (real part at least the
+// smallest wanted one, less the cluster tolerance) and has the larger real part (the
+// other blocks keep their relative order: nothing downstream reads it). The
+// exchanges of a round act on disjoint row/column ranges and commute, so a
+// round is applied as one two-sided update (all rows, then all columns and Z)
+// over the exchanged pairs only. Each exchange is computed by its own thread.
+// ints: 2n ints of scratch (block starts; per exchanged pair its block start
+// and its size/pair index word); ord: 8n values (a 4 x 4 transform per pair;
+// before the first round the block keys).
 template <class R>
-__device__ void order_schur(R* A, R* Z, int n, int ld, R anorm, R* ints_d, R* ord, int* oob) {
+__device__ void order_schur(R* A, R* Z, int n, int ld, int nwant, R anorm, R* ints_d, R* ord, int* oob) {
     constexpr int NT = kEigThreads;
     __shared__ int s_wsum[kEigWarps];
+    __shared__ int s_nb;
+    __shared__ R s_tau;
     int* bstart = reinterpret_cast<int*>(ints_d);  // n
     int* pk = bstart + n;                           // n / 2 (pairs <= blocks / 2)
     int* pinfo = pk + n / 2;                        // n / 2
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ipt = (n + NT - 1) / NT;
-    int quiet = 0;
-    for (int round = 0; round < 2 * n + 4 && quiet < 2; ++round) {
-        // block starts: i = 0 or a zero subdiagonal entry (i, i-1)
-        int cnt = 0;
-        for (int i = tid * ipt; i < min(n, (tid + 1) * ipt); ++i)
-            cnt += (i == 0 || A[i + int64_t(i - 1) * ld] == R(0.0));
+    // exclusive block-wide prefix sum of a per-thread count; total in *tot
+    auto scan = [&](int cnt, int* tot) {
         int incl = cnt;
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(kFull, incl, o);
@@ -266,30 +412,97 @@ __device__ void order_schur(R* A, R* Z, int n, int ld, R anorm, R* ints_d, R* or
         }
         if (lane == 31) s_wsum[warp] = incl;
         __syncthreads();
-        int pos = incl - cnt, nb = 0;
+        int pos = incl - cnt, t = 0;
         for (int w = 0; w < kEigWarps; ++w) {
             if (w < warp) pos += s_wsum[w];
-            nb += s_wsum[w];
+            t += s_wsum[w];
         }
+        __syncthreads();
+        *tot = t;
+        return pos;
+    };
+    // block starts: i = 0 or a zero subdiagonal entry (i, i-1)
+    auto find_blocks = [&]() -> int {
+        int cnt = 0;
+        for (int i = tid * ipt; i < min(n, (tid + 1) * ipt); ++i)
+            cnt += (i == 0 || A[i + int64_t(i - 1) * ld] == R(0.0));
+        int nb;
+        int pos = scan(cnt, &nb);
         for (int i = tid * ipt; i < min(n, (tid + 1) * ipt); ++i)
             if (i == 0 || A[i + int64_t(i - 1) * ld] == R(0.0)) bstart[pos++] = i;
         __syncthreads();
+        return nb;
+    };
+    auto key_of = [&](int k, int sz) {
+        return sz == 1 ? A[k + int64_t(k) * ld] : R(0.5) * (A[k + int64_t(k) * ld] + A[(k + 1) + int64_t(k + 1) * ld]);
+    };
+    // the wanted blocks: those with fewer than nwant eigenvalues in blocks of
+    // larger key (ties: lower position first); tau = the smallest wanted key
+    {
+        const int nb = find_blocks();
+        for (int b = tid; b < nb; b += NT) {
+            const int k = bstart[b], k2 = b + 1 < nb ? bstart[b + 1] : n;
+            ord[b] = key_of(k, k2 - k);
+        }
+        __syncthreads();
+        R tmin = R(0.0);
+        bool have = false;
+        for (int b = tid; b < nb; b += NT) {
+            const R kb = ord[b];
+            int above = 0;
+            for (int j = 0; j < nb; ++j) {
+                const R kj = ord[j];
+                if (kj > kb || (kj == kb && j < b)) above += (j + 1 < nb ? bstart[j + 1] : n) - bstart[j];
+            }
+            if (above < nwant && (!have || kb < tmin)) {
+                tmin = kb;
+                have = true;
+            }
+        }
+        // block minimum over the threads that have a wanted block
+        if (tid == 0) s_nb = 0;
+        __syncthreads();
+        for (int w = 0; w < NT; w += 32) {
+            // one warp at a time keeps this simple: it runs once per call
+            if (warp == w / 32) {
+                for (int l2 = 0; l2 < 32; ++l2) {
+                    if (lane == l2 && have) {
+                        if (s_nb == 0 || tmin < s_tau) s_tau = tmin;
+                        s_nb = 1;
+                    }
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // a 2x2 block's key (half its trace) moves by rounding as it is exchanged:
+    // blocks within the cluster tolerance of the threshold count as wanted, so
+    // that the last wanted block never drops out of the set on the way
+    const R tau = s_tau - R(EigNum<R>::split) * anorm;
+    int quiet = 0;
+    for (int round = 0; round < 2 * n + 4 && quiet < 2; ++round) {
+        const int nb = find_blocks();
         const int par = round & 1;
         const int npairs = max(0, (nb - par) / 2);
-        int any = 0;
-        for (int p = tid; p < npairs; p += NT) {
+        // each thread decides a contiguous range of at most 4 pairs and
+        // computes the exchanges among them
+        const int ppt = (npairs + NT - 1) / NT;
+        const int pa = min(npairs, tid * ppt), pb = min(npairs, pa + ppt);
+        int mykey[4], myk[4];
+        int cnt = 0;
+        for (int p = pa; p < pb; ++p) {
             const int b0 = par + 2 * p;
             const int k = bstart[b0], k2 = bstart[b0 + 1];
             const int k3 = (b0 + 2 < nb) ? bstart[b0 + 2] : n;
             const int n1 = k2 - k, n2 = k3 - k2;
-            const R key1 = n1 == 1 ? A[k + int64_t(k) * ld] : R(0.5) * (A[k + int64_t(k) * ld] + A[(k + 1) + int64_t(k + 1) * ld]);
-            const R key2 = n2 == 1 ? A[k2 + int64_t(k2) * ld]
-                                        : R(0.5) * (A[k2 + int64_t(k2) * ld] + A[(k2 + 1) + int64_t(k2 + 1) * ld]);
-            int f = key2 > key1;
+            const R key1 = key_of(k, n1), key2 = key_of(k2, n2);
+            int f = key2 > key1 && key2 >= tau;
 #ifdef KL_CHECK_BOUNDS
-            // pair and block indices stay inside the scratch (n / 2 pairs) and
-            // the blocks are 1x1 or 2x2; otherwise record it, skip the exchange
-            if (b0 + 1 >= nb || p >= n / 2 || n1 < 1 || n1 > 2 || n2 < 1 || n2 > 2 || k3 > n) {
+            // pair and block indices stay inside the scratch (n / 2 pairs), the
+            // blocks are 1x1 or 2x2 and a thread has at most 4 pairs;
+            // otherwise record it, skip the exchange
+            if (b0 + 1 >= nb || p >= n / 2 || n1 < 1 || n1 > 2 || n2 < 1 || n2 > 2 || k3 > n || ppt > 4) {
                 atomicExch(oob, 1);
                 f = 0;
             }
@@ -301,25 +514,30 @@ __device__ void order_schur(R* A, R* Z, int n, int ld, R anorm, R* ints_d, R* or
                     ord[16 * int64_t(p) + 4] = A[k + int64_t(k) * ld];
                     ord[16 * int64_t(p) + 5] = A[k2 + int64_t(k2) * ld];
                 }
+                mykey[cnt] = (p << 8) | 1 | (n1 << 1) | (n2 << 3);
+                myk[cnt] = k;
+                ++cnt;
             }
-            pk[p] = k;
-            pinfo[p] = f | (n1 << 1) | (n2 << 3);
-            any |= f;
         }
-        any = __syncthreads_or(any);
-        if (!any) {
+        int nswap;
+        int pos = scan(cnt, &nswap);
+        for (int c = 0; c < cnt; ++c) {
+            pk[pos + c] = myk[c];
+            pinfo[pos + c] = mykey[c];
+        }
+        __syncthreads();
+        if (nswap == 0) {
             ++quiet;
             continue;
         }
         quiet = 0;
         // rows of each exchanged span <- Q^T rows (columns k..n-1)
-        for (int64_t e = tid; e < int64_t(npairs) * n; e += NT) {
-            const int p = int(e / n), j = int(e % n);
-            const int info = pinfo[p];
-            if (!(info & 1)) continue;
-            const int k = pk[p], m = ((info >> 1) & 3) + ((info >> 3) & 3);
+        for (int64_t e = tid; e < int64_t(nswap) * n; e += NT) {
+            const int q = int(e / n), j = int(e % n);
+            const int info = pinfo[q];
+            const int k = pk[q], m = ((info >> 1) & 3) + ((info >> 3) & 3);
             if (j < k) continue;
-            const R* Qm = ord + 16 * int64_t(p);
+            const R* Qm = ord + 16 * int64_t(info >> 8);
             R old[4];
             for (int t = 0; t < m; ++t) old[t] = A[(k + t) + int64_t(j) * ld];
             for (int t = 0; t < m; ++t) {
@@ -331,15 +549,14 @@ __device__ void order_schur(R* A, R* Z, int n, int ld, R anorm, R* ints_d, R* or
         __syncthreads();
         // columns of each exchanged span <- columns Q (rows of A above the
         // span's end, all rows of Z)
-        for (int64_t e = tid; e < int64_t(npairs) * 2 * n; e += NT) {
-            const int p = int(e / (2 * n)), i2 = int(e % (2 * n));
-            const int info = pinfo[p];
-            if (!(info & 1)) continue;
-            const int k = pk[p], m = ((info >> 1) & 3) + ((info >> 3) & 3);
+        for (int64_t e = tid; e < int64_t(nswap) * 2 * n; e += NT) {
+            const int q = int(e / (2 * n)), i2 = int(e % (2 * n));
+            const int info = pinfo[q];
+            const int k = pk[q], m = ((info >> 1) & 3) + ((info >> 3) & 3);
             R* M = i2 < n ? A : Z;
             const int r = i2 < n ? i2 : i2 - n;
             if (i2 < n && r >= k + m) continue;
-            const R* Qm = ord + 16 * int64_t(p);
+            const R* Qm = ord + 16 * int64_t(info >> 8);
             R old[4];
             for (int t = 0; t < m; ++t) old[t] = M[r + int64_t(k + t) * ld];
             for (int t = 0; t < m; ++t) {
@@ -351,10 +568,10 @@ __device__ void order_schur(R* A, R* Z, int n, int ld, R anorm, R* ints_d, R* or
         __syncthreads();
         // the exchanged blocks: zero the new (2,1) block; 1x1 pairs take
         // their exchanged diagonal exactly
-        for (int p = tid; p < npairs; p += NT) {
-            const int info = pinfo[p];
-            if (!(info & 1)) continue;
-            const int k = pk[p], n1 = (info >> 1) & 3, n2 = (info >> 3) & 3, m = n1 + n2;
+        for (int q = tid; q < nswap; q += NT) {
+            const int info = pinfo[q];
+            const int k = pk[q], n1 = (info >> 1) & 3, n2 = (info >> 3) & 3, m = n1 + n2;
+            const int p = info >> 8;
             for (int i = k + n2; i < k + m; ++i)
                 for (int j = k; j < k + n2; ++j) A[i + int64_t(j) * ld] = R(0.0);
             if (n1 == 1 && n2 == 1) {
@@ -424,7 +641,7 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         ss = blk_sum(ss, s_red);
         if (tid == 0) {
             R beta = R(0.0);
-            if (ss > R(0.0)) {
+            if (ss > R(EigNum<R>::hess_min)) {
                 const R x0 = hv[0], nrm = sqrt(ss);
                 hv[0] = x0 + (x0 >= R(0.0) ? nrm : -nrm);
                 beta = R(1.0) / (nrm * (nrm + fabs(x0)));
@@ -442,7 +659,7 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                 R s = R(0.0);
                 if (c < ncols)
                     for (int t = p; t < len; t += g) s = fma(hv[t], A[(k + 1 + t) + int64_t(k + c) * ld], s);
-                for (int o = g / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+                for (int o = g / 2; o > 0; o >>= 1) s += shfl_xor(s, o);
                 s *= beta;
                 if (c < ncols)
                     for (int t = p; t < len; t += g) A[(k + 1 + t) + int64_t(k + c) * ld] -= s * hv[t];
@@ -458,7 +675,7 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                 R s = R(0.0);
                 if (it < items)
                     for (int t = p; t < len; t += g2) s = fma(M[i + int64_t(k + 1 + t) * ld], hv[t], s);
-                for (int o = g2 / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+                for (int o = g2 / 2; o > 0; o >>= 1) s += shfl_xor(s, o);
                 s *= beta;
                 if (it < items)
                     for (int t = p; t < len; t += g2) M[i + int64_t(k + 1 + t) * ld] -= s * hv[t];
@@ -678,9 +895,9 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                     row[2 * int64_t(ld)] = a2 - s * v2;
                 }
                 R xx[3];
-                xx[0] = __shfl_sync(kFull, xnew, 1);
-                xx[1] = __shfl_sync(kFull, xnew, 2);
-                xx[2] = __shfl_sync(kFull, xnew, 3);
+                xx[0] = shfl_idx(xnew, 1);
+                xx[1] = shfl_idx(xnew, 2);
+                xx[2] = shfl_idx(xnew, 3);
                 if (tid == 0) {
                     // the 2-element reflector of the window's end after the
                     // last 3-element one
@@ -764,20 +981,20 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                 rank = 0;
             }
 #endif
-            wr_out[rank] = di;
-            if (wi_out) wi_out[rank] = R(0.0);
+            wr_out[rank] = to_d(di);
+            if (wi_out) wi_out[rank] = 0.0;
             rk[i] = rank;
         }
         __syncthreads();
         for (int64_t e = tid; e < nn; e += NT) {
             const int i = int(e % n), c = int(e / n);
             const R z = Z[i + int64_t(c) * ld];
-            if (Vout) Vout[i + int64_t(rk[c]) * n] = z;
-            if (Qout) Qout[i + int64_t(rk[c]) * n] = z;
+            if (Vout) Vout[i + int64_t(rk[c]) * n] = to_d(z);
+            if (Qout) Qout[i + int64_t(rk[c]) * n] = to_d(z);
         }
     } else if (!fail) {
         // ---- ordering of the real Schur form by decreasing real part ----
-        order_schur(A, Z, n, ld, anorm, hv, ord, &s_oob);
+        order_schur(A, Z, n, ld, nv, anorm, hv, ord, &s_oob);
         __syncthreads();
 
         // ---- eigenvalues of the ordered blocks ----
@@ -846,49 +1063,49 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                 // complex pair (col, col+1): vector for lambda = wr + i wi, stored
                 // as real part in column col and imaginary part in column col+1
                 R* xi = X + int64_t(col + 1) * ld;
-                const cplx lam = {wr[col], wi[col]};
+                const cplx lam = {to_d(wr[col]), to_d(wi[col])};
                 for (int i = 0; i < n; ++i) xr[i] = xi[i] = R(0.0);
                 // (b12, lambda - b11) solves the first row of (B - lambda I) x = 0
                 // for the 2x2 block B and is non-zero because lambda is not real
                 const int q = col;
                 xr[q] = A[q + int64_t(q + 1) * ld];
                 xi[q] = R(0.0);
-                xr[q + 1] = lam.re - A[q + int64_t(q) * ld];
-                xi[q + 1] = lam.im;
+                xr[q + 1] = R(lam.re) - A[q + int64_t(q) * ld];
+                xi[q + 1] = R(lam.im);
                 for (int j = q - 1; j >= 0; --j) {
                     const bool two = (j > 0) && A[j + int64_t(j - 1) * ld] != R(0.0);
                     if (!two) {
-                        cplx s = {R(0.0), R(0.0)};
+                        cplx s = {0.0, 0.0};
                         for (int l2 = j + 1; l2 <= q + 1; ++l2) {
-                            s.re += A[j + int64_t(l2) * ld] * xr[l2];
-                            s.im += A[j + int64_t(l2) * ld] * xi[l2];
+                            s.re += to_d(A[j + int64_t(l2) * ld] * xr[l2]);
+                            s.im += to_d(A[j + int64_t(l2) * ld] * xi[l2]);
                         }
-                        cplx den = {A[j + int64_t(j) * ld] - lam.re, -lam.im};
-                        if (fabs(den.re) + fabs(den.im) < small) den.re = small;
+                        cplx den = {to_d(A[j + int64_t(j) * ld]) - lam.re, -lam.im};
+                        if (fabs(den.re) + fabs(den.im) < to_d(small)) den.re = to_d(small);
                         const cplx r = cdiv({-s.re, -s.im}, den);
-                        xr[j] = r.re;
-                        xi[j] = r.im;
+                        xr[j] = R(r.re);
+                        xi[j] = R(r.im);
                     } else {
-                        cplx s1 = {R(0.0), R(0.0)}, s2 = {R(0.0), R(0.0)};
+                        cplx s1 = {0.0, 0.0}, s2 = {0.0, 0.0};
                         for (int l2 = j + 1; l2 <= q + 1; ++l2) {
-                            s1.re += A[(j - 1) + int64_t(l2) * ld] * xr[l2];
-                            s1.im += A[(j - 1) + int64_t(l2) * ld] * xi[l2];
-                            s2.re += A[j + int64_t(l2) * ld] * xr[l2];
-                            s2.im += A[j + int64_t(l2) * ld] * xi[l2];
+                            s1.re += to_d(A[(j - 1) + int64_t(l2) * ld] * xr[l2]);
+                            s1.im += to_d(A[(j - 1) + int64_t(l2) * ld] * xi[l2]);
+                            s2.re += to_d(A[j + int64_t(l2) * ld] * xr[l2]);
+                            s2.im += to_d(A[j + int64_t(l2) * ld] * xi[l2]);
                         }
-                        const cplx a11 = {A[(j - 1) + int64_t(j - 1) * ld] - lam.re, -lam.im};
-                        const cplx a12 = {A[(j - 1) + int64_t(j) * ld], R(0.0)};
-                        const cplx a21 = {A[j + int64_t(j - 1) * ld], R(0.0)};
-                        const cplx a22 = {A[j + int64_t(j) * ld] - lam.re, -lam.im};
+                        const cplx a11 = {to_d(A[(j - 1) + int64_t(j - 1) * ld]) - lam.re, -lam.im};
+                        const cplx a12 = {to_d(A[(j - 1) + int64_t(j) * ld]), 0.0};
+                        const cplx a21 = {to_d(A[j + int64_t(j - 1) * ld]), 0.0};
+                        const cplx a22 = {to_d(A[j + int64_t(j) * ld]) - lam.re, -lam.im};
                         cplx det = {cmul(a11, a22).re - cmul(a12, a21).re, cmul(a11, a22).im - cmul(a12, a21).im};
-                        if (fabs(det.re) + fabs(det.im) < small * small) det.re = small * small;
+                        if (fabs(det.re) + fabs(det.im) < to_d(small * small)) det.re = to_d(small * small);
                         const cplx n1 = {-(cmul(s1, a22).re) + cmul(s2, a12).re, -(cmul(s1, a22).im) + cmul(s2, a12).im};
                         const cplx n2 = {-(cmul(s2, a11).re) + cmul(s1, a21).re, -(cmul(s2, a11).im) + cmul(s1, a21).im};
                         const cplx r1 = cdiv(n1, det), r2 = cdiv(n2, det);
-                        xr[j - 1] = r1.re;
-                        xi[j - 1] = r1.im;
-                        xr[j] = r2.re;
-                        xi[j] = r2.im;
+                        xr[j - 1] = R(r1.re);
+                        xi[j - 1] = R(r1.im);
+                        xr[j] = R(r2.re);
+                        xi[j] = R(r2.im);
                         --j;
                     }
                 }
@@ -919,13 +1136,13 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         }
         __syncthreads();
         for (int i = tid; i < n; i += NT) {
-            wr_out[i] = wr[i];
-            if (wi_out) wi_out[i] = wi[i];
+            wr_out[i] = to_d(wr[i]);
+            if (wi_out) wi_out[i] = to_d(wi[i]);
         }
         if (Vout)
-            for (int64_t e = tid; e < int64_t(n) * nve; e += NT) Vout[e] = Vt[e];
+            for (int64_t e = tid; e < int64_t(n) * nve; e += NT) Vout[e] = to_d(Vt[e]);
         if (Qout)
-            for (int64_t e = tid; e < nn; e += NT) Qout[e] = Z[int(e % n) + int64_t(e / n) * ld];
+            for (int64_t e = tid; e < nn; e += NT) Qout[e] = to_d(Z[int(e % n) + int64_t(e / n) * ld]);
     }
     if (tid == 0) {
         // 3: the bounds-checking build found an index out of range
@@ -972,8 +1189,9 @@ cudaError_t launch_eig_t(const double* H, int n, double* wr, double* wi, double*
 }
 
 cudaError_t launch_eig(const double* H, int n, double* wr, double* wi, double* V, double* Q, double* work,
-                       int* status, int sym, int nvec, bool fp32, cudaStream_t s) {
-    if (n <= 0) return cudaErrorInvalidValue;
+                       int* status, int sym, int nvec, int arith, cudaStream_t s) {
+    // the ordering gives each thread at most 4 block pairs: n <= 1024
+    if (n <= 0 || n > 1024) return cudaErrorInvalidValue;
     const int64_t nn = int64_t(n) * n;
     KL_RANGE(H, nn, double, "eig H");
     KL_RANGE(wr, n, double, "eig wr");
@@ -984,8 +1202,9 @@ cudaError_t launch_eig(const double* H, int n, double* wr, double* wi, double* V
     KL_RANGE(Q, nn, double, "eig Q");
     KL_RANGE(work, nonsym_eig_work_doubles(n), double, "eig work");
     KL_RANGE(status, 4, int, "eig status");
-    return fp32 ? launch_eig_t<float>(H, n, wr, wi, V, Q, work, status, sym, nvec, s)
-                : launch_eig_t<double>(H, n, wr, wi, V, Q, work, status, sym, nvec, s);
+    if (arith == kEigFP32) return launch_eig_t<float>(H, n, wr, wi, V, Q, work, status, sym, nvec, s);
+    if (arith == kEigDF) return launch_eig_t<dfl>(H, n, wr, wi, V, Q, work, status, sym, nvec, s);
+    return launch_eig_t<double>(H, n, wr, wi, V, Q, work, status, sym, nvec, s);
 }
 
 }  // namespace
@@ -1004,12 +1223,12 @@ int64_t sym_eig_work_doubles(int n) { return std::max(nonsym_eig_work_doubles(n)
 cudaError_t launch_sym_eig(const double* H, int n, double* w, double* V, double* work, int* status,
                            cudaStream_t s, bool fp32) {
     if (!fp32 && n <= jacobi_max_n()) return launch_sym_eig_jacobi(H, n, w, V, work, status, s, false);
-    return launch_eig(H, n, w, nullptr, V, nullptr, work, status, 1, n, fp32, s);
+    return launch_eig(H, n, w, nullptr, V, nullptr, work, status, 1, n, fp32 ? kEigFP32 : kEigFP64, s);
 }
 
 cudaError_t launch_nonsym_eig(const double* H, int n, double* wr, double* wi, double* V, double* Q,
-                              double* work, int* status, cudaStream_t s, int nvec, bool fp32) {
-    return launch_eig(H, n, wr, wi, V, Q, work, status, 0, nvec > 0 ? nvec : n, fp32, s);
+                              double* work, int* status, cudaStream_t s, int nvec, int arith) {
+    return launch_eig(H, n, wr, wi, V, Q, work, status, 0, nvec > 0 ? nvec : n, arith, s);
 }
 
 }  // namespace kl

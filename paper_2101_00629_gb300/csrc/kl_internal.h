@@ -192,6 +192,10 @@ cudaError_t launch_chol_rinv(double* G, int n, double* Rinv, int* bad, cudaStrea
 // FP64; accuracy ~1e-7 ||H||), for the restarts of the outer solver.
 cudaError_t launch_sym_eig(const double* H, int n, double* w, double* V, double* work,
                            int* status, cudaStream_t s, bool fp32 = false);
+// Arithmetic of the small eigensolver: FP64, FP32 (accuracy ~1e-7 ||H||) or
+// double-float (pairs of FP32 numbers, ~1e-14 ||H||, several times faster
+// than FP64 on GB300's small FP64 unit).
+enum EigArith { kEigFP64 = 0, kEigFP32 = 1, kEigDF = 2 };
 // Real non-symmetric eigen-decomposition (Hessenberg + Francis QR + ordering
 // of the real Schur form + back substitution). wr/wi eigenvalues by real part
 // descending; Q (optional, n x n) the Schur vectors in the same order, so its
@@ -200,7 +204,7 @@ cudaError_t launch_sym_eig(const double* H, int n, double* w, double* V, double*
 // Re, Im columns; one more column when nvec splits a pair; nvec <= 0: all).
 // status[0]: 0 ok, 1 no convergence.
 cudaError_t launch_nonsym_eig(const double* H, int n, double* wr, double* wi, double* V, double* Q,
-                              double* work, int* status, cudaStream_t s, int nvec = 0, bool fp32 = false);
+                              double* work, int* status, cudaStream_t s, int nvec = 0, int arith = kEigFP64);
 int64_t nonsym_eig_work_doubles(int n);
 int64_t sym_eig_work_doubles(int n);
 // Symmetric eigenproblems of order n <= jacobi_max_n() by parallel Jacobi

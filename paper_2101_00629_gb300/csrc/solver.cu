@@ -166,9 +166,19 @@ int rayleigh_ritz(Ctx& c, const double* V, const double* AV, int nv, double* max
         KL_TRY(sync_copy(c, &status, c.w.ibuf, sizeof(int)));
         if (max_imag) *max_imag = 0.0;
     } else {
+        // reduced-precision solves take their FP64-grade problems in
+        // double-float arithmetic (~1e-14 ||H||, several times faster on
+        // GB300 than FP64), FP64 solves in FP64
+        const int arith = fp32 ? kEigFP32 : (c.h->prm.precision != KL_FP64 ? kEigDF : kEigFP64);
         KL_TRY(ck(c, launch_nonsym_eig(c.w.H, nv, c.w.theta, c.w.thetai, c.w.S, c.w.Q, c.w.la_work,
-                                       c.w.ibuf, c.h->stream, c.nvec, fp32), "nonsym_eig"));
+                                       c.w.ibuf, c.h->stream, c.nvec, arith), "nonsym_eig"));
         KL_TRY(sync_copy(c, &status, c.w.ibuf, sizeof(int)));
+        if (arith == kEigDF && status == 1) {
+            // not converged in double-float: the same matrix in FP64
+            KL_TRY(ck(c, launch_nonsym_eig(c.w.H, nv, c.w.theta, c.w.thetai, c.w.S, c.w.Q, c.w.la_work,
+                                           c.w.ibuf, c.h->stream, c.nvec, kEigFP64), "nonsym_eig"));
+            KL_TRY(sync_copy(c, &status, c.w.ibuf, sizeof(int)));
+        }
         c.schur_ok = status == 0;
         if (status == 2) status = 0;  // complex pairs: eigenvectors valid, Schur order not
     }
@@ -505,8 +515,13 @@ int eigs_impl(kl_solver* h, int M, double tol, double* lambda, double* Vout, int
         }
         const int rprec = h->prm.refine == 2 ? KL_FP64 : prec;
         if (int rc = apply(c, rprec, Y, AY, nk); rc != KL_OK) return rc;
-        // Rayleigh-Ritz on span(Y): reuse V/AV storage for the rotated pair
-        if (int rc = rayleigh_ritz(c, Y, AY, nk, nullptr); rc != KL_OK) return rc;
+        // Rayleigh-Ritz on span(Y): reuse V/AV storage for the rotated pair;
+        // only the M leading pairs are used (and ordered)
+        const int nvec_loop = c.nvec;
+        c.nvec = M;
+        const int rc_rr = rayleigh_ritz(c, Y, AY, nk, nullptr);
+        c.nvec = nvec_loop;
+        if (rc_rr != KL_OK) return rc_rr;
         if (int rc = nn(c, Y, N, c.w.S, nk, V, N, nk, M, 1.0, 0.0); rc != KL_OK) return rc;
         if (int rc = nn(c, AY, N, c.w.S, nk, AV, N, nk, M, 1.0, 0.0); rc != KL_OK) return rc;
         if (int rc = ck(c, launch_copy_block(V, N, Y, N, N, M, h->stream), "copy"); rc != KL_OK) return rc;
