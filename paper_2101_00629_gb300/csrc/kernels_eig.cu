@@ -72,6 +72,13 @@ __device__ inline dfl operator/(dfl a, dfl b) {
     const dfl r = a - b * dfl(q1, 0.f);
     return fast_two_sum(q1, __fdiv_rn(r.hi, b.hi));
 }
+// 1 / b: an FP32 reciprocal refined by one Newton step in double-float
+// (r + r (1 - b r)), about 2^-46 relative
+__device__ inline dfl recip(dfl b) {
+    const float r = __frcp_rn(b.hi);
+    const dfl e = dfl(1.f, 0.f) - b * dfl(r, 0.f);
+    return fast_two_sum(r, __fmul_rn(r, e.hi));
+}
 __device__ inline dfl& operator+=(dfl& a, dfl b) { return a = a + b; }
 __device__ inline dfl& operator-=(dfl& a, dfl b) { return a = a - b; }
 __device__ inline dfl& operator*=(dfl& a, dfl b) { return a = a * b; }
@@ -147,7 +154,10 @@ struct EigNum<double> {
 };
 template <>
 struct EigNum<dfl> {
-    static constexpr double eps = 1e-14;  // a few units of the double-float's last place
+    // the deflation tolerance: about 10 units of the double-float's last place
+    // (a tighter one only buys QR iterations spent at the rounding level:
+    // 1e-14 took 107 iterations where FP64 took 90)
+    static constexpr double eps = 1e-13;
     static constexpr double tiny = 1e-30;  // FP32 range, with room for the low part
     static constexpr double split = 1e-10;
     static constexpr double abs_defl = 1.0;
@@ -246,13 +256,16 @@ __device__ inline void house<dfl>(const dfl* x, int len, dfl* v, dfl& beta) {
     for (int t = 1; t < len; ++t) ss = fma(xs[t], xs[t], ss);
     const dfl nrm = sqrt(ss);
     const dfl alpha = xs[0] + (xs[0].hi >= 0.f ? nrm : -nrm);
+    // one reciprocal (|alpha| >= |x|, in [0.5, 2)), then products
+    const dfl ra = recip(alpha);
     dfl vtv = dfl(1.f, 0.f);
     v[0] = dfl(1.f, 0.f);
     for (int t = 1; t < len; ++t) {
-        v[t] = xs[t] / alpha;
+        v[t] = xs[t] * ra;
         vtv = fma(v[t], v[t], vtv);
     }
-    beta = dfl(2.f, 0.f) / vtv;
+    const dfl rv = recip(vtv);  // v^T v in [1, 3)
+    beta = dfl(2.f * rv.hi, 2.f * rv.lo);
 }
 
 // Deflation test for the subdiagonal entry (l, l-1).
@@ -1221,7 +1234,8 @@ int64_t sym_eig_work_doubles(int n) { return std::max(nonsym_eig_work_doubles(n)
 // clustered K-L eigenvalues came out 1e-4 off, against 1e-6 for the QR path,
 // and restarts from them slowed convergence.)
 cudaError_t launch_sym_eig(const double* H, int n, double* w, double* V, double* work, int* status,
-                           cudaStream_t s, bool fp32) {
+                           cudaStream_t s, bool fp32, bool dfloat) {
+    if (!fp32 && dfloat) return launch_eig(H, n, w, nullptr, V, nullptr, work, status, 1, n, kEigDF, s);
     if (!fp32 && n <= jacobi_max_n()) return launch_sym_eig_jacobi(H, n, w, V, work, status, s, false);
     return launch_eig(H, n, w, nullptr, V, nullptr, work, status, 1, n, fp32 ? kEigFP32 : kEigFP64, s);
 }

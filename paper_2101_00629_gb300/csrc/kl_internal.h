@@ -190,8 +190,10 @@ cudaError_t launch_chol_rinv(double* G, int n, double* Rinv, int* bad, cudaStrea
 // eigenvectors in V (n x n). status[0]: 0 ok, 1 no convergence.
 // fp32: the whole decomposition in FP32 arithmetic (inputs and outputs stay
 // FP64; accuracy ~1e-7 ||H||), for the restarts of the outer solver.
+// dfloat (with fp32 false): the QR path in double-float arithmetic (~1e-13
+// ||H||), for the FP64-grade problems of reduced-precision solves.
 cudaError_t launch_sym_eig(const double* H, int n, double* w, double* V, double* work,
-                           int* status, cudaStream_t s, bool fp32 = false);
+                           int* status, cudaStream_t s, bool fp32 = false, bool dfloat = false);
 // Arithmetic of the small eigensolver: FP64, FP32 (accuracy ~1e-7 ||H||) or
 // double-float (pairs of FP32 numbers, ~1e-14 ||H||, several times faster
 // than FP64 on GB300's small FP64 unit).

@@ -162,8 +162,18 @@ int rayleigh_ritz(Ctx& c, const double* V, const double* AV, int nv, double* max
     int status = 0;
     c.rr_fp32 = fp32;
     if (c.sym) {
-        KL_TRY(ck(c, launch_sym_eig(c.w.H, nv, c.w.theta, c.w.S, c.w.la_work, c.w.ibuf, c.h->stream, fp32), "sym_eig"));
+        // reduced-precision solves: FP64-grade problems in double-float (the
+        // QR path), FP64 solves in FP64
+        const bool dfloat = !fp32 && c.h->prm.precision != KL_FP64;
+        KL_TRY(ck(c, launch_sym_eig(c.w.H, nv, c.w.theta, c.w.S, c.w.la_work, c.w.ibuf, c.h->stream, fp32, dfloat),
+                  "sym_eig"));
         KL_TRY(sync_copy(c, &status, c.w.ibuf, sizeof(int)));
+        if (dfloat && status == 1) {
+            // not converged in double-float: the same matrix in FP64
+            KL_TRY(ck(c, launch_sym_eig(c.w.H, nv, c.w.theta, c.w.S, c.w.la_work, c.w.ibuf, c.h->stream, false),
+                      "sym_eig"));
+            KL_TRY(sync_copy(c, &status, c.w.ibuf, sizeof(int)));
+        }
         if (max_imag) *max_imag = 0.0;
     } else {
         // reduced-precision solves take their FP64-grade problems in
