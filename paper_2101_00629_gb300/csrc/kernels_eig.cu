@@ -75,9 +75,21 @@ __device__ inline dfl operator/(dfl a, dfl b) {
 // 1 / b: an FP32 reciprocal refined by one Newton step in double-float
 // (r + r (1 - b r)), about 2^-46 relative
 __device__ inline dfl recip(dfl b) {
-    const float r = __frcp_rn(b.hi);
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b.hi));  // ~1 ulp; the Newton step squares the error
     const dfl e = dfl(1.f, 0.f) - b * dfl(r, 0.f);
     return fast_two_sum(r, __fmul_rn(r, e.hi));
+}
+// sqrt(a) for a > 0 from an approximate FP32 reciprocal square root y: s = a y,
+// corrected by one Newton step s + (a - s^2) y / 2 in double-float
+__device__ inline dfl sqrt_fast(dfl a) {
+    if (!(a.hi > 0.f)) return dfl(0.f, 0.f);
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a.hi));
+    const float s = __fmul_rn(a.hi, y);
+    const float p = __fmul_rn(s, s);
+    const dfl r = a - dfl(p, __fmaf_rn(s, s, -p));  // a - s^2, s^2 exactly
+    return fast_two_sum(s, __fmul_rn(__fmul_rn(r.hi, y), 0.5f));
 }
 __device__ inline dfl& operator+=(dfl& a, dfl b) { return a = a + b; }
 __device__ inline dfl& operator-=(dfl& a, dfl b) { return a = a - b; }
@@ -247,14 +259,19 @@ __device__ inline void house<dfl>(const dfl* x, int len, dfl* v, dfl& beta) {
         beta = dfl(0.f, 0.f);
         return;
     }
-    int e;
-    frexpf(m, &e);
-    const float sc = ldexpf(1.f, -e);
+    if (m < 1e-30f) {
+        // entries this small (below 1e-30) are dropped with the bulge remnants
+        beta = dfl(0.f, 0.f);
+        return;
+    }
+    // scale by 2^-e with 2^(e-1) <= m < 2^e (exact): exponent bits of m
+    const int e = ((__float_as_int(m) >> 23) & 0xff) - 126;
+    const float sc = __int_as_float((127 - e) << 23);
     dfl xs[3];
     for (int t = 0; t < len; ++t) xs[t] = dfl(x[t].hi * sc, x[t].lo * sc);
     dfl ss = xs[0] * xs[0];
     for (int t = 1; t < len; ++t) ss = fma(xs[t], xs[t], ss);
-    const dfl nrm = sqrt(ss);
+    const dfl nrm = sqrt_fast(ss);  // ss in [0.25, 3)
     const dfl alpha = xs[0] + (xs[0].hi >= 0.f ? nrm : -nrm);
     // one reciprocal (|alpha| >= |x|, in [0.5, 2)), then products
     const dfl ra = recip(alpha);
@@ -670,8 +687,16 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             for (int base = 0; base < ncols; base += per) {
                 const int c = base + tid / g, p = tid % g;
                 R s = R(0.0);
-                if (c < ncols)
-                    for (int t = p; t < len; t += g) s = fma(hv[t], A[(k + 1 + t) + int64_t(k + c) * ld], s);
+                if (c < ncols) {
+                    // four partial sums: the dependent chain is a quarter as long
+                    R s4[4] = {R(0.0), R(0.0), R(0.0), R(0.0)};
+                    const R* col = A + (k + 1) + int64_t(k + c) * ld;
+                    int t = p;
+                    for (; t + 3 * g < len; t += 4 * g)
+                        for (int q = 0; q < 4; ++q) s4[q] = fma(hv[t + q * g], col[t + q * g], s4[q]);
+                    for (; t < len; t += g) s4[0] = fma(hv[t], col[t], s4[0]);
+                    s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+                }
                 for (int o = g / 2; o > 0; o >>= 1) s += shfl_xor(s, o);
                 s *= beta;
                 if (c < ncols)
@@ -686,8 +711,15 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                 R* M = it < n ? A : Z;
                 const int i = it < n ? it : it - n;
                 R s = R(0.0);
-                if (it < items)
-                    for (int t = p; t < len; t += g2) s = fma(M[i + int64_t(k + 1 + t) * ld], hv[t], s);
+                if (it < items) {
+                    R s4[4] = {R(0.0), R(0.0), R(0.0), R(0.0)};
+                    const R* row = M + i + int64_t(k + 1) * ld;
+                    int t = p;
+                    for (; t + 3 * g2 < len; t += 4 * g2)
+                        for (int q = 0; q < 4; ++q) s4[q] = fma(row[int64_t(t + q * g2) * ld], hv[t + q * g2], s4[q]);
+                    for (; t < len; t += g2) s4[0] = fma(row[int64_t(t) * ld], hv[t], s4[0]);
+                    s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+                }
                 for (int o = g2 / 2; o > 0; o >>= 1) s += shfl_xor(s, o);
                 s *= beta;
                 if (it < items)
