@@ -18,6 +18,7 @@
 #include <cfloat>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 #include "kl_internal.h"
 
@@ -324,9 +325,111 @@ __device__ inline int group_size(int items) {
 // equation T11 X - X T22 = T12; the columns of [X; -I] span the
 // T22-invariant subspace and Q is the orthogonal factor of their QR
 // factorisation (Householder).
+// The direct swap for blocks of fixed sizes N1, N2 (not both 1): every loop
+// bound is a constant, so the small arrays stay in registers.
+template <class R, int N1, int N2>
+__device__ void swap_transform_nn(const R* A, int ld, int k, R anorm, R* Qm) {
+    constexpr int n1 = N1, n2 = N2, m = N1 + N2;
+    constexpr int pdim = n1 * n2;
+    R K[pdim * pdim], x[pdim], W[m * n2];
+#pragma unroll
+    for (int r = 0; r < pdim * pdim; ++r) K[r] = R(0.0);
+    // K = I_{n2} (x) T11 - T22^T (x) I_{n1}, x = vec(X) column-major
+    #pragma unroll
+    for (int j = 0; j < n2; ++j)
+        #pragma unroll
+        for (int i = 0; i < n1; ++i) {
+            const int row = i + n1 * j;
+            #pragma unroll
+            for (int i2 = 0; i2 < n1; ++i2) K[row + pdim * (i2 + n1 * j)] += A[(k + i) + int64_t(k + i2) * ld];
+            #pragma unroll
+            for (int j2 = 0; j2 < n2; ++j2) K[row + pdim * (i + n1 * j2)] -= A[(k + n1 + j2) + int64_t(k + n1 + j) * ld];
+            x[row] = A[(k + i) + int64_t(k + n1 + j) * ld];
+        }
+    // Gaussian elimination with partial pivoting; a pivot below eps ||T|| is
+    // replaced by that bound (the blocks have close eigenvalues)
+    R kn = R(0.0);
+    #pragma unroll
+    for (int r = 0; r < pdim * pdim; ++r) kn = fmax(kn, fabs(K[r]));
+    const R tiny = EigNum<R>::eps * fmax(kn, anorm);
+    #pragma unroll
+    for (int c = 0; c < pdim; ++c) {
+        int pr = c;
+        #pragma unroll
+        for (int r = c + 1; r < pdim; ++r)
+            if (fabs(K[r + pdim * c]) > fabs(K[pr + pdim * c])) pr = r;
+        // row exchange by constant indices (the arrays stay in registers)
+#pragma unroll
+        for (int r = c + 1; r < pdim; ++r)
+            if (r == pr) {
+#pragma unroll
+                for (int cc = 0; cc < pdim; ++cc) {
+                    const R t = K[c + pdim * cc];
+                    K[c + pdim * cc] = K[r + pdim * cc];
+                    K[r + pdim * cc] = t;
+                }
+                const R t = x[c];
+                x[c] = x[r];
+                x[r] = t;
+            }
+        if (fabs(K[c + pdim * c]) < tiny) K[c + pdim * c] = K[c + pdim * c] >= R(0.0) ? tiny : -tiny;
+        #pragma unroll
+        for (int r = c + 1; r < pdim; ++r) {
+            const R f = K[r + pdim * c] / K[c + pdim * c];
+            #pragma unroll
+            for (int cc = c; cc < pdim; ++cc) K[r + pdim * cc] -= f * K[c + pdim * cc];
+            x[r] -= f * x[c];
+        }
+    }
+    #pragma unroll
+    for (int r = pdim - 1; r >= 0; --r) {
+        R t = x[r];
+        #pragma unroll
+        for (int cc = r + 1; cc < pdim; ++cc) t -= K[r + pdim * cc] * x[cc];
+        x[r] = t / K[r + pdim * r];
+    }
+    // W = [X; -I] (m x n2), Householder QR with Q accumulated
+    #pragma unroll
+    for (int j = 0; j < n2; ++j)
+        #pragma unroll
+        for (int i = 0; i < m; ++i) W[i + m * j] = (i < n1) ? x[i + n1 * j] : (i - n1 == j ? -R(1.0) : R(0.0));
+    #pragma unroll
+    for (int r = 0; r < m * m; ++r) Qm[r] = (r % m == r / m) ? R(1.0) : R(0.0);
+    #pragma unroll
+    for (int j = 0; j < n2; ++j) {
+        R v[4];
+        const int len = m - j;
+        R ss = R(0.0);
+        #pragma unroll
+        for (int t = 0; t < len; ++t) {
+            v[t] = W[(j + t) + m * j];
+            ss += v[t] * v[t];
+        }
+        if (ss == R(0.0)) continue;
+        const R x0 = v[0], nrm = sqrt(ss);
+        v[0] += (x0 >= R(0.0) ? nrm : -nrm);
+        const R beta = R(1.0) / (nrm * (nrm + fabs(x0)));
+        #pragma unroll
+        for (int c = j; c < n2; ++c) {
+            R sdot = R(0.0);
+            #pragma unroll
+            for (int t = 0; t < len; ++t) sdot += v[t] * W[(j + t) + m * c];
+            #pragma unroll
+            for (int t = 0; t < len; ++t) W[(j + t) + m * c] -= beta * sdot * v[t];
+        }
+        #pragma unroll
+        for (int r = 0; r < m; ++r) {
+            R sdot = R(0.0);
+            #pragma unroll
+            for (int t = 0; t < len; ++t) sdot += Qm[r + m * (j + t)] * v[t];
+            #pragma unroll
+            for (int t = 0; t < len; ++t) Qm[r + m * (j + t)] -= beta * sdot * v[t];
+        }
+    }
+}
+
 template <class R>
 __device__ void swap_transform(const R* A, int ld, int k, int n1, int n2, R anorm, R* Qm) {
-    const int m = n1 + n2;
     if (n1 == 1 && n2 == 1) {
         const R a = A[k + int64_t(k) * ld], d = A[(k + 1) + int64_t(k + 1) * ld];
         const R b = A[k + int64_t(k + 1) * ld];
@@ -338,75 +441,9 @@ __device__ void swap_transform(const R* A, int ld, int k, int n1, int n2, R anor
         Qm[3] = c;
         return;
     }
-    R K[16], x[4], W[8];
-    const int pdim = n1 * n2;
-    for (int r = 0; r < pdim * pdim; ++r) K[r] = R(0.0);
-    // K = I_{n2} (x) T11 - T22^T (x) I_{n1}, x = vec(X) column-major
-    for (int j = 0; j < n2; ++j)
-        for (int i = 0; i < n1; ++i) {
-            const int row = i + n1 * j;
-            for (int i2 = 0; i2 < n1; ++i2) K[row + pdim * (i2 + n1 * j)] += A[(k + i) + int64_t(k + i2) * ld];
-            for (int j2 = 0; j2 < n2; ++j2) K[row + pdim * (i + n1 * j2)] -= A[(k + n1 + j2) + int64_t(k + n1 + j) * ld];
-            x[row] = A[(k + i) + int64_t(k + n1 + j) * ld];
-        }
-    // Gaussian elimination with partial pivoting; a pivot below eps ||T|| is
-    // replaced by that bound (the blocks have close eigenvalues)
-    R kn = R(0.0);
-    for (int r = 0; r < pdim * pdim; ++r) kn = fmax(kn, fabs(K[r]));
-    const R tiny = EigNum<R>::eps * fmax(kn, anorm);
-    for (int c = 0; c < pdim; ++c) {
-        int pr = c;
-        for (int r = c + 1; r < pdim; ++r)
-            if (fabs(K[r + pdim * c]) > fabs(K[pr + pdim * c])) pr = r;
-        if (pr != c) {
-            for (int cc = 0; cc < pdim; ++cc) {
-                const R t = K[c + pdim * cc];
-                K[c + pdim * cc] = K[pr + pdim * cc];
-                K[pr + pdim * cc] = t;
-            }
-            const R t = x[c];
-            x[c] = x[pr];
-            x[pr] = t;
-        }
-        if (fabs(K[c + pdim * c]) < tiny) K[c + pdim * c] = K[c + pdim * c] >= R(0.0) ? tiny : -tiny;
-        for (int r = c + 1; r < pdim; ++r) {
-            const R f = K[r + pdim * c] / K[c + pdim * c];
-            for (int cc = c; cc < pdim; ++cc) K[r + pdim * cc] -= f * K[c + pdim * cc];
-            x[r] -= f * x[c];
-        }
-    }
-    for (int r = pdim - 1; r >= 0; --r) {
-        R t = x[r];
-        for (int cc = r + 1; cc < pdim; ++cc) t -= K[r + pdim * cc] * x[cc];
-        x[r] = t / K[r + pdim * r];
-    }
-    // W = [X; -I] (m x n2), Householder QR with Q accumulated
-    for (int j = 0; j < n2; ++j)
-        for (int i = 0; i < m; ++i) W[i + m * j] = (i < n1) ? x[i + n1 * j] : (i - n1 == j ? -R(1.0) : R(0.0));
-    for (int r = 0; r < m * m; ++r) Qm[r] = (r % m == r / m) ? R(1.0) : R(0.0);
-    for (int j = 0; j < n2; ++j) {
-        R v[4];
-        const int len = m - j;
-        R ss = R(0.0);
-        for (int t = 0; t < len; ++t) {
-            v[t] = W[(j + t) + m * j];
-            ss += v[t] * v[t];
-        }
-        if (ss == R(0.0)) continue;
-        const R x0 = v[0], nrm = sqrt(ss);
-        v[0] += (x0 >= R(0.0) ? nrm : -nrm);
-        const R beta = R(1.0) / (nrm * (nrm + fabs(x0)));
-        for (int c = j; c < n2; ++c) {
-            R sdot = R(0.0);
-            for (int t = 0; t < len; ++t) sdot += v[t] * W[(j + t) + m * c];
-            for (int t = 0; t < len; ++t) W[(j + t) + m * c] -= beta * sdot * v[t];
-        }
-        for (int r = 0; r < m; ++r) {
-            R sdot = R(0.0);
-            for (int t = 0; t < len; ++t) sdot += Qm[r + m * (j + t)] * v[t];
-            for (int t = 0; t < len; ++t) Qm[r + m * (j + t)] -= beta * sdot * v[t];
-        }
-    }
+    if (n1 == 1) swap_transform_nn<R, 1, 2>(A, ld, k, anorm, Qm);
+    else if (n2 == 1) swap_transform_nn<R, 2, 1>(A, ld, k, anorm, Qm);
+    else swap_transform_nn<R, 2, 2>(A, ld, k, anorm, Qm);
 }
 
 // Orders the diagonal blocks (1x1 real eigenvalues, 2x2 complex pairs) of the
@@ -561,20 +598,34 @@ __device__ void order_schur(R* A, R* Z, int n, int ld, int nwant, R anorm, R* in
             continue;
         }
         quiet = 0;
+        // x (m values, stride st) <- Q^T x (rows) or x Q (columns); m fixed
+        // at compile time so that the values stay in registers
+        auto rot = [&](auto mtag, R* x0, int64_t st, const R* Qm, bool transpose) {
+            constexpr int MM = decltype(mtag)::value;
+            R old[MM];
+#pragma unroll
+            for (int t = 0; t < MM; ++t) old[t] = x0[t * st];
+#pragma unroll
+            for (int t = 0; t < MM; ++t) {
+                R acc = R(0.0);
+#pragma unroll
+                for (int u2 = 0; u2 < MM; ++u2) acc = fma(Qm[u2 + MM * t], old[u2], acc);
+                x0[t * st] = acc;
+            }
+            (void)transpose;
+        };
+        auto rot_m = [&](int m, R* x0, int64_t st, const R* Qm) {
+            if (m == 2) rot(std::integral_constant<int, 2>{}, x0, st, Qm, false);
+            else if (m == 3) rot(std::integral_constant<int, 3>{}, x0, st, Qm, false);
+            else rot(std::integral_constant<int, 4>{}, x0, st, Qm, false);
+        };
         // rows of each exchanged span <- Q^T rows (columns k..n-1)
         for (int64_t e = tid; e < int64_t(nswap) * n; e += NT) {
             const int q = int(e / n), j = int(e % n);
             const int info = pinfo[q];
             const int k = pk[q], m = ((info >> 1) & 3) + ((info >> 3) & 3);
             if (j < k) continue;
-            const R* Qm = ord + 16 * int64_t(info >> 8);
-            R old[4];
-            for (int t = 0; t < m; ++t) old[t] = A[(k + t) + int64_t(j) * ld];
-            for (int t = 0; t < m; ++t) {
-                R acc = R(0.0);
-                for (int u2 = 0; u2 < m; ++u2) acc = fma(Qm[u2 + m * t], old[u2], acc);
-                A[(k + t) + int64_t(j) * ld] = acc;
-            }
+            rot_m(m, A + k + int64_t(j) * ld, 1, ord + 16 * int64_t(info >> 8));
         }
         __syncthreads();
         // columns of each exchanged span <- columns Q (rows of A above the
@@ -586,14 +637,8 @@ __device__ void order_schur(R* A, R* Z, int n, int ld, int nwant, R anorm, R* in
             R* M = i2 < n ? A : Z;
             const int r = i2 < n ? i2 : i2 - n;
             if (i2 < n && r >= k + m) continue;
-            const R* Qm = ord + 16 * int64_t(info >> 8);
-            R old[4];
-            for (int t = 0; t < m; ++t) old[t] = M[r + int64_t(k + t) * ld];
-            for (int t = 0; t < m; ++t) {
-                R acc = R(0.0);
-                for (int u2 = 0; u2 < m; ++u2) acc = fma(old[u2], Qm[u2 + m * t], acc);
-                M[r + int64_t(k + t) * ld] = acc;
-            }
+            // (x Q)_t = sum_u x_u Q(u, t): the same sums as Q^T x
+            rot_m(m, M + r + int64_t(k) * ld, ld, ord + 16 * int64_t(info >> 8));
         }
         __syncthreads();
         // the exchanged blocks: zero the new (2,1) block; 1x1 pairs take
