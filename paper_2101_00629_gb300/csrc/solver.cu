@@ -29,6 +29,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -45,7 +46,7 @@ struct EigWs {
     double* la_work;            // eigensolver work
     double* tn_scratch;         // gemm_tn partials
     int64_t tn_len;
-    int* ibuf;                  // status + bad flags (mmax + 1)
+    int* ibuf;                  // eigensolver status, or the two CholQR passes' pivot flags
 };
 
 struct Ctx {
@@ -92,6 +93,22 @@ int sync_copy(Ctx& c, void* dst, const void* src, size_t bytes) {
     return KL_OK;
 }
 
+// Several device->host copies behind one synchronisation (each host round
+// trip leaves the GPU idle between the solve's small kernels).
+struct HostCopy {
+    void* dst;
+    const void* src;
+    size_t bytes;
+};
+int sync_copies(Ctx& c, std::initializer_list<HostCopy> list) {
+    cudaError_t e = cudaSuccess;
+    for (const HostCopy& hc : list)
+        if (e == cudaSuccess && hc.bytes) e = cudaMemcpyAsync(hc.dst, hc.src, hc.bytes, cudaMemcpyDeviceToHost, c.h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.h->stream);
+    if (e != cudaSuccess) return cuda_fail(c.h, e, "device->host copy");
+    return KL_OK;
+}
+
 // Two classical Gram-Schmidt passes of W (N x bw) against V[:, :nv].
 int project_out(Ctx& c, const double* V, int nv, double* W, int bw) {
     if (nv <= 0) return KL_OK;
@@ -107,13 +124,26 @@ int project_out(Ctx& c, const double* V, int nv, double* W, int bw) {
 // vectors and the procedure repeats.
 int orthonormalize(Ctx& c, const double* V, int nv, double* W, int bw) {
     std::vector<double> norms(2 * bw);
-    std::vector<int> bad(bw);
+    std::vector<int> flags(2 * bw), bad(bw);
     for (int attempt = 0; attempt < 6; ++attempt) {
-        // column norms before and after two Gram-Schmidt passes (one sync)
+        // column norms before and after two Gram-Schmidt passes, then CholQR
+        // twice (W R^-1 stays orthogonal to V because it only mixes columns
+        // of W); a collapsed Cholesky pivot is flagged and replaced by 1, so
+        // W stays finite. Everything is checked after one synchronisation:
+        // a column that collapsed in the projection or in either pass is
+        // replaced by a random direction and the block is done again (the
+        // other columns keep their span: the factors are triangular).
         KL_TRY(ck(c, launch_col_norms(W, c.N, c.N, bw, c.w.norms, c.h->stream), "norms"));
         KL_TRY(project_out(c, V, nv, W, bw));
         KL_TRY(ck(c, launch_col_norms(W, c.N, c.N, bw, c.w.norms + bw, c.h->stream), "norms"));
-        KL_TRY(sync_copy(c, norms.data(), c.w.norms, 2 * bw * sizeof(double)));
+        for (int pass = 0; pass < 2; ++pass) {
+            KL_TRY(tn(c, W, c.N, W, c.N, c.w.G, bw, bw, bw));
+            KL_TRY(ck(c, launch_chol_rinv(c.w.G, bw, c.w.Rinv, c.w.ibuf + pass * bw, c.h->stream), "chol"));
+            KL_TRY(nn(c, W, c.N, c.w.Rinv, bw, c.w.T2, c.N, bw, bw, 1.0, 0.0));
+            KL_TRY(ck(c, launch_copy_block(c.w.T2, c.N, W, c.N, c.N, bw, c.h->stream), "copy"));
+        }
+        KL_TRY(sync_copies(c, {{norms.data(), c.w.norms, 2 * bw * sizeof(double)},
+                               {flags.data(), c.w.ibuf, 2 * bw * sizeof(int)}}));
         bool any = false;
         for (int j = 0; j < bw; ++j) {
             // a NaN or Inf in a new block (the operator produced it, or the
@@ -122,19 +152,9 @@ int orthonormalize(Ctx& c, const double* V, int nv, double* W, int bw) {
             if (!std::isfinite(norms[j]))
                 return fail(c.h, KL_ERR_NUMERIC, "NaN or Inf in a block of the Krylov basis");
             const double before = norms[j], after = norms[bw + j];
-            bad[j] = !(after > 1e-10 * before) || !(after > 1e-290) || !std::isfinite(after);
+            bad[j] = !(after > 1e-10 * before) || !(after > 1e-290) || !std::isfinite(after) || flags[j] != 0 ||
+                     flags[bw + j] != 0;
             any |= bad[j] != 0;
-        }
-        // CholQR twice; W R^-1 stays orthogonal to V because it only mixes
-        // columns of W
-        for (int pass = 0; pass < 2 && !any; ++pass) {
-            KL_TRY(tn(c, W, c.N, W, c.N, c.w.G, bw, bw, bw));
-            KL_TRY(ck(c, launch_chol_rinv(c.w.G, bw, c.w.Rinv, c.w.ibuf, c.h->stream), "chol"));
-            KL_TRY(sync_copy(c, bad.data(), c.w.ibuf, bw * sizeof(int)));
-            for (int j = 0; j < bw; ++j) any |= bad[j] != 0;
-            if (any) break;
-            KL_TRY(nn(c, W, c.N, c.w.Rinv, bw, c.w.T2, c.N, bw, bw, 1.0, 0.0));
-            KL_TRY(ck(c, launch_copy_block(c.w.T2, c.N, W, c.N, c.N, bw, c.h->stream), "copy"));
         }
         if (!any) return KL_OK;
         for (int j = 0; j < bw; ++j) {
@@ -239,7 +259,7 @@ int eig_basis_cap(int64_t N, int M, int b) {
 int64_t eig_workspace_doubles(int64_t N, int mcap) {
     const int64_t tn_len = std::max(gemm_tn_scratch_doubles(mcap, mcap, N), int64_t(1));
     const int64_t la = std::max(sym_eig_work_doubles(mcap), nonsym_eig_work_doubles(mcap));
-    return 4 * N * mcap + 5 * int64_t(mcap) * mcap + 8 * int64_t(mcap) + la + tn_len + (int64_t(mcap) + 2) / 2 + 64;
+    return 4 * N * mcap + 5 * int64_t(mcap) * mcap + 8 * int64_t(mcap) + la + tn_len + (2 * int64_t(mcap) + 8) / 2 + 64;
 }
 
 }  // namespace kl
@@ -346,7 +366,7 @@ int eigs_impl(kl_solver* h, int M, double tol, double* lambda, double* Vout, int
     c.w.la_work = take(la);
     c.w.tn_scratch = take(tn_len);
     c.w.tn_len = tn_len;
-    c.w.ibuf = reinterpret_cast<int*>(take((int64_t(mcap) + 2) / 2 + 2));
+    c.w.ibuf = reinterpret_cast<int*>(take((2 * int64_t(mcap) + 8) / 2 + 2));  // two flag sets of <= mcap
 
     double* V = c.w.V;
     double* AV = c.w.AV;
@@ -389,11 +409,11 @@ int eigs_impl(kl_solver* h, int M, double tol, double* lambda, double* Vout, int
         if (int rc = nn(c, V, N, c.w.S, nv, c.w.T1, N, nv, mr, 1.0, 0.0); rc != KL_OK) return rc;
         if (int rc = nn(c, AV, N, c.w.S, nv, c.w.T2, N, nv, mr, 1.0, 0.0); rc != KL_OK) return rc;
         if (int rc = ck(c, launch_resid_norms(c.w.T1, N, c.w.T2, N, c.w.theta, N, mr, c.w.norms, h->stream), "resid"); rc != KL_OK) return rc;
-        if (int rc = sync_copy(c, th.data(), c.w.theta, nv * sizeof(double)); rc != KL_OK) return rc;
-        if (!c.sym) {
-            if (int rc = sync_copy(c, thi.data(), c.w.thetai, nv * sizeof(double)); rc != KL_OK) return rc;
-        }
-        if (int rc = sync_copy(c, rn.data(), c.w.norms, mr * sizeof(double)); rc != KL_OK) return rc;
+        if (int rc = sync_copies(c, {{th.data(), c.w.theta, nv * sizeof(double)},
+                                     {thi.data(), c.w.thetai, c.sym ? 0 : nv * sizeof(double)},
+                                     {rn.data(), c.w.norms, mr * sizeof(double)}});
+            rc != KL_OK)
+            return rc;
         const double scale = std::max(std::fabs(th[0]), 1e-300);
         nconv = 0;
         last_resid = 0.0;
@@ -540,11 +560,11 @@ int eigs_impl(kl_solver* h, int M, double tol, double* lambda, double* Vout, int
         if (int rc = nn(c, AV, N, c.w.S, nv, AY, N, nv, M, 1.0, 0.0); rc != KL_OK) return rc;
     }
     if (int rc = ck(c, launch_resid_norms(Y, N, AY, N, c.w.theta, N, M, c.w.norms, h->stream), "resid"); rc != KL_OK) return rc;
-    if (int rc = sync_copy(c, th.data(), c.w.theta, M * sizeof(double)); rc != KL_OK) return rc;
-    if (!c.sym) {
-        if (int rc = sync_copy(c, thi.data(), c.w.thetai, M * sizeof(double)); rc != KL_OK) return rc;
-    }
-    if (int rc = sync_copy(c, rn.data(), c.w.norms, M * sizeof(double)); rc != KL_OK) return rc;
+    if (int rc = sync_copies(c, {{th.data(), c.w.theta, M * sizeof(double)},
+                                 {thi.data(), c.w.thetai, c.sym ? 0 : M * sizeof(double)},
+                                 {rn.data(), c.w.norms, M * sizeof(double)}});
+        rc != KL_OK)
+        return rc;
     const double scale = std::max(std::fabs(th[0]), 1e-300);
     double max_res = 0.0;
     nconv = 0;
