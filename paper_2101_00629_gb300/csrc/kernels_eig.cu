@@ -187,18 +187,24 @@ struct EigNum<float> {
     static constexpr float hess_min = 0.f;
 };
 
-struct cplx {
-    double re, im;
+// complex numbers over the working arithmetic R
+template <class R>
+struct cpx {
+    R re, im;
 };
-__device__ inline cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
-__device__ inline cplx cdiv(cplx a, cplx b) {
-    // Smith's algorithm
+template <class R>
+__device__ inline cpx<R> cmul_r(cpx<R> a, cpx<R> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+// a / b by Smith's algorithm (ratio of the smaller to the larger part of b)
+template <class R>
+__device__ inline cpx<R> cdiv_r(cpx<R> a, cpx<R> b) {
     if (fabs(b.re) >= fabs(b.im)) {
-        const double r = b.im / b.re, d = b.re + b.im * r;
-        return {(a.re + a.im * r) / d, (a.im - a.re * r) / d};
+        const R r = b.im / b.re, d = R(1.0) / (b.re + b.im * r);
+        return {(a.re + a.im * r) * d, (a.im - a.re * r) * d};
     }
-    const double r = b.re / b.im, d = b.re * r + b.im;
-    return {(a.re * r + a.im) / d, (a.im * r - a.re) / d};
+    const R r = b.re / b.im, d = R(1.0) / (b.re * r + b.im);
+    return {(a.re * r + a.im) * d, (a.im * r - a.re) * d};
 }
 
 template <class R>
@@ -1112,117 +1118,154 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         // vanishing pivot, so the vectors of a (numerically) multiple
         // eigenvalue stay independent (its invariant subspace is spanned by
         // Schur vectors).
+        // All columns are solved together, one block row of T (1x1 or 2x2)
+        // per step from the bottom up: X(i, c) holds the partial sum
+        // sum_{l > i} T(i, l) x_c(l) until row i is reached, then x_c(i). A
+        // step solves its rows for every active column (one thread each),
+        // then adds their contributions to the rows above (one thread per
+        // entry). The real and imaginary columns of a complex pair take the
+        // same real update.
         const int nve = (nv < n && wi[nv - 1] > R(0.0)) ? nv + 1 : nv;
         const R small = EigNum<R>::eps * fmax(anorm, EigNum<R>::tiny);
         const R clus = EigNum<R>::split * anorm;
-        for (int col = tid; col < nve; col += NT) {
-            R* xr = X + int64_t(col) * ld;
-            if (wi[col] == R(0.0)) {
-                const R lam = wr[col];
-                for (int i = 0; i < n; ++i) xr[i] = R(0.0);
-                xr[col] = R(1.0);
-                for (int j = col - 1; j >= 0; --j) {
-                    const bool two = (j > 0) && A[j + int64_t(j - 1) * ld] != R(0.0);
-                    if (!two) {
-                        R s = R(0.0);
-                        for (int l2 = j + 1; l2 <= col; ++l2) s = fma(A[j + int64_t(l2) * ld], xr[l2], s);
-                        R den = A[j + int64_t(j) * ld] - lam;
-                        if (fabs(den) <= clus) {
-                            xr[j] = R(0.0);
-                            continue;
-                        }
-                        if (fabs(den) < small) den = small;
-                        xr[j] = -s / den;
-                    } else {
-                        // 2x2 system for rows j-1, j
-                        R s1 = R(0.0), s2 = R(0.0);
-                        for (int l2 = j + 1; l2 <= col; ++l2) {
-                            s1 = fma(A[(j - 1) + int64_t(l2) * ld], xr[l2], s1);
-                            s2 = fma(A[j + int64_t(l2) * ld], xr[l2], s2);
-                        }
-                        const R a11 = A[(j - 1) + int64_t(j - 1) * ld] - lam, a12 = A[(j - 1) + int64_t(j) * ld];
-                        const R a21 = A[j + int64_t(j - 1) * ld], a22 = A[j + int64_t(j) * ld] - lam;
-                        R det = a11 * a22 - a12 * a21;
-                        if (fabs(det) < small * small) det = small * small;
-                        xr[j - 1] = (-s1 * a22 + s2 * a12) / det;
-                        xr[j] = (-s2 * a11 + s1 * a21) / det;
-                        --j;
-                    }
-                }
-            } else if (wi[col] > R(0.0)) {
-                // complex pair (col, col+1): vector for lambda = wr + i wi, stored
-                // as real part in column col and imaginary part in column col+1
-                R* xi = X + int64_t(col + 1) * ld;
-                const cplx lam = {to_d(wr[col]), to_d(wi[col])};
-                for (int i = 0; i < n; ++i) xr[i] = xi[i] = R(0.0);
-                // (b12, lambda - b11) solves the first row of (B - lambda I) x = 0
-                // for the 2x2 block B and is non-zero because lambda is not real
-                const int q = col;
-                xr[q] = A[q + int64_t(q + 1) * ld];
-                xi[q] = R(0.0);
-                xr[q + 1] = R(lam.re) - A[q + int64_t(q) * ld];
-                xi[q + 1] = R(lam.im);
-                for (int j = q - 1; j >= 0; --j) {
-                    const bool two = (j > 0) && A[j + int64_t(j - 1) * ld] != R(0.0);
-                    if (!two) {
-                        cplx s = {0.0, 0.0};
-                        for (int l2 = j + 1; l2 <= q + 1; ++l2) {
-                            s.re += to_d(A[j + int64_t(l2) * ld] * xr[l2]);
-                            s.im += to_d(A[j + int64_t(l2) * ld] * xi[l2]);
-                        }
-                        cplx den = {to_d(A[j + int64_t(j) * ld]) - lam.re, -lam.im};
-                        if (fabs(den.re) + fabs(den.im) < to_d(small)) den.re = to_d(small);
-                        const cplx r = cdiv({-s.re, -s.im}, den);
-                        xr[j] = R(r.re);
-                        xi[j] = R(r.im);
-                    } else {
-                        cplx s1 = {0.0, 0.0}, s2 = {0.0, 0.0};
-                        for (int l2 = j + 1; l2 <= q + 1; ++l2) {
-                            s1.re += to_d(A[(j - 1) + int64_t(l2) * ld] * xr[l2]);
-                            s1.im += to_d(A[(j - 1) + int64_t(l2) * ld] * xi[l2]);
-                            s2.re += to_d(A[j + int64_t(l2) * ld] * xr[l2]);
-                            s2.im += to_d(A[j + int64_t(l2) * ld] * xi[l2]);
-                        }
-                        const cplx a11 = {to_d(A[(j - 1) + int64_t(j - 1) * ld]) - lam.re, -lam.im};
-                        const cplx a12 = {to_d(A[(j - 1) + int64_t(j) * ld]), 0.0};
-                        const cplx a21 = {to_d(A[j + int64_t(j - 1) * ld]), 0.0};
-                        const cplx a22 = {to_d(A[j + int64_t(j) * ld]) - lam.re, -lam.im};
-                        cplx det = {cmul(a11, a22).re - cmul(a12, a21).re, cmul(a11, a22).im - cmul(a12, a21).im};
-                        if (fabs(det.re) + fabs(det.im) < to_d(small * small)) det.re = to_d(small * small);
-                        const cplx n1 = {-(cmul(s1, a22).re) + cmul(s2, a12).re, -(cmul(s1, a22).im) + cmul(s2, a12).im};
-                        const cplx n2 = {-(cmul(s2, a11).re) + cmul(s1, a21).re, -(cmul(s2, a11).im) + cmul(s1, a21).im};
-                        const cplx r1 = cdiv(n1, det), r2 = cdiv(n2, det);
-                        xr[j - 1] = R(r1.re);
-                        xi[j - 1] = R(r1.im);
-                        xr[j] = R(r2.re);
-                        xi[j] = R(r2.im);
-                        --j;
-                    }
-                }
-            }
-            // wi < 0: second member of a pair, written by its partner
-        }
-        __syncthreads();
-        // V = Z X for the leading columns (X(:, c) vanishes below row c + 1),
-        // then unit columns (complex pairs jointly)
-        R* Vt = A;  // the Schur form is no longer needed
         for (int64_t e = tid; e < int64_t(n) * nve; e += NT) {
             const int i = int(e % n), c = int(e / n);
-            const int top = min(n - 1, c + 1);
-            R s = R(0.0);
-            for (int l2 = 0; l2 <= top; ++l2) s = fma(Z[i + int64_t(l2) * ld], X[l2 + int64_t(c) * ld], s);
-            Vt[i + int64_t(c) * n] = s;
+            R v = R(0.0);
+            if (wi[c] == R(0.0)) {
+                // real eigenvalue: x_c(c) = 1, zero below
+                v = i < c ? A[i + int64_t(c) * ld] : i == c ? R(1.0) : R(0.0);
+            } else if (wi[c] > R(0.0)) {
+                // complex pair (c, c+1), lambda = wr + i wi: the vector is
+                // real part in column c, imaginary part in column c+1. Its
+                // rows c, c+1 are (b12, lambda - b11), which solves the first
+                // row of (B - lambda I) x = 0 for the 2x2 block B and is non-
+                // zero because lambda is not real.
+                const R b12 = A[c + int64_t(c + 1) * ld], d = wr[c] - A[c + int64_t(c) * ld];
+                if (i < c) v = A[i + int64_t(c) * ld] * b12 + A[i + int64_t(c + 1) * ld] * d;
+                else if (i == c) v = b12;
+                else if (i == c + 1) v = d;
+            } else {
+                // imaginary part of the pair (c-1, c)
+                const int q = c - 1;
+                if (i < q) v = A[i + int64_t(c) * ld] * wi[q];
+                else if (i == c) v = wi[q];
+            }
+            X[i + int64_t(c) * ld] = v;
         }
         __syncthreads();
-        for (int c = tid; c < nve; c += NT) {
-            if (wi[c] < R(0.0)) continue;
-            const int w2 = (wi[c] > R(0.0)) ? 2 : 1;
-            R s = R(0.0);
-            for (int t = 0; t < w2; ++t)
-                for (int i = 0; i < n; ++i) s = fma(Vt[i + int64_t(c + t) * n], Vt[i + int64_t(c + t) * n], s);
-            s = s > R(0.0) ? R(1.0) / sqrt(s) : R(1.0);
-            for (int t = 0; t < w2; ++t)
-                for (int i = 0; i < n; ++i) Vt[i + int64_t(c + t) * n] *= s;
+        {
+            // rows below the block of the last column's eigenvalue are known
+            const int cl = nve - 1;
+            int j = (wi[cl] < R(0.0) ? cl - 1 : cl) - 1;
+            while (j >= 0) {
+                // j is the bottom row of a diagonal block of T, so columns
+                // c > j are exactly those whose eigenvalue block lies below
+                const bool two = (j > 0) && A[j + int64_t(j - 1) * ld] != R(0.0);
+                const int jl = two ? j - 1 : j;
+                for (int c = j + 1 + tid; c < nve; c += NT) {
+                    if (wi[c] < R(0.0)) continue;  // solved with its partner
+                    R* xr = X + int64_t(c) * ld;
+                    if (wi[c] == R(0.0)) {
+                        const R lam = wr[c];
+                        if (!two) {
+                            R den = A[j + int64_t(j) * ld] - lam;
+                            if (fabs(den) <= clus) {
+                                xr[j] = R(0.0);
+                            } else {
+                                if (fabs(den) < small) den = small;
+                                xr[j] = -xr[j] / den;
+                            }
+                        } else {
+                            // 2x2 system for rows j-1, j
+                            const R s1 = xr[j - 1], s2 = xr[j];
+                            const R a11 = A[(j - 1) + int64_t(j - 1) * ld] - lam, a12 = A[(j - 1) + int64_t(j) * ld];
+                            const R a21 = A[j + int64_t(j - 1) * ld], a22 = A[j + int64_t(j) * ld] - lam;
+                            R det = a11 * a22 - a12 * a21;
+                            if (fabs(det) < small * small) det = small * small;
+                            const R rdet = R(1.0) / det;
+                            xr[j - 1] = (s2 * a12 - s1 * a22) * rdet;
+                            xr[j] = (s1 * a21 - s2 * a11) * rdet;
+                        }
+                    } else {
+                        R* xi = X + int64_t(c + 1) * ld;
+                        const cpx<R> lam = {wr[c], wi[c]};
+                        if (!two) {
+                            cpx<R> den = {A[j + int64_t(j) * ld] - lam.re, -lam.im};
+                            if (fabs(den.re) + fabs(den.im) < small) den.re = small;
+                            const cpx<R> r = cdiv_r(cpx<R>{-xr[j], -xi[j]}, den);
+                            xr[j] = r.re;
+                            xi[j] = r.im;
+                        } else {
+                            const cpx<R> s1 = {xr[j - 1], xi[j - 1]}, s2 = {xr[j], xi[j]};
+                            const cpx<R> a11 = {A[(j - 1) + int64_t(j - 1) * ld] - lam.re, -lam.im};
+                            const R a12 = A[(j - 1) + int64_t(j) * ld], a21 = A[j + int64_t(j - 1) * ld];
+                            const cpx<R> a22 = {A[j + int64_t(j) * ld] - lam.re, -lam.im};
+                            const cpx<R> p = cmul_r(a11, a22);
+                            cpx<R> det = {p.re - a12 * a21, p.im};
+                            if (fabs(det.re) + fabs(det.im) < small * small) det.re = small * small;
+                            const cpx<R> q1 = cmul_r(s1, a22), q2 = cmul_r(s2, a11);
+                            const cpx<R> r1 = cdiv_r(cpx<R>{s2.re * a12 - q1.re, s2.im * a12 - q1.im}, det);
+                            const cpx<R> r2 = cdiv_r(cpx<R>{s1.re * a21 - q2.re, s1.im * a21 - q2.im}, det);
+                            xr[j - 1] = r1.re;
+                            xi[j - 1] = r1.im;
+                            xr[j] = r2.re;
+                            xi[j] = r2.im;
+                        }
+                    }
+                }
+                __syncthreads();
+                // contributions of rows jl..j to the rows above
+                const int nact = nve - (j + 1);
+                for (int e = tid; e < jl * nact; e += NT) {
+                    const int i = e % jl;
+                    R* x = X + int64_t(j + 1 + e / jl) * ld;
+                    R sum = fma(A[i + int64_t(j) * ld], x[j], x[i]);
+                    if (two) sum = fma(A[i + int64_t(j - 1) * ld], x[j - 1], sum);
+                    x[i] = sum;
+                }
+                __syncthreads();
+                j = jl - 1;
+            }
+        }
+        // V = Z X for the leading columns (X(:, c) vanishes below row c + 1),
+        // four columns per thread, then unit columns (complex pairs jointly)
+        R* Vt = A;  // the Schur form is no longer needed
+        const int ng = (nve + 3) / 4;
+        for (int64_t e = tid; e < int64_t(n) * ng; e += NT) {
+            const int i = int(e % n), c0 = 4 * int(e / n);
+            const int top = min(n - 1, c0 + 4);
+            // columns past the last one repeat it (computed, not stored)
+            const R* x0 = X + int64_t(c0) * ld;
+            const R* x1 = X + int64_t(min(c0 + 1, nve - 1)) * ld;
+            const R* x2 = X + int64_t(min(c0 + 2, nve - 1)) * ld;
+            const R* x3 = X + int64_t(min(c0 + 3, nve - 1)) * ld;
+            R s0 = R(0.0), s1 = R(0.0), s2 = R(0.0), s3 = R(0.0);
+            for (int l2 = 0; l2 <= top; ++l2) {
+                const R z = Z[i + int64_t(l2) * ld];
+                s0 = fma(z, x0[l2], s0);
+                s1 = fma(z, x1[l2], s1);
+                s2 = fma(z, x2[l2], s2);
+                s3 = fma(z, x3[l2], s3);
+            }
+            Vt[i + int64_t(c0) * n] = s0;
+            if (c0 + 1 < nve) Vt[i + int64_t(c0 + 1) * n] = s1;
+            if (c0 + 2 < nve) Vt[i + int64_t(c0 + 2) * n] = s2;
+            if (c0 + 3 < nve) Vt[i + int64_t(c0 + 3) * n] = s3;
+        }
+        __syncthreads();
+        {
+            const int lane = tid & 31, warp = tid >> 5;
+            for (int c = warp; c < nve; c += kEigWarps) {
+                if (wi[c] < R(0.0)) continue;
+                const int w2 = (wi[c] > R(0.0)) ? 2 : 1;
+                R s = R(0.0);
+                for (int t = 0; t < w2; ++t)
+                    for (int i = lane; i < n; i += 32) s = fma(Vt[i + int64_t(c + t) * n], Vt[i + int64_t(c + t) * n], s);
+                for (int o = 16; o > 0; o >>= 1) s += shfl_xor(s, o);
+                s = s > R(0.0) ? R(1.0) / sqrt(s) : R(1.0);
+                for (int t = 0; t < w2; ++t)
+                    for (int i = lane; i < n; i += 32) Vt[i + int64_t(c + t) * n] *= s;
+            }
         }
         __syncthreads();
         for (int i = tid; i < n; i += NT) {
