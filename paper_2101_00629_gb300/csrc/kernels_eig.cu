@@ -626,8 +626,8 @@ __device__ void order_schur(R* A, R* Z, int n, int ld, int nwant, R anorm, R* in
             else rot(std::integral_constant<int, 4>{}, x0, st, Qm, false);
         };
         // rows of each exchanged span <- Q^T rows (columns k..n-1)
-        for (int64_t e = tid; e < int64_t(nswap) * n; e += NT) {
-            const int q = int(e / n), j = int(e % n);
+        for (int e = tid; e < nswap * n; e += NT) {
+            const int q = int(unsigned(e) / unsigned(n)), j = e - q * n;
             const int info = pinfo[q];
             const int k = pk[q], m = ((info >> 1) & 3) + ((info >> 3) & 3);
             if (j < k) continue;
@@ -636,8 +636,8 @@ __device__ void order_schur(R* A, R* Z, int n, int ld, int nwant, R anorm, R* in
         __syncthreads();
         // columns of each exchanged span <- columns Q (rows of A above the
         // span's end, all rows of Z)
-        for (int64_t e = tid; e < int64_t(nswap) * 2 * n; e += NT) {
-            const int q = int(e / (2 * n)), i2 = int(e % (2 * n));
+        for (int e = tid; e < nswap * 2 * n; e += NT) {
+            const int q = int(unsigned(e) / unsigned(2 * n)), i2 = e - q * 2 * n;
             const int info = pinfo[q];
             const int k = pk[q], m = ((info >> 1) & 3) + ((info >> 3) & 3);
             R* M = i2 < n ? A : Z;
@@ -750,8 +750,24 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                 }
                 for (int o = g / 2; o > 0; o >>= 1) s += shfl_xor(s, o);
                 s *= beta;
-                if (c < ncols)
-                    for (int t = p; t < len; t += g) A[(k + 1 + t) + int64_t(k + c) * ld] -= s * hv[t];
+                if (c < ncols) {
+                    // four elements per step: loads of a step issue together
+                    // (hv and A are both shared memory, so a store orders
+                    // every later load)
+                    R* col = A + (k + 1) + int64_t(k + c) * ld;
+                    int t = p;
+                    for (; t + 3 * g < len; t += 4 * g) {
+                        R a4[4], h4[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            a4[q] = col[t + q * g];
+                            h4[q] = hv[t + q * g];
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) col[t + q * g] = a4[q] - s * h4[q];
+                    }
+                    for (; t < len; t += g) col[t] -= s * hv[t];
+                }
             }
             __syncthreads();
             // right: all rows of A and of Z, columns k+1..n-1
@@ -773,8 +789,21 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                 }
                 for (int o = g2 / 2; o > 0; o >>= 1) s += shfl_xor(s, o);
                 s *= beta;
-                if (it < items)
-                    for (int t = p; t < len; t += g2) M[i + int64_t(k + 1 + t) * ld] -= s * hv[t];
+                if (it < items) {
+                    R* row = M + i + int64_t(k + 1) * ld;
+                    int t = p;
+                    for (; t + 3 * g2 < len; t += 4 * g2) {
+                        R a4[4], h4[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            a4[q] = row[int64_t(t + q * g2) * ld];
+                            h4[q] = hv[t + q * g2];
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) row[int64_t(t + q * g2) * ld] = a4[q] - s * h4[q];
+                    }
+                    for (; t < len; t += g2) row[int64_t(t) * ld] -= s * hv[t];
+                }
             }
         }
         __syncthreads();

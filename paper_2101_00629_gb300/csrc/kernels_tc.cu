@@ -507,11 +507,18 @@ __device__ __forceinline__ Unit sym_unit_of(const TcInstance& I, int64_t u) {
     return r;
 }
 
-// Index of the transposed partial sum of tile I and chunk c >= 2I + 2 among
-// all of them (tile by tile, chunk by chunk): tiles I' < I contribute
-// nchunks - 2 - 2 I' each.
-__host__ __device__ __forceinline__ int64_t sym_p2_index(int64_t I, int64_t c, int64_t nchunks) {
-    return I * (nchunks - 2) - I * (I - 1) + (c - 2 * I - 2);
+// Index of the transposed partial sum of tile I and chunk c >= 2I + 2 within
+// the band of tiles [b0, b1), chunk by chunk and, within a chunk, tile by
+// tile: the sums a chunk's reduction reads are contiguous. Chunk c' holds
+// g(c' / 2) of them, g(m) = clamp(m, b0, b1) - b0 (the band's tiles I < c' / 2),
+// and the sum of g(m) over m < M is G(M) = x (x - 1) / 2 + max(0, M - b1) (b1 - b0)
+// with x = max(0, min(M, b1) - b0).
+__host__ __device__ __forceinline__ int64_t sym_p2_index(int64_t c, int64_t I, int64_t b0, int64_t b1) {
+    const int64_t M = c >> 1;
+    const int64_t x = (M < b1 ? M : b1) - b0;
+    const int64_t G = x > 0 ? x * (x - 1) / 2 + (M > b1 ? (M - b1) * (b1 - b0) : 0) : 0;
+    const int64_t gM = (M < b0 ? b0 : M > b1 ? b1 : M) - b0;
+    return 2 * G + ((c & 1) ? gM : 0) + (I - b0);
 }
 
 // Symmetric mode layout (split BF16, N = 16): shared memory holds the ring of
@@ -707,8 +714,9 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
             // accumulator of product m (buffer m & 1; M = 64 rows: row 16 q + l
             // in lane l < 16 of the lane quarter q; warpgroup w the columns
             // [8 w, 8 w + 8)) and store it as the FP32 partial sum of the 64
-            // sources of its chunk (p2: its index within the band).
-            auto drain = [&](int64_t p2, uint32_t m) {
+            // sources of its chunk ch.
+            auto drain = [&](int64_t ch, uint32_t m) {
+                const int64_t p2 = sym_p2_index(ch, un.tile, I.sym_tile0, I.sym_tile1);
                 const bool got = ok && warp_wait(&d2full_bar[m & 1], (m >> 1) & 1u, wlim);
                 if (!got) ok = false;
                 tc_fence_after();
@@ -729,9 +737,6 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                 tc_fence_before();
                 mbar_arrive(&d2free_bar[m & 1]);
             };
-            // transposed partial sum of the unit's first chunk with one
-            // (2 tile + 2), relative to the band's first
-            const int64_t p2_unit = SYM ? sym_p2_index(un.tile, 2 * un.tile + 2, I.nchunks) - I.sym_p2_off0 : 0;
             const int first_offd = SYM ? int(2 * un.tile + 2 - un.c0) : un.nloc;  // local index
             // One chunk: wait for its record and a free kernel-tile stage,
             // evaluate, split, store into tensor memory (and, for a transposed
@@ -802,7 +807,7 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                     // og - 2 has long finished, and its buffer is the one the
                     // next product needs
                     if (og >= drained + 2) {
-                        drain(p2_unit + (jl - 2 - first_offd), drained);
+                        drain(un.c0 + (jl - 2), drained);
                         ++drained;
                     }
                     ++og;
@@ -818,7 +823,7 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
                     if (!chunk_step(jl, std::true_type{})) ok = false;
                 // the unit's last (up to two) transposed products
                 while (ok && drained < og) {
-                    drain(p2_unit + (un.nloc - int(og - drained) - first_offd), drained);
+                    drain(un.c0 + (un.nloc - int(og - drained)), drained);
                     ++drained;
                 }
             }
@@ -1036,31 +1041,6 @@ cudaError_t launch_batch_prec(const TcBatch& b, int np, bool sym, int sm_count, 
     }
 }
 
-// W = sigma^2 * post * sum over source splits of the (hi, lo) partial sums,
-// in a fixed order.
-__global__ void tc_reduce_kernel(const float2* __restrict__ part, int splits, int64_t T, int k, double sigma2,
-                                 const double* __restrict__ post, double* __restrict__ Y, int64_t ldy) {
-    const int64_t total = T * k;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
-         i += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t c = i / T, t = i - c * T;
-        // double-float accumulation (error-free two-sum into hi, errors and
-        // the partials' low parts into lo): FP32 instructions, ~48 bits
-        float hi = 0.f, lo = 0.f;
-        for (int sp = 0; sp < splits; ++sp) {
-            const float2 v = part[(int64_t(sp) * k + c) * T + t];
-            const float sum = __fadd_rn(hi, v.x);
-            const float bb = __fsub_rn(sum, hi);
-            const float er = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(v.x, bb));
-            hi = sum;
-            lo = __fadd_rn(lo, __fadd_rn(er, v.y));
-        }
-        double s = (double(hi) + double(lo)) * sigma2;
-        if (post) s *= post[t];
-        Y[c * ldy + t] = s;
-    }
-}
-
 // Adds v (FP32, or an FP32 (hi, lo) pair) into the double-float (hi, lo):
 // error-free two-sum into hi, the error and v's low part into lo.
 __device__ __forceinline__ void df_add(float& hi, float& lo, float v, float vlo) {
@@ -1071,91 +1051,152 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float v, float vlo)
     lo = __fadd_rn(lo, __fadd_rn(er, vlo));
 }
 
-// Symmetric mode, one band of tiles [tile0, tile1). A block serves the
-// 32 / kstride consecutive points t >= tile0 * 128 held by one transposed-sum
-// row segment (lane: point, then column; kstride = k rounded up to 8) with 8
-// threads each (threadIdx.y): thread y sums, as a double-float, the y-th
-// eighth of the direct partial sums of the point's tile (when the tile is in
-// the band) and the y-th eighth of the transposed partial sums of the band's
-// tiles I below the point's tile (I ascending). The eight sums are then added
-// in the order y = 0..7 after the running sum of the earlier bands (acc; none
-// for the first band): a fixed order, with eight loads in flight per thread.
-// Points of the band's tiles are then complete, W = sigma^2 post (hi + lo);
-// later points keep the running sum in acc.
-constexpr int kSymRedSplit = 8;
-__global__ void __launch_bounds__(32 * kSymRedSplit)
-tc_sym_reduce_kernel(const float2* __restrict__ part1, const float* __restrict__ part2,
-                     const int2* __restrict__ tab, int64_t nchunks, int64_t T, int k, int tile0, int tile1,
-                     int64_t unit_begin, int64_t p2_off0, int first, float2* __restrict__ acc, double sigma2,
-                     const double* __restrict__ post, double* __restrict__ Y, int64_t ldy) {
-    __shared__ float2 sh[kSymRedSplit][32];
-    const int kstride = (k + 7) & ~7;
-    const int tpb = 32 / kstride;  // points per block
-    const int64_t t0 = int64_t(tile0) * 128;
-    const int64_t rows = T - t0;
-    const int64_t nblocks = (rows + tpb - 1) / tpb;
+// W = sigma^2 * post * sum over source splits of the (hi, lo) partial sums,
+// in a fixed order. A block serves 32 consecutive points of one column with
+// 8 warps: warp y sums the y-th eighth of the splits as a double-float (eight
+// loads in flight per thread), then warp 0 adds the eight sums in the order
+// y = 0..7. Many outputs are short of threads otherwise (T k / 256 blocks of
+// one load chain each cannot keep enough loads in flight to stream the
+// partial sums at HBM rate).
+constexpr int kRedSplit = 8;
+__global__ void __launch_bounds__(32 * kRedSplit)
+tc_reduce_kernel(const float2* __restrict__ part, int splits, int64_t T, int k, double sigma2,
+                 const double* __restrict__ post, double* __restrict__ Y, int64_t ldy) {
+    __shared__ float2 sh[kRedSplit][32];
+    const int64_t tblocks = (T + 31) / 32;
     const int y = threadIdx.y;
-    const int c = threadIdx.x % kstride;
-    for (int64_t b = blockIdx.x; b < nblocks; b += gridDim.x) {
-        const int64_t t = t0 + b * tpb + threadIdx.x / kstride;
-        const bool valid = t < T && c < k;
+    const int sa = splits * y / kRedSplit, sb = splits * (y + 1) / kRedSplit;
+    const int64_t st = int64_t(k) * T;  // from one split to the next
+    for (int64_t b = blockIdx.x; b < tblocks * k; b += gridDim.x) {
+        const int c = int(b / tblocks);
+        const int64_t t = (b - int64_t(c) * tblocks) * 32 + threadIdx.x;
         float hi = 0.f, lo = 0.f;
-        if (valid) {
-            const int J = int(t / 128);
-            const int64_t ch = t / 64;
-            const int row = int(t % 64);
-            if (J < tile1) {
-                const int64_t u0 = tab[J].x, n1 = tab[J + 1].x - u0;
-                const int64_t ua = u0 + n1 * y / kSymRedSplit, ub = u0 + n1 * (y + 1) / kSymRedSplit;
-                for (int64_t u = ua; u < ub; ++u) {
-                    const float2 v = part1[((u - unit_begin) * k + c) * 128 + (t % 128)];
-                    df_add(hi, lo, v.x, v.y);
-                }
-            }
-            const int iend = J < tile1 ? J : tile1;
-            const int n2 = iend - tile0;
-            const int ia = tile0 + int(int64_t(n2) * y / kSymRedSplit);
-            const int ib = tile0 + int(int64_t(n2) * (y + 1) / kSymRedSplit);
-            // transposed sums of (I, ch) for I = ia, ia + 1, ...: their indices
-            // grow by nchunks - 4 - 2 I from one I to the next
-            const int64_t step = int64_t(64) * kstride;
-            const float* p2 = part2 + int64_t(row) * kstride + c + (sym_p2_index(ia, ch, nchunks) - p2_off0) * step;
-            int64_t d = (nchunks - 4 - 2 * int64_t(ia)) * step;
-            const int64_t dd = 2 * step;
-            int I = ia;
-            for (; I + 8 <= ib; I += 8) {
-                float v[8];
+        if (t < T) {
+            // groups of 8 splits, the last one predicated: every group's
+            // loads are in flight together
+            const float2* pp = part + (int64_t(sa) * k + c) * T + t;
+            for (int sp = sa; sp < sb; sp += 8) {
+                float2 v[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    v[q] = *p2;
-                    p2 += d;
-                    d -= dd;
-                }
+                for (int q = 0; q < 8; ++q)
+                    if (sp + q < sb) v[q] = pp[q * st];
+                pp += 8 * st;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) df_add(hi, lo, v[q], 0.f);
-            }
-            for (; I < ib; ++I) {
-                df_add(hi, lo, *p2, 0.f);
-                p2 += d;
-                d -= dd;
+                for (int q = 0; q < 8; ++q)
+                    if (sp + q < sb) df_add(hi, lo, v[q].x, v[q].y);
             }
         }
         sh[y][threadIdx.x] = make_float2(hi, lo);
         __syncthreads();
-        if (y == 0 && valid) {
+        if (y == 0 && t < T) {
             float h = 0.f, l = 0.f;
-            if (!first) {
-                const float2 a = acc[c * T + t];
-                h = a.x;
-                l = a.y;
+            for (int q = 0; q < kRedSplit; ++q) df_add(h, l, sh[q][threadIdx.x].x, sh[q][threadIdx.x].y);
+            double v = (double(h) + double(l)) * sigma2;
+            if (post) v *= post[t];
+            Y[c * ldy + t] = v;
+        }
+        __syncthreads();
+    }
+}
+
+
+// Symmetric mode, one band of tiles [tile0, tile1). A block serves the
+// 32 / (kstride / 2) consecutive points t >= tile0 * 128 of one transposed-
+// sum row segment (kstride = k rounded up to 8), a thread two columns of a
+// point (lane: point, then column pair) with 8 threads per point and column
+// pair (threadIdx.y): thread y sums, as double-floats, the y-th eighth of the
+// direct partial sums of the point's tile (when the tile is in the band) and
+// the y-th eighth of the transposed partial sums of the band's tiles I below
+// the point's tile (I ascending; one 8-byte load per tile, in groups of eight
+// loads in flight). The eight sums are then added in the order y = 0..7
+// after the running sum of the earlier bands (acc; none for the first band):
+// a fixed order. Column k of a transposed row (k odd) is padding: read,
+// never written out. 32-bit offsets: a band's partial sums stay under 2^31
+// floats and points under 2^26 (tc_sym_eligible).
+constexpr int kSymRedSplit = 8;
+constexpr int kSymRedLoads = 8;  // loads in flight per thread
+__global__ void __launch_bounds__(32 * kSymRedSplit)
+tc_sym_reduce_kernel(const float2* __restrict__ part1, const float* __restrict__ part2,
+                     const int2* __restrict__ tab, int64_t T, int k, int tile0, int tile1,
+                     int64_t unit_begin, int first, float2* __restrict__ acc, double sigma2,
+                     const double* __restrict__ post, double* __restrict__ Y, int64_t ldy) {
+    __shared__ float4 sh[kSymRedSplit][32];
+    const int kstride = (k + 7) & ~7;
+    const int ng = kstride / 2;    // column pairs per point
+    const int tpb = 32 / ng;       // points per block
+    const int t0 = tile0 * 128;
+    const int nblocks = (int(T) - t0 + tpb - 1) / tpb;
+    const int y = threadIdx.y;
+    const int c0 = 2 * (threadIdx.x % ng);
+    const int step = 32 * kstride;  // one 64 x kstride block of transposed sums, in 8-byte vectors
+    const float2* p2base = reinterpret_cast<const float2*>(part2);
+    for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
+        const int t = t0 + b * tpb + threadIdx.x / ng;
+        const bool valid = t < int(T) && c0 < k;
+        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+        if (valid) {
+            const int J = t >> 7;
+            if (J < tile1) {
+                const int u0 = tab[J].x, n1 = tab[J + 1].x - u0;
+                const int ua = u0 + n1 * y / kSymRedSplit, ub = u0 + n1 * (y + 1) / kSymRedSplit;
+                const float2* pu = part1 + ((int(ua - unit_begin) * k + c0) * 128 + (t & 127));
+                for (int u = ua; u < ub; ++u, pu += k * 128) {
+                    const float2 v0 = pu[0];
+                    df_add(h0, l0, v0.x, v0.y);
+                    if (c0 + 1 < k) {
+                        const float2 v1 = pu[128];
+                        df_add(h1, l1, v1.x, v1.y);
+                    }
+                }
             }
-            for (int q = 0; q < kSymRedSplit; ++q) df_add(h, l, sh[q][threadIdx.x].x, sh[q][threadIdx.x].y);
-            if (int(t / 128) < tile1) {
-                double v = (double(h) + double(l)) * sigma2;
-                if (post) v *= post[t];
-                Y[c * ldy + t] = v;
+            const int n2 = (J < tile1 ? J : tile1) - tile0;
+            const int ia = tile0 + n2 * y / kSymRedSplit;
+            const int ib = tile0 + n2 * (y + 1) / kSymRedSplit;
+            // transposed sums of (I, ch) for I = ia, ia + 1, ...: consecutive
+            // blocks
+            const float2* p2 = p2base + ((t & 63) * kstride + c0) / 2;
+            int off = int(sym_p2_index(t >> 6, ia, tile0, tile1)) * step;
+            for (int I = ia; I < ib; I += kSymRedLoads) {
+                float2 v[kSymRedLoads];
+#pragma unroll
+                for (int q = 0; q < kSymRedLoads; ++q) {
+                    if (I + q < ib) v[q] = p2[off];
+                    off += step;
+                }
+#pragma unroll
+                for (int q = 0; q < kSymRedLoads; ++q)
+                    if (I + q < ib) {
+                        df_add(h0, l0, v[q].x, 0.f);
+                        df_add(h1, l1, v[q].y, 0.f);
+                    }
+            }
+        }
+        sh[y][threadIdx.x] = make_float4(h0, l0, h1, l1);
+        __syncthreads();
+        if (y == 0 && valid) {
+            float a0 = 0.f, b0 = 0.f, a1 = 0.f, b1 = 0.f;
+            if (!first) {
+                const float2 r0 = acc[int64_t(c0) * T + t];
+                a0 = r0.x;
+                b0 = r0.y;
+                if (c0 + 1 < k) {
+                    const float2 r1 = acc[int64_t(c0 + 1) * T + t];
+                    a1 = r1.x;
+                    b1 = r1.y;
+                }
+            }
+            for (int q = 0; q < kSymRedSplit; ++q) {
+                const float4 w = sh[q][threadIdx.x];
+                df_add(a0, b0, w.x, w.y);
+                df_add(a1, b1, w.z, w.w);
+            }
+            if ((t >> 7) < tile1) {
+                const double m = post ? sigma2 * post[t] : sigma2;
+                Y[c0 * ldy + t] = (double(a0) + double(b0)) * m;
+                if (c0 + 1 < k) Y[(c0 + 1) * ldy + t] = (double(a1) + double(b1)) * m;
             } else {
-                acc[c * T + t] = make_float2(h, l);
+                acc[int64_t(c0) * T + t] = make_float2(a0, b0);
+                if (c0 + 1 < k) acc[int64_t(c0 + 1) * T + t] = make_float2(a1, b1);
             }
         }
         __syncthreads();
@@ -1303,9 +1344,9 @@ cudaError_t tc_finish(const TcArgs& a, cudaStream_t s, int* launched) {
     KL_RANGE(part, p.part_doubles, float2, "tc_reduce partial sums");
     KL_RANGE(a.Y, block_extent(a.T, a.k, a.ldy), double, "tc_reduce Y");
     KL_RANGE(a.post, a.T, double, "tc_reduce post");
-    const int64_t total = a.T * a.k;
-    const int g = int(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, int64_t(a.sm_count) * 8)));
-    tc_reduce_kernel<<<g, 256, 0, s>>>(part, p.splits, a.T, a.k, a.ks.sigma2, a.post, a.Y, a.ldy);
+    const int64_t nblk = (a.T + 31) / 32 * a.k;
+    const int g = int(std::max<int64_t>(1, std::min<int64_t>(nblk, int64_t(a.sm_count) * 16)));
+    tc_reduce_kernel<<<g, dim3(32, kRedSplit), 0, s>>>(part, p.splits, a.T, a.k, a.ks.sigma2, a.post, a.Y, a.ldy);
     ++*launched;
     return cudaGetLastError();
 }
@@ -1314,7 +1355,11 @@ cudaError_t tc_finish(const TcArgs& a, cudaStream_t s, int* launched) {
 // more tiles make more bands.
 constexpr int64_t kSymP2Cap = int64_t(128) << 20;
 
-bool tc_sym_eligible(int64_t T, int k, bool tf32) { return !tf32 && k >= 1 && k <= 16 && T >= 1; }
+// T <= 2^26 keeps the symmetric reduction's 32-bit offsets in range (one
+// tile's transposed sums: at most 2^30 floats)
+bool tc_sym_eligible(int64_t T, int k, bool tf32) {
+    return !tf32 && k >= 1 && k <= 16 && T >= 1 && T <= (int64_t(1) << 26);
+}
 
 TcSymPlan tc_sym_plan(int64_t T, int kcap, int sm_count) {
     TcSymPlan p;
@@ -1430,7 +1475,6 @@ cudaError_t launch_pair_tc_sym(const TcArgs& a, cudaStream_t s, int* launched) {
         I.sym_tab = tab;
         I.part2 = part2;
         I.sym_unit_begin = p.tab[tile0].x;
-        I.sym_p2_off0 = sym_p2_index(tile0, 2 * int64_t(tile0) + 2, p.nchunks);
         I.sym_tile0 = tile0;
         I.sym_tile1 = tile1;
         batch.nunits = int64_t(p.tab[tile1].x) - p.tab[tile0].x;
@@ -1454,10 +1498,11 @@ cudaError_t launch_pair_tc_sym(const TcArgs& a, cudaStream_t s, int* launched) {
         ++*launched;
         if (e != cudaSuccess) return e;
         const int64_t rows = a.T - int64_t(tile0) * 128;
-        const int64_t nblk = (rows + 32 / ((a.k + 7) / 8 * 8) - 1) / (32 / ((a.k + 7) / 8 * 8));
+        const int tpb = 32 / ((a.k + 7) / 8 * 4);  // points per block: 2 columns per thread
+        const int64_t nblk = (rows + tpb - 1) / tpb;
         const int g = int(std::max<int64_t>(1, std::min<int64_t>(nblk, int64_t(a.sm_count) * 16)));
-        tc_sym_reduce_kernel<<<g, dim3(32, kSymRedSplit), 0, s>>>(part1, part2, tab, p.nchunks, a.T, a.k, tile0, tile1,
-                                               I.sym_unit_begin, I.sym_p2_off0, b == 0, acc, a.ks.sigma2, a.post,
+        tc_sym_reduce_kernel<<<g, dim3(32, kSymRedSplit), 0, s>>>(part1, part2, tab, a.T, a.k, tile0, tile1,
+                                               I.sym_unit_begin, b == 0, acc, a.ks.sigma2, a.post,
                                                a.Y, a.ldy);
         ++*launched;
         e = cudaGetLastError();

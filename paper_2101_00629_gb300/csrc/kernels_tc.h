@@ -49,11 +49,11 @@ struct TcInstance {
     float cscale;
     // symmetric mode only: per tile {first unit, chunks per unit} (one entry
     // more than tiles, global unit numbering), the launch's first unit and
-    // tile range [sym_tile0, sym_tile1), the transposed partial sums and the
-    // index of the band's first one
+    // tile range [sym_tile0, sym_tile1) and the band's transposed partial
+    // sums (chunk-major within the band)
     const int2* sym_tab;
     float* part2;
-    int64_t sym_unit_begin, sym_p2_off0;
+    int64_t sym_unit_begin;
     int sym_tile0, sym_tile1;
 };
 // Instances of one launch (same precision and N rounded to 16); passed by
