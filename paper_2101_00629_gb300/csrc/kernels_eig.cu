@@ -968,14 +968,19 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             __syncthreads();
             continue;
         }
-        // Francis R-shift step on the window [l, u] (size ns >= 3). The
-        // reflector of bulge step kk + 1 is formed from column r0 of rows
-        // r0 + 1 .. r0 + 3 once step kk's right application has updated them:
-        // warp 0 applies step kk to exactly those rows (lanes 1..3) and hands
-        // the new entries to lane 0, which forms the next reflector while the
-        // other warps apply step kk to the remaining rows of A and to Z. Two
-        // block barriers per bulge step instead of three, and the reflector's
-        // chain of dependent FP64 operations runs beside the applications.
+        // Francis R-shift step on the window [l, u] (size ns >= 3). Bulge
+        // step kk applies the reflector P (rows and columns r0..r0+2) as
+        // H <- P H P and Z <- Z P. Only the core block, rows r0..rmax
+        // (rmax = min(r0 + 3, u)) of columns r0..r0+2, takes both the left
+        // and the right product; the next reflector is formed from its
+        // column r0 (rows r0+1..r0+3). Warp 0 applies P to the core (left
+        // product on its three columns, lanes 0..2, then right product on
+        // its rows, lanes 0..nq) and lane 0 forms the next reflector, while
+        // the other warps apply the left product to the other columns
+        // (c0 = r0 - 1 and r0+3..), the right product to the rows above the
+        // core, and Z. These sets are disjoint and the left and right
+        // products commute, so one block barrier per bulge step suffices:
+        // after it, the next core's columns carry every earlier update.
         // Reflectors alternate between two shared slots (the next one is
         // written while the current one is still being read).
         ++total_its;
@@ -992,32 +997,34 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             const R v0 = s_vb[b][0], v1 = s_vb[b][1], v2 = s_vb[b][2], beta = s_bb[b];
             const int r0 = l + kk;
             const int c0 = l + (kk > 0 ? kk - 1 : 0);
+            // symmetric input: the matrix is tridiagonal (plus the bulge), so
+            // columns past r0 + 4 and rows before r0 - 2 hold only rounding
+            // remnants and are never read
             const int jend = sym ? min(n, r0 + 5) : n;
-            for (int j = c0 + tid; j < jend; j += NT) {
-                R* col = A + int64_t(j) * ld + r0;
-                const R a0 = col[0], a1 = col[1], a2 = col[2];
-                const R s = beta * fma(v2, a2, fma(v1, a1, v0 * a0));
-                col[0] = a0 - s * v0;
-                col[1] = a1 - s * v1;
-                col[2] = a2 - s * v2;
-            }
-            __syncthreads();
-            // rows of A touched: i0 .. rmax = min(r0 + 3, u); rows r0 + 1 ..
-            // rmax (nq of them, 2 or 3) go to warp 0, rows i0 .. r0 and all
-            // of Z to the other warps
             const int rmax = min(r0 + 3, u);
             const int nq = rmax - r0;
-            const int i0 = sym ? max(0, r0 - 2) : 0;  // first row of A touched
+            const int i0 = sym ? max(0, r0 - 2) : 0;
             if (tid < 32) {
+                // core, left product: columns r0 + lane, rows r0..r0+2
+                if (tid < 3 && r0 + tid < jend) {
+                    R* col = A + int64_t(r0 + tid) * ld + r0;
+                    const R a0 = col[0], a1 = col[1], a2 = col[2];
+                    const R sc = beta * fma(v2, a2, fma(v1, a1, v0 * a0));
+                    col[0] = a0 - sc * v0;
+                    col[1] = a1 - sc * v1;
+                    col[2] = a2 - sc * v2;
+                }
+                __syncwarp();
+                // core, right product: rows r0 + lane, columns r0..r0+2
                 R xnew = R(0.0);
-                if (tid >= 1 && tid <= nq) {
+                if (tid <= nq) {
                     R* row = A + (r0 + tid) + int64_t(r0) * ld;
                     const R a0 = row[0], a1 = row[ld], a2 = row[2 * int64_t(ld)];
-                    const R s = beta * fma(a2, v2, fma(a1, v1, a0 * v0));
-                    xnew = a0 - s * v0;
+                    const R sc = beta * fma(a2, v2, fma(a1, v1, a0 * v0));
+                    xnew = a0 - sc * v0;
                     row[0] = xnew;
-                    row[ld] = a1 - s * v1;
-                    row[2 * int64_t(ld)] = a2 - s * v2;
+                    row[ld] = a1 - sc * v1;
+                    row[2 * int64_t(ld)] = a2 - sc * v2;
                 }
                 R xx[3];
                 xx[0] = shfl_idx(xnew, 1);
@@ -1032,16 +1039,30 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
                     s_bb[b ^ 1] = bt;
                 }
             } else {
-                const int na = r0 + 1 - i0;
-                for (int e = tid - 32; e < na + n; e += NT - 32) {
-                    R* M = e < na ? A : Z;
-                    const int i = e < na ? e + i0 : e - na;
-                    R* row = M + i + int64_t(r0) * ld;
-                    const R a0 = row[0], a1 = row[ld], a2 = row[2 * int64_t(ld)];
-                    const R s = beta * fma(a2, v2, fma(a1, v1, a0 * v0));
-                    row[0] = a0 - s * v0;
-                    row[ld] = a1 - s * v1;
-                    row[2 * int64_t(ld)] = a2 - s * v2;
+                // left product on column c0 (kk > 0) and columns r0+3..jend-1,
+                // right product on rows i0..r0-1 of A and on every row of Z
+                const int lc = c0 < r0 ? 1 : 0;
+                const int nl = lc + max(0, jend - (r0 + 3));
+                const int nr = max(0, r0 - i0);
+                for (int e = tid - 32; e < nl + nr + n; e += NT - 32) {
+                    if (e < nl) {
+                        const int j = (e < lc) ? c0 : r0 + 3 + (e - lc);
+                        R* col = A + int64_t(j) * ld + r0;
+                        const R a0 = col[0], a1 = col[1], a2 = col[2];
+                        const R sc = beta * fma(v2, a2, fma(v1, a1, v0 * a0));
+                        col[0] = a0 - sc * v0;
+                        col[1] = a1 - sc * v1;
+                        col[2] = a2 - sc * v2;
+                    } else {
+                        R* M = e < nl + nr ? A : Z;
+                        const int i = e < nl + nr ? i0 + (e - nl) : e - nl - nr;
+                        R* row = M + i + int64_t(r0) * ld;
+                        const R a0 = row[0], a1 = row[ld], a2 = row[2 * int64_t(ld)];
+                        const R sc = beta * fma(a2, v2, fma(a1, v1, a0 * v0));
+                        row[0] = a0 - sc * v0;
+                        row[ld] = a1 - sc * v1;
+                        row[2 * int64_t(ld)] = a2 - sc * v2;
+                    }
                 }
             }
             __syncthreads();

@@ -449,16 +449,24 @@ int eigs_impl(kl_solver* h, int M, double tol, double* lambda, double* Vout, int
         // wanted pairs the slowest one keeps the largest residual high long
         // after the first ones converged); a convergence claim FP32 cannot
         // resolve is re-checked in FP64. FP64 solves stay in FP64.
-        // Symmetric problems with the final refinement: the residuals of FP32
-        // Ritz pairs are those of actual vectors of the basis (computed in
-        // FP64 from A'V), and within a cluster of nearly equal eigenvalues any
-        // vector of its invariant subspace has a small residual, so an FP32
-        // claim that all wanted pairs converged is kept (the refinement then
-        // computes the pairs in FP64); FP32 is tried first also where the
-        // restart needs FP64, and the FP64 problem is solved only when that
-        // try does not converge.
+        // Solves with the final refinement: the residuals of FP32 Ritz pairs
+        // are those of actual vectors of the basis (computed in FP64 from
+        // A'V), and a small residual is a small backward error (the pair is
+        // exact for A' - r y^T; for symmetric A', within a cluster of nearly
+        // equal eigenvalues any vector of its invariant subspace has a small
+        // residual), so an FP32 claim that all wanted pairs converged is kept:
+        // the refinement then computes the pairs in FP64-grade arithmetic on
+        // an FP64-orthonormalised basis of the FP32 Ritz (symmetric) or Schur
+        // (non-symmetric) vectors. FP32 is tried first also where the restart
+        // needs FP64, and the FP64-grade problem is solved only when that try
+        // does not converge: for symmetric problems at every such restart
+        // (the FP32 problem costs a fraction of the FP64 one), for non-
+        // symmetric ones once the last largest wanted residual is within
+        // 1e3 tol (their FP32 problem costs a third of the double-float one,
+        // a try that fails is paid in full).
         const bool use32 = prec != KL_FP64 && (tol >= kFp32RrTol || last_min_resid > std::max(1e3 * tol, 1e-3));
-        const bool trust32 = c.sym && prec != KL_FP64 && h->prm.refine > 0 && tol < kFp32RrTol && tol >= kFp32ClaimTol;
+        const bool trust32 = (c.sym || last_resid <= 1e3 * tol) && prec != KL_FP64 && h->prm.refine > 0 &&
+                             tol < kFp32RrTol && tol >= kFp32ClaimTol;
         bool claimed32 = false;
         if (use32 || trust32) {
             if (int rc = rr_residuals(true); rc != KL_OK) return rc;
