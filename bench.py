@@ -36,6 +36,9 @@ WORKLOAD = "cube_p2_e16_expsep"
 ALU_OPS_PER_PAIR = {"gauss": (1, 6), "exp_sep": (1, 5), "exp": (2, 6), "matern32": (2, 8), "const": (1, 1)}
 METHODS = ("galerkin", "collocation")
 MIXED = "bf16"
+# SMs each solve's pairwise product leaves free in the concurrent step
+# (kl_set_shared_sms; measured on GB300: 8 of 152 gave the shortest step)
+SHARED_SMS = 8
 
 
 def _args():
@@ -505,6 +508,11 @@ def run_gpu(a):
         return kl.kl_create(p, st if st is not None else stream)
 
     handles = {m: make(m, a.precision, streams[m]) for m in METHODS}
+    # in the concurrent step each solve's pairwise product leaves SHARED_SMS
+    # SMs to the other stream, whose short kernels would otherwise wait for
+    # the end of every product (a persistent grid over all SMs holds them all)
+    for m in METHODS:
+        kl.kl_set_shared_sms(handles[m], SHARED_SMS)
     N = kl.kl_dims(handles["galerkin"])[0]
     lam = {m: np.zeros(M) for m in METHODS}
     res = {m: np.zeros(M) for m in METHODS}
@@ -598,6 +606,11 @@ def run_gpu(a):
     # the same steps with the solves one after the other; the pairwise
     # kernel's per-launch durations for the roofline are taken here (no
     # other stream shares the GPU)
+    # alone, a solve's pairwise product takes every SM (one untimed step
+    # captures the graphs of that grid)
+    for m in METHODS:
+        kl.kl_set_shared_sms(handles[m], 0)
+    step_sequential()
     for m in METHODS:
         kl.kl_profile_enable(handles[m], True)
     for _ in range(a.steps):
@@ -759,6 +772,7 @@ def run_gpu(a):
                    **({"autotune": tuned} if a.autotune else {}),
                    "precision": a.precision, "l2": "flushed between steps (256 MB write)",
                    "step": "the Galerkin and the collocation solve run concurrently on two streams",
+                   "shared_sms": SHARED_SMS,
                    "parallelism": "replicas" if world > 1 else "single"},
         "ms_per_step_sequential": float(np.mean(seq_ms)),
         "solve_ms_p50": p50, "solve_ms_p99": p99,

@@ -309,6 +309,16 @@ int kl_sample(kl_solver* h, int M, const double* lambda, const double* V, int64_
  * handles run by a server. Turning it off drops the captured graphs.
  * Synchronises the stream. */
 int kl_set_graphs(kl_solver* h, int on);
+/* SMs the handle's tensor-core pairwise product leaves free (0 <= n < SM
+ * count; 0 at creation): its persistent grid of two CTAs per SM spans the
+ * other SMs. For solves that run concurrently with other work on the same
+ * GPU (several handles on their own streams): a grid over every SM holds all
+ * of them for the length of the product, so the short kernels of the other
+ * streams wait for its end; a few free SMs let them run beside it. Results
+ * are bitwise the same for every n (the work units and their reduction order
+ * do not depend on the grid). Synchronises the stream and drops captured
+ * graphs. Errors: KL_ERR_ARG (h NULL or n out of range), KL_ERR_CUDA. */
+int kl_set_shared_sms(kl_solver* h, int n);
 /* Block size (vectors per operator application) the handle uses: params'
  * block_k, or the autotuned value for block_k = 0 (see kl_autotune). */
 int kl_block_size(const kl_solver* h);

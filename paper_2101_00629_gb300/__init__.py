@@ -19,7 +19,7 @@ __all__ = [
     "kl_profile_read", "kl_launch_count", "kl_memory", "kl_last_error",
     "kl_status_string", "kl_measure_peaks", "kl_pairwise_noalloc", "kl_estimate_bytes",
     "kl_serve_config", "kl_serve_result", "kl_serve_stats", "kl_serve_open", "kl_serve_submit",
-    "kl_serve_poll", "kl_serve_get_stats", "kl_serve_close", "kl_set_graphs", "kl_block_size",
+    "kl_serve_poll", "kl_serve_get_stats", "kl_serve_close", "kl_set_graphs", "kl_set_shared_sms", "kl_block_size",
     "kl_autotune", "kl_sample_size", "kl_sample_points", "kl_sample", "kl_bounds_checked", "kl_debug_set", "library_path",
     "EXPORTED_SYMBOLS",
 ]
@@ -44,7 +44,7 @@ EXPORTED_SYMBOLS = (
     "kl_profile_read", "kl_launch_count", "kl_memory", "kl_last_error",
     "kl_status_string", "kl_measure_peaks", "kl_pairwise_noalloc", "kl_estimate_bytes",
     "kl_serve_open", "kl_serve_submit", "kl_serve_poll", "kl_serve_get_stats", "kl_serve_close",
-    "kl_set_graphs", "kl_block_size", "kl_autotune", "kl_sample_size", "kl_sample_points", "kl_sample",
+    "kl_set_graphs", "kl_set_shared_sms", "kl_block_size", "kl_autotune", "kl_sample_size", "kl_sample_points", "kl_sample",
     "kl_bounds_checked", "kl_debug_set",
 )
 
@@ -171,6 +171,7 @@ def _load():
         "kl_serve_get_stats": (c_int, [vp, ctypes.POINTER(kl_serve_stats)]),
         "kl_serve_close": (c_int, [vp]),
         "kl_set_graphs": (c_int, [vp, c_int]),
+        "kl_set_shared_sms": (c_int, [vp, c_int]),
         "kl_block_size": (c_int, [vp]),
         "kl_autotune": (c_int, [ctypes.POINTER(kl_params), c_int, dbl, vp, ctypes.c_char_p, ctypes.POINTER(c_int),
                                 ctypes.POINTER(dbl)]),
@@ -378,6 +379,11 @@ def kl_serve_close(s):
 
 def kl_set_graphs(h, on=True):
     return _check(h, _load().kl_set_graphs(h, int(bool(on))))
+
+
+def kl_set_shared_sms(h, n):
+    """SMs the handle's pairwise product leaves free for other streams."""
+    return _check(h, _load().kl_set_shared_sms(h, int(n)))
 
 
 def kl_block_size(h):

@@ -280,6 +280,7 @@ static int pairwise(kl_solver* h, int precision, const double* U, double* W, int
         a.post = post; a.ks = ks; a.tf32 = precision == KL_MIXED_TF32;
         a.scratch = h->pair_scratch; a.scratch_len = h->pair_scratch_len;
         a.sm_count = h->sm_count;
+        a.grid_sms = h->sm_count - h->shared_sms;
         a.err = h->d_err;
         a.wait_limit = h->wait_limit;
         int launched = 0;
@@ -951,6 +952,18 @@ int kl_set_graphs(kl_solver* h, int on) {
     if (e != cudaSuccess) return cuda_fail(h, e, "kl_set_graphs");
     h->use_graphs = on != 0;
     if (!h->use_graphs) clear_graphs(h);
+    return KL_OK;
+}
+
+int kl_set_shared_sms(kl_solver* h, int n) {
+    if (!h) return KL_ERR_ARG;
+    if (n < 0 || n >= h->sm_count) return fail(h, KL_ERR_ARG, "shared SMs must lie in [0, SM count)");
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "kl_set_shared_sms");
+    if (n != h->shared_sms) {
+        h->shared_sms = n;
+        clear_graphs(h);  // captured launches hold the old grid
+    }
     return KL_OK;
 }
 

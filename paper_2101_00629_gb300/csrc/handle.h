@@ -28,6 +28,7 @@ struct kl_solver {
     cudaStream_t stream = nullptr;
     int device = 0;
     int sm_count = 152;
+    int shared_sms = 0;  // SMs the pairwise product leaves to other streams (kl_set_shared_sms)
     int cc_major = 0, cc_minor = 0;
     std::string err;
 

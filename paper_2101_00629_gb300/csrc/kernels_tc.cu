@@ -1494,7 +1494,7 @@ cudaError_t launch_pair_tc_sym(const TcArgs& a, cudaStream_t s, int* launched) {
             KL_RANGE(a.err, 1, int, "tc error word");
         }
 #endif
-        cudaError_t e = launch_batch_prec<false>(batch, 16, true, a.sm_count, a.err, s);
+        cudaError_t e = launch_batch_prec<false>(batch, 16, true, a.grid_sms > 0 ? a.grid_sms : a.sm_count, a.err, s);
         ++*launched;
         if (e != cudaSuccess) return e;
         const int64_t rows = a.T - int64_t(tile0) * 128;
@@ -1518,7 +1518,7 @@ cudaError_t launch_pair_tc(const TcArgs& a, cudaStream_t s, int* launched) {
     int np = 16;
     cudaError_t e = tc_prepare(a, s, b.inst, &b.ninst, &np, launched);
     if (e != cudaSuccess) return e;
-    e = tc_launch_batch(b, a.tf32, np, a.sm_count, a.err, s);
+    e = tc_launch_batch(b, a.tf32, np, a.grid_sms > 0 ? a.grid_sms : a.sm_count, a.err, s);
     ++*launched;
     if (e != cudaSuccess) return e;
     return tc_finish(a, s, launched);

@@ -27,6 +27,9 @@ struct TcArgs {
     double* scratch;
     int64_t scratch_len;  // doubles
     int sm_count;
+    // SMs the persistent pairwise grid spans (2 CTAs each; 0: sm_count):
+    // fewer leave SMs free for kernels of other streams
+    int grid_sms;
     int* err;  // device word set when a bounded wait inside the kernel gives up
     long long wait_limit;  // clock cycles per pipeline wait (0: default, about a second)
     // symmetric mode (Galerkin: targets = sources, same coordinates): the plan

@@ -147,3 +147,29 @@ def test_symmetric_full_size_cube(kl, elems, k):
               f"symmetric {prof['pair_tc_bf16_sym']['ms']:.3f} ms")
     finally:
         kl.kl_destroy(h)
+
+
+@pytest.mark.parametrize("method", ["galerkin", "collocation"])
+def test_shared_sms_same_bits(kl, method):
+    """A pairwise grid that leaves SMs free for other streams
+    (kl_set_shared_sms) gives the same bits: the work units and the order of
+    their reduction do not depend on the grid. Out-of-range counts are
+    refused."""
+    import torch
+    w = WORKLOADS["cube_p2_e16_expsep"]
+    args = problem_args(w)
+    p = kl.params(geometry=args["geometry"], degree=args["p"], elems=args["elems"], kernel=args["kernel"],
+                  sigma=args["sigma"], L=args["L"], method=method, precision="bf16")
+    h = kl.kl_create(p, torch.cuda.current_stream())
+    try:
+        N, _, _ = kl.kl_dims(h)
+        X = random_block(N, 8, seed=77)
+        Y0 = _apply(kl, h, X)
+        for n in (8, 37, 0):
+            kl.kl_set_shared_sms(h, n)
+            assert np.array_equal(_apply(kl, h, X), Y0), n
+        for bad in (-1, 100000):
+            with pytest.raises(kl.KLError):
+                kl.kl_set_shared_sms(h, bad)
+    finally:
+        kl.kl_destroy(h)
