@@ -513,11 +513,14 @@ __device__ __forceinline__ Unit sym_unit_of(const TcInstance& I, int64_t u) {
 // g(c' / 2) of them, g(m) = clamp(m, b0, b1) - b0 (the band's tiles I < c' / 2),
 // and the sum of g(m) over m < M is G(M) = x (x - 1) / 2 + max(0, M - b1) (b1 - b0)
 // with x = max(0, min(M, b1) - b0).
-__host__ __device__ __forceinline__ int64_t sym_p2_index(int64_t c, int64_t I, int64_t b0, int64_t b1) {
-    const int64_t M = c >> 1;
-    const int64_t x = (M < b1 ? M : b1) - b0;
-    const int64_t G = x > 0 ? x * (x - 1) / 2 + (M > b1 ? (M - b1) * (b1 - b0) : 0) : 0;
-    const int64_t gM = (M < b0 ? b0 : M > b1 ? b1 : M) - b0;
+// Every term is below the band's block count (its transposed sums fit the
+// band cap, or the band is one tile), so 32-bit arithmetic holds; the kernel
+// evaluates this once per drained product.
+__host__ __device__ __forceinline__ int sym_p2_index(int c, int I, int b0, int b1) {
+    const int M = c >> 1;
+    const int x = (M < b1 ? M : b1) - b0;
+    const int G = x > 0 ? x * (x - 1) / 2 + (M > b1 ? (M - b1) * (b1 - b0) : 0) : 0;
+    const int gM = (M < b0 ? b0 : M > b1 ? b1 : M) - b0;
     return 2 * G + ((c & 1) ? gM : 0) + (I - b0);
 }
 
@@ -716,7 +719,7 @@ pair_tc_kernel(const __grid_constant__ TcBatch batch, int* __restrict__ err) {
             // [8 w, 8 w + 8)) and store it as the FP32 partial sum of the 64
             // sources of its chunk ch.
             auto drain = [&](int64_t ch, uint32_t m) {
-                const int64_t p2 = sym_p2_index(ch, un.tile, I.sym_tile0, I.sym_tile1);
+                const int64_t p2 = sym_p2_index(int(ch), int(un.tile), I.sym_tile0, I.sym_tile1);
                 const bool got = ok && warp_wait(&d2full_bar[m & 1], (m >> 1) & 1u, wlim);
                 if (!got) ok = false;
                 tc_fence_after();
@@ -1100,64 +1103,67 @@ tc_reduce_kernel(const float2* __restrict__ part, int splits, int64_t T, int k, 
 }
 
 
-// Symmetric mode, one band of tiles [tile0, tile1). A block serves the
-// 32 / (kstride / 2) consecutive points t >= tile0 * 128 of one transposed-
-// sum row segment (kstride = k rounded up to 8), a thread two columns of a
-// point (lane: point, then column pair) with 8 threads per point and column
-// pair (threadIdx.y): thread y sums, as double-floats, the y-th eighth of the
-// direct partial sums of the point's tile (when the tile is in the band) and
-// the y-th eighth of the transposed partial sums of the band's tiles I below
-// the point's tile (I ascending; one 8-byte load per tile, in groups of eight
-// loads in flight). The eight sums are then added in the order y = 0..7
-// after the running sum of the earlier bands (acc; none for the first band):
-// a fixed order. Column k of a transposed row (k odd) is padding: read,
-// never written out. 32-bit offsets: a band's partial sums stay under 2^31
-// floats and points under 2^26 (tc_sym_eligible).
-constexpr int kSymRedSplit = 8;
-constexpr int kSymRedLoads = 8;  // loads in flight per thread
-__global__ void __launch_bounds__(32 * kSymRedSplit)
+// Symmetric mode, one band of tiles [tile0, tile1). A block serves one chunk
+// of 64 points (chunks from the last, the largest sums, to the first 2 tile0):
+// a thread takes one row (point) and four columns of it (16 bytes of a
+// transposed-sum row; kstride = k rounded up to 8), and the block's S =
+// 512 / (16 kstride) slices (threadIdx.x / (16 kstride)) split the work by
+// range: slice y sums, as double-floats, the y-th part of the direct partial
+// sums of the point's tile (when the tile is in the band) and the y-th part of
+// the transposed partial sums of the band's tiles I below it (I ascending).
+// The transposed sums of one chunk are consecutive 64 x kstride blocks (chunk-
+// major layout), so a slice's loads stream one contiguous range, six 16-byte
+// loads in flight per thread (the last group predicated). The S sums
+// are then added in slice order after the running sum of the earlier bands
+// (acc; none for the first band): a fixed order. Columns k..kstride-1 of a
+// transposed row are padding (products with zero columns of X): read, never
+// written out. 32-bit offsets: a band's partial sums stay under 2^31 floats
+// and points under 2^26 (tc_sym_eligible).
+constexpr int kSymRedThreads = 512;
+constexpr int kSymRedLoads = 6;  // 16-byte loads in flight per thread
+__global__ void __launch_bounds__(kSymRedThreads, 2)
 tc_sym_reduce_kernel(const float2* __restrict__ part1, const float* __restrict__ part2,
-                     const int2* __restrict__ tab, int64_t T, int k, int tile0, int tile1,
+                     const int2* __restrict__ tab, int64_t nchunks, int64_t T, int k, int tile0, int tile1,
                      int64_t unit_begin, int first, float2* __restrict__ acc, double sigma2,
                      const double* __restrict__ post, double* __restrict__ Y, int64_t ldy) {
-    __shared__ float4 sh[kSymRedSplit][32];
+    __shared__ float4 sh[kSymRedThreads][2];
     const int kstride = (k + 7) & ~7;
-    const int ng = kstride / 2;    // column pairs per point
-    const int tpb = 32 / ng;       // points per block
-    const int t0 = tile0 * 128;
-    const int nblocks = (int(T) - t0 + tpb - 1) / tpb;
-    const int y = threadIdx.y;
-    const int c0 = 2 * (threadIdx.x % ng);
-    const int step = 32 * kstride;  // one 64 x kstride block of transposed sums, in 8-byte vectors
-    const float2* p2base = reinterpret_cast<const float2*>(part2);
-    for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
-        const int t = t0 + b * tpb + threadIdx.x / ng;
-        const bool valid = t < int(T) && c0 < k;
-        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+    const int ng = kstride / 4;   // 16-byte column groups per row
+    const int per = 64 * ng;      // threads per 64 x kstride block
+    const int S = kSymRedThreads / per;
+    const int tid = threadIdx.x;
+    const int y = tid / per, lane = tid % per;
+    const int r = lane / ng, c0 = 4 * (lane % ng);
+    const int nch = int(nchunks) - 2 * tile0;  // chunks of the band's points and the later ones
+    const int step = 16 * kstride;             // one block of transposed sums, in 16-byte vectors
+    const float4* p2base = reinterpret_cast<const float4*>(part2);
+    for (int b = blockIdx.x; b < nch; b += gridDim.x) {
+        const int ch = int(nchunks) - 1 - b;
+        const int t = ch * 64 + r;
+        const int J = ch >> 1;
+        const bool valid = t < int(T);
+        float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
         if (valid) {
-            const int J = t >> 7;
             if (J < tile1) {
                 const int u0 = tab[J].x, n1 = tab[J + 1].x - u0;
-                const int ua = u0 + n1 * y / kSymRedSplit, ub = u0 + n1 * (y + 1) / kSymRedSplit;
-                const float2* pu = part1 + ((int(ua - unit_begin) * k + c0) * 128 + (t & 127));
-                for (int u = ua; u < ub; ++u, pu += k * 128) {
-                    const float2 v0 = pu[0];
-                    df_add(h0, l0, v0.x, v0.y);
-                    if (c0 + 1 < k) {
-                        const float2 v1 = pu[128];
-                        df_add(h1, l1, v1.x, v1.y);
-                    }
+                const int ua = u0 + n1 * y / S, ub = u0 + n1 * (y + 1) / S;
+                for (int u = ua; u < ub; ++u) {
+                    const float2* pu = part1 + ((int(u - unit_begin) * k + c0) * 128 + (t & 127));
+                    float2 v[4];
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc)
+                        if (c0 + cc < k) v[cc] = pu[cc * 128];
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc)
+                        if (c0 + cc < k) df_add(hi[cc], lo[cc], v[cc].x, v[cc].y);
                 }
             }
             const int n2 = (J < tile1 ? J : tile1) - tile0;
-            const int ia = tile0 + n2 * y / kSymRedSplit;
-            const int ib = tile0 + n2 * (y + 1) / kSymRedSplit;
-            // transposed sums of (I, ch) for I = ia, ia + 1, ...: consecutive
-            // blocks
-            const float2* p2 = p2base + ((t & 63) * kstride + c0) / 2;
-            int off = int(sym_p2_index(t >> 6, ia, tile0, tile1)) * step;
+            const int ia = tile0 + n2 * y / S, ib = tile0 + n2 * (y + 1) / S;
+            const float4* p2 = p2base + (r * kstride + c0) / 4;
+            int off = sym_p2_index(ch, ia, tile0, tile1) * step;
             for (int I = ia; I < ib; I += kSymRedLoads) {
-                float2 v[kSymRedLoads];
+                float4 v[kSymRedLoads];
 #pragma unroll
                 for (int q = 0; q < kSymRedLoads; ++q) {
                     if (I + q < ib) v[q] = p2[off];
@@ -1166,37 +1172,41 @@ tc_sym_reduce_kernel(const float2* __restrict__ part1, const float* __restrict__
 #pragma unroll
                 for (int q = 0; q < kSymRedLoads; ++q)
                     if (I + q < ib) {
-                        df_add(h0, l0, v[q].x, 0.f);
-                        df_add(h1, l1, v[q].y, 0.f);
+                        df_add(hi[0], lo[0], v[q].x, 0.f);
+                        df_add(hi[1], lo[1], v[q].y, 0.f);
+                        df_add(hi[2], lo[2], v[q].z, 0.f);
+                        df_add(hi[3], lo[3], v[q].w, 0.f);
                     }
             }
         }
-        sh[y][threadIdx.x] = make_float4(h0, l0, h1, l1);
+        sh[tid][0] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        sh[tid][1] = make_float4(lo[0], lo[1], lo[2], lo[3]);
         __syncthreads();
         if (y == 0 && valid) {
-            float a0 = 0.f, b0 = 0.f, a1 = 0.f, b1 = 0.f;
+            float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
             if (!first) {
-                const float2 r0 = acc[int64_t(c0) * T + t];
-                a0 = r0.x;
-                b0 = r0.y;
-                if (c0 + 1 < k) {
-                    const float2 r1 = acc[int64_t(c0 + 1) * T + t];
-                    a1 = r1.x;
-                    b1 = r1.y;
-                }
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc)
+                    if (c0 + cc < k) {
+                        const float2 a2 = acc[int64_t(c0 + cc) * T + t];
+                        h[cc] = a2.x;
+                        l[cc] = a2.y;
+                    }
             }
-            for (int q = 0; q < kSymRedSplit; ++q) {
-                const float4 w = sh[q][threadIdx.x];
-                df_add(a0, b0, w.x, w.y);
-                df_add(a1, b1, w.z, w.w);
+            for (int q = 0; q < S; ++q) {
+                const float4 w = sh[q * per + lane][0], wl = sh[q * per + lane][1];
+                df_add(h[0], l[0], w.x, wl.x);
+                df_add(h[1], l[1], w.y, wl.y);
+                df_add(h[2], l[2], w.z, wl.z);
+                df_add(h[3], l[3], w.w, wl.w);
             }
-            if ((t >> 7) < tile1) {
-                const double m = post ? sigma2 * post[t] : sigma2;
-                Y[c0 * ldy + t] = (double(a0) + double(b0)) * m;
-                if (c0 + 1 < k) Y[(c0 + 1) * ldy + t] = (double(a1) + double(b1)) * m;
-            } else {
-                acc[int64_t(c0) * T + t] = make_float2(a0, b0);
-                if (c0 + 1 < k) acc[int64_t(c0 + 1) * T + t] = make_float2(a1, b1);
+            const bool done = J < tile1;
+            const double m = post ? sigma2 * post[t] : sigma2;
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                if (c0 + cc >= k) break;
+                if (done) Y[(c0 + cc) * ldy + t] = (double(h[cc]) + double(l[cc])) * m;
+                else acc[int64_t(c0 + cc) * T + t] = make_float2(h[cc], l[cc]);
             }
         }
         __syncthreads();
@@ -1497,11 +1507,9 @@ cudaError_t launch_pair_tc_sym(const TcArgs& a, cudaStream_t s, int* launched) {
         cudaError_t e = launch_batch_prec<false>(batch, 16, true, a.grid_sms > 0 ? a.grid_sms : a.sm_count, a.err, s);
         ++*launched;
         if (e != cudaSuccess) return e;
-        const int64_t rows = a.T - int64_t(tile0) * 128;
-        const int tpb = 32 / ((a.k + 7) / 8 * 4);  // points per block: 2 columns per thread
-        const int64_t nblk = (rows + tpb - 1) / tpb;
-        const int g = int(std::max<int64_t>(1, std::min<int64_t>(nblk, int64_t(a.sm_count) * 16)));
-        tc_sym_reduce_kernel<<<g, dim3(32, kSymRedSplit), 0, s>>>(part1, part2, tab, a.T, a.k, tile0, tile1,
+        // one block per chunk of the band's points and the later ones
+        const int g = int(std::max<int64_t>(1, p.nchunks - 2 * int64_t(tile0)));
+        tc_sym_reduce_kernel<<<g, kSymRedThreads, 0, s>>>(part1, part2, tab, p.nchunks, a.T, a.k, tile0, tile1,
                                                I.sym_unit_begin, b == 0, acc, a.ks.sigma2, a.post,
                                                a.Y, a.ldy);
         ++*launched;
