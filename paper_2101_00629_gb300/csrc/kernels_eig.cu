@@ -767,8 +767,8 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
     constexpr int NT = kEigThreads;
 
     R amax = R(0.0);
-    for (int64_t e = tid; e < nn; e += NT) {
-        const int i = int(e % n), j = int(e / n);
+    for (int e = tid; e < int(nn); e += NT) {
+        const int j = int(unsigned(e) / unsigned(n)), i = e - j * n;
         const R a = sym ? R(0.5) * (H[e] + H[j + int64_t(i) * n]) : H[e];
         A[i + int64_t(j) * ld] = a;
         Z[i + int64_t(j) * ld] = (i == j) ? R(1.0) : R(0.0);
@@ -1282,10 +1282,12 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             }
             __syncthreads();
         }
-        // clean the bulge remnants below the subdiagonal of the window
-        for (int e = tid; e < ns * ns; e += NT) {
-            const int i = l + e % ns, j = l + e / ns;
-            if (i > j + 1) A[i + int64_t(j) * ld] = R(0.0);
+        // clean the bulge remnants of the window: the chase leaves rounding
+        // remnants only on its second and third subdiagonals (each step's
+        // left product annihilates rows r0+1, r0+2 of column r0-1)
+        for (int e = tid; e < 2 * ns; e += NT) {
+            const int j = l + (e >> 1), i = j + 2 + (e & 1);
+            if (i <= u) A[i + int64_t(j) * ld] = R(0.0);
         }
         __syncthreads();
     }
@@ -1314,8 +1316,8 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
             rk[i] = rank;
         }
         __syncthreads();
-        for (int64_t e = tid; e < nn; e += NT) {
-            const int i = int(e % n), c = int(e / n);
+        for (int e = tid; e < int(nn); e += NT) {
+            const int c = int(unsigned(e) / unsigned(n)), i = e - c * n;
             const R z = Z[i + int64_t(c) * ld];
             if (Vout) Vout[i + int64_t(rk[c]) * n] = to_d(z);
             if (Qout) Qout[i + int64_t(rk[c]) * n] = to_d(z);
@@ -1360,8 +1362,8 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         const int nve = (nv < n && wi[nv - 1] > R(0.0)) ? nv + 1 : nv;
         const R small = EigNum<R>::eps * fmax(anorm, EigNum<R>::tiny);
         const R clus = EigNum<R>::split * anorm;
-        for (int64_t e = tid; e < int64_t(n) * nve; e += NT) {
-            const int i = int(e % n), c = int(e / n);
+        for (int e = tid; e < n * nve; e += NT) {
+            const int c = int(unsigned(e) / unsigned(n)), i = e - c * n;
             R v = R(0.0);
             if (wi[c] == R(0.0)) {
                 // real eigenvalue: x_c(c) = 1, zero below
@@ -1463,8 +1465,8 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         // four columns per thread, then unit columns (complex pairs jointly)
         R* Vt = A;  // the Schur form is no longer needed
         const int ng = (nve + 3) / 4;
-        for (int64_t e = tid; e < int64_t(n) * ng; e += NT) {
-            const int i = int(e % n), c0 = 4 * int(e / n);
+        for (int e = tid; e < n * ng; e += NT) {
+            const int cg = int(unsigned(e) / unsigned(n)), i = e - cg * n, c0 = 4 * cg;
             const int top = min(n - 1, c0 + 4);
             // columns past the last one repeat it (computed, not stored)
             const R* x0 = X + int64_t(c0) * ld;
@@ -1507,7 +1509,10 @@ __global__ void __launch_bounds__(kEigThreads) nonsym_eig_kernel(const double* _
         if (Vout)
             for (int64_t e = tid; e < int64_t(n) * nve; e += NT) Vout[e] = to_d(Vt[e]);
         if (Qout)
-            for (int64_t e = tid; e < nn; e += NT) Qout[e] = to_d(Z[int(e % n) + int64_t(e / n) * ld]);
+            for (int e = tid; e < int(nn); e += NT) {
+                const int c = int(unsigned(e) / unsigned(n));
+                Qout[e] = to_d(Z[(e - c * n) + int64_t(c) * ld]);
+            }
     }
     if (tid == 0) {
         // 3: the bounds-checking build found an index out of range
