@@ -114,9 +114,9 @@ __global__ void __launch_bounds__(256) gemm_tn_narrow_kernel(const double* __res
 
 // C = alpha * (sum of the splits' partial products) + beta * C. A block
 // takes 32 outputs (one per lane, coalesced) and its 8 warps take every 8th
-// split, so that the dependent chain of FP64 additions is splits / 8 long
-// (GB300: a dependent FP64 add waits about 63 cycles); the 8 partial sums
-// are added in a fixed order.
+// split, each with four partial sums, so that the dependent chain of FP64
+// additions (GB300: a dependent FP64 add waits about 63 cycles) and of loads
+// is splits / 32 long; the partial sums are added in a fixed order.
 __global__ void __launch_bounds__(256) gemm_tn_reduce(const double* __restrict__ part, int splits, int m, int n,
                                                       double alpha, double beta, double* C, int64_t ldc) {
     __shared__ double red[8][33];
@@ -125,8 +125,19 @@ __global__ void __launch_bounds__(256) gemm_tn_reduce(const double* __restrict__
     for (int base = blockIdx.x * 32; base < total; base += gridDim.x * 32) {
         const int e = base + tx;
         double s = 0.0;
-        if (e < total)
-            for (int sp = ty; sp < splits; sp += 8) s += part[int64_t(sp) * total + e];
+        if (e < total) {
+            // four independent loads and partial sums per step
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int sp = ty;
+            for (; sp + 24 < splits; sp += 32) {
+                s0 += part[int64_t(sp) * total + e];
+                s1 += part[int64_t(sp + 8) * total + e];
+                s2 += part[int64_t(sp + 16) * total + e];
+                s3 += part[int64_t(sp + 24) * total + e];
+            }
+            for (; sp < splits; sp += 8) s0 += part[int64_t(sp) * total + e];
+            s = (s0 + s1) + (s2 + s3);
+        }
         red[ty][tx] = s;
         __syncthreads();
         if (ty == 0 && e < total) {
@@ -252,6 +263,23 @@ constexpr int kCholSmemN = 96;
 
 size_t chol_smem_bytes(int n) { return (2 * size_t(n) * n + 3 * size_t(n)) * sizeof(double); }
 
+// 1 / sqrt(x) for x > 0 finite: x = m 4^e with m in [1, 4) (exact, from the
+// exponent bits), an FP32 approximate reciprocal square root of m refined by
+// three Newton steps y <- y (3 - m y^2) / 2 in FP64 (each squares the relative
+// error: 2^-22 -> about 2^-52), then scaled by 2^-e.
+__device__ inline double rsqrt_newton(double x) {
+    const long long bits = __double_as_longlong(x);
+    const int ex = int((bits >> 52) & 0x7ff) - 1023;  // x = f 2^ex, f in [1, 2)
+    if (ex == -1023) return 1.0 / sqrt(x);            // subnormal x
+    const int e = ex >> 1;                            // floor(ex / 2)
+    const double m = __longlong_as_double(bits - (static_cast<long long>(2 * e) << 52));  // in [1, 4)
+    float yf;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(float(m)));
+    double y = yf;
+    for (int it = 0; it < 3; ++it) y = y * fma(-0.5 * m, y * y, 1.5);
+    return y * __longlong_as_double(static_cast<long long>(1023 - e) << 52);
+}
+
 __global__ void __launch_bounds__(256) chol_rinv_smem_kernel(double* G, int n, double* Rinv, int* bad) {
     extern __shared__ double sm[];
     double* L = sm;                       // n x n, column-major
@@ -283,11 +311,14 @@ __global__ void __launch_bounds__(256) chol_rinv_smem_kernel(double* G, int n, d
         if (tid == 0) {
             const double d2 = L[j + j * n];
             const bool b = !(d2 > 1e-28 * maxd) || !(d2 > 1e-14 * g0[j]) || !isfinite(d2);
-            const double d = b ? 1.0 : sqrt(d2);
+            // 1 / sqrt(d2) by Newton steps from an FP32 seed, sqrt(d2) = d2 / sqrt(d2):
+            // the pivot's chain is a few dependent FP64 FMAs (each waits about 63
+            // cycles on GB300) instead of a square root and a division
+            const double y = b ? 1.0 : rsqrt_newton(d2);
             s_bad = b ? 1 : 0;
-            s_inv = b ? 1.0 : 1.0 / d;
-            inv[j] = s_inv;
-            L[j + j * n] = d;
+            s_inv = y;
+            inv[j] = y;
+            L[j + j * n] = b ? 1.0 : d2 * y;
             if (b) bad[j] = 1;
         }
         __syncthreads();

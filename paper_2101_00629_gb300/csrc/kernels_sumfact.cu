@@ -272,14 +272,28 @@ __device__ inline double block_sum(double v, double* sh) {
 // One block per column: out[c] = sqrt(sum_i w_i X_ic^2) (w may be NULL).
 __global__ void weighted_norms_kernel(const double* __restrict__ X, int64_t ldx, int64_t K,
                                       const double* __restrict__ w, double* out) {
+    // four independent loads and partial sums per step: one dependent chain
+    // of DRAM round trips per thread would be K / blockDim long
     __shared__ double sh[32];
     const int c = blockIdx.x;
     const double* x = X + c * ldx;
-    double s = 0.0;
-    for (int64_t i = threadIdx.x; i < K; i += blockDim.x) {
-        const double v = x[i];
-        s += (w ? w[i] : 1.0) * v * v;
+    const int64_t bd = blockDim.x;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int64_t i = threadIdx.x;
+    for (; i + 3 * bd < K; i += 4 * bd) {
+        const double v0 = x[i], v1 = x[i + bd], v2 = x[i + 2 * bd], v3 = x[i + 3 * bd];
+        const double w0 = w ? w[i] : 1.0, w1 = w ? w[i + bd] : 1.0;
+        const double w2 = w ? w[i + 2 * bd] : 1.0, w3 = w ? w[i + 3 * bd] : 1.0;
+        s0 = fma(w0 * v0, v0, s0);
+        s1 = fma(w1 * v1, v1, s1);
+        s2 = fma(w2 * v2, v2, s2);
+        s3 = fma(w3 * v3, v3, s3);
     }
+    for (; i < K; i += bd) {
+        const double v = x[i];
+        s0 = fma((w ? w[i] : 1.0) * v, v, s0);
+    }
+    double s = (s0 + s1) + (s2 + s3);
     s = block_sum<kThreads>(s, sh);
     if (threadIdx.x == 0) out[c] = sqrt(s);
 }
@@ -322,14 +336,28 @@ __global__ void sign_fix_kernel(double* X, int64_t ldx, int64_t K) {
 __global__ void resid_norms_kernel(const double* __restrict__ Y, int64_t ldy,
                                    const double* __restrict__ AY, int64_t lday,
                                    const double* __restrict__ theta, int64_t K, double* out) {
+    // four independent loads and partial sums per step (see weighted_norms_kernel)
     __shared__ double sh[32];
     const int c = blockIdx.x;
     const double th = theta[c];
-    double s = 0.0;
-    for (int64_t i = threadIdx.x; i < K; i += blockDim.x) {
-        const double r = AY[c * lday + i] - th * Y[c * ldy + i];
-        s += r * r;
+    const double* y = Y + c * ldy;
+    const double* ay = AY + c * lday;
+    const int64_t bd = blockDim.x;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int64_t i = threadIdx.x;
+    for (; i + 3 * bd < K; i += 4 * bd) {
+        const double r0 = ay[i] - th * y[i], r1 = ay[i + bd] - th * y[i + bd];
+        const double r2 = ay[i + 2 * bd] - th * y[i + 2 * bd], r3 = ay[i + 3 * bd] - th * y[i + 3 * bd];
+        s0 = fma(r0, r0, s0);
+        s1 = fma(r1, r1, s1);
+        s2 = fma(r2, r2, s2);
+        s3 = fma(r3, r3, s3);
     }
+    for (; i < K; i += bd) {
+        const double r = ay[i] - th * y[i];
+        s0 = fma(r, r, s0);
+    }
+    double s = (s0 + s1) + (s2 + s3);
     s = block_sum<kThreads>(s, sh);
     if (threadIdx.x == 0) out[c] = sqrt(s);
 }
