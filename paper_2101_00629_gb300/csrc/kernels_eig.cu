@@ -3,17 +3,22 @@
 // method, whose projected matrix H = V^T A' V is decomposed here).
 //
 // One CTA of four warps per matrix: Householder reduction to Hessenberg form,
-// Francis double-shift QR to real Schur form with accumulated Schur vectors,
-// ordering of the Schur form by decreasing real part, and eigenvectors of the
-// leading columns by back substitution.
+// then, for a general matrix, Francis double-shift QR to real Schur form with
+// accumulated Schur vectors, ordering of the Schur form by decreasing real
+// part, and eigenvectors of the leading columns by back substitution; for a
+// symmetric matrix (whose Hessenberg form is tridiagonal) implicit QR steps
+// with Wilkinson shifts on the tridiagonal form, the rotations accumulated
+// into the eigenvectors.
 //
 // GB300 has a small FP64 unit: one warp-wide FP64 instruction issues every
 // 64 cycles per SM sub-partition, and a dependent FP64 FMA waits 63 cycles
 // (square root and division take about 650). The kernel is therefore laid
-// out so that every FP64 operation that can run in parallel does (four warps
-// on the four sub-partitions, reductions by shuffles, deflation and ordering
-// decisions evaluated by all threads at once) and only the Householder vector
-// of the bulge chase is a one-thread chain.
+// out so that every operation that can run in parallel does (four warps on
+// the four sub-partitions, reductions by shuffles, deflation and ordering
+// decisions evaluated by all threads at once); the one-thread chains are the
+// core of each bulge step with its next Householder vector (general case)
+// and the scalar sweep of the tridiagonal QR (symmetric case), which the
+// other warps' updates of the Schur vectors run beside.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
